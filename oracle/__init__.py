@@ -1,0 +1,247 @@
+"""ctypes view of the CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg import this package.  The CUDA library never does, and nothing here is
+shared with it.  See ``ca_oracle.h`` for what each function computes and the
+paper passage it follows.
+"""
+import ctypes as C
+
+import numpy as np
+
+from .build import build
+
+_lib = None
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("n_strips", C.c_int32), ("cands_per_strip", C.c_int32),
+        ("n_hyps", C.c_int32), ("refine_iters", C.c_int32),
+        ("alpha", C.c_float), ("t_g", C.c_float), ("t_theta_deg", C.c_float),
+        ("t_iota", C.c_float), ("t_ps", C.c_float), ("t_cs", C.c_float),
+        ("t_px", C.c_float), ("t_ri", C.c_float), ("r_min", C.c_float),
+        ("r_max", C.c_float), ("d_max", C.c_float),
+        ("sup_px", C.c_int32), ("hyp_mode", C.c_int32), ("score_norm", C.c_int32),
+        ("sobel_norm", C.c_int32), ("seed", C.c_uint64),
+    ]
+
+
+class OrcResult(C.Structure):
+    _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("r", C.c_float),
+                ("score", C.c_float), ("valid", C.c_int32), ("n_inliers", C.c_int32)]
+
+
+class OrcDebug(C.Structure):
+    _fields_ = [
+        ("cand_cap", C.c_int32), ("n_cands", C.POINTER(C.c_int32)),
+        ("cand_x", C.POINTER(C.c_int16)), ("cand_y", C.POINTER(C.c_int16)),
+        ("cand_s", C.POINTER(C.c_uint16)),
+        ("hyp_cap", C.c_int32), ("n_hyps", C.POINTER(C.c_int32)),
+        ("triple", C.POINTER(C.c_int32)), ("hyp_n_inl", C.POINTER(C.c_int32)),
+        ("hyp_score", C.POINTER(C.c_uint32)), ("hyp_pass", C.POINTER(C.c_int32)),
+        ("hyp_circle", C.POINTER(C.c_float)), ("best_h", C.POINTER(C.c_int32)),
+        ("best_inl", C.POINTER(C.c_uint8)),
+    ]
+
+
+LUT_G, LUT_T, LUT_I = 5772, 8193, 256
+HYP_RANDOM, HYP_EXHAUSTIVE = 0, 1
+NORM_2N, NORM_NK, NORM_RAW = 0, 1, 2
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P = C.POINTER
+        L.orc_params_default.argtypes = [P(OrcParams)]
+        L.orc_strip_rows.argtypes = [C.c_int, C.c_int, C.c_float, C.c_void_p]
+        L.orc_build_luts.argtypes = [P(OrcParams), C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_luma.argtypes = [C.c_int] * 3
+        L.orc_strip_scores.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int,
+                                       P(OrcParams), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]
+        L.orc_score_exact.argtypes = [C.c_int] * 5 + [P(OrcParams)]
+        L.orc_score_exact.restype = C.c_double
+        L.orc_candidates.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(OrcParams),
+                                     C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
+        L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
+        L.orc_circumcircle.argtypes = [C.c_int] * 6 + [C.c_void_p]
+        L.orc_ls_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_i128_to_f32.argtypes = [C.c_int64, C.c_uint64]
+        L.orc_i128_to_f32.restype = C.c_float
+        L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_uint64,
+                                   P(OrcParams), P(OrcResult), P(OrcDebug)]
+        L.orc_mask.argtypes = [P(OrcResult), C.c_int, C.c_int, C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def params(**kw) -> OrcParams:
+    p = OrcParams()
+    lib().orc_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def strip_rows(H, N, alpha=8.0):
+    out = np.zeros(N, np.int32)
+    if lib().orc_strip_rows(H, N, alpha, _ptr(out)) != 0:
+        raise ValueError("bad strip arguments")
+    return out
+
+
+def luts(p=None):
+    p = p or params()
+    g = np.zeros(LUT_G, np.uint16)
+    t = np.zeros(LUT_T, np.uint16)
+    i = np.zeros(LUT_I, np.uint16)
+    lib().orc_build_luts(C.byref(p), _ptr(g), _ptr(t), _ptr(i))
+    return g, t, i
+
+
+def luma(r, g, b):
+    return lib().orc_luma(int(r), int(g), int(b))
+
+
+def _frame(frame):
+    f = np.ascontiguousarray(frame, dtype=np.uint8)
+    assert f.ndim == 3 and f.shape[2] == 3
+    return f
+
+
+def strip_scores(frame, row, p=None):
+    f = _frame(frame)
+    H, W = f.shape[:2]
+    p = p or params()
+    s = np.zeros(W, np.uint16)
+    gx = np.zeros(W, np.int32)
+    gy = np.zeros(W, np.int32)
+    io = np.zeros(W, np.uint8)
+    if lib().orc_strip_scores(_ptr(f), H, W, W * 3, row, C.byref(p), _ptr(s), _ptr(gx),
+                              _ptr(gy), _ptr(io)) != 0:
+        raise ValueError("bad strip row")
+    return s, gx, gy, io
+
+
+def score_exact(gx, gy, cx2, cy2, iota, p=None):
+    p = p or params()
+    return lib().orc_score_exact(int(gx), int(gy), int(cx2), int(cy2), int(iota), C.byref(p))
+
+
+def candidates(frame, p=None):
+    f = _frame(frame)
+    H, W = f.shape[:2]
+    p = p or params()
+    cap = p.n_strips * p.cands_per_strip
+    xs = np.zeros(cap, np.int16)
+    ys = np.zeros(cap, np.int16)
+    ss = np.zeros(cap, np.uint16)
+    M = C.c_int32(0)
+    if lib().orc_candidates(_ptr(f), H, W, W * 3, C.byref(p), cap, _ptr(xs), _ptr(ys),
+                            _ptr(ss), C.byref(M)) != 0:
+        raise ValueError("bad candidate arguments")
+    m = M.value
+    return xs[:m].copy(), ys[:m].copy(), ss[:m].copy()
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def triple(seed, frame_key, h, M):
+    out = np.zeros(3, np.int32)
+    lib().orc_triple(seed, frame_key, h, M, _ptr(out))
+    return out
+
+
+def triple_exhaustive(h, M):
+    out = np.zeros(3, np.int32)
+    lib().orc_triple_exhaustive(h, M, _ptr(out))
+    return out
+
+
+def circumcircle(a, b, c):
+    out = np.zeros(3, np.float32)
+    ok = lib().orc_circumcircle(int(a[0]), int(a[1]), int(b[0]), int(b[1]), int(c[0]),
+                                int(c[1]), _ptr(out))
+    return out if ok else None
+
+
+def ls_fit(X, Y):
+    X = np.ascontiguousarray(X, np.int32)
+    Y = np.ascontiguousarray(Y, np.int32)
+    out = np.zeros(3, np.float32)
+    ok = lib().orc_ls_fit(_ptr(X), _ptr(Y), len(X), _ptr(out))
+    return out if ok else None
+
+
+def i128_to_f32(v: int) -> np.float32:
+    v &= (1 << 128) - 1
+    hi = v >> 64
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return np.float32(lib().orc_i128_to_f32(hi, v & ((1 << 64) - 1)))
+
+
+def estimate(frame, frame_key=0, p=None, debug=False, hyp_cap=None):
+    """Run the whole pipeline on one frame.  Returns (result dict, debug dict)."""
+    f = _frame(frame)
+    H, W = f.shape[:2]
+    p = p or params()
+    res = OrcResult()
+    dbg = None
+    d = {}
+    if debug:
+        cap = p.n_strips * p.cands_per_strip
+        if hyp_cap is None:
+            hyp_cap = p.n_hyps if p.hyp_mode == HYP_RANDOM else cap * (cap - 1) * (cap - 2) // 6
+        d = dict(n_cands=np.zeros(1, np.int32), cand_x=np.zeros(cap, np.int16),
+                 cand_y=np.zeros(cap, np.int16), cand_s=np.zeros(cap, np.uint16),
+                 n_hyps=np.zeros(1, np.int32), triple=np.zeros(3 * hyp_cap, np.int32),
+                 hyp_n_inl=np.zeros(hyp_cap, np.int32), hyp_score=np.zeros(hyp_cap, np.uint32),
+                 hyp_pass=np.zeros(hyp_cap, np.int32),
+                 hyp_circle=np.zeros(3 * hyp_cap, np.float32),
+                 best_h=np.zeros(1, np.int32), best_inl=np.zeros(cap, np.uint8))
+        dbg = OrcDebug()
+        dbg.cand_cap = cap
+        dbg.hyp_cap = hyp_cap
+        for k, a in d.items():
+            setattr(dbg, k, a.ctypes.data_as(dict(OrcDebug._fields_)[k]))
+    rc = lib().orc_estimate(_ptr(f), H, W, W * 3, frame_key, C.byref(p), C.byref(res),
+                            C.byref(dbg) if dbg is not None else None)
+    if rc != 0:
+        raise ValueError("bad estimate arguments")
+    out = dict(cx=res.cx, cy=res.cy, r=res.r, score=res.score, valid=res.valid,
+               n_inliers=res.n_inliers)
+    if debug:
+        M = int(d["n_cands"][0])
+        nh = min(int(d["n_hyps"][0]), hyp_cap)
+        d = dict(M=M, cand_x=d["cand_x"][:M], cand_y=d["cand_y"][:M], cand_s=d["cand_s"][:M],
+                 n_hyps=int(d["n_hyps"][0]), triple=d["triple"][:3 * nh].reshape(nh, 3),
+                 hyp_n_inl=d["hyp_n_inl"][:nh], hyp_score=d["hyp_score"][:nh],
+                 hyp_pass=d["hyp_pass"][:nh], hyp_circle=d["hyp_circle"][:3 * nh].reshape(nh, 3),
+                 best_h=int(d["best_h"][0]), best_inl=d["best_inl"][:M].astype(bool))
+    return out, d
+
+
+def mask(result, H, W):
+    res = OrcResult(result["cx"], result["cy"], result["r"], result["score"],
+                    result["valid"], result["n_inliers"])
+    out = np.zeros((H, W), np.uint8)
+    lib().orc_mask(C.byref(res), H, W, _ptr(out))
+    return out

@@ -1,0 +1,135 @@
+/*
+ * ca_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, single-threaded CPU implementation of the lean content-area
+ * pipeline of Budd et al., "Rapid and robust endoscopic content area
+ * estimation" (arXiv 2210.14771): strip sampling (Sec. 2.2.2, Eq. 1),
+ * handcrafted edge scoring (Sec. 2.2.3, Eq. 2-3), candidate selection and
+ * RANSAC + least-squares circle fitting (Sec. 2.2.5) and the content-area
+ * mask (Sec. 1.1, Fig. 1).
+ *
+ * It exists to check the CUDA library.  Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg may load it; the library never does.  It
+ * shares no code, header, table or constant generator with the CUDA path.
+ *
+ * Every floating-point step that decides an integer (a quantised score index,
+ * an inlier flag, a filter) is taken in the precision the CUDA kernels use
+ * (IEEE binary32, round-to-nearest, no fused multiply-add), so that both sides
+ * take the same decisions; everything else is exact integer arithmetic.
+ */
+#ifndef CA_ORACLE_H
+#define CA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_HYP_RANDOM = 0, ORC_HYP_EXHAUSTIVE = 1 };
+enum { ORC_NORM_2N = 0, ORC_NORM_NK = 1, ORC_NORM_RAW = 2 };
+
+/* Sizes of the quantised score tables (index ranges are 0..N-1). */
+enum { ORC_LUT_G = 5772, ORC_LUT_T = 8193, ORC_LUT_I = 256 };
+
+typedef struct {
+    int32_t n_strips;        /* N, Eq. 1 (Appendix A: 16) */
+    int32_t cands_per_strip; /* K, even; K/2 picks per half-strip (paper: 2) */
+    int32_t n_hyps;          /* RANSAC attempts (random mode) */
+    int32_t refine_iters;    /* least-squares refits (Sec. 2.2.5: 3) */
+    float alpha;             /* Eq. 1 (8) */
+    float t_g;               /* Eq. 2 (20) */
+    float t_theta_deg;       /* Eq. 2 (30 degrees) */
+    float t_iota;            /* Eq. 2 (25) */
+    float t_ps;              /* point-score filter (0.03) */
+    float t_cs;              /* circle-score acceptance (0.06) */
+    float t_px;              /* edge-distance filter in pixels (3) */
+    float t_ri;              /* RANSAC inlier distance in pixels (3) */
+    float r_min, r_max;      /* radius limits, multiples of W (0.1, 0.8) */
+    float d_max;             /* centre-offset limit, multiple of W (0.2) */
+    int32_t sup_px;          /* suppression half-window between picks of a half */
+    int32_t hyp_mode;        /* ORC_HYP_* */
+    int32_t score_norm;      /* ORC_NORM_*: divisor of the circle score */
+    int32_t sobel_norm;      /* 1 = raw 3x3 Sobel, 8 = Sobel / 8 */
+    uint64_t seed;           /* Philox key */
+} orc_params;
+
+typedef struct {
+    float cx, cy, r;   /* pixel-index coordinates (pixel centre = integer) */
+    float score;       /* S_best / (32768 * norm) */
+    int32_t valid;     /* 0: content area is the whole rectangle */
+    int32_t n_inliers; /* final inlier count of the best circle */
+} orc_result;
+
+/* Optional dumps of one frame's intermediate values.  Every pointer may be
+ * NULL; arrays are filled up to the stated capacity. */
+typedef struct {
+    int32_t cand_cap;     /* capacity of the candidate arrays */
+    int32_t *n_cands;     /* out: M, candidates kept after filtering */
+    int16_t *cand_x, *cand_y;
+    uint16_t *cand_s;     /* Q15 score */
+    int32_t hyp_cap;      /* capacity of the per-hypothesis arrays */
+    int32_t *n_hyps;      /* out: hypotheses evaluated */
+    int32_t *triple;      /* 3 per hypothesis: candidate indices */
+    int32_t *hyp_n_inl;   /* final inlier count */
+    uint32_t *hyp_score;  /* S_h, sum of Q15 scores of the final inliers */
+    int32_t *hyp_pass;    /* 1 if the final circle passed the filters */
+    float *hyp_circle;    /* 3 per hypothesis: final cx, cy, r (origin-relative) */
+    int32_t *best_h;      /* out: index of the winning hypothesis or -1 */
+    uint8_t *best_inl;    /* M flags: final inlier set of the winner */
+} orc_debug;
+
+void orc_params_default(orc_params *p);
+
+/* Eq. 1 strip rows: floor, then clamp to [1, H-2]. Returns 0 on success. */
+int orc_strip_rows(int H, int N, float alpha, int32_t *rows);
+
+/* Quantised score tables (Eq. 2); sizes ORC_LUT_G, ORC_LUT_T, ORC_LUT_I. */
+void orc_build_luts(const orc_params *p, uint16_t *lut_g, uint16_t *lut_t, uint16_t *lut_i);
+
+/* BT.601 integer luma of one RGB pixel. */
+int orc_luma(int r, int g, int b);
+
+/* Per-pixel Q15 scores s_q of the strip centred on `row` (W outputs), plus
+ * optional features (any may be NULL): gx, gy, iota. */
+int orc_strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int row,
+                     const orc_params *p, uint16_t *s_out, int32_t *gx_out,
+                     int32_t *gy_out, uint8_t *iota_out);
+
+/* The same score in double precision straight from Eq. 2-3 (no tables). */
+double orc_score_exact(int gx, int gy, int cx2, int cy2, int iota, const orc_params *p);
+
+/* Candidates of a frame, in order (strip, left picks, right picks). */
+int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                   int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M);
+
+/* Philox4x32-10 (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Hypothesis h's distinct candidate triple, drawn with Philox. */
+void orc_triple(uint64_t seed, uint64_t frame_key, uint32_t h, int M, int32_t out[3]);
+
+/* h-th triple (i<j<k) in lexicographic order. */
+void orc_triple_exhaustive(int64_t h, int M, int32_t out[3]);
+
+/* Circle through three integer points; 0 if collinear. out = cx, cy, r. */
+int orc_circumcircle(int ax, int ay, int bx, int by, int cx, int cy, float out[3]);
+
+/* Algebraic least-squares circle (Coope 1993) of n integer points; 0 if the
+ * fit is degenerate (n < 3 or zero determinant).  out = cx, cy, r. */
+int orc_ls_fit(const int32_t *X, const int32_t *Y, int n, float out[3]);
+
+/* Correctly rounded conversion of the 128-bit integer hi*2^64+lo. */
+float orc_i128_to_f32(int64_t hi, uint64_t lo);
+
+/* Whole pipeline for one frame (device-independent, single-threaded). */
+int orc_estimate(const uint8_t *rgb, int H, int W, int64_t pitch, uint64_t frame_key,
+                 const orc_params *p, orc_result *res, orc_debug *dbg);
+
+/* Content-area mask of a result: disc intersected with the rectangle, or the
+ * whole rectangle when the circle is not valid.  H*W bytes, 0/1. */
+void orc_mask(const orc_result *res, int H, int W, uint8_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,166 @@
+"""Seeded synthetic endoscopic frames with a known content-area circle.
+
+The paper's datasets (CholecECA, RobustECA, PseudoECA; Sec. 2.1) are not
+available, so frames are drawn from a generator shaped like the footage the
+paper describes (Sec. 1.1-1.3, Fig. 1-3): a bright, textured circular
+projection over a dark, slightly noisy border, joined by a 2-pixel edge ramp,
+in the three regimes of Fig. 1 (clipped circle, full circle, no border) plus
+hard cases (saturated blobs, dark tissue touching the edge, vignetting).
+
+This module only draws inputs and their ground truth.  It contains none of the
+estimation method, and both the CUDA path and the CPU oracle are fed from it.
+Every frame is a pure function of (seed, index, H, W, geometry).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GEOMETRIES = ("centred", "clipped", "full", "none", "hard")
+
+# Mix of the 1080p workload: 40 % clipped, 30 % full circle, 20 % no border,
+# 10 % hard cases, assigned by frame index modulo 10.
+_MIX10 = ("clipped",) * 4 + ("full",) * 3 + ("none",) * 2 + ("hard",)
+
+
+def geometry_of(mix: str, idx: int) -> str:
+    if mix == "centred":
+        return "centred"
+    if mix == "mixed":
+        return _MIX10[idx % 10]
+    if mix in GEOMETRIES:
+        return mix
+    raise ValueError(mix)
+
+
+def frame_key(seed: int, idx: int) -> int:
+    """Key of frame `idx` of stream/batch `seed` (feeds the RANSAC draws)."""
+    return ((seed & 0xFFFFFFFF) << 32) | (idx & 0xFFFFFFFF)
+
+
+def _cubic_weights(n_out: int, n_grid: int) -> np.ndarray:
+    """(n_out, n_grid) matrix of Catmull-Rom weights (bicubic upsampling)."""
+    u = (np.arange(n_out, dtype=np.float64) + 0.5) * n_grid / n_out - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    t = u - i0
+    w = np.zeros((n_out, n_grid))
+    taps = (
+        (-1, ((-0.5 * t + 1.0) * t - 0.5) * t),
+        (0, (1.5 * t - 2.5) * t * t + 1.0),
+        (1, ((-1.5 * t + 2.0) * t + 0.5) * t),
+        (2, (0.5 * t - 0.5) * t * t),
+    )
+    rows = np.arange(n_out)
+    for off, wt in taps:
+        idx = np.clip(i0 + off, 0, n_grid - 1)
+        np.add.at(w, (rows, idx), wt)
+    return w.astype(np.float32)
+
+
+def _texture(rng, H, W, grid=8, sigma=25.0) -> np.ndarray:
+    g = rng.standard_normal((grid, grid)).astype(np.float32)
+    t = _cubic_weights(H, grid) @ g @ _cubic_weights(W, grid).T
+    sd = float(t.std()) or 1.0
+    return t * (sigma / sd)
+
+
+def _draw_circle(rng, kind, H, W):
+    c0x, c0y = (W - 1) / 2.0, (H - 1) / 2.0
+    if kind == "centred":
+        cx = c0x + rng.uniform(-0.1, 0.1) * W
+        cy = c0y + rng.uniform(-0.1, 0.1) * H
+        r = rng.uniform(0.45, 0.60) * W
+    elif kind == "clipped":
+        cx = c0x + rng.uniform(-0.1, 0.1) * W
+        cy = c0y + rng.uniform(-0.1, 0.1) * H
+        r = rng.uniform(0.5, 0.7) * W
+    elif kind == "full":
+        r = rng.uniform(0.25, 0.45) * H
+        lo_x, hi_x = max(r + 2, c0x - 0.1 * W), min(W - 3 - r, c0x + 0.1 * W)
+        lo_y, hi_y = max(r + 2, c0y - 0.1 * H), min(H - 3 - r, c0y + 0.1 * H)
+        cx = rng.uniform(lo_x, hi_x) if hi_x > lo_x else c0x
+        cy = rng.uniform(lo_y, hi_y) if hi_y > lo_y else c0y
+    else:
+        raise ValueError(kind)
+    return float(cx), float(cy), float(r)
+
+
+def gt_valid(cx, cy, r, H, W) -> bool:
+    """The circle bounds the content area iff some pixel centre lies outside
+    it; otherwise the content area is the whole rectangle."""
+    corners = ((0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1))
+    return any(math.hypot(x - cx, y - cy) > r for x, y in corners)
+
+
+def frame(seed: int, idx: int, H: int, W: int, geometry: str = "centred"):
+    """One RGB uint8 frame (H, W, 3) and its ground truth dict."""
+    rng = np.random.default_rng([seed & 0xFFFFFFFF, idx & 0xFFFFFFFF, H, W])
+    kind = geometry
+    base = kind
+    if kind == "hard":
+        base = "clipped" if rng.uniform() < 0.5 else "full"
+
+    # interior: per-frame mean 80-200 with a mild per-channel tint, low-frequency
+    # texture (sigma 25) and a little pixel noise
+    mean = rng.uniform(80, 200)
+    tint = rng.uniform(-15, 15, size=3)
+    gains = rng.uniform(0.8, 1.2, size=3)
+    tex = _texture(rng, H, W)
+    noise_in = rng.standard_normal((H, W, 3), dtype=np.float32) * 2.0
+    interior = (mean + tint[None, None, :]).astype(np.float32) + tex[:, :, None] * gains[None, None, :].astype(np.float32) + noise_in
+
+    # border: level 0-15 plus pixel noise sigma 3
+    level = rng.uniform(0, 15)
+    border = level + rng.standard_normal((H, W, 3), dtype=np.float32) * 3.0
+
+    if base == "none":
+        img = interior
+        gt = dict(cx=0.0, cy=0.0, r=0.0, valid=False, kind=kind)
+    else:
+        cx, cy, r = _draw_circle(rng, base, H, W)
+        ys = np.arange(H, dtype=np.float32)[:, None]
+        xs = np.arange(W, dtype=np.float32)[None, :]
+        d = np.sqrt((xs - np.float32(cx)) ** 2 + (ys - np.float32(cy)) ** 2)
+        if kind == "hard":
+            # radial vignetting I * (1 - 0.5 (d/r)^2) inside the projection
+            vig = 1.0 - 0.5 * np.minimum(d / np.float32(r), 1.0) ** 2
+            interior = interior * vig[:, :, None]
+            # dark tissue patches (10-30) touching the circle edge
+            for _ in range(int(rng.integers(1, 3))):
+                ang = rng.uniform(0, 2 * math.pi)
+                pr = rng.uniform(0.08, 0.2) * min(H, W)
+                px, py = cx + r * math.cos(ang), cy + r * math.sin(ang)
+                dp = np.sqrt((xs - np.float32(px)) ** 2 + (ys - np.float32(py)) ** 2)
+                beta = np.clip((pr + 1 - dp) / 2, 0, 1)[:, :, None]
+                interior = interior * (1 - beta) + rng.uniform(10, 30) * beta
+            # saturated specular blobs (255, radius 5-30)
+            for _ in range(int(rng.integers(1, 5))):
+                ang = rng.uniform(0, 2 * math.pi)
+                rad = r * math.sqrt(rng.uniform(0.0, 0.9))
+                px, py = cx + rad * math.cos(ang), cy + rad * math.sin(ang)
+                br = rng.uniform(5, 30)
+                dp = np.sqrt((xs - np.float32(px)) ** 2 + (ys - np.float32(py)) ** 2)
+                beta = np.clip((br + 1 - dp) / 2, 0, 1)[:, :, None]
+                interior = interior * (1 - beta) + 255.0 * beta
+        # 2-pixel linear edge ramp between projection and border
+        a = np.clip((np.float32(r) + 1.0 - d) / 2.0, 0.0, 1.0)[:, :, None]
+        img = interior * a + border * (1.0 - a)
+        gt = dict(cx=cx, cy=cy, r=r, valid=gt_valid(cx, cy, r, H, W), kind=kind)
+    out = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    return out, gt
+
+
+def batch(seed: int, n: int, H: int, W: int, mix: str = "centred"):
+    """n frames (n, H, W, 3), their ground truths and frame keys."""
+    frames = np.empty((n, H, W, 3), np.uint8)
+    gts, keys = [], []
+    for i in range(n):
+        frames[i], gt = frame(seed, i, H, W, geometry_of(mix, i))
+        gts.append(gt)
+        keys.append(frame_key(seed, i))
+    return frames, gts, keys
+
+
+# Resolutions of the mixed-resolution workload (25 % each).
+MIXED_RESOLUTIONS = ((576, 720), (1024, 1280), (1080, 1920), (2160, 3840))
