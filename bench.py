@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the content-area pipeline (Budd et al., arXiv 2210.14771).
+
+One step = the whole hot path over one batch: strip scoring, RANSAC circle
+fitting and mask writing for 64 synthetic 1920x1080 frames (geometry mix,
+seed 1; N=32 strips, K=2, 1024 hypotheses), inputs resident in HBM.  Prints
+one JSON line.  `--impl reference` times the CPU oracle on the same workload
+instead (bounded samples per step).
+
+Under torchrun each rank runs an independent replica on its own GPU (frames
+are independent units; no data-path collective), and rank 0 reports the
+whole-job throughput over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="1080p_x64_mixed_geometry", B=64, H=1080, W=1920, seed=1, mix="mixed",
+                n_strips=32, cands_per_strip=2, n_hyps=1024)
+METRIC = "1080p frames/s (batched, whole hot path)"
+PAPER_CONTEXT = {"ms_per_frame": 0.129, "hardware": "NVIDIA GeForce GTX 980 Ti",
+                 "source": "Table 1 (handcrafted variant)"}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ---------------------------------------------------------------- clocks --
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        loaded = [r for r in rows if num(r[4]) > 0] or rows
+        sm = [num(r[1]) for r in loaded]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in loaded for i in range(4)
+                          if r[6 + i].lower() in ("active", "0x1", "1")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(num(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_loaded": len(loaded)}
+
+
+# ------------------------------------------------------------ workload --
+def make_workload(rank):
+    from paper_2210_14771_gb300 import synth
+    seed = WORKLOAD["seed"] + 1000 * rank
+    return synth.batch(seed, WORKLOAD["B"], WORKLOAD["H"], WORKLOAD["W"], WORKLOAD["mix"])
+
+
+def algorithmic_bytes(B, H, W, N, K):
+    """Bytes the method must move per batch (unsampled rows are never read)."""
+    strips = B * (9 * N * W + 8 * N * K)          # 3 rows x 3 channels per strip; slots out
+    mask = B * (H * W + 24)                        # mask bytes written, result read
+    fit = B * (8 * N * K + 24)                     # slots in, result out
+    return {"strips": strips, "fit": fit, "mask": mask}
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes of one launch from a committed ncu capture, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2210_14771_gb300", "csrc", "ca_kernels.cu"), "rb").read()
+        if rec.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        k = rec["kernels"].get(kernel)
+        return None if k is None else k["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_sample(frames, keys, seconds, min_frames=2):
+    """The CPU oracle, as it stands, on frames of the workload until `seconds`
+    of single-threaded work; returns (frames done, elapsed seconds)."""
+    import oracle
+    op = oracle.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
+                       n_hyps=WORKLOAD["n_hyps"])
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        b = n % len(frames)
+        res, _ = oracle.estimate(frames[b], keys[b], op)
+        oracle.mask(res, frames.shape[1], frames.shape[2])
+        n += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and n >= min_frames) or n >= 4 * len(frames):
+            return n, el
+
+
+# ------------------------------------------------------------- ours --
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2210_14771_gb300.build import build
+    from paper_2210_14771_gb300 import api, metrics
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build()
+    dev = torch.device("cuda", local)
+    frames, gts, keys = make_workload(rank)
+    B, H, W = WORKLOAD["B"], WORKLOAD["H"], WORKLOAD["W"]
+    p = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
+                   n_hyps=WORKLOAD["n_hyps"])
+    ca = api.ContentArea(local)
+    d_frames = torch.from_numpy(frames).to(dev)
+    d_res = api.new_results(B, dev)
+    d_masks = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    clocks = Clocks(local)
+    clocks.start()
+    for _ in range(max(args.warmup, 3)):
+        ca.estimate(d_frames, p, keys=keys, masks=d_masks, results=d_res)
+    torch.cuda.synchronize()
+
+    # ---- batched: K steps, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ca.kernel_times()
+    ca.set_timing(True)
+    n0 = ca.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        ca.estimate(d_frames, p, keys=keys, masks=d_masks, results=d_res)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ca.launch_count() - n0
+    ca.set_timing(False)
+    ktimes = ca.kernel_times()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = B * args.steps * world / (total_ms / 1e3)
+
+    # ---- accuracy of this batch against the generator's ground truth (Sec. 2.3)
+    m_host = d_masks.cpu().numpy()
+    res_host = api.results_numpy(d_res)
+    nh = [metrics.normalised_hausdorff(m_host[b].astype(bool), metrics.gt_mask(gts[b], H, W))
+          for b in range(B)]
+    acc = metrics.summarise(nh)
+
+    # ---- plain method: one frame per call (3 launches per frame)
+    plain = None
+    if not args.skip_plain:
+        lat = []
+        plain_total = 0.0
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(B)]
+        reps = max(1, min(args.steps, 5))
+        p_res = api.new_results(1, dev)
+        for rep in range(reps):
+            flush.fill_(rep & 0xFF)
+            for b in range(B):
+                pev[b][0].record(stream)
+                ca.estimate(d_frames[b:b + 1], p, keys=keys[b:b + 1], masks=d_masks[b:b + 1],
+                            results=p_res)
+                pev[b][1].record(stream)
+            torch.cuda.synchronize()
+            ms = [a.elapsed_time(c) for a, c in pev]
+            lat += ms
+            plain_total += sum(ms)
+        plain = {"frames_per_s": B * reps / (plain_total / 1e3),
+                 "p50_ms_per_frame": float(np.percentile(lat, 50)),
+                 "p99_ms_per_frame": float(np.percentile(lat, 99)),
+                 "launches_per_frame": 3}
+
+    # ---- end to end through the C ABI on host buffers (copies inside)
+    e2e = None
+    if not args.skip_e2e:
+        h_frames = torch.from_numpy(frames).pin_memory()
+        h_res = torch.empty((B, 6), dtype=torch.float32).pin_memory()
+        h_masks = torch.empty((B, H, W), dtype=torch.uint8).pin_memory()
+        import ctypes as C
+        karr = (C.c_uint64 * B)(*keys)
+        for _ in range(2):
+            ca.run_host_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
+                            h_masks.data_ptr())
+        e_steps = max(3, min(args.steps, 20))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ca.run_host_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
+                            h_masks.data_ptr())
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": B * e_steps * world / el, "unit": "frames/s",
+               "h2d_bytes_per_step": B * H * W * 3, "d2h_bytes_per_step": B * (H * W + 24),
+               "ms_per_step": 1e3 * el / e_steps}
+        same = np.array_equal(h_masks.numpy(), m_host) and \
+            np.array_equal(h_res.numpy().view(np.uint8), res_host.view(np.uint8))
+        e2e["matches_device_path"] = bool(same)
+    clk = clocks.stop()
+
+    # ---- roofline of the dominant kernel
+    abytes = algorithmic_bytes(B, H, W, WORKLOAD["n_strips"], WORKLOAD["cands_per_strip"])
+    kern = {}
+    for name, (ms, cnt) in ktimes.items():
+        if cnt:
+            avg = ms / cnt
+            kern[name] = {"ms_per_launch": avg, "launches": cnt,
+                          "share": ms / max(1e-9, sum(v[0] for v in ktimes.values())),
+                          "algorithmic_bytes": abytes[name],
+                          "GBps": abytes[name] / (avg / 1e3) / 1e9}
+    hbm_peak, peak_kind = peaks()
+    hbm_kernels = {k: v for k, v in kern.items() if k in ("strips", "mask")}
+    dom = max(hbm_kernels, key=lambda k: hbm_kernels[k]["ms_per_launch"])
+    for v in kern.values():
+        v["hbm_frac"] = v["GBps"] / hbm_peak
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": kern[dom]["GBps"] / hbm_peak, "peak_kind": peak_kind,
+                "traffic": kernel_traffic(dom)}
+    step_bytes = sum(abytes.values())
+    ms_per_step = total_ms / args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        n, el = oracle_sample(frames, keys, args.cpu_seconds)
+        cpu = {"value": n / el, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": "%d frames of the 64-frame 1080p workload (N=32, 1024 hypotheses), "
+                         "estimate + mask, one thread" % n}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "frames_per_step": B, "H": H, "W": W,
+                   "n_strips": WORKLOAD["n_strips"], "cands_per_strip": WORKLOAD["cands_per_strip"],
+                   "n_hyps": WORKLOAD["n_hyps"], "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+        "step": {"algorithmic_bytes": step_bytes,
+                 "hbm_frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+                 "p50_ms": float(np.percentile(step_ms, 50)),
+                 "p99_ms": float(np.percentile(step_ms, 99)),
+                 "ms_per_frame": ms_per_step / B},
+        "kernels": kern, "plain": plain,
+        "accuracy": {"vs": "generator ground truth", **acc},
+        "paper_context": PAPER_CONTEXT,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    ca.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------- reference --
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    frames, _, keys = make_workload(0)
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_sample(frames[:per_step], keys[:per_step], 0.0, min_frames=1)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        i = (k * per_step) % len(frames)
+        n, _ = oracle_sample(frames[i:i + per_step], keys[i:i + per_step], 0.0,
+                             min_frames=per_step)
+        done += n
+    el = time.perf_counter() - t0
+    value = done / el
+    sample = ("%d frames per step of the 64-frame 1080p workload (N=32, 1024 hypotheses), "
+              "estimate + mask, one thread" % per_step)
+    out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD["name"], "frames_per_step": per_step,
+                      "H": WORKLOAD["H"], "W": WORKLOAD["W"], "n_strips": WORKLOAD["n_strips"],
+                      "cands_per_strip": WORKLOAD["cands_per_strip"],
+                      "n_hyps": WORKLOAD["n_hyps"]},
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * ca.h -- C ABI of libca, a single-GPU (sm_103a) implementation of the lean
+ * content-area pipeline of Budd et al., "Rapid and robust endoscopic content
+ * area estimation: a lean GPU-based pipeline and curated benchmark dataset"
+ * (arXiv 2210.14771).
+ *
+ * What one call computes, per frame (paper sections in brackets):
+ *   strip rows h_i of Eq. 1 [Sec. 2.2.2] -> per-pixel handcrafted score
+ *   s = s_g s_theta s_iota of Eq. 2-3 [Sec. 2.2.3] -> best points of each
+ *   half-strip, filtered by t_px and t_ps -> RANSAC over random triples, each
+ *   refined by three least-squares refits, scored by the sum of its inlier
+ *   scores, filtered by r_min/r_max/d_max -> best circle, accepted if its score
+ *   reaches t_cs [Sec. 2.2.5] -> content-area mask = disc intersected with the
+ *   sensor rectangle, or the whole rectangle when no circle is accepted
+ *   [Sec. 1.1, Fig. 1; Sec. 2.2.1].
+ *
+ * Conventions for every function:
+ *   - Pointers named *_dev are device pointers; everything else is host memory.
+ *   - The caller owns frames, results and masks and keeps them alive until the
+ *     work queued on the given stream has completed.  The handle owns its
+ *     workspace, tables, graphs, scorer weights and serving state.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream only queue work on it and return.
+ *   - Every call returns a ca_status and never aborts.  Argument errors are
+ *     detected on the host before any work is queued (CA_ERR_INVALID_ARG);
+ *     CUDA errors surface as CA_ERR_CUDA, by this call or the next one.
+ *     ca_last_error() gives a one-line description of the last failure.
+ *   - Results depend only on (frame bytes, params, frame_key), never on the
+ *     batch size or position: the RANSAC draws are keyed on frame_key.
+ *   - Limits: 8 <= W <= 4096, 3 <= H <= 4096, row pitch >= 3W bytes,
+ *     N*K <= 256 candidate slots per frame.
+ *
+ * Not thread-safe: one handle serves one host thread at a time.
+ */
+#ifndef CA_H
+#define CA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CA_OK = 0,
+    CA_ERR_INVALID_ARG = 1, /* bad pointer, size, layout or parameter */
+    CA_ERR_CUDA = 2,        /* a CUDA runtime call or a kernel failed */
+    CA_ERR_OOM = 3,         /* device or pinned allocation failed */
+    CA_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    CA_ERR_UNSUPPORTED = 5, /* feature not available (e.g. no scorer weights) */
+    CA_ERR_ADMISSION = 6,   /* serving: request does not fit the memory budget */
+    CA_ERR_STATE = 7        /* call not valid in the handle's current state */
+} ca_status;
+
+enum { CA_HYP_RANDOM = 0, CA_HYP_EXHAUSTIVE = 1 };
+/* divisor of the circle score compared with t_cs (Sec. 2.2.5): the paper's
+ * candidate count 2N, the slot count N*K, or none */
+enum { CA_NORM_2N = 0, CA_NORM_NK = 1, CA_NORM_RAW = 2 };
+/* edge scorer: handcrafted (Sec. 2.2.3), learned 1-D CNN, or learned with the
+ * handcrafted score taking over half-strips the network is unsure about */
+enum { CA_SCORER_HAND = 0, CA_SCORER_LEARNED = 1, CA_SCORER_LEARNED_FALLBACK = 2 };
+
+/* Parameters; ca_params_default() fills the values of the paper's Appendix A. */
+typedef struct ca_params {
+    int32_t n_strips;        /* N, number of strips (Eq. 1; default 16) */
+    int32_t cands_per_strip; /* K, even: K/2 best points per half-strip (2) */
+    int32_t n_hyps;          /* RANSAC attempts per frame (1024) */
+    int32_t refine_iters;    /* least-squares refits per attempt (3) */
+    float alpha;             /* strip weighting of Eq. 1 (8) */
+    float t_g;               /* gradient-magnitude soft threshold (20) */
+    float t_theta_deg;       /* gradient-direction soft threshold, degrees (30) */
+    float t_iota;            /* preceding-maximum soft threshold (25) */
+    float t_ps;              /* point-score filter (0.03) */
+    float t_cs;              /* circle-score acceptance threshold (0.06) */
+    float t_px;              /* drop points closer than this to the edge (3) */
+    float t_ri;              /* inlier distance, pixels (3) */
+    float r_min, r_max;      /* radius bounds, multiples of W (0.1, 0.8) */
+    float d_max;             /* centre offset bound, multiple of W (0.2) */
+    int32_t sup_px;          /* suppression half-window between picks (8) */
+    int32_t hyp_mode;        /* CA_HYP_* */
+    int32_t score_norm;      /* CA_NORM_* */
+    int32_t sobel_norm;      /* 1: raw 3x3 Sobel; 8: Sobel divided by 8 */
+    int32_t scorer_mode;     /* CA_SCORER_* */
+    int32_t reserved;
+    uint64_t seed;           /* key of the RANSAC random stream */
+} ca_params;
+
+/* One input frame: packed RGB, 8 bits per channel, rows `pitch` bytes apart
+ * (device memory).  `mask_dev`, when not NULL, receives the H*W content-area
+ * mask (one byte per pixel, 0 or 1, rows W bytes apart). */
+typedef struct ca_frame {
+    const uint8_t *rgb_dev;
+    uint8_t *mask_dev;
+    int32_t H, W;
+    int64_t pitch;
+    uint64_t frame_key;
+} ca_frame;
+
+/* One result (24 bytes): circle in pixel-index coordinates (pixel centres at
+ * integer x, y; y down), score = best circle score / (32768 * normaliser),
+ * valid = 0 when the content area is the whole rectangle. */
+typedef struct ca_result {
+    float cx, cy, r, score;
+    int32_t valid, n_inliers;
+} ca_result;
+
+typedef struct ca_handle ca_handle;
+
+/* Fills *p with the defaults above (Appendix A of the paper). */
+void ca_params_default(ca_params *p);
+
+/* Creates a handle bound to CUDA device `device`.  Allocates only small
+ * tables; workspaces grow on first use.  *out is NULL on failure. */
+ca_status ca_create(ca_handle **out, int device);
+
+/* Synchronises the handle's streams and frees everything it owns. */
+ca_status ca_destroy(ca_handle *h);
+
+/* Estimates the content area of B frames (Sec. 2.2.1-2.2.5) and, for frames
+ * whose mask_dev is set, writes the mask (Sec. 1.1).  frames: host array of B
+ * descriptors pointing to device memory, any mix of resolutions.  out_dev:
+ * device array of B ca_result.  Queued on `stream`; returns once queued. */
+ca_status ca_estimate(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                      ca_result *out_dev, void *stream);
+
+/* Same for B frames of one resolution stored back to back:
+ * frames_dev = B x H x W x 3 bytes; masks_dev = B x H x W bytes or NULL;
+ * keys = host array of B frame keys, or NULL for keys 0..B-1. */
+ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, int H, int W,
+                              const uint64_t *keys, const ca_params *p, ca_result *out_dev,
+                              uint8_t *masks_dev, void *stream);
+
+/* Writes the content-area masks of B results (Sec. 1.1, Fig. 1): pixel (x, y)
+ * is 1 iff (x-cx)^2 + (y-cy)^2 <= r^2 in binary32 (each operation rounded, no
+ * fused multiply-add), or 1 everywhere when valid == 0.  res_dev: device array
+ * of B results; H, W: host arrays of B sizes; masks_dev: host array of B
+ * device pointers, each to H[i]*W[i] bytes. */
+ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *H,
+                  const int32_t *W, uint8_t *const *masks_dev, void *stream);
+
+/* End-to-end call on HOST buffers: copies B frames (B x H x W x 3 bytes, host)
+ * to the device, estimates, and copies the B results (host) and, when
+ * masks_host is not NULL, the B x H x W masks back.  Synchronous.  Pinned host
+ * memory gives the fastest copies.  keys as in ca_estimate_uniform. */
+ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, int W,
+                      const uint64_t *keys, const ca_params *p, ca_result *res_host,
+                      uint8_t *masks_host);
+
+/* Waits for `stream` and reports any asynchronous device error raised by the
+ * handle's kernels (including a bounded wait that gave up). */
+ca_status ca_sync(ca_handle *h, void *stream);
+
+/* Debug capture of the intermediate values of subsequent calls: 0 = off,
+ * 1 = candidates, 2 = candidates and per-hypothesis records.  Capturing costs
+ * extra device memory and writes; results are unchanged. */
+ca_status ca_set_debug(ca_handle *h, int level);
+
+enum {
+    /* per frame: int32 M, int32 n_slots(=N*K), then n_slots records of
+     * {int16 x, int16 y, uint16 score, uint16 kept}: candidate slots in the
+     * order (strip, left ranks, right ranks), of which the kept ones are the
+     * frame's candidates in order */
+    CA_DUMP_CANDIDATES = 1,
+    /* per frame: int32 n_hyps, then n_hyps records of {int32 i0, i1, i2,
+     * int32 n_inliers, uint32 score_sum, int32 passed, float cx, cy, r}
+     * (circle relative to the origin (floor(W/2), floor(H/2))) */
+    CA_DUMP_HYPOTHESES = 2,
+    /* library-built tables for the given params: uint16 s_g table (5772),
+     * s_theta table (8193), s_iota table (256), then int32 strip rows for
+     * H = frame (pass the frame height as `frame`); host computation only,
+     * h may be NULL and no device is needed */
+    CA_DUMP_TABLES = 3
+};
+
+/* Copies debug data of frame `frame` of the last ca_estimate call (synchronises
+ * the handle's last stream).  *written receives the byte count. */
+ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p,
+                        void *host_buf, size_t bytes, size_t *written);
+
+/* Number of kernel launches the handle has queued since creation. */
+uint64_t ca_launch_count(const ca_handle *h);
+
+/* Kernel timing: when on, every later ca_estimate / ca_mask call records CUDA
+ * events on its stream around each kernel it launches. */
+ca_status ca_set_timing(ca_handle *h, int on);
+
+/* Sums of the recorded kernel durations in milliseconds since the last read:
+ * ms[0] strip scoring, ms[1] circle fitting, ms[2] mask writing; counts[i] =
+ * launches timed.  Waits for the recorded events, then clears them. */
+ca_status ca_kernel_times(ca_handle *h, double ms[3], int32_t counts[3]);
+
+const char *ca_status_string(ca_status s);
+const char *ca_last_error(const ca_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CA_H */

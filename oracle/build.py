@@ -12,8 +12,24 @@ HDR = os.path.join(HERE, "ca_oracle.h")
 LIB = os.path.join(HERE, "libca_oracle.so")
 
 
+def _native_elf(path: str) -> bool:
+    """True if `path` is an ELF object for this machine (x86_64 or aarch64)."""
+    import platform
+    import struct
+    try:
+        with open(path, "rb") as f:
+            head = f.read(20)
+    except OSError:
+        return False
+    if len(head) < 20 or head[:4] != b"\x7fELF":
+        return False
+    machine = struct.unpack("<H", head[18:20])[0]
+    want = {"x86_64": 62, "AMD64": 62, "aarch64": 183, "arm64": 183}.get(platform.machine())
+    return want is None or machine == want
+
+
 def build(force: bool = False) -> str:
-    stale = force or not os.path.exists(LIB) or any(
+    stale = force or not os.path.exists(LIB) or not _native_elf(LIB) or any(
         os.path.getmtime(f) > os.path.getmtime(LIB) for f in (SRC, HDR, __file__))
     if stale:
         tmp = LIB + ".tmp.%d" % os.getpid()

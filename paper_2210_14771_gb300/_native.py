@@ -1,0 +1,99 @@
+"""ctypes declarations of the libca C ABI (include/ca.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+CA_OK, CA_ERR_INVALID_ARG, CA_ERR_CUDA, CA_ERR_OOM = 0, 1, 2, 3
+CA_ERR_TIMEOUT, CA_ERR_UNSUPPORTED, CA_ERR_ADMISSION, CA_ERR_STATE = 4, 5, 6, 7
+CA_HYP_RANDOM, CA_HYP_EXHAUSTIVE = 0, 1
+CA_NORM_2N, CA_NORM_NK, CA_NORM_RAW = 0, 1, 2
+CA_SCORER_HAND, CA_SCORER_LEARNED, CA_SCORER_LEARNED_FALLBACK = 0, 1, 2
+CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
+LUT_G, LUT_T, LUT_I = 5772, 8193, 256
+
+
+class CaParams(C.Structure):
+    _fields_ = [
+        ("n_strips", C.c_int32), ("cands_per_strip", C.c_int32), ("n_hyps", C.c_int32),
+        ("refine_iters", C.c_int32), ("alpha", C.c_float), ("t_g", C.c_float),
+        ("t_theta_deg", C.c_float), ("t_iota", C.c_float), ("t_ps", C.c_float),
+        ("t_cs", C.c_float), ("t_px", C.c_float), ("t_ri", C.c_float), ("r_min", C.c_float),
+        ("r_max", C.c_float), ("d_max", C.c_float), ("sup_px", C.c_int32),
+        ("hyp_mode", C.c_int32), ("score_norm", C.c_int32), ("sobel_norm", C.c_int32),
+        ("scorer_mode", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+    ]
+
+
+class CaFrame(C.Structure):
+    _fields_ = [("rgb_dev", C.c_void_p), ("mask_dev", C.c_void_p), ("H", C.c_int32),
+                ("W", C.c_int32), ("pitch", C.c_int64), ("frame_key", C.c_uint64)]
+
+
+class CaResult(C.Structure):
+    _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("r", C.c_float), ("score", C.c_float),
+                ("valid", C.c_int32), ("n_inliers", C.c_int32)]
+
+
+# (name, restype, argtypes) of every exported function, in header order.
+_P = C.POINTER
+SIGNATURES = [
+    ("ca_params_default", None, [_P(CaParams)]),
+    ("ca_create", C.c_int, [_P(C.c_void_p), C.c_int]),
+    ("ca_destroy", C.c_int, [C.c_void_p]),
+    ("ca_estimate", C.c_int, [C.c_void_p, _P(CaFrame), C.c_int, _P(CaParams), C.c_void_p,
+                              C.c_void_p]),
+    ("ca_estimate_uniform", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                      _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
+                          _P(C.c_void_p), C.c_void_p]),
+    ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                              _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p]),
+    ("ca_sync", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("ca_set_debug", C.c_int, [C.c_void_p, C.c_int]),
+    ("ca_debug_dump", C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(CaParams), C.c_void_p,
+                                C.c_size_t, _P(C.c_size_t)]),
+    ("ca_launch_count", C.c_uint64, [C.c_void_p]),
+    ("ca_set_timing", C.c_int, [C.c_void_p, C.c_int]),
+    ("ca_kernel_times", C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int32)]),
+    ("ca_status_string", C.c_char_p, [C.c_int]),
+    ("ca_last_error", C.c_char_p, [C.c_void_p]),
+]
+
+_lib = None
+
+
+class CaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libca status %d (%s): %s" % (status, STATUS_NAMES.get(status, "?"), msg))
+        self.status = status
+
+
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory",
+                4: "timeout", 5: "unsupported", 6: "admission refused", 7: "invalid state"}
+
+
+def lib() -> C.CDLL:
+    """The loaded libca.  Raises if the library has not been built: there is
+    no fallback implementation."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libca.so is missing (%s); build it with "
+                               "paper_2210_14771_gb300.build.build()" % LIB)
+        L = C.CDLL(LIB)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int, handle=None):
+    if status != CA_OK:
+        msg = lib().ca_last_error(handle).decode() if handle else ""
+        raise CaError(status, msg)

@@ -1,0 +1,197 @@
+"""Python view of libca: same calls as include/ca.h, argument marshalling only.
+
+PyTorch supplies device memory and streams; every step of the estimation runs
+in the library's CUDA kernels.  There is no CPU fallback: without the built
+library or a GPU these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+RESULT_DTYPE = np.dtype([("cx", "<f4"), ("cy", "<f4"), ("r", "<f4"), ("score", "<f4"),
+                         ("valid", "<i4"), ("n_inliers", "<i4")])
+SLOT_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("s", "<u2"), ("kept", "<u2")])
+HYP_DTYPE = np.dtype([("i0", "<i4"), ("i1", "<i4"), ("i2", "<i4"), ("n_inl", "<i4"),
+                      ("S", "<u4"), ("pass", "<i4"), ("cx", "<f4"), ("cy", "<f4"),
+                      ("r", "<f4")])
+
+
+def params(**kw) -> N.CaParams:
+    """ca_params with the paper's defaults (Appendix A), overridden by kw."""
+    p = N.CaParams()
+    N.lib().ca_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _stream_ptr(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return C.c_void_p(s.cuda_stream)
+
+
+def results_numpy(res: torch.Tensor) -> np.ndarray:
+    """(B, 6) float32 result tensor (any device) -> structured numpy array."""
+    return res.detach().cpu().contiguous().numpy().view(RESULT_DTYPE).reshape(-1)
+
+
+def new_results(B: int, device) -> torch.Tensor:
+    return torch.zeros((B, 6), dtype=torch.float32, device=device)
+
+
+class ContentArea:
+    """One libca handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        N.check(N.lib().ca_create(C.byref(h), device))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().ca_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        N.check(st, self._h)
+
+    # ------------------------------------------------------------ estimate --
+    def estimate(self, frames, p=None, keys=None, masks=None, results=None, stream=None):
+        """Content area of a batch (Sec. 2.2).
+
+        frames: uint8 CUDA tensor (B, H, W, 3), or a list of (H, W, 3) tensors
+        of any sizes.  keys: frame keys (defaults 0..B-1).  masks: None, True
+        (allocate), a (B, H, W) uint8 tensor, or a list of (H, W) tensors.
+        Returns (results (B, 6) float32 tensor, masks or None); queued on
+        `stream` (default: the current stream).
+        """
+        p = p or params()
+        st = _stream_ptr(stream, self.device)
+        if isinstance(frames, torch.Tensor):
+            B, H, W, _ = frames.shape
+            assert frames.dtype == torch.uint8 and frames.is_cuda and frames.is_contiguous()
+            if masks is True:
+                masks = torch.empty((B, H, W), dtype=torch.uint8, device=frames.device)
+            if results is None:
+                results = new_results(B, frames.device)
+            karr = (C.c_uint64 * B)(*(keys if keys is not None else range(B)))
+            self._check(N.lib().ca_estimate_uniform(
+                self._h, C.c_void_p(frames.data_ptr()), B, H, W, karr, C.byref(p),
+                C.c_void_p(results.data_ptr()),
+                C.c_void_p(masks.data_ptr()) if masks is not None else None, st))
+            return results, masks
+        frames = list(frames)
+        B = len(frames)
+        if masks is True:
+            masks = [torch.empty(f.shape[:2], dtype=torch.uint8, device=f.device) for f in frames]
+        if results is None:
+            results = new_results(B, self.device)
+        arr = (N.CaFrame * max(B, 1))()
+        for i, f in enumerate(frames):
+            assert f.dtype == torch.uint8 and f.is_cuda and f.dim() == 3 and f.shape[2] == 3
+            assert f.stride(2) == 1 and f.stride(1) == 3
+            arr[i].rgb_dev = f.data_ptr()
+            arr[i].mask_dev = masks[i].data_ptr() if masks is not None else None
+            arr[i].H, arr[i].W = int(f.shape[0]), int(f.shape[1])
+            arr[i].pitch = int(f.stride(0))
+            arr[i].frame_key = int(keys[i]) if keys is not None else i
+        self._check(N.lib().ca_estimate(self._h, arr, B, C.byref(p),
+                                        C.c_void_p(results.data_ptr()), st))
+        return results, masks
+
+    def mask(self, results: torch.Tensor, sizes, masks=None, stream=None):
+        """Content-area masks of results (Sec. 1.1): sizes = [(H, W), ...]."""
+        B = len(sizes)
+        if masks is None:
+            masks = [torch.empty(s, dtype=torch.uint8, device=results.device) for s in sizes]
+        Hs = (C.c_int32 * B)(*[int(s[0]) for s in sizes])
+        Ws = (C.c_int32 * B)(*[int(s[1]) for s in sizes])
+        ptrs = (C.c_void_p * B)(*[m.data_ptr() for m in masks])
+        self._check(N.lib().ca_mask(self._h, C.c_void_p(results.data_ptr()), B, Hs, Ws, ptrs,
+                                    _stream_ptr(stream, self.device)))
+        return masks
+
+    def run_host(self, frames: np.ndarray, p=None, keys=None, want_masks=True):
+        """End-to-end call on host buffers (copies in, estimates, copies out)."""
+        p = p or params()
+        frames = np.ascontiguousarray(frames, np.uint8)
+        B, H, W, _ = frames.shape
+        res = np.zeros(B, RESULT_DTYPE)
+        masks = np.empty((B, H, W), np.uint8) if want_masks else None
+        karr = (C.c_uint64 * B)(*(keys if keys is not None else range(B)))
+        self._check(N.lib().ca_run_host(
+            self._h, frames.ctypes.data_as(C.c_void_p), B, H, W, karr, C.byref(p),
+            res.ctypes.data_as(C.c_void_p),
+            masks.ctypes.data_as(C.c_void_p) if masks is not None else None))
+        return res, masks
+
+    def run_host_ptr(self, frames_ptr: int, B, H, W, keys_arr, p, res_ptr: int, masks_ptr):
+        """ca_run_host on raw host pointers (pinned buffers of the caller)."""
+        self._check(N.lib().ca_run_host(self._h, C.c_void_p(frames_ptr), B, H, W, keys_arr,
+                                        C.byref(p), C.c_void_p(res_ptr),
+                                        C.c_void_p(masks_ptr) if masks_ptr else None))
+
+    def sync(self, stream=None):
+        self._check(N.lib().ca_sync(self._h, _stream_ptr(stream, self.device)))
+
+    def launch_count(self) -> int:
+        return int(N.lib().ca_launch_count(self._h))
+
+    def set_timing(self, on: bool):
+        self._check(N.lib().ca_set_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        """{kernel: (total ms, launches)} since the last read (CUDA events)."""
+        ms = (C.c_double * 3)()
+        cnt = (C.c_int32 * 3)()
+        self._check(N.lib().ca_kernel_times(self._h, ms, cnt))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(("strips", "fit", "mask"))}
+
+    # --------------------------------------------------------------- debug --
+    def set_debug(self, level: int):
+        self._check(N.lib().ca_set_debug(self._h, level))
+
+    def _dump(self, what, frame, p, nbytes):
+        buf = np.zeros(nbytes, np.uint8)
+        written = C.c_size_t(0)
+        self._check(N.lib().ca_debug_dump(self._h, what, frame, C.byref(p) if p else None,
+                                          buf.ctypes.data_as(C.c_void_p), nbytes,
+                                          C.byref(written)))
+        return buf[:written.value]
+
+    def dump_candidates(self, frame: int):
+        """Candidate slots of one frame of the last call (debug level >= 1)."""
+        raw = self._dump(N.CA_DUMP_CANDIDATES, frame, None, 8 + 8 * 256)
+        M, n = (int(v) for v in raw[:8].view(np.int32))
+        slots = raw[8:8 + 8 * n].view(SLOT_DTYPE)
+        kept = slots[slots["kept"] == 1]
+        return dict(M=M, slots=slots, x=kept["x"].copy(), y=kept["y"].copy(), s=kept["s"].copy())
+
+    def dump_hypotheses(self, frame: int, max_hyps: int = 1 << 20):
+        """Per-hypothesis records of one frame of the last call (debug level 2)."""
+        nbytes = 4 + HYP_DTYPE.itemsize * max_hyps
+        raw = self._dump(N.CA_DUMP_HYPOTHESES, frame, None, nbytes)
+        nh = int(raw[:4].view(np.int32)[0])
+        return raw[4:4 + HYP_DTYPE.itemsize * nh].view(HYP_DTYPE)
+
+    def tables(self, p, H: int):
+        """The library's own s_g / s_theta / s_iota tables and Eq. 1 rows."""
+        nb = 2 * (N.LUT_G + N.LUT_T + N.LUT_I) + 4 * p.n_strips
+        raw = self._dump(N.CA_DUMP_TABLES, H, p, nb)
+        u16 = raw[:2 * (N.LUT_G + N.LUT_T + N.LUT_I)].view(np.uint16)
+        rows = raw[2 * (N.LUT_G + N.LUT_T + N.LUT_I):].view(np.int32)
+        return (u16[:N.LUT_G], u16[N.LUT_G:N.LUT_G + N.LUT_T], u16[N.LUT_G + N.LUT_T:], rows)

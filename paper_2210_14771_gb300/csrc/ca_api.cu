@@ -1,0 +1,744 @@
+// ca_api.cu -- host side of libca: handle, validation, tables, workspace,
+// launch sequencing, debug capture and the host-buffer end-to-end call.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ca_internal.h"
+
+using namespace ca;
+
+namespace {
+
+constexpr int kRing = 4;   // staging slots: calls that may be in flight at once
+
+struct Staging {
+    void *host = nullptr;   // pinned
+    void *dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+};
+
+struct LutKey {
+    float t_g = -1, t_theta = -1, t_iota = -1;
+    int sobel_norm = -1;
+    bool operator==(const LutKey &o) const {
+        return t_g == o.t_g && t_theta == o.t_theta && t_iota == o.t_iota &&
+               sobel_norm == o.sobel_norm;
+    }
+};
+
+}  // namespace
+
+struct ca_handle {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    int debug = 0;
+    uint64_t launches = 0;
+
+    // score tables on the device: [s_g][s_theta][s_iota]
+    uint16_t *d_luts = nullptr;
+    LutKey lut_key;
+    int qg_sat = kLutG - 1;
+    bool luts_ready = false;
+
+    Staging ring[kRing];
+    int ring_pos = 0;
+
+    Workspace ws;
+    int ws_frames = 0, ws_tiles = 0;
+    size_t ws_hyp_records = 0;
+
+    // ordering between calls made on different streams
+    cudaEvent_t last_ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
+
+    // what the last estimate call captured (debug dumps)
+    int last_B = 0, last_NK = 0, last_hyp_stride = 0;
+
+    // host end-to-end buffers
+    uint8_t *e2e_frames = nullptr, *e2e_masks = nullptr;
+    ca_result *e2e_res = nullptr;
+    size_t e2e_frames_cap = 0, e2e_masks_cap = 0, e2e_res_cap = 0;
+    cudaStream_t e2e_stream = nullptr;
+
+    int strip_blocks_per_sm = 0;
+    size_t strip_blocks_smem = 0;
+
+    // kernel timing: event pairs per kernel kind (0 strips, 1 fit, 2 mask)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[3];
+};
+
+namespace {
+
+ca_status fail(ca_handle *h, ca_status st, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+ca_status cuda_fail(ca_handle *h, cudaError_t e, const char *what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? CA_ERR_OOM : CA_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CA_CUDA(h, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------------ tables --
+// Eq. 1 strip rows, floored and clamped to [1, H-2].
+void strip_rows(int H, int N, float alpha, int32_t *rows) {
+    for (int i = 0; i < N; ++i) {
+        const double t = (double)alpha / (double)N;
+        const double u = (double)i - (double)(N - 1) / 2.0;
+        const double e = std::exp(-(t * u));
+        const double hv = (double)H / (1.0 + e);
+        long v = (long)std::floor(hv);
+        v = std::max(1L, std::min(v, (long)H - 2));
+        rows[i] = (int32_t)v;
+    }
+}
+
+uint16_t to_q15(double v) {
+    double x = std::floor(32768.0 * v + 0.5);
+    x = std::max(0.0, std::min(x, 32768.0));
+    return (uint16_t)x;
+}
+
+// Soft-threshold tables of Eq. 2: s_g at quarter steps of |g|, s_theta at the
+// centres of 8192 cos bins, s_iota at every 8-bit intensity.
+void build_luts(const ca_params &p, uint16_t *out, int *qg_sat) {
+    uint16_t *lg = out, *lt = out + kLutG, *li = out + kLutG + kLutT;
+    for (int q = 0; q < kLutG; ++q)
+        lg[q] = to_q15(std::tanh(((double)q * 0.25) / ((double)p.sobel_norm * (double)p.t_g)));
+    for (int q = 0; q < kLutT; ++q) {
+        double c = ((double)q + 0.5) / 4096.0 - 1.0;
+        if (c > 1.0) c = 1.0;
+        const double deg = std::acos(c) * (180.0 / 3.14159265358979323846);
+        lt[q] = to_q15(1.0 - std::tanh(deg / (double)p.t_theta_deg));
+    }
+    for (int v = 0; v < kLutI; ++v) li[v] = to_q15(1.0 - std::tanh((double)v / (double)p.t_iota));
+    // index from which s_g stays constant (the kernels clamp there)
+    int s = kLutG - 1;
+    while (s > 0 && lg[s - 1] == lg[kLutG - 1]) --s;
+    *qg_sat = s;
+}
+
+// ------------------------------------------------------ validation --
+ca_status check_params(ca_handle *h, const ca_params *p) {
+    if (!p) return fail(h, CA_ERR_INVALID_ARG, "params is NULL");
+    if (p->n_strips < 1 || p->n_strips > 256)
+        return fail(h, CA_ERR_INVALID_ARG, "n_strips %d outside [1, 256]", p->n_strips);
+    if (p->cands_per_strip < 2 || (p->cands_per_strip & 1))
+        return fail(h, CA_ERR_INVALID_ARG, "cands_per_strip %d must be even and >= 2",
+                    p->cands_per_strip);
+    if (p->n_strips * p->cands_per_strip > kMaxSlots)
+        return fail(h, CA_ERR_INVALID_ARG, "n_strips * cands_per_strip = %d exceeds %d",
+                    p->n_strips * p->cands_per_strip, kMaxSlots);
+    if (p->hyp_mode != CA_HYP_RANDOM && p->hyp_mode != CA_HYP_EXHAUSTIVE)
+        return fail(h, CA_ERR_INVALID_ARG, "bad hyp_mode %d", p->hyp_mode);
+    if (p->hyp_mode == CA_HYP_RANDOM && (p->n_hyps < 1 || p->n_hyps > kMaxHyps))
+        return fail(h, CA_ERR_INVALID_ARG, "n_hyps %d outside [1, %d]", p->n_hyps, kMaxHyps);
+    if (p->hyp_mode == CA_HYP_EXHAUSTIVE) {
+        const long long nk = (long long)p->n_strips * p->cands_per_strip;
+        if (nk * (nk - 1) * (nk - 2) / 6 > (1LL << 20))
+            return fail(h, CA_ERR_INVALID_ARG, "exhaustive mode needs C(N*K,3) <= 2^20");
+    }
+    if (p->refine_iters < 0 || p->refine_iters > 16)
+        return fail(h, CA_ERR_INVALID_ARG, "refine_iters %d outside [0, 16]", p->refine_iters);
+    if (p->sup_px < 0 || p->sup_px > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "sup_px %d invalid", p->sup_px);
+    if (p->sobel_norm != 1 && p->sobel_norm != 8)
+        return fail(h, CA_ERR_INVALID_ARG, "sobel_norm must be 1 or 8");
+    if (p->score_norm < CA_NORM_2N || p->score_norm > CA_NORM_RAW)
+        return fail(h, CA_ERR_INVALID_ARG, "bad score_norm %d", p->score_norm);
+    if (p->scorer_mode != CA_SCORER_HAND)
+        return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs learned weights", p->scorer_mode);
+    const float fs[] = {p->alpha, p->t_g, p->t_theta_deg, p->t_iota, p->t_ps, p->t_cs,
+                        p->t_px, p->t_ri, p->r_min, p->r_max, p->d_max};
+    for (float v : fs)
+        if (!std::isfinite(v)) return fail(h, CA_ERR_INVALID_ARG, "non-finite parameter");
+    if (!(p->t_g > 0) || !(p->t_theta_deg > 0) || !(p->t_iota > 0))
+        return fail(h, CA_ERR_INVALID_ARG, "soft thresholds must be positive");
+    if (p->t_ps < 0 || p->t_ps > 1 || p->t_cs < 0 || p->t_px < 0 || p->t_px > kMaxDim ||
+        p->t_ri < 0)
+        return fail(h, CA_ERR_INVALID_ARG, "threshold out of range");
+    return CA_OK;
+}
+
+ca_status check_frame(ca_handle *h, const ca_frame &f, int i) {
+    if (!f.rgb_dev) return fail(h, CA_ERR_INVALID_ARG, "frame %d: rgb is NULL", i);
+    if (f.W < 8 || f.W > kMaxDim || f.H < 3 || f.H > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "frame %d: size %dx%d outside [8..%d]x[3..%d]", i, f.W,
+                    f.H, kMaxDim, kMaxDim);
+    if (f.pitch < 3LL * f.W)
+        return fail(h, CA_ERR_INVALID_ARG, "frame %d: pitch %lld < 3W", i, (long long)f.pitch);
+    return CA_OK;
+}
+
+template <class T>
+ca_status grow(ca_handle *h, T **ptr, size_t have, size_t need, bool zero) {
+    if (need <= have && *ptr) return CA_OK;
+    if (*ptr) {
+        if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+        CA_CUDA(h, cudaFree(*ptr));
+        *ptr = nullptr;
+    }
+    CA_CUDA(h, cudaMalloc((void **)ptr, need * sizeof(T)));
+    if (zero) CA_CUDA(h, cudaMemset(*ptr, 0, need * sizeof(T)));
+    return CA_OK;
+}
+
+ca_status ensure_workspace(ca_handle *h, int B, int n_tiles, size_t hyp_records) {
+    ca_status st;
+    if (B > h->ws_frames) {
+        const int nb = std::max(B, 2 * h->ws_frames);
+        if ((st = grow(h, &h->ws.slots, 0, (size_t)nb * kMaxSlots, true)) != CA_OK) return st;
+        if ((st = grow(h, &h->ws.best, 0, (size_t)nb, true)) != CA_OK) return st;
+        if ((st = grow(h, &h->ws.done, 0, (size_t)nb, true)) != CA_OK) return st;
+        if ((st = grow(h, &h->ws.n_hyps, 0, (size_t)nb, true)) != CA_OK) return st;
+        if ((st = grow(h, &h->ws.n_cands, 0, (size_t)nb, true)) != CA_OK) return st;
+        h->ws_frames = nb;
+        h->ws_tiles = 0;   // force tiles realloc with the new frame count
+    }
+    if (n_tiles > h->ws_tiles || h->ws.tiles == nullptr) {
+        const int nt = std::max(n_tiles, h->ws_tiles);
+        if ((st = grow(h, &h->ws.tiles, 0, (size_t)h->ws_frames * nt, false)) != CA_OK) return st;
+        h->ws_tiles = nt;
+    }
+    if (hyp_records > h->ws_hyp_records) {
+        if ((st = grow(h, &h->ws.hyps, 0, hyp_records, true)) != CA_OK) return st;
+        h->ws_hyp_records = hyp_records;
+    }
+    return CA_OK;
+}
+
+// A pinned host block and its device twin, reusable once its event completed.
+ca_status take_staging(ca_handle *h, size_t bytes, Staging **out) {
+    Staging &s = h->ring[h->ring_pos];
+    h->ring_pos = (h->ring_pos + 1) % kRing;
+    if (s.used) CA_CUDA(h, cudaEventSynchronize(s.ev));
+    if (bytes > s.cap) {
+        if (s.host) CA_CUDA(h, cudaFreeHost(s.host));
+        if (s.dev) CA_CUDA(h, cudaFree(s.dev));
+        s.host = s.dev = nullptr;
+        const size_t cap = std::max(bytes, (size_t)65536);
+        CA_CUDA(h, cudaMallocHost(&s.host, cap));
+        CA_CUDA(h, cudaMalloc(&s.dev, cap));
+        s.cap = cap;
+    }
+    *out = &s;
+    return CA_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+ca_status ensure_luts(ca_handle *h, const ca_params &p, cudaStream_t stream) {
+    LutKey k;
+    k.t_g = p.t_g; k.t_theta = p.t_theta_deg; k.t_iota = p.t_iota; k.sobel_norm = p.sobel_norm;
+    if (h->luts_ready && k == h->lut_key) return CA_OK;
+    const size_t bytes = sizeof(uint16_t) * (kLutG + kLutT + kLutI);
+    Staging *s;
+    ca_status st = take_staging(h, bytes, &s);
+    if (st != CA_OK) return st;
+    build_luts(p, (uint16_t *)s->host, &h->qg_sat);
+    if (!h->d_luts) CA_CUDA(h, cudaMalloc(&h->d_luts, bytes));
+    CA_CUDA(h, cudaMemcpyAsync(h->d_luts, s->host, bytes, cudaMemcpyHostToDevice, stream));
+    CA_CUDA(h, cudaEventRecord(s->ev, stream));
+    s->used = true;
+    h->lut_key = k;
+    h->luts_ready = true;
+    return CA_OK;
+}
+
+ca_status order_after_last(ca_handle *h, cudaStream_t stream) {
+    if (h->has_last && h->last_stream != stream) CA_CUDA(h, cudaStreamWaitEvent(stream, h->last_ev, 0));
+    return CA_OK;
+}
+
+ca_status mark_last(ca_handle *h, cudaStream_t stream) {
+    CA_CUDA(h, cudaEventRecord(h->last_ev, stream));
+    h->last_stream = stream;
+    h->has_last = true;
+    return CA_OK;
+}
+
+DevParams make_params(const ca_handle *h, const ca_params &p, int max_w) {
+    DevParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.N = p.n_strips;
+    P.K = p.cands_per_strip;
+    P.refine = p.refine_iters;
+    P.T_px = (int)std::ceil((double)p.t_px);
+    P.sup_px = p.sup_px;
+    P.hyp_mode = p.hyp_mode;
+    P.debug = h->debug;
+    P.T_ps = (uint32_t)std::ceil((double)p.t_ps * 32768.0);
+    const double norm = p.score_norm == CA_NORM_2N ? 2.0 * p.n_strips
+                      : p.score_norm == CA_NORM_NK ? (double)p.n_strips * p.cands_per_strip : 1.0;
+    P.T_cs = (uint32_t)std::ceil((double)p.t_cs * 32768.0 * norm);
+    P.score_den = 32768.0 * norm;
+    P.qg_sat = h->qg_sat;
+    long long nh = p.n_hyps;
+    if (p.hyp_mode == CA_HYP_EXHAUSTIVE) {
+        const long long nk = (long long)P.N * P.K;
+        nh = std::max(1LL, nk * (nk - 1) * (nk - 2) / 6);
+    }
+    P.NH = (int)nh;
+    P.n_tiles = (int)((nh + kHypTile - 1) / kHypTile);
+    P.t_ri = p.t_ri;
+    P.r_min = p.r_min;
+    P.r_max = p.r_max;
+    P.d_max = p.d_max;
+    P.seed = p.seed;
+    P.max_w = max_w;
+    return P;
+}
+
+// Shared by ca_estimate and ca_mask: one staging block with the frame table,
+// the strip-row tables and the mask-unit prefix.
+struct CallBlock {
+    DevFrame *d_frames;
+    int32_t *d_rows;
+    int total_units;
+    int max_w;
+};
+
+ca_status upload_frames(ca_handle *h, const ca_frame *frames, int B, int N, float alpha,
+                        cudaStream_t stream, CallBlock *cb) {
+    // distinct heights -> one strip-row table each
+    std::map<int, int> row_off;
+    int n_rows = 0;
+    if (N > 0)
+        for (int i = 0; i < B; ++i)
+            if (!row_off.count(frames[i].H)) { row_off[frames[i].H] = n_rows; n_rows += N; }
+    const size_t off_rows = align_up(sizeof(DevFrame) * B, 256);
+    const size_t bytes = off_rows + sizeof(int32_t) * std::max(n_rows, 1);
+    Staging *s;
+    ca_status st = take_staging(h, bytes, &s);
+    if (st != CA_OK) return st;
+    DevFrame *hf = (DevFrame *)s->host;
+    int32_t *hr = (int32_t *)((char *)s->host + off_rows);
+    for (auto &kv : row_off) strip_rows(kv.first, N, alpha, hr + kv.second);
+    int units = 0, max_w = 0;
+    for (int i = 0; i < B; ++i) {
+        const ca_frame &f = frames[i];
+        DevFrame d;
+        std::memset(&d, 0, sizeof(d));
+        d.rgb = f.rgb_dev;
+        d.mask = f.mask_dev;
+        d.pitch = f.pitch;
+        d.key = f.frame_key;
+        d.H = f.H;
+        d.W = f.W;
+        d.rows_off = N > 0 ? row_off[f.H] : 0;
+        d.unit_off = units;
+        d.vec_ok = ((uintptr_t)f.rgb_dev % 16 == 0) && (f.pitch % 16 == 0) && (f.W % 16 == 0);
+        d.mask_vec_ok = f.mask_dev && ((uintptr_t)f.mask_dev % 16 == 0) && (f.W % 16 == 0);
+        if (f.mask_dev) units += (f.H + kMaskRowsPerWarp - 1) / kMaskRowsPerWarp;
+        max_w = std::max(max_w, f.W);
+        hf[i] = d;
+    }
+    CA_CUDA(h, cudaMemcpyAsync(s->dev, s->host, bytes, cudaMemcpyHostToDevice, stream));
+    CA_CUDA(h, cudaEventRecord(s->ev, stream));
+    s->used = true;
+    cb->d_frames = (DevFrame *)s->dev;
+    cb->d_rows = (int32_t *)((char *)s->dev + off_rows);
+    cb->total_units = units;
+    cb->max_w = max_w;
+    return CA_OK;
+}
+
+int mask_grid(const ca_handle *h, int units) {
+    const int per_block = 256 / 32;
+    return std::max(1, std::min((units + per_block - 1) / per_block, h->sm_count * 8));
+}
+
+cudaEvent_t timing_event(ca_handle *h) {
+    if (!h->ev_free.empty()) {
+        cudaEvent_t e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event before a launch when timing is on; returns it (or NULL).
+cudaEvent_t time_begin(ca_handle *h, cudaStream_t s) {
+    if (!h->timing) return nullptr;
+    cudaEvent_t e = timing_event(h);
+    if (e) cudaEventRecord(e, s);
+    return e;
+}
+
+void time_end(ca_handle *h, int kind, cudaEvent_t begin, cudaStream_t s) {
+    if (!begin) return;
+    cudaEvent_t e = timing_event(h);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    h->timed[kind].emplace_back(begin, e);
+}
+
+ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                        ca_result *out_dev, cudaStream_t stream) {
+    ca_status st = check_params(h, p);
+    if (st != CA_OK) return st;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return CA_OK;
+    if (!frames || !out_dev) return fail(h, CA_ERR_INVALID_ARG, "frames or out_dev is NULL");
+    for (int i = 0; i < B; ++i)
+        if ((st = check_frame(h, frames[i], i)) != CA_OK) return st;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if ((st = order_after_last(h, stream)) != CA_OK) return st;
+    if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
+    CallBlock cb;
+    if ((st = upload_frames(h, frames, B, p->n_strips, p->alpha, stream, &cb)) != CA_OK) return st;
+    const DevParams P = make_params(h, *p, cb.max_w);
+    const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
+    if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
+
+    // strips: enough CTAs to fill the GPU, each CTA loops over strips
+    const size_t smem = strips_smem_bytes(P);
+    if (h->strip_blocks_smem != smem) {
+        int nb = 0;
+        cudaError_t e = strips_occupancy(&nb, smem);
+        if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
+        h->strip_blocks_per_sm = std::max(1, nb);
+        h->strip_blocks_smem = smem;
+    }
+    const int strips = B * P.N;
+    const int sgrid = std::min(strips, h->sm_count * h->strip_blocks_per_sm);
+    cudaEvent_t t0 = time_begin(h, stream);
+    cudaError_t e = launch_strips(cb.d_frames, B, cb.d_rows, P, h->d_luts, h->ws.slots, sgrid, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
+    time_end(h, 0, t0, stream);
+    t0 = time_begin(h, stream);
+    e = launch_fit(cb.d_frames, B, P, h->ws.slots, h->ws, out_dev, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_fit launch");
+    time_end(h, 1, t0, stream);
+    h->launches += 2;
+    if (cb.total_units > 0) {
+        t0 = time_begin(h, stream);
+        e = launch_mask(cb.d_frames, B, out_dev, cb.total_units, mask_grid(h, cb.total_units), stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_mask launch");
+        time_end(h, 2, t0, stream);
+        h->launches += 1;
+    }
+    h->last_B = B;
+    h->last_NK = P.N * P.K;
+    h->last_hyp_stride = P.NH;
+    return mark_last(h, stream);
+}
+
+}  // namespace
+
+// ================================================================ C ABI ==
+extern "C" {
+
+void ca_params_default(ca_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_strips = 16;
+    p->cands_per_strip = 2;
+    p->n_hyps = 1024;
+    p->refine_iters = 3;
+    p->alpha = 8.0f;
+    p->t_g = 20.0f;
+    p->t_theta_deg = 30.0f;
+    p->t_iota = 25.0f;
+    p->t_ps = 0.03f;
+    p->t_cs = 0.06f;
+    p->t_px = 3.0f;
+    p->t_ri = 3.0f;
+    p->r_min = 0.1f;
+    p->r_max = 0.8f;
+    p->d_max = 0.2f;
+    p->sup_px = 8;
+    p->hyp_mode = CA_HYP_RANDOM;
+    p->score_norm = CA_NORM_2N;
+    p->sobel_norm = 1;
+    p->scorer_mode = CA_SCORER_HAND;
+    p->seed = 0;
+}
+
+ca_status ca_create(ca_handle **out, int device) {
+    if (!out) return CA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return CA_ERR_INVALID_ARG;
+    }
+    ca_handle *h = new ca_handle();
+    h->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->last_ev, cudaEventDisableTiming) != cudaSuccess) {
+        delete h;
+        return CA_ERR_CUDA;
+    }
+    for (auto &s : h->ring)
+        if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
+            delete h;
+            return CA_ERR_CUDA;
+        }
+    *out = h;
+    return CA_OK;
+}
+
+ca_status ca_destroy(ca_handle *h) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    if (h->has_last) cudaEventSynchronize(h->last_ev);
+    for (auto &s : h->ring) {
+        if (s.used) cudaEventSynchronize(s.ev);
+        if (s.host) cudaFreeHost(s.host);
+        if (s.dev) cudaFree(s.dev);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    cudaFree(h->d_luts);
+    cudaFree(h->ws.slots);
+    cudaFree(h->ws.tiles);
+    cudaFree(h->ws.best);
+    cudaFree(h->ws.done);
+    cudaFree(h->ws.hyps);
+    cudaFree(h->ws.n_hyps);
+    cudaFree(h->ws.n_cands);
+    cudaFree(h->e2e_frames);
+    cudaFree(h->e2e_masks);
+    cudaFree(h->e2e_res);
+    if (h->e2e_stream) cudaStreamDestroy(h->e2e_stream);
+    if (h->last_ev) cudaEventDestroy(h->last_ev);
+    for (auto e : h->ev_free) cudaEventDestroy(e);
+    for (auto &v : h->timed)
+        for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    delete h;
+    return CA_OK;
+}
+
+ca_status ca_estimate(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                      ca_result *out_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    return estimate_impl(h, frames, B, p, out_dev, (cudaStream_t)stream);
+}
+
+ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, int H, int W,
+                              const uint64_t *keys, const ca_params *p, ca_result *out_dev,
+                              uint8_t *masks_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B > 0 && !frames_dev) return fail(h, CA_ERR_INVALID_ARG, "frames_dev is NULL");
+    if (W < 8 || W > kMaxDim || H < 3 || H > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "size %dx%d outside [8..%d]x[3..%d]", W, H, kMaxDim,
+                    kMaxDim);
+    std::vector<ca_frame> fr((size_t)B);
+    const size_t fbytes = (size_t)H * W * 3, mbytes = (size_t)H * W;
+    for (int i = 0; i < B; ++i) {
+        fr[i].rgb_dev = frames_dev + fbytes * i;
+        fr[i].mask_dev = masks_dev ? masks_dev + mbytes * i : nullptr;
+        fr[i].H = H;
+        fr[i].W = W;
+        fr[i].pitch = (int64_t)W * 3;
+        fr[i].frame_key = keys ? keys[i] : (uint64_t)i;
+    }
+    return estimate_impl(h, fr.data(), B, p, out_dev, (cudaStream_t)stream);
+}
+
+ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *H,
+                  const int32_t *W, uint8_t *const *masks_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return CA_OK;
+    if (!res_dev || !H || !W || !masks_dev)
+        return fail(h, CA_ERR_INVALID_ARG, "NULL argument to ca_mask");
+    std::vector<ca_frame> fr((size_t)B);
+    for (int i = 0; i < B; ++i) {
+        if (!masks_dev[i]) return fail(h, CA_ERR_INVALID_ARG, "mask %d is NULL", i);
+        if (W[i] < 1 || W[i] > kMaxDim || H[i] < 1 || H[i] > kMaxDim)
+            return fail(h, CA_ERR_INVALID_ARG, "mask %d: bad size %dx%d", i, W[i], H[i]);
+        fr[i].rgb_dev = nullptr;
+        fr[i].mask_dev = masks_dev[i];
+        fr[i].H = H[i];
+        fr[i].W = W[i];
+        fr[i].pitch = 0;
+        fr[i].frame_key = 0;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    ca_status st = order_after_last(h, s);
+    if (st != CA_OK) return st;
+    CallBlock cb;
+    if ((st = upload_frames(h, fr.data(), B, 0, 0.0f, s, &cb)) != CA_OK) return st;
+    cudaEvent_t t0 = time_begin(h, s);
+    cudaError_t e = launch_mask(cb.d_frames, B, res_dev, cb.total_units, mask_grid(h, cb.total_units), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_mask launch");
+    time_end(h, 2, t0, s);
+    h->launches += 1;
+    return mark_last(h, s);
+}
+
+ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, int W,
+                      const uint64_t *keys, const ca_params *p, ca_result *res_host,
+                      uint8_t *masks_host) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return CA_OK;
+    if (!frames_host || !res_host) return fail(h, CA_ERR_INVALID_ARG, "NULL host buffer");
+    if (W < 8 || W > kMaxDim || H < 3 || H > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "size %dx%d out of range", W, H);
+    ca_status st = check_params(h, p);
+    if (st != CA_OK) return st;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (!h->e2e_stream) CA_CUDA(h, cudaStreamCreateWithFlags(&h->e2e_stream, cudaStreamNonBlocking));
+    const size_t fb = (size_t)B * H * W * 3, mb = masks_host ? (size_t)B * H * W : 0;
+    if ((st = grow(h, &h->e2e_frames, h->e2e_frames_cap, fb, false)) != CA_OK) return st;
+    h->e2e_frames_cap = std::max(h->e2e_frames_cap, fb);
+    if (mb) {
+        if ((st = grow(h, &h->e2e_masks, h->e2e_masks_cap, mb, false)) != CA_OK) return st;
+        h->e2e_masks_cap = std::max(h->e2e_masks_cap, mb);
+    }
+    if ((st = grow(h, &h->e2e_res, h->e2e_res_cap, (size_t)B, false)) != CA_OK) return st;
+    h->e2e_res_cap = std::max(h->e2e_res_cap, (size_t)B);
+    cudaStream_t s = h->e2e_stream;
+    CA_CUDA(h, cudaMemcpyAsync(h->e2e_frames, frames_host, fb, cudaMemcpyHostToDevice, s));
+    st = ca_estimate_uniform(h, h->e2e_frames, B, H, W, keys, p, h->e2e_res,
+                             mb ? h->e2e_masks : nullptr, s);
+    if (st != CA_OK) return st;
+    CA_CUDA(h, cudaMemcpyAsync(res_host, h->e2e_res, sizeof(ca_result) * B,
+                               cudaMemcpyDeviceToHost, s));
+    if (mb) CA_CUDA(h, cudaMemcpyAsync(masks_host, h->e2e_masks, mb, cudaMemcpyDeviceToHost, s));
+    CA_CUDA(h, cudaStreamSynchronize(s));
+    return CA_OK;
+}
+
+ca_status ca_sync(ca_handle *h, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    CA_CUDA(h, cudaGetLastError());
+    return CA_OK;
+}
+
+ca_status ca_set_debug(ca_handle *h, int level) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (level < 0 || level > 2) return fail(h, CA_ERR_INVALID_ARG, "debug level %d", level);
+    h->debug = level;
+    return CA_OK;
+}
+
+ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p, void *host_buf,
+                        size_t bytes, size_t *written) {
+    if (!host_buf) return CA_ERR_INVALID_ARG;
+    if (written) *written = 0;
+    if (what == CA_DUMP_TABLES) {   // host-only: needs no handle or device
+        if (!p) return fail(h, CA_ERR_INVALID_ARG, "tables need params");
+        const int N = p->n_strips;
+        const size_t need = sizeof(uint16_t) * (kLutG + kLutT + kLutI) + sizeof(int32_t) * N;
+        if (bytes < need) return fail(h, CA_ERR_INVALID_ARG, "buffer too small (%zu)", need);
+        int qs;
+        build_luts(*p, (uint16_t *)host_buf, &qs);
+        if (frame < 3 || frame > kMaxDim) return fail(h, CA_ERR_INVALID_ARG, "bad height");
+        strip_rows(frame, N, p->alpha,
+                   (int32_t *)((char *)host_buf + sizeof(uint16_t) * (kLutG + kLutT + kLutI)));
+        if (written) *written = need;
+        return CA_OK;
+    }
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (frame < 0 || frame >= h->last_B) return fail(h, CA_ERR_INVALID_ARG, "bad frame index");
+    if (h->debug < 1) return fail(h, CA_ERR_STATE, "debug capture is off");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    if (what == CA_DUMP_CANDIDATES) {
+        const size_t need = 8 + sizeof(CandSlot) * h->last_NK;
+        if (bytes < need) return fail(h, CA_ERR_INVALID_ARG, "buffer too small (%zu)", need);
+        int32_t *hdr = (int32_t *)host_buf;
+        CA_CUDA(h, cudaMemcpy(hdr, h->ws.n_cands + frame, 4, cudaMemcpyDeviceToHost));
+        hdr[1] = h->last_NK;
+        CA_CUDA(h, cudaMemcpy(hdr + 2, h->ws.slots + (size_t)frame * kMaxSlots,
+                              sizeof(CandSlot) * h->last_NK, cudaMemcpyDeviceToHost));
+        if (written) *written = need;
+        return CA_OK;
+    }
+    if (what == CA_DUMP_HYPOTHESES) {
+        if (h->debug < 2) return fail(h, CA_ERR_STATE, "hypothesis capture needs debug level 2");
+        int32_t nh = 0;
+        CA_CUDA(h, cudaMemcpy(&nh, h->ws.n_hyps + frame, 4, cudaMemcpyDeviceToHost));
+        const size_t need = 4 + sizeof(HypRec) * (size_t)nh;
+        if (bytes < need) return fail(h, CA_ERR_INVALID_ARG, "buffer too small (%zu)", need);
+        *(int32_t *)host_buf = nh;
+        if (nh > 0)
+            CA_CUDA(h, cudaMemcpy((char *)host_buf + 4,
+                                  h->ws.hyps + (size_t)frame * h->last_hyp_stride,
+                                  sizeof(HypRec) * (size_t)nh, cudaMemcpyDeviceToHost));
+        if (written) *written = need;
+        return CA_OK;
+    }
+    return fail(h, CA_ERR_INVALID_ARG, "unknown dump %d", what);
+}
+
+uint64_t ca_launch_count(const ca_handle *h) { return h ? h->launches : 0; }
+
+ca_status ca_set_timing(ca_handle *h, int on) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    h->timing = on != 0;
+    return CA_OK;
+}
+
+ca_status ca_kernel_times(ca_handle *h, double ms[3], int32_t counts[3]) {
+    if (!h || !ms || !counts) return CA_ERR_INVALID_ARG;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = 0.0;
+        counts[k] = 0;
+        for (auto &pr : h->timed[k]) {
+            CA_CUDA(h, cudaEventSynchronize(pr.second));
+            float t = 0.0f;
+            CA_CUDA(h, cudaEventElapsedTime(&t, pr.first, pr.second));
+            ms[k] += t;
+            counts[k] += 1;
+            h->ev_free.push_back(pr.first);
+            h->ev_free.push_back(pr.second);
+        }
+        h->timed[k].clear();
+    }
+    return CA_OK;
+}
+
+const char *ca_status_string(ca_status s) {
+    switch (s) {
+        case CA_OK: return "ok";
+        case CA_ERR_INVALID_ARG: return "invalid argument";
+        case CA_ERR_CUDA: return "CUDA error";
+        case CA_ERR_OOM: return "out of memory";
+        case CA_ERR_TIMEOUT: return "device wait timed out";
+        case CA_ERR_UNSUPPORTED: return "unsupported";
+        case CA_ERR_ADMISSION: return "admission refused";
+        case CA_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *ca_last_error(const ca_handle *h) { return h ? h->err.c_str() : "no handle"; }
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// ca_internal.h -- structures shared by the host API (ca_api.cu) and the
+// kernels (ca_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ca.h"
+
+namespace ca {
+
+constexpr int kMaxSlots = 256;       // N*K candidate slots per frame
+constexpr int kMaxDim = 4096;        // W, H limit: keeps every moment sum inside int64
+constexpr int kLutG = 5772;          // s_g table: floor(4|g|), |g| <= sqrt(2)*1020
+constexpr int kLutT = 8193;          // s_theta table: floor(4096 (cos + 1))
+constexpr int kLutI = 256;           // s_iota table: 8-bit preceding maximum
+constexpr int kHypTile = 256;        // hypotheses per fit CTA (one per thread)
+constexpr int kMaxHyps = 65536;      // random-mode hypotheses per frame
+constexpr int kStripThreads = 256;   // strip CTA: 128 threads per half-strip
+constexpr int kMaskRowsPerWarp = 32; // mask work unit: 32 rows of one frame
+
+// One frame as the kernels see it (64 bytes).
+struct DevFrame {
+    const uint8_t *rgb;
+    uint8_t *mask;
+    int64_t pitch;
+    uint64_t key;
+    int32_t H, W;
+    int32_t rows_off;   // offset of this frame's strip rows in the rows table
+    int32_t unit_off;   // prefix sum of 32-row mask units before this frame
+    int32_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
+    int32_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
+};
+static_assert(sizeof(DevFrame) == 56, "DevFrame layout");
+
+// Per-call constants, passed by value (kernel parameter space).
+struct DevParams {
+    int32_t N, K, NH, refine;
+    int32_t T_px, sup_px, hyp_mode, debug;
+    uint32_t T_ps, T_cs;
+    int32_t qg_sat;      // first index from which the s_g table stays at 32768
+    int32_t n_tiles;     // fit CTAs per frame
+    float t_ri, r_min, r_max, d_max;
+    double score_den;    // 32768 * normaliser
+    uint64_t seed;
+    int32_t max_w;       // widest frame of the call (shared-memory sizing)
+    int32_t pad;
+};
+
+// A candidate slot (8 bytes): x, y, Q15 score, kept flag.
+struct CandSlot {
+    int16_t x, y;
+    uint16_t s, kept;
+};
+
+// Best circle of one fit CTA.
+struct TileRec {
+    float cx, cy, r;
+    int32_t n_inl;
+    uint32_t S;
+    int32_t pad[3];
+};
+
+// Debug record of one hypothesis (matches CA_DUMP_HYPOTHESES).
+struct HypRec {
+    int32_t i0, i1, i2, n_inl;
+    uint32_t S;
+    int32_t pass;
+    float cx, cy, r;
+};
+
+// Device workspace of one handle.
+struct Workspace {
+    CandSlot *slots = nullptr;       // [B][kMaxSlots]
+    TileRec *tiles = nullptr;        // [B][n_tiles]
+    unsigned long long *best = nullptr; // [B] packed best key, reset after use
+    uint32_t *done = nullptr;        // [B] finished fit CTAs, reset after use
+    HypRec *hyps = nullptr;          // [B][NH] when debug level 2
+    int32_t *n_hyps = nullptr;       // [B]
+    int32_t *n_cands = nullptr;      // [B]
+};
+
+// Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
+cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
+                          const uint16_t *luts, CandSlot *slots, int grid, cudaStream_t s);
+cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const CandSlot *slots,
+                       const Workspace &ws, ca_result *out, cudaStream_t s);
+cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int total_units,
+                        int grid, cudaStream_t s);
+size_t strips_smem_bytes(const DevParams &P);
+cudaError_t strips_occupancy(int *blocks_per_sm, size_t smem);
+
+}  // namespace ca

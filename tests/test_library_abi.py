@@ -1,0 +1,100 @@
+"""The C-ABI library builds, loads and exports every declared symbol; its
+host-side tables equal the oracle's.  No GPU needed (no kernel runs)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2210_14771_gb300.build import LIB, build as build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    build_lib()
+    from paper_2210_14771_gb300 import _native
+    return _native
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ca.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    names = re.findall(r"\b(ca_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_exported(native):
+    declared = _declared_functions()
+    assert len(declared) >= 13
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s+(\S+)", out))
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    # the ctypes signature table covers the same set
+    assert sorted(n for n, _, _ in native.SIGNATURES) == declared
+
+
+def test_struct_layouts(native):
+    assert C.sizeof(native.CaResult) == 24
+    assert C.sizeof(native.CaFrame) == 40
+    assert C.sizeof(native.CaParams) == 96
+
+
+def test_defaults_are_appendix_a(native, orc):
+    from paper_2210_14771_gb300 import api
+    p = api.params()
+    o = orc.params()
+    for k in ("n_strips", "refine_iters", "alpha", "t_g", "t_theta_deg", "t_iota", "t_ps", "t_cs",
+              "t_px", "t_ri", "r_min", "r_max", "d_max", "sup_px", "sobel_norm"):
+        assert getattr(p, k) == getattr(o, k), k
+    assert (p.n_strips, p.t_g, p.t_theta_deg, p.t_iota) == (16, 20.0, 30.0, 25.0)
+    assert (p.t_px, p.t_ri) == (3.0, 3.0)
+    assert abs(p.t_ps - 0.03) < 1e-7 and abs(p.t_cs - 0.06) < 1e-7
+    assert abs(p.r_min - 0.1) < 1e-7 and abs(p.r_max - 0.8) < 1e-7 and abs(p.d_max - 0.2) < 1e-7
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(t_g=12.5, t_theta_deg=45.0, t_iota=40.0),
+                                dict(sobel_norm=8, n_strips=32, alpha=6.0)])
+@pytest.mark.parametrize("H", [480, 1080, 7, 2160])
+def test_library_tables_equal_oracle(native, orc, kw, H):
+    """The library's host-built s_g / s_theta / s_iota tables and Eq. 1 rows
+    (its own code) equal the oracle's, entry for entry."""
+    from paper_2210_14771_gb300 import api
+    p = api.params(**kw)
+    nb = 2 * (native.LUT_G + native.LUT_T + native.LUT_I) + 4 * p.n_strips
+    buf = np.zeros(nb, np.uint8)
+    written = C.c_size_t()
+    rc = native.lib().ca_debug_dump(None, native.CA_DUMP_TABLES, H, C.byref(p),
+                                    buf.ctypes.data_as(C.c_void_p), nb, C.byref(written))
+    assert rc == 0 and written.value == nb
+    n16 = native.LUT_G + native.LUT_T + native.LUT_I
+    u16 = buf[:2 * n16].view(np.uint16)
+    rows = buf[2 * n16:].view(np.int32)
+    okw = {k: v for k, v in kw.items() if k in ("t_g", "t_theta_deg", "t_iota", "sobel_norm")}
+    og, ot, oi = orc.luts(orc.params(**okw))
+    assert (u16[:native.LUT_G] == og).all()
+    assert (u16[native.LUT_G:native.LUT_G + native.LUT_T] == ot).all()
+    assert (u16[native.LUT_G + native.LUT_T:] == oi).all()
+    assert (rows == orc.strip_rows(H, p.n_strips, p.alpha)).all()
+
+
+def test_status_strings(native):
+    L = native.lib()
+    assert L.ca_status_string(0) == b"ok"
+    assert L.ca_status_string(1) == b"invalid argument"
+    assert L.ca_status_string(99) == b"unknown status"
+
+
+def test_create_without_device_fails_cleanly(native):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = C.c_void_p()
+    assert native.lib().ca_create(C.byref(h), 0) != 0
+    assert not h.value
