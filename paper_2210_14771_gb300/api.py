@@ -81,6 +81,8 @@ class ContentArea:
         """
         p = p or params()
         st = _stream_ptr(stream, self.device)
+        if masks is False:
+            masks = None
         if isinstance(frames, torch.Tensor):
             B, H, W, _ = frames.shape
             assert frames.dtype == torch.uint8 and frames.is_cuda and frames.is_contiguous()

