@@ -131,6 +131,41 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
                               const uint64_t *keys, const ca_params *p, ca_result *out_dev,
                               uint8_t *masks_dev, void *stream);
 
+/* Allocation-free estimate, for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a packaging variant of
+ * ca_estimate_uniform (same arguments and results, bit for bit) with no handle.
+ *
+ * Who needs it: applications that reserve their whole device-memory budget up
+ * front and forbid libraries from allocating on their own (a video appliance
+ * that must not fail a cudaMalloc in the middle of a procedure, or a host
+ * framework whose memory pool owns the device), and frame loops that cannot
+ * absorb the stalls of cudaMalloc / cudaFree, which may synchronise the
+ * device.  This call makes no cudaMalloc, cudaFree or other allocating call.
+ *
+ * Instead it uses one fixed scratch array of CA_STATIC_SCRATCH_BYTES of device
+ * memory, defined in the library, which every GPU that loads the library holds
+ * until the process exits.  The caller still passes the inputs and outputs
+ * (frames_dev, out_dev, masks_dev, keys as in ca_estimate_uniform).
+ *   - Limits: B <= CA_STATIC_MAX_FRAMES, and at most CA_STATIC_MAX_HYPS
+ *     hypotheses per frame (n_hyps, or C(N*K,3) in exhaustive mode); larger
+ *     requests return CA_ERR_INVALID_ARG before any work is queued.  The other
+ *     limits are those of ca_estimate_uniform.  No debug capture.
+ *   - The first call on each device looks up the array's device address, with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call uses the same array, which keeps the last call's contents:
+ *     the call clears what must start at zero, but calls whose work overlaps
+ *     on the GPU (other streams, other host threads) race and corrupt each
+ *     other.  Order them on one stream or wait between them.
+ *   - The parameter tables (about 43 KB) are copied from host memory on each
+ *     call with ordinary asynchronous copies; the call returns once queued.
+ *   - Errors: a status only (there is no handle for ca_last_error). */
+#define CA_STATIC_MAX_FRAMES 256
+#define CA_STATIC_MAX_HYPS 4096
+#define CA_STATIC_SCRATCH_BYTES 702464
+ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H, int W, const uint64_t *keys,
+                             const ca_params *p, ca_result *out_dev, uint8_t *masks_dev,
+                             void *stream);
+
 /* Writes the content-area masks of B results (Sec. 1.1, Fig. 1): pixel (x, y)
  * is 1 iff (x-cx)^2 + (y-cy)^2 <= r^2 in binary32 (each operation rounded, no
  * fused multiply-add), or 1 everywhere when valid == 0.  res_dev: device array

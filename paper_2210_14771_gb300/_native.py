@@ -48,6 +48,8 @@ SIGNATURES = [
     ("ca_estimate_uniform", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                       _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    ("ca_estimate_static", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _P(C.c_uint64),
+                                     _P(CaParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,

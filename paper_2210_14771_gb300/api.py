@@ -46,6 +46,25 @@ def new_results(B: int, device) -> torch.Tensor:
     return torch.zeros((B, 6), dtype=torch.float32, device=device)
 
 
+def estimate_static(frames: torch.Tensor, p=None, keys=None, masks=None, results=None,
+                    stream=None):
+    """ca_estimate_static: the estimate of a uniform batch without any device
+    allocation by the library (for callers that cannot allocate; see ca.h).
+    `results` and `masks` must be preallocated by the caller (or None for no
+    masks); frames (B, H, W, 3) uint8 CUDA, B <= 256."""
+    p = p or params()
+    B, H, W, _ = frames.shape
+    assert frames.dtype == torch.uint8 and frames.is_cuda and frames.is_contiguous()
+    assert results is not None and results.shape == (B, 6)
+    karr = (C.c_uint64 * max(B, 1))(*(keys if keys is not None else range(B)))
+    N.check(N.lib().ca_estimate_static(
+        C.c_void_p(frames.data_ptr()), B, H, W, karr, C.byref(p),
+        C.c_void_p(results.data_ptr()),
+        C.c_void_p(masks.data_ptr()) if masks is not None else None,
+        _stream_ptr(stream, frames.device)))
+    return results, masks
+
+
 class ContentArea:
     """One libca handle bound to one CUDA device."""
 

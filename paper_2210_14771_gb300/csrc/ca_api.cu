@@ -104,6 +104,10 @@ ca_status cuda_fail(ca_handle *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
     } while (0)
 
+}  // namespace
+
+namespace ca {
+
 // ------------------------------------------------------------ tables --
 // Eq. 1 strip rows, floored and clamped to [1, H-2].
 void strip_rows(int H, int N, float alpha, int32_t *rows) {
@@ -184,6 +188,10 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
         return fail(h, CA_ERR_INVALID_ARG, "threshold out of range");
     return CA_OK;
 }
+
+}  // namespace ca
+
+namespace {
 
 ca_status check_frame(ca_handle *h, const ca_frame &f, int i) {
     if (!f.rgb_dev) return fail(h, CA_ERR_INVALID_ARG, "frame %d: rgb is NULL", i);

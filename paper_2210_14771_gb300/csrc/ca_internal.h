@@ -89,4 +89,9 @@ cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int
 size_t strips_smem_bytes(const DevParams &P);
 cudaError_t strips_occupancy(int *blocks_per_sm, size_t smem);
 
+// Host helpers (ca_api.cu).
+void strip_rows(int H, int N, float alpha, int32_t *rows);        // Eq. 1 rows
+void build_luts(const ca_params &p, uint16_t *out, int *qg_sat);  // Eq. 2 tables
+ca_status check_params(ca_handle *h, const ca_params *p);         // h may be NULL
+
 }  // namespace ca
