@@ -32,7 +32,8 @@ WORKLOAD = dict(name="1080p_x64_mixed_geometry", B=64, H=1080, W=1920, seed=1, m
 METRIC = "1080p frames/s (batched, whole hot path)"
 PAPER_CONTEXT = {"ms_per_frame": 0.129, "hardware": "NVIDIA GeForce GTX 980 Ti",
                  "source": "Table 1 (handcrafted variant)"}
-L2_FLUSH_BYTES = 512 << 20
+ROTATE_INPUTS = 4   # resident copies of the batch, used in turn (1.6 GB > L2)
+ROTATE_MASKS = 2
 
 
 def parse():
@@ -187,40 +188,48 @@ def run_ours(args):
     p = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
                    n_hyps=WORKLOAD["n_hyps"])
     ca = api.ContentArea(local)
-    d_frames = torch.from_numpy(frames).to(dev)
+    # the batch is resident in ROTATE_INPUTS copies used in turn, so no step
+    # finds its strip rows in L2 (1.6 GB of inputs, no cache flush needed and
+    # no foreign dirty lines to write back inside the timed region)
+    d_frames_all = [torch.from_numpy(frames).to(dev)]
+    for _ in range(ROTATE_INPUTS - 1):
+        d_frames_all.append(d_frames_all[0].clone())
+    d_frames = d_frames_all[0]
     d_res = api.new_results(B, dev)
-    d_masks = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    d_masks_all = [torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+                   for _ in range(ROTATE_MASKS)]
+    d_masks = d_masks_all[0]
     stream = torch.cuda.current_stream(dev)
 
     clocks = Clocks(local)
     clocks.start()
-    for _ in range(max(args.warmup, 3)):
-        ca.estimate(d_frames, p, keys=keys, masks=d_masks, results=d_res)
+    for w in range(max(args.warmup, 3)):
+        ca.estimate(d_frames_all[w % ROTATE_INPUTS], p, keys=keys,
+                    masks=d_masks_all[w % ROTATE_MASKS], results=d_res)
     torch.cuda.synchronize()
 
-    # ---- batched: K steps, L2 flushed between steps (outside the events)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    # ---- batched: K steps back to back on rotating inputs
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ca.kernel_times()
     ca.set_timing(True)
     n0 = ca.launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    ev[0].record(stream)
     for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        ca.estimate(d_frames, p, keys=keys, masks=d_masks, results=d_res)
-        ev[k][1].record(stream)
+        ca.estimate(d_frames_all[k % ROTATE_INPUTS], p, keys=keys,
+                    masks=d_masks_all[k % ROTATE_MASKS], results=d_res)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     launches = ca.launch_count() - n0
     ca.set_timing(False)
     ktimes = ca.kernel_times()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    d_masks = d_masks_all[(args.steps - 1) % ROTATE_MASKS]
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -244,10 +253,11 @@ def run_ours(args):
         reps = max(1, min(args.steps, 5))
         p_res = api.new_results(1, dev)
         for rep in range(reps):
-            flush.fill_(rep & 0xFF)
+            src = d_frames_all[rep % ROTATE_INPUTS]
+            dst = d_masks_all[rep % ROTATE_MASKS]
             for b in range(B):
                 pev[b][0].record(stream)
-                ca.estimate(d_frames[b:b + 1], p, keys=keys[b:b + 1], masks=d_masks[b:b + 1],
+                ca.estimate(src[b:b + 1], p, keys=keys[b:b + 1], masks=dst[b:b + 1],
                             results=p_res)
                 pev[b][1].record(stream)
             torch.cuda.synchronize()
@@ -325,7 +335,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "frames_per_step": B, "H": H, "W": W,
                    "n_strips": WORKLOAD["n_strips"], "cands_per_strip": WORKLOAD["cands_per_strip"],
-                   "n_hyps": WORKLOAD["n_hyps"], "l2": "flushed between steps (512 MiB write)",
+                   "n_hyps": WORKLOAD["n_hyps"],
+                   "l2": "no flush: steps rotate over %d resident copies of the batch "
+                         "(%.2f GB of inputs > 129 MB L2)" % (ROTATE_INPUTS,
+                                                              ROTATE_INPUTS * B * H * W * 3 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,

@@ -82,7 +82,9 @@ typedef struct ca_params {
     int32_t score_norm;      /* CA_NORM_* */
     int32_t sobel_norm;      /* 1: raw 3x3 Sobel; 8: Sobel divided by 8 */
     int32_t scorer_mode;     /* CA_SCORER_* */
-    int32_t reserved;
+    int32_t hyp_threads;     /* threads per RANSAC hypothesis: 0 = chosen per call
+                                from the work size, or 1, 2, 4, 8; results do not
+                                depend on it */
     uint64_t seed;           /* key of the RANSAC random stream */
 } ca_params;
 
@@ -161,7 +163,7 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
  *   - Errors: a status only (there is no handle for ca_last_error). */
 #define CA_STATIC_MAX_FRAMES 256
 #define CA_STATIC_MAX_HYPS 4096
-#define CA_STATIC_SCRATCH_BYTES 702464
+#define CA_STATIC_SCRATCH_BYTES 704512
 ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H, int W, const uint64_t *keys,
                              const ca_params *p, ca_result *out_dev, uint8_t *masks_dev,
                              void *stream);

@@ -82,7 +82,8 @@ static uint16_t q15(double v) { /* v in [0,1] -> round(32768 v) */
 /* s_g = tanh(|g| / t_g) sampled at |g| = q/4 (quarter-level steps of the raw
  * Sobel magnitude, divided by sobel_norm);
  * s_theta = 1 - tanh(theta / t_theta), theta in degrees, sampled at the
- * centre of cos-bin q (bin width 1/4096);
+ * centre of bin q of the signed squared cosine u = cos|cos| (bin width
+ * 1/4096, q = floor(4096 (u + 1)));
  * s_iota = 1 - tanh(iota / t_iota) for every 8-bit iota. */
 void orc_build_luts(const orc_params *p, uint16_t *lut_g, uint16_t *lut_t, uint16_t *lut_i) {
     for (int q = 0; q < ORC_LUT_G; ++q) {
@@ -90,8 +91,9 @@ void orc_build_luts(const orc_params *p, uint16_t *lut_g, uint16_t *lut_t, uint1
         lut_g[q] = q15(tanh(arg));
     }
     for (int q = 0; q < ORC_LUT_T; ++q) {
-        double c = ((double)q + 0.5) / 4096.0 - 1.0;
-        if (c > 1.0) c = 1.0;
+        double u = ((double)q + 0.5) / 4096.0 - 1.0;
+        if (u > 1.0) u = 1.0;
+        double c = u < 0.0 ? -sqrt(-u) : sqrt(u);
         double deg = acos(c) * (180.0 / 3.14159265358979323846);
         lut_t[q] = q15(1.0 - tanh(deg / (double)p->t_theta_deg));
     }
@@ -170,11 +172,12 @@ static void strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int ro
         if (ng != 0 && nc != 0) {
             int64_t qg = isqrt64(16 * ng);
             if (qg > ORC_LUT_G - 1) qg = ORC_LUT_G - 1;
+            /* angle bin: q = floor(4096 (u + 1)), u = dot |dot| / (ng nc) the
+             * signed squared cosine, as an exact integer quotient */
             int64_t dot = (int64_t)gx * cx2 + (int64_t)gy * cy2;
-            float den = sqrtf((float)ng * (float)nc);
-            float cosf_ = (float)dot / den;
-            int qt = (int)((cosf_ + 1.0f) * 4096.0f);
-            if (qt < 0) qt = 0;
+            int64_t P = ng * nc;
+            int64_t d2 = dot * (dot < 0 ? -dot : dot);
+            int64_t qt = (4096 * (d2 + P)) / P;
             if (qt > ORC_LUT_T - 1) qt = ORC_LUT_T - 1;
             uint32_t gt = ((uint32_t)lut_g[qg] * lut_t[qt] + 16384u) >> 15;
             s = (gt * lut_i[iota[x]] + 16384u) >> 15;

@@ -23,7 +23,7 @@ class CaParams(C.Structure):
         ("t_cs", C.c_float), ("t_px", C.c_float), ("t_ri", C.c_float), ("r_min", C.c_float),
         ("r_max", C.c_float), ("d_max", C.c_float), ("sup_px", C.c_int32),
         ("hyp_mode", C.c_int32), ("score_norm", C.c_int32), ("sobel_norm", C.c_int32),
-        ("scorer_mode", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+        ("scorer_mode", C.c_int32), ("hyp_threads", C.c_int32), ("seed", C.c_uint64),
     ]
 
 

@@ -47,6 +47,7 @@ struct ca_handle {
     uint16_t *d_luts = nullptr;
     LutKey lut_key;
     int qg_sat = kLutG - 1;
+    uint16_t li_host[kLutI] = {};   // host copy of the s_iota table
     bool luts_ready = false;
 
     Staging ring[kRing];
@@ -129,14 +130,16 @@ uint16_t to_q15(double v) {
 }
 
 // Soft-threshold tables of Eq. 2: s_g at quarter steps of |g|, s_theta at the
-// centres of 8192 cos bins, s_iota at every 8-bit intensity.
+// centres of 8192 bins of the signed squared cosine cos|cos|, s_iota at every
+// 8-bit intensity.
 void build_luts(const ca_params &p, uint16_t *out, int *qg_sat) {
     uint16_t *lg = out, *lt = out + kLutG, *li = out + kLutG + kLutT;
     for (int q = 0; q < kLutG; ++q)
         lg[q] = to_q15(std::tanh(((double)q * 0.25) / ((double)p.sobel_norm * (double)p.t_g)));
     for (int q = 0; q < kLutT; ++q) {
-        double c = ((double)q + 0.5) / 4096.0 - 1.0;
-        if (c > 1.0) c = 1.0;
+        double u = ((double)q + 0.5) / 4096.0 - 1.0;
+        if (u > 1.0) u = 1.0;
+        const double c = u < 0.0 ? -std::sqrt(-u) : std::sqrt(u);
         const double deg = std::acos(c) * (180.0 / 3.14159265358979323846);
         lt[q] = to_q15(1.0 - std::tanh(deg / (double)p.t_theta_deg));
     }
@@ -145,6 +148,36 @@ void build_luts(const ca_params &p, uint16_t *out, int *qg_sat) {
     int s = kLutG - 1;
     while (s > 0 && lg[s - 1] == lg[kLutG - 1]) --s;
     *qg_sat = s;
+}
+
+static int64_t isqrt_floor(int64_t n) {
+    int64_t r = (int64_t)std::sqrt((double)n);
+    while (r > 0 && r * r > n) --r;
+    while ((r + 1) * (r + 1) <= n) ++r;
+    return r;
+}
+
+void pack_device_tables(const uint16_t *luts, int qg_sat, uint16_t *out) {
+    std::memset(out, 0, sizeof(uint16_t) * kDevTableU16);
+    const uint16_t *lg = luts, *lt = luts + kLutG, *li = luts + kLutG + kLutT;
+    std::memcpy(out + kDevOffT, lt, sizeof(uint16_t) * kLutT);
+    std::memcpy(out + kDevOffI, li, sizeof(uint16_t) * kLutI);
+    // s_g at the top of each bin of 16 values of ng: an upper bound of s_g for
+    // every ng of the bin (the table is non-decreasing)
+    for (int j = 0; j < kBoundBins; ++j) {
+        const int64_t q = std::min<int64_t>(isqrt_floor(16 * (16 * (int64_t)j + 15)), qg_sat);
+        out[kDevOffB + j] = lg[q];
+    }
+    std::memcpy(out + kDevOffG, lg, sizeof(uint16_t) * kLutG);
+}
+
+// Smallest preceding maximum whose s_iota is below T_ps (256 if none): the
+// score bound s_g s_iota of such pixels, and of every later pixel of the scan,
+// stays below T_ps.
+int iota_cut(const uint16_t *li, uint32_t T_ps) {
+    for (int v = 0; v < kLutI; ++v)
+        if (li[v] < T_ps) return v;
+    return kLutI;
 }
 
 // ------------------------------------------------------ validation --
@@ -175,6 +208,9 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
         return fail(h, CA_ERR_INVALID_ARG, "sobel_norm must be 1 or 8");
     if (p->score_norm < CA_NORM_2N || p->score_norm > CA_NORM_RAW)
         return fail(h, CA_ERR_INVALID_ARG, "bad score_norm %d", p->score_norm);
+    if (p->hyp_threads != 0 && p->hyp_threads != 1 && p->hyp_threads != 2 &&
+        p->hyp_threads != 4 && p->hyp_threads != 8)
+        return fail(h, CA_ERR_INVALID_ARG, "hyp_threads %d not in {0, 1, 2, 4, 8}", p->hyp_threads);
     if (p->scorer_mode != CA_SCORER_HAND)
         return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs learned weights", p->scorer_mode);
     const float fs[] = {p->alpha, p->t_g, p->t_theta_deg, p->t_iota, p->t_ps, p->t_cs,
@@ -264,11 +300,14 @@ ca_status ensure_luts(ca_handle *h, const ca_params &p, cudaStream_t stream) {
     LutKey k;
     k.t_g = p.t_g; k.t_theta = p.t_theta_deg; k.t_iota = p.t_iota; k.sobel_norm = p.sobel_norm;
     if (h->luts_ready && k == h->lut_key) return CA_OK;
-    const size_t bytes = sizeof(uint16_t) * (kLutG + kLutT + kLutI);
+    const size_t bytes = sizeof(uint16_t) * kDevTableU16;
     Staging *s;
     ca_status st = take_staging(h, bytes, &s);
     if (st != CA_OK) return st;
-    build_luts(p, (uint16_t *)s->host, &h->qg_sat);
+    std::vector<uint16_t> host((size_t)kLutG + kLutT + kLutI);
+    build_luts(p, host.data(), &h->qg_sat);
+    std::memcpy(h->li_host, host.data() + kLutG + kLutT, sizeof(h->li_host));
+    pack_device_tables(host.data(), h->qg_sat, (uint16_t *)s->host);
     if (!h->d_luts) CA_CUDA(h, cudaMalloc(&h->d_luts, bytes));
     CA_CUDA(h, cudaMemcpyAsync(h->d_luts, s->host, bytes, cudaMemcpyHostToDevice, stream));
     CA_CUDA(h, cudaEventRecord(s->ev, stream));
@@ -290,7 +329,7 @@ ca_status mark_last(ca_handle *h, cudaStream_t stream) {
     return CA_OK;
 }
 
-DevParams make_params(const ca_handle *h, const ca_params &p, int max_w) {
+DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int B) {
     DevParams P;
     std::memset(&P, 0, sizeof(P));
     P.N = p.n_strips;
@@ -306,13 +345,16 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w) {
     P.T_cs = (uint32_t)std::ceil((double)p.t_cs * 32768.0 * norm);
     P.score_den = 32768.0 * norm;
     P.qg_sat = h->qg_sat;
+    P.io_cut = iota_cut(h->li_host, P.T_ps);
     long long nh = p.n_hyps;
     if (p.hyp_mode == CA_HYP_EXHAUSTIVE) {
         const long long nk = (long long)P.N * P.K;
         nh = std::max(1LL, nk * (nk - 1) * (nk - 2) / 6);
     }
     P.NH = (int)nh;
-    P.n_tiles = (int)((nh + kHypTile - 1) / kHypTile);
+    P.hyp_threads = choose_hyp_threads(p.hyp_threads, B, nh, h->sm_count);
+    const long long per_tile = kHypTile / P.hyp_threads;
+    P.n_tiles = (int)((nh + per_tile - 1) / per_tile);
     P.t_ri = p.t_ri;
     P.r_min = p.r_min;
     P.r_max = p.r_max;
@@ -362,7 +404,7 @@ ca_status upload_frames(ca_handle *h, const ca_frame *frames, int B, int N, floa
         d.unit_off = units;
         d.vec_ok = ((uintptr_t)f.rgb_dev % 16 == 0) && (f.pitch % 16 == 0) && (f.W % 16 == 0);
         d.mask_vec_ok = f.mask_dev && ((uintptr_t)f.mask_dev % 16 == 0) && (f.W % 16 == 0);
-        if (f.mask_dev) units += (f.H + kMaskRowsPerWarp - 1) / kMaskRowsPerWarp;
+        if (f.mask_dev) units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
         max_w = std::max(max_w, f.W);
         hf[i] = d;
     }
@@ -378,7 +420,8 @@ ca_status upload_frames(ca_handle *h, const ca_frame *frames, int B, int N, floa
 
 int mask_grid(const ca_handle *h, int units) {
     const int per_block = 256 / 32;
-    return std::max(1, std::min((units + per_block - 1) / per_block, h->sm_count * 8));
+    return std::max(1, std::min((units + per_block - 1) / per_block,
+                                h->sm_count * mask_blocks_per_sm()));
 }
 
 cudaEvent_t timing_event(ca_handle *h) {
@@ -422,7 +465,7 @@ ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_pa
     if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
     CallBlock cb;
     if ((st = upload_frames(h, frames, B, p->n_strips, p->alpha, stream, &cb)) != CA_OK) return st;
-    const DevParams P = make_params(h, *p, cb.max_w);
+    const DevParams P = make_params(h, *p, cb.max_w, B);
     const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
     if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
 
@@ -435,8 +478,9 @@ ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_pa
         h->strip_blocks_per_sm = std::max(1, nb);
         h->strip_blocks_smem = smem;
     }
-    const int strips = B * P.N;
-    const int sgrid = std::min(strips, h->sm_count * h->strip_blocks_per_sm);
+    // one half-strip per quad of warps (K = 2) or per warp (K > 2); CTAs beyond
+    // the resident ones wait for a free slot, which balances uneven half-strips
+    const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
     cudaEvent_t t0 = time_begin(h, stream);
     cudaError_t e = launch_strips(cb.d_frames, B, cb.d_rows, P, h->d_luts, h->ws.slots, sgrid, stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
@@ -487,6 +531,7 @@ void ca_params_default(ca_params *p) {
     p->score_norm = CA_NORM_2N;
     p->sobel_norm = 1;
     p->scorer_mode = CA_SCORER_HAND;
+    p->hyp_threads = 0;
     p->seed = 0;
 }
 

@@ -13,10 +13,18 @@ constexpr int kMaxDim = 4096;        // W, H limit: keeps every moment sum insid
 constexpr int kLutG = 5772;          // s_g table: floor(4|g|), |g| <= sqrt(2)*1020
 constexpr int kLutT = 8193;          // s_theta table: floor(4096 (cos + 1))
 constexpr int kLutI = 256;           // s_iota table: 8-bit preceding maximum
+constexpr int kBoundBins = 1024;     // s_g upper bounds over bins of 16 values of |g|^2
+// Device copy of the tables, 16-byte aligned pieces (uint16 offsets):
+// [s_theta (8200)][s_iota (256)][s_g bin bounds (1024)][s_g (5776)].
+constexpr int kDevOffT = 0;
+constexpr int kDevOffI = 8200;
+constexpr int kDevOffB = kDevOffI + kLutI;
+constexpr int kDevOffG = kDevOffB + kBoundBins;
+constexpr int kDevTableU16 = kDevOffG + 5776;
 constexpr int kHypTile = 256;        // hypotheses per fit CTA (one per thread)
 constexpr int kMaxHyps = 65536;      // random-mode hypotheses per frame
 constexpr int kStripThreads = 256;   // strip CTA: 128 threads per half-strip
-constexpr int kMaskRowsPerWarp = 32; // mask work unit: 32 rows of one frame
+constexpr int kMaskRowsPerUnit = 8;  // mask work unit: 8 rows of one frame (one warp)
 
 // One frame as the kernels see it (64 bytes).
 struct DevFrame {
@@ -26,7 +34,7 @@ struct DevFrame {
     uint64_t key;
     int32_t H, W;
     int32_t rows_off;   // offset of this frame's strip rows in the rows table
-    int32_t unit_off;   // prefix sum of 32-row mask units before this frame
+    int32_t unit_off;   // prefix sum of mask units before this frame
     int32_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
     int32_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
 };
@@ -38,11 +46,13 @@ struct DevParams {
     int32_t T_px, sup_px, hyp_mode, debug;
     uint32_t T_ps, T_cs;
     int32_t qg_sat;      // first index from which the s_g table stays at 32768
-    int32_t n_tiles;     // fit CTAs per frame
+    int32_t n_tiles;     // fit CTAs per frame (each 256 / hyp_threads hypotheses)
     float t_ri, r_min, r_max, d_max;
     double score_den;    // 32768 * normaliser
     uint64_t seed;
     int32_t max_w;       // widest frame of the call (shared-memory sizing)
+    int32_t hyp_threads; // threads per hypothesis in k_fit: 1, 2, 4 or 8
+    int32_t io_cut;      // preceding maxima >= io_cut have s_iota < T_ps: never kept
     int32_t pad;
 };
 
@@ -86,6 +96,10 @@ cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const 
                        const Workspace &ws, ca_result *out, cudaStream_t s);
 cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int total_units,
                         int grid, cudaStream_t s);
+int mask_blocks_per_sm();   // resident k_mask CTAs per SM (occupancy), cached
+int fit_threads_per_sm(int hyp_threads);   // resident k_fit threads per SM, cached
+// Threads per hypothesis for B frames of NH hypotheses on `sms` SMs.
+int choose_hyp_threads(int requested, long long B, long long NH, int sms);
 size_t strips_smem_bytes(const DevParams &P);
 cudaError_t strips_occupancy(int *blocks_per_sm, size_t smem);
 
@@ -93,5 +107,8 @@ cudaError_t strips_occupancy(int *blocks_per_sm, size_t smem);
 void strip_rows(int H, int N, float alpha, int32_t *rows);        // Eq. 1 rows
 void build_luts(const ca_params &p, uint16_t *out, int *qg_sat);  // Eq. 2 tables
 ca_status check_params(ca_handle *h, const ca_params *p);         // h may be NULL
+int iota_cut(const uint16_t *li, uint32_t T_ps);                  // see ca_api.cu
+// Device table block (kDevTableU16 entries) from build_luts' [s_g][s_theta][s_iota].
+void pack_device_tables(const uint16_t *luts, int qg_sat, uint16_t *out);
 
 }  // namespace ca

@@ -8,7 +8,8 @@
 //
 // Bit-exactness: every decision is taken either in exact integer arithmetic or
 // in binary32/binary64 with explicitly rounded intrinsics (no contraction into
-// fused multiply-adds), so the results are fully determined by the inputs.
+// fused multiply-adds), so the results are fully determined by the inputs and
+// do not depend on launch shapes.
 #include <cstdint>
 
 #include "ca_internal.h"
@@ -21,7 +22,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
     return v;
@@ -38,19 +39,20 @@ __device__ __forceinline__ uint32_t luma(uint32_t r, uint32_t g, uint32_t b) {
     return (77u * r + 150u * g + 29u * b + 128u) >> 8;
 }
 
-// 16 pixels (48 bytes of packed RGB) -> 16 luma bytes.
+// 16 pixels (48 bytes of packed RGB) -> 16 luma bytes, with byte dot products:
+// pixel 4m+t occupies bytes 12m+3t .. 12m+3t+2, so each pixel is one or two
+// dp4a of its words against the weights (77, 150, 29) placed at its bytes.
+__device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2) {
+    const uint32_t y0 = __dp4a(w0, 77u | (150u << 8) | (29u << 16), 128u) >> 8;
+    const uint32_t y1 = __dp4a(w0, 77u << 24, __dp4a(w1, 150u | (29u << 8), 128u)) >> 8;
+    const uint32_t y2 = __dp4a(w1, (77u << 16) | (150u << 24), __dp4a(w2, 29u, 128u)) >> 8;
+    const uint32_t y3 = __dp4a(w2, (77u << 8) | (150u << 16) | (29u << 24), 128u) >> 8;
+    return __byte_perm(__byte_perm(y0, y1, 0x3340), __byte_perm(y2, y3, 0x3340), 0x5410);
+}
+
 __device__ __forceinline__ uint4 luma16(uint4 a, uint4 b, uint4 c) {
-    const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-    uint32_t o[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int i0 = 3 * j, i1 = 3 * j + 1, i2 = 3 * j + 2;
-        const uint32_t r = (w[i0 >> 2] >> ((i0 & 3) * 8)) & 0xffu;
-        const uint32_t g = (w[i1 >> 2] >> ((i1 & 3) * 8)) & 0xffu;
-        const uint32_t bl = (w[i2 >> 2] >> ((i2 & 3) * 8)) & 0xffu;
-        o[j >> 2] |= luma(r, g, bl) << ((j & 3) * 8);
-    }
-    return make_uint4(o[0], o[1], o[2], o[3]);
+    return make_uint4(luma4(a.x, a.y, a.z), luma4(a.w, b.x, b.y), luma4(b.z, b.w, c.x),
+                      luma4(c.y, c.z, c.w));
 }
 
 // floor(sqrt(16 ng)) clamped to qsat (exact; the float estimate only seeds it).
@@ -68,186 +70,346 @@ __device__ __forceinline__ int qmag(int ng, int qsat) {
 }  // namespace
 
 // ============================================================== k_strips ==
-// One CTA per strip (grid-stride), 256 threads: threads 0-127 take the left
-// half-strip, 128-255 the right one; each thread owns a contiguous chunk of
-// its half in scan order (outer edge inwards).
-struct StripSmem {
-    uint16_t *lt, *lg, *li;
-    uint8_t *Y;   // 3 rows of luma, row stride Wp
-    uint32_t *keys;
-    int Wp;
-};
+// One warp per half-strip: work items (frame, strip, half) are spread over all
+// warps of the grid, and a warp never waits for another one.  The 8 warps of a
+// CTA share the score tables in shared memory.  A warp keeps its half-strip
+// plus one column of the other half as one 32-bit word per column: luma of
+// rows h-1, h, h+1 in bytes 0, 1, 2.
+constexpr int kStripWarps = kStripThreads / 32;
 
-__device__ __forceinline__ StripSmem strip_smem(unsigned char *base, const DevParams &P) {
-    StripSmem s;
-    s.lt = reinterpret_cast<uint16_t *>(base);
-    s.lg = s.lt + ((kLutT + 7) & ~7);
-    s.li = s.lg + ((kLutG + 7) & ~7);
-    s.Y = reinterpret_cast<uint8_t *>(s.li + kLutI);
-    s.Wp = (P.max_w + 15) & ~15;
-    s.keys = reinterpret_cast<uint32_t *>(s.Y + 3 * s.Wp);
-    return s;
+__host__ __device__ __forceinline__ int strip_lg_len(const DevParams &P) {
+    return (P.qg_sat + 1 + 7) & ~7;
+}
+
+// Columns one warp may hold: half of the widest frame, the halo column and
+// 16-pixel alignment at both ends.
+__host__ __device__ __forceinline__ int strip_cols(const DevParams &P) {
+    return ((P.max_w / 2 + 1 + 15) & ~15) + 32;
+}
+
+// Shared memory: part of the device table block -- s_iota, the s_g bounds of
+// bins of 16 values of ng = |g|^2 (bin j holds ng in [16 j, 16 j + 15]; ng
+// beyond the last bin is bounded by 32768) and s_g up to its saturation --
+// then the column words of each warp and, for K > 2 only, the score of each
+// pixel and the picks of each warp.  s_theta, needed only by the few pixels
+// that get an exact score, is read through L1.
+__host__ __device__ __forceinline__ size_t strip_tables_bytes(const DevParams &P) {
+    return 2 * (size_t)(kDevOffG - kDevOffI + strip_lg_len(P));
 }
 
 size_t strips_smem_bytes(const DevParams &P) {
-    const size_t Wp = (size_t)((P.max_w + 15) & ~15);
-    size_t b = 2 * (size_t)(((kLutT + 7) & ~7) + ((kLutG + 7) & ~7) + kLutI) + 3 * Wp;
-    if (P.K > 2) b += 4 * Wp;
+    size_t b = strip_tables_bytes(P) + (size_t)kStripWarps * strip_cols(P) * 4;
+    if (P.K > 2) b += (size_t)kStripWarps * (strip_cols(P) * 2 + 4 * (kMaxSlots / 2));
     return b;
 }
 
-// Q15 edge score of pixel x of the strip (Eq. 2-3 through the tables).  Scores
-// that cannot reach T_ps (bounded by the s_g s_iota product) are returned as 0:
-// such pixels are never kept, so the kept candidates are unchanged.
-__device__ __forceinline__ uint32_t pixel_score(const StripSmem &sm, int x, int W, int cy2,
-                                                int iota, const DevParams &P) {
-    if (x <= 0 || x >= W - 1) return 0u;
-    const uint8_t *Yu = sm.Y, *Ym = sm.Y + sm.Wp, *Yd = sm.Y + 2 * sm.Wp;
-    const int gx = ((int)Yu[x + 1] + 2 * (int)Ym[x + 1] + (int)Yd[x + 1]) -
-                   ((int)Yu[x - 1] + 2 * (int)Ym[x - 1] + (int)Yd[x - 1]);
-    const int gy = ((int)Yd[x - 1] + 2 * (int)Yd[x] + (int)Yd[x + 1]) -
-                   ((int)Yu[x - 1] + 2 * (int)Yu[x] + (int)Yu[x + 1]);
+namespace {
+
+// Barrier over the 128 threads of quad `quad` (0 or 1) of a 256-thread CTA;
+// the ids are immediates so that only barriers 1 and 2 are reserved.
+__device__ __forceinline__ void quad_barrier(int quad) {
+    if (quad == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+    else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// Luma of rows h-1, h, h+1 for 4 pixels (bytes of a, b, c) -> 4 column words.
+__device__ __forceinline__ uint4 interleave4(uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t t01 = __byte_perm(a, b, 0x5140), t23 = __byte_perm(a, b, 0x7362);
+    return make_uint4(__byte_perm(t01, c, 0x0410), __byte_perm(t01, c, 0x0532),
+                      __byte_perm(t23, c, 0x0610), __byte_perm(t23, c, 0x0732));
+}
+
+// Angle bin floor(4096 (u + 1)), u = dot |dot| / (ng nc) the signed squared
+// cosine between g and c, as an exact integer quotient: a float estimate is
+// corrected by one exact comparison (the estimate is within one bin).
+__device__ __forceinline__ int qtheta(int dot, int ng, int nc) {
+    const long long P = (long long)ng * nc;
+    const long long d2 = (long long)dot * (dot < 0 ? -dot : dot);
+    const long long num = (d2 + P) << 12;
+    const float uf = __fdividef(__ll2float_rn(d2), __ll2float_rn(P));
+    int q = __float2int_rz(__fmul_rn(__fadd_rn(uf, 1.0f), 4096.0f));
+    q = min(max(q, 0), kLutT - 1);
+    const long long t = (long long)q * P;
+    if (t > num) --q;
+    else if (t + P <= num) ++q;
+    return min(max(q, 0), kLutT - 1);
+}
+
+struct StripCtx {
+    int W, cy2;
+    const uint16_t *lt, *lg, *li;
+};
+
+// Q15 score of Eq. 2-3 through the tables from a pixel's gradient.  Scores
+// that cannot reach T_ps (bounded by the s_g s_iota product) count as 0: such
+// pixels are never kept, and every kept pick is unchanged by it.
+__device__ __forceinline__ uint32_t score_from_g(const StripCtx &c, int gx, int gy, int x,
+                                                 int iota, const DevParams &P) {
     const int ng = gx * gx + gy * gy;
-    const int cx2 = W - 1 - 2 * x;
-    const int nc = cx2 * cx2 + cy2 * cy2;
+    const int cx2 = c.W - 1 - 2 * x;
+    const int nc = cx2 * cx2 + c.cy2 * c.cy2;
     if (ng == 0 || nc == 0) return 0u;
-    const uint32_t g = sm.lg[qmag(ng, P.qg_sat)];
-    const uint32_t ii = sm.li[iota];
+    const uint32_t g = c.lg[qmag(ng, P.qg_sat)];
+    const uint32_t ii = c.li[iota];
     if (((g * ii + 16384u) >> 15) < P.T_ps) return 0u;
-    const int dot = gx * cx2 + gy * cy2;
-    const float den = __fsqrt_rn(__fmul_rn(__int2float_rn(ng), __int2float_rn(nc)));
-    const float cs = __fdiv_rn(__int2float_rn(dot), den);
-    int qt = __float2int_rz(__fmul_rn(__fadd_rn(cs, 1.0f), 4096.0f));
-    qt = min(max(qt, 0), kLutT - 1);
-    const uint32_t gt = (g * (uint32_t)sm.lt[qt] + 16384u) >> 15;
+    const uint32_t gt =
+        (g * (uint32_t)__ldg(c.lt + qtheta(gx * cx2 + gy * c.cy2, ng, nc)) + 16384u) >> 15;
     return (gt * ii + 16384u) >> 15;
 }
+
+}  // namespace
 
 __global__ void __launch_bounds__(kStripThreads)
     k_strips(const DevFrame *__restrict__ frames, int B, const int32_t *__restrict__ rows,
              DevParams P, const uint16_t *__restrict__ luts, CandSlot *__restrict__ slots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const StripSmem sm = strip_smem(smem_raw, P);
-    __shared__ uint32_t s_red[8];
-    __shared__ int s_wmax[8];
-    __shared__ int s_pick[2][kMaxSlots / 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cols = strip_cols(P);
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);   // table block from s_iota on
+    const uint16_t *lt = luts + kDevOffT;                      // global, through L1
+    const uint16_t *li = tab, *lgb = tab + (kDevOffB - kDevOffI), *lg = tab + (kDevOffG - kDevOffI);
+    unsigned char *wmem = smem_raw + strip_tables_bytes(P);
+    uint32_t *yy = reinterpret_cast<uint32_t *>(wmem) + warp * cols;
+    uint16_t *sc = reinterpret_cast<uint16_t *>(wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
+    int *s_pick = reinterpret_cast<int *>(wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
+    {
+        // copy the table block from s_iota on: every 16-byte load of a thread
+        // is issued before its stores (one L2 round trip per CTA)
+        constexpr int kPer = ((kDevTableU16 - kDevOffI) / 8 + kStripThreads - 1) / kStripThreads;
+        const int n16 = (int)(strip_tables_bytes(P) / 16);
+        const uint4 *src = reinterpret_cast<const uint4 *>(luts + kDevOffI);
+        uint4 *dst = reinterpret_cast<uint4 *>(tab);
+        uint4 v[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kStripThreads;
+            if (i < n16) v[k] = __ldg(src + i);
+        }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kStripThreads;
+            if (i < n16) dst[i] = v[k];
+        }
+    }
+    __syncthreads();
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // tables: luts = [s_g (kLutG)][s_theta (kLutT)][s_iota (kLutI)]
-    for (int i = tid; i <= P.qg_sat; i += blockDim.x) sm.lg[i] = luts[i];
-    for (int i = tid; i < kLutT; i += blockDim.x) sm.lt[i] = luts[kLutG + i];
-    for (int i = tid; i < kLutI; i += blockDim.x) sm.li[i] = luts[kLutG + kLutT + i];
-
-    const int half = tid >> 7;          // 0 left, 1 right
-    const int ht = tid & 127;           // thread index within the half
-    const int kk = P.K >> 1;            // picks per half-strip
-    const int total = B * P.N;
-
-    for (int s = blockIdx.x; s < total; s += gridDim.x) {
-        const int f = s / P.N, i = s - f * P.N;
+    const int kk = P.K >> 1;   // picks per half-strip
+    const int items = B * P.N * 2;
+    // K = 2: a quad of 4 warps takes a half-strip, each warp a quarter of its
+    // scan; K > 2: one warp takes a half-strip.  Items are interleaved across
+    // frames (consecutive items belong to consecutive frames), so every CTA and
+    // SM gets a mix of cheap and expensive half-strips.
+    __shared__ int s_qmax[kStripWarps];
+    __shared__ uint32_t s_qbest[kStripWarps];
+    const bool quads = kk == 1;
+    const int quad = warp >> 2, qw = warp & 3;
+    const int per_cta = quads ? kStripWarps / 4 : kStripWarps;
+    const int gid = quads ? quad : warp;
+    const int nseg = quads ? 4 : 1, seg_id = quads ? qw : 0;
+    for (int it = blockIdx.x * per_cta + gid; it < items; it += gridDim.x * per_cta) {
+        const int j = it / B;
+        const int f = it - j * B;
+        const int i = j >> 1, half = j & 1;
         const DevFrame fr = frames[f];
         const int W = fr.W, H = fr.H;
         const int y = rows[fr.rows_off + i];
-        __syncthreads();   // previous strip finished with Y / keys / picks; tables loaded
+        const int hw = W >> 1;
+        const int c_lo = half ? hw - 1 : 0, c_hi = half ? W : hw + 1;   // columns of the half
+        const int len = half ? (W - hw) : hw;
+        // this warp's scan positions [q0, q1) (whole rounds of 32) and the
+        // columns they need (one neighbour on each side)
+        const int seg = nseg == 1 ? len : ((len + 32 * nseg - 1) / (32 * nseg)) * 32;
+        const int q0 = min(seg_id * seg, len), q1 = min(q0 + seg, len);
+        int col_lo = c_lo, col_hi = c_lo;
+        if (q0 < q1) {
+            const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
+            col_lo = max(xa - 1, c_lo);
+            col_hi = min(xb + 2, c_hi);
+        }
+        int base;
+        __syncwarp();   // the previous item is done with yy / sc
 
-        // ---- rows y-1, y, y+1 -> luma (16-byte loads when aligned)
+        // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned)
         if (fr.vec_ok) {
-            const int G = W >> 4;
-            for (int g = tid; g < 3 * G; g += blockDim.x) {
-                const int k = g / G, grp = g - k * G;
-                const uint8_t *src = fr.rgb + (int64_t)(y - 1 + k) * fr.pitch + grp * 48;
-                const uint4 a = ld_nc_v4(src), b = ld_nc_v4(src + 16), c = ld_nc_v4(src + 32);
-                *reinterpret_cast<uint4 *>(sm.Y + k * sm.Wp + grp * 16) = luma16(a, b, c);
+            const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
+            base = g0 << 4;
+            const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
+            for (int g = g0 + lane; g < g1; g += 32) {
+                const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+                const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
+                const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
+                const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
+                const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
+                uint4 *dst = reinterpret_cast<uint4 *>(yy + (g - g0) * 16);
+                dst[0] = interleave4(L0.x, L1.x, L2.x);
+                dst[1] = interleave4(L0.y, L1.y, L2.y);
+                dst[2] = interleave4(L0.z, L1.z, L2.z);
+                dst[3] = interleave4(L0.w, L1.w, L2.w);
             }
         } else {
-            for (int idx = tid; idx < 3 * W; idx += blockDim.x) {
-                const int k = idx / W, x = idx - k * W;
-                const uint8_t *src = fr.rgb + (int64_t)(y - 1 + k) * fr.pitch + 3 * x;
-                sm.Y[k * sm.Wp + x] = (uint8_t)luma(src[0], src[1], src[2]);
+            base = col_lo;
+            for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
+                const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
+                const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+                yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
+                                (luma(p2[0], p2[1], p2[2]) << 16);
             }
         }
-        __syncthreads();
+        __syncwarp();
 
-        // ---- preceding maximum of the middle row, scanned from the outer edge
-        const uint8_t *Ym = sm.Y + sm.Wp;
-        const int hw = W >> 1;
-        const int len = half ? (W - hw) : hw;
-        const int c = (len + 127) >> 7;
-        const int p0 = min(ht * c, len), p1 = min(p0 + c, len);
-        int lm = 0;
-        for (int p = p0; p < p1; ++p) lm = max(lm, (int)Ym[half ? (W - 1 - p) : p]);
-        int inc = lm;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc = max(inc, t);
-        }
-        int excl = __shfl_up_sync(kFull, inc, 1);
-        if (lane == 0) excl = 0;
-        if (lane == 31) s_wmax[warp] = inc;
-        __syncthreads();
-        for (int w = half * 4; w < warp; ++w) excl = max(excl, s_wmax[w]);
-
-        // ---- scores and keys: (s << 16) | outwardness
-        const int cy2 = H - 1 - 2 * y;
+        const StripCtx ctx{W, H - 1 - 2 * y, lt, lg, li};
+        const int dir = half ? -1 : 1;
         uint32_t best = 0u;
-        int run = excl;
-        for (int p = p0; p < p1; ++p) {
-            const int x = half ? (W - 1 - p) : p;
-            const uint32_t sc = pixel_score(sm, x, W, cy2, run, P);
-            const uint32_t key = (sc << 16) | (uint32_t)(half ? x : (0xFFFF - x));
-            if (kk == 1) best = max(best, key);
-            else sm.keys[x] = key;
-            run = max(run, (int)Ym[x]);
+
+        if (kk == 1) {
+            // preceding maximum before this warp's quarter: maxima of the
+            // earlier quarters of the quad
+            int qm = 0;
+            for (int p = q0 + lane; p < q1; p += 32)
+                qm = max(qm, (int)((yy[(half ? W - 1 - p : p) - base] >> 8) & 0xff));
+            qm = __reduce_max_sync(kFull, qm);
+            if (lane == 0) s_qmax[warp] = qm;
+            quad_barrier(quad);
+            int carry = 0;
+            for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
+            // ---- rounds of 32 consecutive pixels in scan order (outer edge
+            // inwards), one per lane; `carry` is the preceding maximum before
+            // the round, `best` this warp's best key so far
+            for (int r0 = q0; r0 < q1; r0 += 32) {
+                // no remaining pixel of the quarter can be kept (iota cut) or
+                // beat `best`: their s_iota <= s_iota(carry) bounds their scores
+                if (carry >= P.io_cut || (best != 0u && (best >> 16) >= (uint32_t)li[carry])) break;
+                const int p = r0 + lane;
+                const bool act = p < q1;
+                const int x = half ? (W - 1 - p) : p;
+                const int xc = act ? x : (half ? W - q1 : q1 - 1);
+                const uint32_t w1 = yy[xc - base];
+                const int m1 = (w1 >> 8) & 0xff;
+                int inc = act ? m1 : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc = max(inc, t);
+                }
+                int excl = __shfl_up_sync(kFull, inc, 1);
+                if (lane == 0) excl = 0;
+                const int iota = max(carry, excl);
+                const int carry_next = max(carry, __shfl_sync(kFull, inc, 31));
+                uint32_t key = 0u;
+                const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
+                if (act && iota < P.io_cut && (x == 0 || x == W - 1)) {
+                    key = rank;   // no gradient on the first and last column: score 0
+                } else if (act && iota < P.io_cut) {
+                    const uint32_t w0 = yy[x - 1 - base], w2 = yy[x + 1 - base];
+                    const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
+                    const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
+                    const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
+                    const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
+                    const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
+                    const int ng = gx * gx + gy * gy;
+                    const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
+                    const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
+                    if (((bound << 16) | rank) > best)   // could beat the best so far
+                        key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
+                }
+                best = max(best, __reduce_max_sync(kFull, key));
+                carry = carry_next;
+            }
+            // best of the quad
+            if (lane == 0) s_qbest[warp] = best;
+            quad_barrier(quad);
+            best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
+                       max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
+        } else {
+            // ---- K > 2: exact score per pixel over this lane's chunk, with a
+            // sliding window of the vertical Sobel sums
+            const int cpl = (len + 31) >> 5;
+            const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
+            const int xs = half ? (W - 1 - p0) : p0;
+            int lm = 0;
+            for (int p = p0, x = xs; p < p1; ++p, x += dir) lm = max(lm, (int)((yy[x - base] >> 8) & 0xff));
+            int inc = lm;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc = max(inc, t);
+            }
+            int run = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) run = 0;
+            auto col = [&](int cc, int &S, int &T, int &M) {
+                cc = min(max(cc, c_lo), c_hi - 1);
+                const uint32_t w = yy[cc - base];
+                const int u = w & 0xff, m = (w >> 8) & 0xff, d = (w >> 16) & 0xff;
+                S = u + 2 * m + d;
+                T = d - u;
+                M = m;
+            };
+            int S0, T0, M0, S1, T1, M1;
+            col(xs - dir, S0, T0, M0);
+            col(xs, S1, T1, M1);
+            // the preceding maximum never decreases along the scan: once it
+            // reaches io_cut no later pixel of the half can be kept
+            for (int p = p0, x = xs; p < p1; ++p, x += dir) {
+                uint32_t sv = 0u;
+                if (run < P.io_cut) {
+                    int S2, T2, M2;
+                    col(x + dir, S2, T2, M2);
+                    if (x != 0 && x != W - 1)
+                        sv = score_from_g(ctx, dir * (S2 - S0), T0 + 2 * T1 + T2, x, run, P);
+                    run = max(run, M1);
+                    S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
+                }
+                sc[x - base] = (uint16_t)sv;
+            }
         }
 
         // ---- K/2 picks per half, each excluding +-sup_px around earlier picks
         for (int r = 0; r < kk; ++r) {
             if (kk > 1) {
-                if (r > 0) __syncthreads();   // s_pick of round r-1 visible
-                best = 0u;
-                for (int p = p0; p < p1; ++p) {
-                    const int x = half ? (W - 1 - p) : p;
+                const int cpl = (len + 31) >> 5;
+                const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
+                const int xs = half ? (W - 1 - p0) : p0;
+                uint32_t b = 0u;
+                for (int p = p0, x = xs; p < p1; ++p, x += dir) {
                     bool sup = false;
-                    for (int j = 0; j < r; ++j) sup |= abs(x - s_pick[half][j]) <= P.sup_px;
-                    if (!sup) best = max(best, sm.keys[x]);
+                    for (int j = 0; j < r; ++j) sup |= abs(x - s_pick[j]) <= P.sup_px;
+                    if (!sup)
+                        b = max(b, ((uint32_t)sc[x - base] << 16) | (uint32_t)(half ? x : (0xFFFF - x)));
                 }
+                best = __reduce_max_sync(kFull, b);
             }
-            const uint32_t wbest = __reduce_max_sync(kFull, best);
-            if (lane == 0) s_red[warp] = wbest;
-            __syncthreads();
-            if (ht == 0) {
-                uint32_t hb = 0u;
-                for (int w = half * 4; w < half * 4 + 4; ++w) hb = max(hb, s_red[w]);
-                CandSlot out;
-                out.kept = 0;
-                out.x = -1;
-                out.y = (int16_t)y;
-                out.s = 0;
-                int px = -1000000;
-                if (hb != 0u) {
-                    const int rank = (int)(hb & 0xFFFFu);
-                    px = half ? rank : (0xFFFF - rank);
-                    const uint32_t sc = hb >> 16;
-                    out.x = (int16_t)px;
-                    out.s = (uint16_t)sc;
-                    out.kept = (uint16_t)(sc >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
-                                          y >= P.T_px && y <= H - 1 - P.T_px);
-                }
-                s_pick[half][r] = px;
+            int px = -1000000;
+            CandSlot out;
+            out.kept = 0;
+            out.x = -1;
+            out.y = (int16_t)y;
+            out.s = 0;
+            if (best != 0u) {
+                const int rank = (int)(best & 0xFFFFu);
+                px = half ? rank : (0xFFFF - rank);
+                const uint32_t scv = best >> 16;
+                out.x = (int16_t)px;
+                out.s = (uint16_t)scv;
+                out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
+                                      y >= P.T_px && y <= H - 1 - P.T_px);
+            }
+            if (lane == 0 && (!quads || qw == 0)) {
+                if (kk > 1) s_pick[r] = px;
                 slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
             }
+            __syncwarp();   // this round's pick visible to the whole warp
         }
     }
 }
 
 namespace {
-// Largest dynamic shared memory k_strips can ask for (W = 4096, K > 2).
+// Largest dynamic shared memory k_strips can ask for (W = 4096, full s_g table).
 cudaError_t strips_allow_max_smem() {
     static cudaError_t once = [] {
         DevParams P{};
         P.max_w = kMaxDim;
         P.K = 4;
+        P.qg_sat = kLutG - 1;
         return cudaFuncSetAttribute(k_strips, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)strips_smem_bytes(P));
     }();
@@ -329,6 +491,33 @@ struct Moments {
     uint32_t S;
 };
 
+// Lanes of the T-thread group that contains this lane.  Groups of one warp
+// take different branches (hypotheses past the end, early exits), so their
+// shuffles name only their own lanes.
+template <int T>
+__device__ __forceinline__ unsigned group_mask() {
+    return T >= 32 ? kFull : (((1u << T) - 1u) << ((threadIdx.x & 31) & ~(T - 1)));
+}
+
+// Sum of the moments held by the T threads of one hypothesis group.
+template <int T>
+__device__ __forceinline__ void group_sum(Moments &m, unsigned gm) {
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) {
+        m.n += __shfl_xor_sync(gm, m.n, o);
+        m.Sx += __shfl_xor_sync(gm, m.Sx, o);
+        m.Sy += __shfl_xor_sync(gm, m.Sy, o);
+        m.Sxx += __shfl_xor_sync(gm, m.Sxx, o);
+        m.Sxy += __shfl_xor_sync(gm, m.Sxy, o);
+        m.Syy += __shfl_xor_sync(gm, m.Syy, o);
+        m.Sxxx += __shfl_xor_sync(gm, m.Sxxx, o);
+        m.Sxxy += __shfl_xor_sync(gm, m.Sxxy, o);
+        m.Sxyy += __shfl_xor_sync(gm, m.Sxyy, o);
+        m.Syyy += __shfl_xor_sync(gm, m.Syyy, o);
+        m.S += __shfl_xor_sync(gm, m.S, o);
+    }
+}
+
 // Algebraic least-squares circle (Coope 1993) from exact integer moments.
 __device__ __forceinline__ bool ls_fit(const Moments &m, Circle &o) {
     if (m.n < 3) return false;
@@ -359,20 +548,28 @@ __device__ __forceinline__ bool ls_fit(const Moments &m, Circle &o) {
     return true;
 }
 
+// One candidate point in shared memory (32 bytes: two 16-byte loads).
+struct __align__(16) Pt {
+    float fx, fy;
+    int32_t X, Y;
+    int32_t XX, XY, YY;
+    uint32_t S;
+};
+
 struct FitSmem {
-    int32_t X[kMaxSlots], Y[kMaxSlots], XX[kMaxSlots], XY[kMaxSlots], YY[kMaxSlots];
-    float fX[kMaxSlots], fY[kMaxSlots];
-    uint32_t S[kMaxSlots];
+    Pt pt[kMaxSlots];
     int wcount[kHypTile / 32];
     unsigned long long wbest[kHypTile / 32];
     int last;
 };
 
-// Inliers of circle c among the M candidates, as a bit set (8 words for up to
-// 256 points), with their moments (if `moments`) and score sum.  Returns true
-// if the set differs from `bits` on entry; `bits` receives the new set.
-__device__ __forceinline__ bool inlier_pass(const FitSmem &sm, int M, const Circle &c, float t_ri,
-                                            bool moments, uint32_t (&bits)[8], Moments &m) {
+// Inliers of circle c among this thread's share of the candidates (points
+// j = sub, sub + T, ...), as a bit set, with their moments (if `moments`) and
+// score sum.  Returns true if this share of the set differs from `bits`.
+template <int T>
+__device__ __forceinline__ bool inlier_pass(const FitSmem &sm, int M, int sub, const Circle &c,
+                                            float t_ri, bool moments, uint32_t (&bits)[8 / T],
+                                            Moments &m) {
     float lo = __fsub_rn(c.r, t_ri);
     if (lo < 0.0f) lo = 0.0f;
     const float hi = __fadd_rn(c.r, t_ri);
@@ -380,22 +577,25 @@ __device__ __forceinline__ bool inlier_pass(const FitSmem &sm, int M, const Circ
     m = Moments{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0u};
     bool changed = false;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < 8 / T; ++w) {
         uint32_t word = 0u;
-        if (w * 32 < M) {
-            const int jend = min(32, M - w * 32);
-            for (int b = 0; b < jend; ++b) {
-                const int j = w * 32 + b;
-                const float dx = __fsub_rn(sm.fX[j], c.cx);
-                const float dy = __fsub_rn(sm.fY[j], c.cy);
+        const int j0 = sub + T * 32 * w;
+        if (j0 < M) {
+            const int nb = min(32, (M - j0 + T - 1) / T);
+            for (int b = 0; b < nb; ++b) {
+                const int j = j0 + T * b;
+                const uint4 q0 = *reinterpret_cast<const uint4 *>(&sm.pt[j]);
+                const float dx = __fsub_rn(__uint_as_float(q0.x), c.cx);
+                const float dy = __fsub_rn(__uint_as_float(q0.y), c.cy);
                 const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
                 if (d2 >= lo2 && d2 <= hi2) {
+                    const uint4 q1 = *reinterpret_cast<const uint4 *>(&sm.pt[j].XX);
                     word |= 1u << b;
                     m.n += 1;
-                    m.S += sm.S[j];
+                    m.S += q1.w;
                     if (moments) {
-                        const int X = sm.X[j], Y = sm.Y[j];
-                        const int XX = sm.XX[j], XY = sm.XY[j], YY = sm.YY[j];
+                        const int X = (int)q0.z, Y = (int)q0.w;
+                        const int XX = (int)q1.x, XY = (int)q1.y, YY = (int)q1.z;
                         m.Sx += X;
                         m.Sy += Y;
                         m.Sxx += XX;
@@ -449,12 +649,17 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 
 }  // namespace
 
-__global__ void __launch_bounds__(kHypTile)
+// T threads share one hypothesis (points split among them, moments combined
+// by shuffles); a CTA holds 256 / T hypotheses of one frame.
+template <int T>
+__global__ void __launch_bounds__(kHypTile, 4)
     k_fit(const DevFrame *__restrict__ frames, int B, DevParams P,
           const CandSlot *__restrict__ slots, Workspace ws, ca_result *__restrict__ out) {
     __shared__ FitSmem sm;
+    constexpr int HPT = kHypTile / T;
     const int f = blockIdx.x, tile = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = tid & (T - 1);
     const DevFrame fr = frames[f];
     const int NK = P.N * P.K;
     const int ox = fr.W >> 1, oy = fr.H >> 1;
@@ -476,16 +681,18 @@ __global__ void __launch_bounds__(kHypTile)
     if (kept) {
         const int j = off + __popc(bal & ((1u << lane) - 1u));
         const int X = c.x - ox, Y = c.y - oy;
-        sm.X[j] = X; sm.Y[j] = Y;
-        sm.XX[j] = X * X; sm.XY[j] = X * Y; sm.YY[j] = Y * Y;
-        sm.fX[j] = __int2float_rn(X); sm.fY[j] = __int2float_rn(Y);
-        sm.S[j] = c.s;
+        Pt p;
+        p.fx = __int2float_rn(X); p.fy = __int2float_rn(Y);
+        p.X = X; p.Y = Y;
+        p.XX = X * X; p.XY = X * Y; p.YY = Y * Y;
+        p.S = c.s;
+        sm.pt[j] = p;
     }
     __syncthreads();
 
     long long NH = 0;
     if (M >= 3) NH = P.hyp_mode == CA_HYP_EXHAUSTIVE ? (long long)M * (M - 1) * (M - 2) / 6 : P.NH;
-    const long long h = (long long)tile * kHypTile + tid;
+    const long long h = (long long)tile * HPT + tid / T;
     if (P.debug >= 1 && tile == 0 && tid == 0) {
         ws.n_cands[f] = M;
         ws.n_hyps[f] = (int)NH;
@@ -496,7 +703,7 @@ __global__ void __launch_bounds__(kHypTile)
     int n_fin = 0;
     uint32_t S_fin = 0u;
     int t0 = 0, t1 = 0, t2 = 0, pass = 0;
-    if (h < NH) {
+    if (h < NH) {   // uniform across the T threads of a group
         if (P.hyp_mode == CA_HYP_EXHAUSTIVE) {
             unrank_triple(h, M, t0, t1, t2);
         } else {
@@ -517,18 +724,28 @@ __global__ void __launch_bounds__(kHypTile)
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
         if (s1 > s2) { tmp = s1; s1 = s2; s2 = tmp; }
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
-        if (circumcircle(sm.X[s0], sm.Y[s0], sm.X[s1], sm.Y[s1], sm.X[s2], sm.Y[s2], c0)) {
-            uint32_t bits[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (circumcircle(sm.pt[s0].X, sm.pt[s0].Y, sm.pt[s1].X, sm.pt[s1].Y, sm.pt[s2].X,
+                         sm.pt[s2].Y, c0)) {
+            uint32_t bits[8 / T];
+#pragma unroll
+            for (int w = 0; w < 8 / T; ++w) bits[w] = 0u;
             Moments m;
             bool final_known = false;
+            const unsigned gm = group_mask<T>();
             for (int it = 0; it < P.refine; ++it) {
-                const bool changed = inlier_pass(sm, M, c0, P.t_ri, true, bits, m);
+                int changed = inlier_pass<T>(sm, M, sub, c0, P.t_ri, true, bits, m) ? 1 : 0;
+                group_sum<T>(m, gm);
+#pragma unroll
+                for (int o = 1; o < T; o <<= 1) changed |= __shfl_xor_sync(gm, changed, o);
                 if (it > 0 && !changed) { final_known = true; break; }   // fit would repeat
                 Circle nc;
                 if (!ls_fit(m, nc)) { final_known = true; break; }       // circle unchanged
                 c0 = nc;
             }
-            if (!final_known) inlier_pass(sm, M, c0, P.t_ri, false, bits, m);
+            if (!final_known) {
+                inlier_pass<T>(sm, M, sub, c0, P.t_ri, false, bits, m);
+                group_sum<T>(m, gm);
+            }
             n_fin = m.n;
             S_fin = m.S;
             const float Wf = __int2float_rn(fr.W);
@@ -538,12 +755,12 @@ __global__ void __launch_bounds__(kHypTile)
             const float dx = __fsub_rn(c0.cx, ex), dy = __fsub_rn(c0.cy, ey);
             pass = c0.r >= rlo && c0.r <= rhi &&
                    __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= __fmul_rn(dm, dm);
-            if (pass)
+            if (pass && sub == 0)
                 key = ((unsigned long long)(S_fin + 1u) << 32) | (0xFFFFFFFFu - (uint32_t)h);
         } else {
             c0 = Circle{0.f, 0.f, 0.f};
         }
-        if (P.debug >= 2) {
+        if (P.debug >= 2 && sub == 0) {
             HypRec rec;
             rec.i0 = t0; rec.i1 = t1; rec.i2 = t2;
             rec.n_inl = n_fin; rec.S = S_fin; rec.pass = pass;
@@ -589,7 +806,7 @@ __global__ void __launch_bounds__(kHypTile)
         if (k != 0ull) {
             const uint32_t hb = 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
             const uint32_t S = (uint32_t)(k >> 32) - 1u;
-            const volatile TileRec *tr = ws.tiles + (int64_t)f * P.n_tiles + hb / kHypTile;
+            const volatile TileRec *tr = ws.tiles + (int64_t)f * P.n_tiles + hb / HPT;
             res.cx = __fadd_rn(__int2float_rn(ox), tr->cx);
             res.cy = __fadd_rn(__int2float_rn(oy), tr->cy);
             res.r = tr->r;
@@ -603,10 +820,40 @@ __global__ void __launch_bounds__(kHypTile)
     }
 }
 
+int fit_threads_per_sm(int T) {
+    static int cache[9] = {0};
+    if (T < 1 || T > 8) return 1024;
+    if (cache[T] == 0) {
+        int v = 0;
+        cudaError_t e = cudaErrorInvalidValue;
+        if (T == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fit<1>, kHypTile, 0);
+        if (T == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fit<2>, kHypTile, 0);
+        if (T == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fit<4>, kHypTile, 0);
+        if (T == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fit<8>, kHypTile, 0);
+        cache[T] = (e == cudaSuccess && v > 0 ? v : 2) * kHypTile;
+    }
+    return cache[T];
+}
+
+int choose_hyp_threads(int requested, long long B, long long NH, int sms) {
+    if (requested == 1 || requested == 2 || requested == 4 || requested == 8) return requested;
+    // the largest split whose threads still fit one wave of resident CTAs
+    // (more threads per hypothesis shorten each thread's serial work)
+    int T = 1;
+    while (T < 8 && B * NH * (2 * T) <= (long long)sms * fit_threads_per_sm(2 * T)) T <<= 1;
+    return T;
+}
+
 cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const CandSlot *slots,
                        const Workspace &ws, ca_result *out, cudaStream_t s) {
     dim3 grid((unsigned)B, (unsigned)P.n_tiles);
-    k_fit<<<grid, kHypTile, 0, s>>>(frames, B, P, slots, ws, out);
+    switch (P.hyp_threads) {
+        case 1: k_fit<1><<<grid, kHypTile, 0, s>>>(frames, B, P, slots, ws, out); break;
+        case 2: k_fit<2><<<grid, kHypTile, 0, s>>>(frames, B, P, slots, ws, out); break;
+        case 4: k_fit<4><<<grid, kHypTile, 0, s>>>(frames, B, P, slots, ws, out); break;
+        case 8: k_fit<8><<<grid, kHypTile, 0, s>>>(frames, B, P, slots, ws, out); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -667,24 +914,26 @@ __device__ __forceinline__ uint32_t span_word(int x0, int a, int b) {
     return w;
 }
 
-__device__ __forceinline__ uint32_t exact_word(int x0, const ca_result &res, float dy2) {
+__device__ __forceinline__ uint32_t exact_word(int x0, float cx, float dy2, float rr) {
     uint32_t w = 0u;
-    const float rr = __fmul_rn(res.r, res.r);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w |= (uint32_t)in_disc(x0 + j, res.cx, dy2, rr) << (8 * j);
+    for (int j = 0; j < 4; ++j) w |= (uint32_t)in_disc(x0 + j, cx, dy2, rr) << (8 * j);
     return w;
 }
 
 }  // namespace
 
-// One warp per 32-row unit of one frame; lanes stride over the unit's 16-byte
-// vectors (row-major), so every lane stores on every iteration.
+// One warp per unit of 8 rows of one frame: lane r computes the span of row r,
+// then the warp stores each row with consecutive 16-byte vectors per lane.
 __global__ void __launch_bounds__(256)
     k_mask(const DevFrame *__restrict__ frames, int B, const ca_result *__restrict__ results,
            int total_units) {
     const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total_units; u += nw) {
+    const int wpb = blockDim.x >> 5;
+    const int nw = gridDim.x * wpb;
+    const uint4 ones = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+    const uint4 zeros = make_uint4(0u, 0u, 0u, 0u);
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < total_units; u += nw) {
         int lo = 0, hi = B - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -695,58 +944,56 @@ __global__ void __launch_bounds__(256)
         if (fr.mask == nullptr) continue;
         const ca_result res = results[lo];
         const int W = fr.W, H = fr.H;
-        const int y0 = (u - fr.unit_off) * kMaskRowsPerWarp;
-        const int nrows = min(kMaskRowsPerWarp, H - y0);
+        const int y0 = (u - fr.unit_off) * kMaskRowsPerUnit;
+        const int nrows = min(kMaskRowsPerUnit, H - y0);
         const RowSpan sp = row_span(res, W, y0 + min(lane, nrows - 1));
-        if (fr.mask_vec_ok) {
-            const int VW = W >> 4;
-            const int nvec = nrows * VW;
-            int row = lane / VW, col = lane - row * VW;
-            for (int base = 0; base < nvec; base += 32) {
-                const int src = min(row, 31);
-                const int a = __shfl_sync(kFull, sp.a, src);
-                const int b = __shfl_sync(kFull, sp.b, src);
-                const int ex = __shfl_sync(kFull, sp.exact, src);
-                if (base + lane < nvec) {
-                    const int x0 = col << 4;
-                    uint4 v;
-                    if (ex && x0 >= a && x0 + 15 <= b) {
-                        v = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-                    } else if (ex && (x0 + 15 < a || x0 > b)) {
-                        v = make_uint4(0u, 0u, 0u, 0u);
-                    } else if (ex) {
-                        v = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
-                                       span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
+        const float rr = __fmul_rn(res.r, res.r);
+        for (int r = 0; r < nrows; ++r) {
+            const int a = __shfl_sync(kFull, sp.a, r);
+            const int b = __shfl_sync(kFull, sp.b, r);
+            const int ex = __shfl_sync(kFull, sp.exact, r);
+            const int y = y0 + r;
+            uint8_t *row = fr.mask + (int64_t)y * W;
+            const float dy = __fsub_rn(__int2float_rn(y), res.cy);
+            const float dy2 = __fmul_rn(dy, dy);
+            if (fr.mask_vec_ok) {
+                const int VW = W >> 4;
+                for (int v = lane; v < VW; v += 32) {
+                    const int x0 = v << 4;
+                    uint4 val;
+                    if (ex) {
+                        if (x0 >= a && x0 + 15 <= b) val = ones;
+                        else if (x0 > b || x0 + 15 < a) val = zeros;
+                        else val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
+                                              span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
                     } else {
-                        const float dy = __fsub_rn(__int2float_rn(y0 + row), res.cy);
-                        const float dy2 = __fmul_rn(dy, dy);
-                        v = make_uint4(exact_word(x0, res, dy2), exact_word(x0 + 4, res, dy2),
-                                       exact_word(x0 + 8, res, dy2), exact_word(x0 + 12, res, dy2));
+                        val = make_uint4(exact_word(x0, res.cx, dy2, rr),
+                                         exact_word(x0 + 4, res.cx, dy2, rr),
+                                         exact_word(x0 + 8, res.cx, dy2, rr),
+                                         exact_word(x0 + 12, res.cx, dy2, rr));
                     }
-                    st_cs_v4(fr.mask + (int64_t)(y0 + row) * W + x0, v);
+                    st_cs_v4(row + x0, val);
                 }
-                col += 32;
-                while (col >= VW) { col -= VW; ++row; }
-            }
-        } else {
-            for (int r = 0; r < nrows; ++r) {
-                const int a = __shfl_sync(kFull, sp.a, r);
-                const int b = __shfl_sync(kFull, sp.b, r);
-                const int ex = __shfl_sync(kFull, sp.exact, r);
-                const int y = y0 + r;
-                const float dy = __fsub_rn(__int2float_rn(y), res.cy);
-                const float dy2 = __fmul_rn(dy, dy);
-                const float rr = __fmul_rn(res.r, res.r);
+            } else {
                 for (int x = lane; x < W; x += 32) {
                     uint8_t v;
                     if (!res.valid) v = 1;
                     else if (ex) v = (uint8_t)(x >= a && x <= b);
                     else v = (uint8_t)in_disc(x, res.cx, dy2, rr);
-                    fr.mask[(int64_t)y * W + x] = v;
+                    row[x] = v;
                 }
             }
         }
     }
+}
+
+int mask_blocks_per_sm() {
+    static int nb = [] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_mask, 256, 0) != cudaSuccess) v = 4;
+        return v < 1 ? 1 : v;
+    }();
+    return nb;
 }
 
 cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int total_units,

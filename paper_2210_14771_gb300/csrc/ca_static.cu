@@ -20,7 +20,7 @@ namespace {
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 constexpr int kTilesStatic = CA_STATIC_MAX_HYPS / kHypTile;
-constexpr size_t kLutBytes = sizeof(uint16_t) * (kLutG + kLutT + kLutI);
+constexpr size_t kLutBytes = sizeof(uint16_t) * kDevTableU16;
 constexpr size_t kOffLuts = 0;
 constexpr size_t kOffRows = align256(kOffLuts + kLutBytes);
 constexpr size_t kOffFrames = align256(kOffRows + sizeof(int32_t) * kMaxSlots);
@@ -65,6 +65,7 @@ ca_status static_scratch(int dev, unsigned char **out) {
 // with ordinary (pageable) asynchronous copies, which allocate nothing.
 struct HostTables {
     uint16_t luts[kLutG + kLutT + kLutI];
+    uint16_t dev[kDevTableU16];
     int32_t rows[kMaxSlots];
 };
 
@@ -99,6 +100,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     HostTables ht;
     int qg_sat = kLutG - 1;
     build_luts(*p, ht.luts, &qg_sat);
+    pack_device_tables(ht.luts, qg_sat, ht.dev);
     strip_rows(H, p->n_strips, p->alpha, ht.rows);
     DevParams P;
     std::memset(&P, 0, sizeof(P));
@@ -116,8 +118,15 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     P.T_cs = (uint32_t)std::ceil((double)p->t_cs * 32768.0 * norm);
     P.score_den = 32768.0 * norm;
     P.qg_sat = qg_sat;
+    P.io_cut = iota_cut(ht.luts + kLutG + kLutT, P.T_ps);
     P.NH = (int)nh;
-    P.n_tiles = (int)((nh + kHypTile - 1) / kHypTile);
+    P.hyp_threads = choose_hyp_threads(p->hyp_threads, B, nh, sms);
+    P.n_tiles = (int)((nh + kHypTile / P.hyp_threads - 1) / (kHypTile / P.hyp_threads));
+    // the tile records of all frames must fit the scratch's tile region
+    while (P.hyp_threads > 1 && (long long)B * P.n_tiles > (long long)kTilesStatic * CA_STATIC_MAX_FRAMES) {
+        P.hyp_threads >>= 1;
+        P.n_tiles = (int)((nh + kHypTile / P.hyp_threads - 1) / (kHypTile / P.hyp_threads));
+    }
     P.t_ri = p->t_ri;
     P.r_min = p->r_min;
     P.r_max = p->r_max;
@@ -128,7 +137,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     // frame descriptors (uniform batch stored back to back)
     DevFrame frames[CA_STATIC_MAX_FRAMES];
     const size_t fbytes = (size_t)H * W * 3, mbytes = (size_t)H * W;
-    const int units_per_frame = (H + kMaskRowsPerWarp - 1) / kMaskRowsPerWarp;
+    const int units_per_frame = (H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
     for (int i = 0; i < B; ++i) {
         DevFrame &d = frames[i];
         std::memset(&d, 0, sizeof(d));
@@ -153,7 +162,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     ws.best = reinterpret_cast<unsigned long long *>(scratch + kOffBest);
     ws.done = reinterpret_cast<uint32_t *>(scratch + kOffDone);
 
-    if (cudaMemcpyAsync(d_luts, ht.luts, kLutBytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(d_luts, ht.dev, kLutBytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_rows, ht.rows, sizeof(int32_t) * P.N, cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(d_frames, frames, sizeof(DevFrame) * B, cudaMemcpyHostToDevice, s) !=
@@ -166,13 +175,14 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
 
     int nb = 0;
     if (strips_occupancy(&nb, strips_smem_bytes(P)) != cudaSuccess) return CA_ERR_CUDA;
-    const int sgrid = std::min(B * P.N, sms * std::max(1, nb));
+    const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
+    (void)nb;
     if (launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, s) != cudaSuccess ||
         launch_fit(d_frames, B, P, ws.slots, ws, out_dev, s) != cudaSuccess)
         return CA_ERR_CUDA;
     if (masks_dev) {
         const int units = units_per_frame * B;
-        const int mgrid = std::max(1, std::min((units + 7) / 8, sms * 8));
+        const int mgrid = std::max(1, std::min((units + 7) / 8, sms * mask_blocks_per_sm()));
         if (launch_mask(d_frames, B, out_dev, units, mgrid, s) != cudaSuccess) return CA_ERR_CUDA;
     }
     return CA_OK;

@@ -234,3 +234,33 @@ def test_argument_errors(ca, orc):
         ca.estimate(t, api.params(scorer_mode=1))
     assert e.value.status == 5
     ca.sync()   # the context is healthy after rejected calls
+
+
+@pytest.mark.parametrize("T", [1, 2, 4, 8])
+def test_hypothesis_split_invariance(ca, orc, T):
+    """Splitting each hypothesis over 1, 2, 4 or 8 threads changes nothing."""
+    frames, _, keys = synth.batch(12, 6, 480, 640, "centred")
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=4, n_hyps=300, hyp_threads=T)
+    gres, gmask = _gpu_batch(ca, frames, keys, lp, debug=2)
+    for b in range(len(frames)):
+        _compare_frame(orc, ca, b, frames[b], keys[b], lp, op, gres, gmask[b], True)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_parity_zero_thresholds(ca, orc, K):
+    """t_ps = 0 and t_px = 0 keep zero-score picks (flat runs, image edges):
+    the pruned scans must still pick exactly the oracle's pixels."""
+    frames = []
+    rng = np.random.default_rng(3)
+    for i, (H, W) in enumerate([(64, 96), (40, 72), (33, 50)]):
+        f, _ = synth.frame(60, i, H, W, "centred")
+        f = f.copy()
+        f[: H // 3] = 20                            # flat rows: every score 0
+        f[:, : W // 4] = rng.integers(0, 3, size=(H, W // 4, 3))
+        frames.append(f)
+    keys = [5, 6, 7]
+    lp, op = both_params(orc, n_strips=8, cands_per_strip=K, n_hyps=200, t_ps=0.0, t_px=0.0,
+                         t_cs=0.0)
+    gres, gmask = _gpu_batch(ca, frames, keys, lp, debug=2)
+    for b, f in enumerate(frames):
+        _compare_frame(orc, ca, b, f, keys[b], lp, op, gres, gmask[b], True)

@@ -119,12 +119,15 @@ def test_lut_special_values(orc):
     assert g[80] == round(32768 * _tanh_via_exp(1.0))          # |g| = t_g = 20
     assert t[-1] == 32768 and t[0] == 0                         # theta = 0 / 180 deg
     assert all(np.diff(t.astype(int)) >= 0)
-    # cos-bin whose centre is cos = 0.5 exactly does not exist; the bin centred
-    # at q + 0.5 = 6144 + 0.5 is within half a bin of 60 degrees
-    q = 6144
-    lo = 1 - _tanh_via_exp(math.degrees(math.acos(q / 4096 - 1)) / 30)
-    hi = 1 - _tanh_via_exp(math.degrees(math.acos((q + 1) / 4096 - 1)) / 30)
-    assert round(32768 * lo) <= t[q] <= round(32768 * hi)
+    # bin q covers the signed squared cosine u in [q/4096 - 1, (q+1)/4096 - 1):
+    # q = 6144 starts at u = 0.5, i.e. theta = 45 degrees; q = 7168 at 30 degrees
+    for q in (6144, 7168, 4096, 1000):
+        def theta(u):
+            c = math.copysign(math.sqrt(abs(u)), u)
+            return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+        lo = 1 - _tanh_via_exp(theta(q / 4096 - 1) / 30)
+        hi = 1 - _tanh_via_exp(theta((q + 1) / 4096 - 1) / 30)
+        assert round(32768 * lo) <= t[q] <= round(32768 * hi), q
     assert i[0] == 32768 and i[25] == round(32768 * (1 - _tanh_via_exp(1.0)))
     assert all(np.diff(i.astype(int)) <= 0)
 
@@ -141,8 +144,9 @@ def test_quantised_score_close_to_eq2(orc):
         for x in range(0, 640, 3):
             ref = orc.score_exact(gx[x], gy[x], 639 - 2 * x, 479 - 2 * int(y), iota[x], p)
             worst = max(worst, abs(s[x] / 32768.0 - ref))
-    # |g| steps of 1/4 (<= 0.25/t_g), cos bins of 1/4096 (<= 0.035 near 0 deg), rounding
-    assert worst <= 0.25 / 20 + 0.035 + 1e-3, worst
+    # |g| steps of 1/4 (<= 0.25/t_g); squared-cosine bins of 1/4096 span at most
+    # 0.9 degrees (near 0 and 90 degrees), i.e. <= tanh(0.9/30) in s_theta; rounding
+    assert worst <= 0.25 / 20 + math.tanh(0.9 / 30) + 1e-3, worst
 
 
 def test_score_direction_reading(orc):
