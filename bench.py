@@ -32,6 +32,7 @@ WORKLOAD = dict(name="1080p_x64_mixed_geometry", B=64, H=1080, W=1920, seed=1, m
 METRIC = "1080p frames/s (batched, whole hot path)"
 PAPER_CONTEXT = {"ms_per_frame": 0.129, "hardware": "NVIDIA GeForce GTX 980 Ti",
                  "source": "Table 1 (handcrafted variant)"}
+MIXED = dict(B=512, seed=2, unique=128)   # 4 resolutions, 25 % each
 ROTATE_INPUTS = 4   # resident copies of the batch, used in turn (1.6 GB > L2)
 ROTATE_MASKS = 2
 
@@ -45,6 +46,7 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batching", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -118,11 +120,14 @@ def make_workload(rank):
 
 
 def algorithmic_bytes(B, H, W, N, K):
-    """Bytes the method must move per batch (unsampled rows are never read)."""
+    """Bytes the method must move per batch (unsampled rows are never read).
+    The fused kernel moves the sum: strip rows in, masks and results out (its
+    candidate slots stay in L2 between phases)."""
     strips = B * (9 * N * W + 8 * N * K)          # 3 rows x 3 channels per strip; slots out
     mask = B * (H * W + 24)                        # mask bytes written, result read
     fit = B * (8 * N * K + 24)                     # slots in, result out
-    return {"strips": strips, "fit": fit, "mask": mask}
+    return {"strips": strips, "fit": fit, "mask": mask,
+            "fused": B * (9 * N * W + H * W + 24)}
 
 
 def kernel_traffic(kernel):
@@ -169,67 +174,148 @@ def oracle_sample(frames, keys, seconds, min_frames=2):
 
 
 # ------------------------------------------------------------- ours --
+def timed_loop(stream, steps, fn):
+    """Runs fn(k) for k < steps between CUDA events on `stream`; returns
+    (total ms, per-step ms list)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(steps):
+        fn(k)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[steps]), [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+
+
+def plain_leg(ca, p, frames_dev, keys, masks_dev, stream, reps):
+    """The plain method: one frame per call (three launches per frame, staged)."""
+    import numpy as np
+    import torch
+    from paper_2210_14771_gb300 import api
+    q = api.params(**{k: getattr(p, k) for k, _ in p._fields_})
+    q.batch_mode = 1
+    res = api.new_results(1, frames_dev[0].device)
+    lat = []
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(len(frames_dev))]
+    for _ in range(reps):
+        for b, f in enumerate(frames_dev):
+            pev[b][0].record(stream)
+            ca.estimate([f], q, keys=[keys[b]], masks=[masks_dev[b]], results=res)
+            pev[b][1].record(stream)
+        torch.cuda.synchronize()
+        lat += [a.elapsed_time(c) for a, c in pev]
+    return {"frames_per_s": len(lat) / (sum(lat) / 1e3),
+            "p50_ms_per_frame": float(np.percentile(lat, 50)),
+            "p99_ms_per_frame": float(np.percentile(lat, 99)), "launches_per_frame": 3}
+
+
+def batching_leg(ca, mixed, p_ref, stream, steps, warmup):
+    """512 frames at four resolutions in one persistent, graph-captured launch:
+    launch shapes tuned by ca_tune, N/K/NH by the accuracy-constrained sweep
+    on a calibration subset; timed against the plain one-frame-per-launch
+    method on the same frames."""
+    import numpy as np
+    import torch
+    from paper_2210_14771_gb300 import api, tune
+    mf, mg, mk = mixed
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ts = [torch.from_numpy(f).to(dev) for f in mf]
+    ms = [torch.empty(f.shape[:2], dtype=torch.uint8, device=dev) for f in mf]
+    B = len(ts)
+    out = {"workload": "mixed_x%d" % B, "frames": B,
+           "resolutions": sorted({"%dx%d" % (f.shape[1], f.shape[0]) for f in mf}),
+           "unique_contents": len({id(f) for f in mf})}
+    byts = sum(9 * p_ref.n_strips * f.shape[1] + f.shape[0] * f.shape[1] for f in mf)
+
+    def run_plan(p, tag):
+        t = ca.tune(ts, p, keys=mk, masks=ms)
+        res = api.new_results(B, dev)
+        plan = ca.plan(ts, p, keys=mk, masks=ms, results=res)
+        for _ in range(max(warmup, 3)):
+            plan.launch()
+        total, per = timed_loop(stream, steps, lambda k: plan.launch())
+        ca.sync()
+        plan.close()
+        return {"params": {"N": p.n_strips, "K": p.cands_per_strip, "NH": p.n_hyps},
+                "launch": {k: t[k] for k in ("batch_mode", "hyp_threads", "wave_frames")},
+                "frames_per_s": B * steps / (total / 1e3), "ms_per_call": total / steps,
+                "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+                "hbm_frac_of_measured": byts / (total / steps / 1e3) / 1e9 / peaks()[0],
+                "tune_ms": {k: t[k] for k in ("ms", "ms_staged", "ms_fused", "ms_untuned")}}, res
+
+    out["batched"], res = run_plan(p_ref, "default")
+    out["plain"] = plain_leg(ca, p_ref, ts, mk, ms, stream, 1)
+    out["speedup_vs_plain"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
+    # accuracy-constrained sweep of N, K, NH on a calibration subset
+    cal = list(range(0, B, max(1, B // 32)))[:32]
+    trials, ref_t, best = tune.sweep(ca, [ts[i] for i in cal], [mg[i] for i in cal],
+                                     [mk[i] for i in cal])
+    out["sweep"] = {"calibration_frames": len(cal), "reference": tune.as_dict(ref_t),
+                    "chosen": tune.as_dict(best), "trials": [tune.as_dict(t) for t in trials]}
+    if (best.N, best.K, best.NH) != (ref_t.N, ref_t.K, ref_t.NH):
+        q = api.params(n_strips=best.N, cands_per_strip=best.K, n_hyps=best.NH)
+        out["batched_autotuned"], _ = run_plan(q, "autotuned")
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
     from paper_2210_14771_gb300.build import build
-    from paper_2210_14771_gb300 import api, metrics
+    from paper_2210_14771_gb300 import api, metrics, synth
 
     rank, world, local = dist_env()
+    # inputs first: the mixed workload is drawn in spawned processes
+    frames, gts, keys = make_workload(rank)
+    mixed = None
+    if not args.skip_batching:
+        mixed = synth.mixed_batch(MIXED["seed"] + 1000 * rank, MIXED["B"], unique=MIXED["unique"],
+                                  workers=min(16, os.cpu_count() or 1))
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     build()
     dev = torch.device("cuda", local)
-    frames, gts, keys = make_workload(rank)
     B, H, W = WORKLOAD["B"], WORKLOAD["H"], WORKLOAD["W"]
     p = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
                    n_hyps=WORKLOAD["n_hyps"])
     ca = api.ContentArea(local)
+    stream = torch.cuda.current_stream(dev)
     # the batch is resident in ROTATE_INPUTS copies used in turn, so no step
     # finds its strip rows in L2 (1.6 GB of inputs, no cache flush needed and
     # no foreign dirty lines to write back inside the timed region)
     d_frames_all = [torch.from_numpy(frames).to(dev)]
     for _ in range(ROTATE_INPUTS - 1):
         d_frames_all.append(d_frames_all[0].clone())
-    d_frames = d_frames_all[0]
-    d_res = api.new_results(B, dev)
     d_masks_all = [torch.empty((B, H, W), dtype=torch.uint8, device=dev)
                    for _ in range(ROTATE_MASKS)]
-    d_masks = d_masks_all[0]
-    stream = torch.cuda.current_stream(dev)
+    d_res = api.new_results(B, dev)
+
+    # ---- launch shapes tuned on this batch (results unchanged), then one
+    # captured plan per resident copy: a step is one graph launch
+    tuning = ca.tune(list(d_frames_all[0]), p, keys=keys, masks=list(d_masks_all[0]))
+    plans = [ca.plan(list(d_frames_all[k % ROTATE_INPUTS]), p, keys=keys,
+                     masks=list(d_masks_all[k % ROTATE_MASKS]), results=d_res)
+             for k in range(ROTATE_INPUTS)]
 
     clocks = Clocks(local)
     clocks.start()
     for w in range(max(args.warmup, 3)):
-        ca.estimate(d_frames_all[w % ROTATE_INPUTS], p, keys=keys,
-                    masks=d_masks_all[w % ROTATE_MASKS], results=d_res)
+        plans[w % ROTATE_INPUTS].launch()
     torch.cuda.synchronize()
-
-    # ---- batched: K steps back to back on rotating inputs
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    ca.kernel_times()
-    ca.set_timing(True)
     n0 = ca.launch_count()
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        ca.estimate(d_frames_all[k % ROTATE_INPUTS], p, keys=keys,
-                    masks=d_masks_all[k % ROTATE_MASKS], results=d_res)
-        ev[k + 1].record(stream)
-    torch.cuda.synchronize()
+    total_ms, step_ms = timed_loop(stream, args.steps, lambda k: plans[k % ROTATE_INPUTS].launch())
     if world > 1:
         dist.barrier()
+    ca.sync()
     launches = ca.launch_count() - n0
-    ca.set_timing(False)
-    ktimes = ca.kernel_times()
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    d_masks = d_masks_all[(args.steps - 1) % ROTATE_MASKS]
+    last_masks = d_masks_all[(args.steps - 1) % ROTATE_MASKS]
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -237,37 +323,33 @@ def run_ours(args):
     value = B * args.steps * world / (total_ms / 1e3)
 
     # ---- accuracy of this batch against the generator's ground truth (Sec. 2.3)
-    m_host = d_masks.cpu().numpy()
+    m_host = last_masks.cpu().numpy()
     res_host = api.results_numpy(d_res)
     nh = [metrics.normalised_hausdorff(m_host[b].astype(bool), metrics.gt_mask(gts[b], H, W))
           for b in range(B)]
     acc = metrics.summarise(nh)
 
-    # ---- plain method: one frame per call (3 launches per frame)
+    # ---- per-phase kernels of the staged launch (CUDA events per kernel)
+    q = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
+                   n_hyps=WORKLOAD["n_hyps"], batch_mode=1)
+    for w in range(3):
+        ca.estimate(d_frames_all[w % ROTATE_INPUTS], q, keys=keys,
+                    masks=d_masks_all[w % ROTATE_MASKS], results=d_res)
+    torch.cuda.synchronize()
+    ca.kernel_times()
+    ca.set_timing(True)
+    staged_steps = min(args.steps, 20)
+    staged_ms, _ = timed_loop(stream, staged_steps, lambda k: ca.estimate(
+        d_frames_all[k % ROTATE_INPUTS], q, keys=keys, masks=d_masks_all[k % ROTATE_MASKS],
+        results=d_res))
+    ca.set_timing(False)
+    ktimes = ca.kernel_times()
+    same_staged = api.results_numpy(d_res).tobytes() == res_host.tobytes()
+
     plain = None
     if not args.skip_plain:
-        lat = []
-        plain_total = 0.0
-        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(B)]
-        reps = max(1, min(args.steps, 5))
-        p_res = api.new_results(1, dev)
-        for rep in range(reps):
-            src = d_frames_all[rep % ROTATE_INPUTS]
-            dst = d_masks_all[rep % ROTATE_MASKS]
-            for b in range(B):
-                pev[b][0].record(stream)
-                ca.estimate(src[b:b + 1], p, keys=keys[b:b + 1], masks=dst[b:b + 1],
-                            results=p_res)
-                pev[b][1].record(stream)
-            torch.cuda.synchronize()
-            ms = [a.elapsed_time(c) for a, c in pev]
-            lat += ms
-            plain_total += sum(ms)
-        plain = {"frames_per_s": B * reps / (plain_total / 1e3),
-                 "p50_ms_per_frame": float(np.percentile(lat, 50)),
-                 "p99_ms_per_frame": float(np.percentile(lat, 99)),
-                 "launches_per_frame": 3}
+        plain = plain_leg(ca, p, list(d_frames_all[0]), keys, list(d_masks_all[0]), stream,
+                          max(1, min(args.steps, 3)))
 
     # ---- end to end through the C ABI on host buffers (copies inside)
     e2e = None
@@ -294,32 +376,42 @@ def run_ours(args):
             el = float(t.item())
         e2e = {"value": B * e_steps * world / el, "unit": "frames/s",
                "h2d_bytes_per_step": B * H * W * 3, "d2h_bytes_per_step": B * (H * W + 24),
-               "ms_per_step": 1e3 * el / e_steps}
+               "ms_per_step": 1e3 * el / e_steps, "call": "ca_run_host (pinned host buffers)"}
         same = np.array_equal(h_masks.numpy(), m_host) and \
             h_res.numpy().tobytes() == res_host.tobytes()
         e2e["matches_device_path"] = bool(same)
+
+    batching = None
+    if mixed is not None:
+        batching = batching_leg(ca, mixed, p, stream, max(5, min(args.steps, 20)), args.warmup)
     clk = clocks.stop()
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline: the step is one fused kernel per graph launch
+    hbm_peak, peak_kind = peaks()
     abytes = algorithmic_bytes(B, H, W, WORKLOAD["n_strips"], WORKLOAD["cands_per_strip"])
+    step_bytes = abytes["fused"]
+    ms_per_step = total_ms / args.steps
+    fused = tuning["batch_mode"] == 2
+    dom = "fused" if fused else "mask"
     kern = {}
     for name, (ms, cnt) in ktimes.items():
         if cnt:
             avg = ms / cnt
             kern[name] = {"ms_per_launch": avg, "launches": cnt,
-                          "share": ms / max(1e-9, sum(v[0] for v in ktimes.values())),
                           "algorithmic_bytes": abytes[name],
-                          "GBps": abytes[name] / (avg / 1e3) / 1e9}
-    hbm_peak, peak_kind = peaks()
-    hbm_kernels = {k: v for k, v in kern.items() if k in ("strips", "mask")}
-    dom = max(hbm_kernels, key=lambda k: hbm_kernels[k]["ms_per_launch"])
-    for v in kern.values():
-        v["hbm_frac"] = v["GBps"] / hbm_peak
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": hbm_peak,
-                "unit": "GB/s", "frac": kern[dom]["GBps"] / hbm_peak, "peak_kind": peak_kind,
-                "traffic": kernel_traffic(dom)}
-    step_bytes = sum(abytes.values())
-    ms_per_step = total_ms / args.steps
+                          "GBps": abytes[name] / (avg / 1e3) / 1e9,
+                          "hbm_frac": abytes[name] / (avg / 1e3) / 1e9 / hbm_peak,
+                          "launch": "staged (three kernels)"}
+    step_gbps = step_bytes / (ms_per_step / 1e3) / 1e9
+    if fused:
+        kern["fused"] = {"ms_per_launch": ms_per_step, "launches": args.steps,
+                         "algorithmic_bytes": step_bytes, "GBps": step_gbps,
+                         "hbm_frac": step_gbps / hbm_peak,
+                         "launch": "one k_batch per graph launch (events around each launch)"}
+    roofline = {"bound": "hbm", "kernel": "k_batch" if fused else "k_mask",
+                "achieved": kern[dom]["GBps"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": kern[dom]["GBps"] / hbm_peak, "peak_kind": peak_kind,
+                "traffic": kernel_traffic("k_batch" if fused else "k_mask")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -336,23 +428,28 @@ def run_ours(args):
         "config": {"workload": WORKLOAD["name"], "frames_per_step": B, "H": H, "W": W,
                    "n_strips": WORKLOAD["n_strips"], "cands_per_strip": WORKLOAD["cands_per_strip"],
                    "n_hyps": WORKLOAD["n_hyps"],
+                   "step": "one graph launch of a captured plan (ca_plan_launch)",
+                   "launch": {k: tuning[k] for k in ("batch_mode", "hyp_threads", "wave_frames")},
                    "l2": "no flush: steps rotate over %d resident copies of the batch "
                          "(%.2f GB of inputs > 129 MB L2)" % (ROTATE_INPUTS,
                                                               ROTATE_INPUTS * B * H * W * 3 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk,
-        "step": {"algorithmic_bytes": step_bytes,
-                 "hbm_frac": step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak,
+        "step": {"algorithmic_bytes": step_bytes, "hbm_frac": step_gbps / hbm_peak,
                  "p50_ms": float(np.percentile(step_ms, 50)),
                  "p99_ms": float(np.percentile(step_ms, 99)),
                  "ms_per_frame": ms_per_step / B},
-        "kernels": kern, "plain": plain,
+        "tuning": tuning, "kernels": kern,
+        "staged": {"ms_per_call": staged_ms / staged_steps, "results_equal": bool(same_staged)},
+        "plain": plain, "batching": batching,
         "accuracy": {"vs": "generator ground truth", **acc},
         "paper_context": PAPER_CONTEXT,
     }
     if rank == 0:
         print(json.dumps(out))
+    for pl in plans:
+        pl.close()
     ca.close()
     if world > 1:
         dist.destroy_process_group()

@@ -60,6 +60,11 @@ enum { CA_NORM_2N = 0, CA_NORM_NK = 1, CA_NORM_RAW = 2 };
 /* edge scorer: handcrafted (Sec. 2.2.3), learned 1-D CNN, or learned with the
  * handcrafted score taking over half-strips the network is unsure about */
 enum { CA_SCORER_HAND = 0, CA_SCORER_LEARNED = 1, CA_SCORER_LEARNED_FALLBACK = 2 };
+/* how a call is launched (results never depend on it): AUTO = the fastest
+ * configuration ca_tune found for this shape of batch, else a size-based
+ * choice; STAGED = three kernels (strips, fit, mask); FUSED = one persistent
+ * kernel that runs all three phases, frames pipelined in waves */
+enum { CA_BATCH_AUTO = 0, CA_BATCH_STAGED = 1, CA_BATCH_FUSED = 2 };
 
 /* Parameters; ca_params_default() fills the values of the paper's Appendix A. */
 typedef struct ca_params {
@@ -85,6 +90,9 @@ typedef struct ca_params {
     int32_t hyp_threads;     /* threads per RANSAC hypothesis: 0 = chosen per call
                                 from the work size, or 1, 2, 4, 8; results do not
                                 depend on it */
+    int32_t batch_mode;      /* CA_BATCH_* (results do not depend on it) */
+    int32_t wave_frames;     /* fused launch: frames per pipeline wave, 0 = chosen
+                                per call (results do not depend on it) */
     uint64_t seed;           /* key of the RANSAC random stream */
 } ca_params;
 
@@ -163,10 +171,52 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
  *   - Errors: a status only (there is no handle for ca_last_error). */
 #define CA_STATIC_MAX_FRAMES 256
 #define CA_STATIC_MAX_HYPS 4096
-#define CA_STATIC_SCRATCH_BYTES 704512
+#define CA_STATIC_SCRATCH_BYTES 706560
 ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H, int W, const uint64_t *keys,
                              const ca_params *p, ca_result *out_dev, uint8_t *masks_dev,
                              void *stream);
+
+/* ---- Batching: autotuner and captured plans (no counterpart in the paper,
+ * which runs one frame per launch, Sec. 2.2.6). */
+
+/* Outcome of ca_tune.  Times are mean milliseconds per call on the tuning
+ * batch, measured with CUDA events on the call's stream. */
+typedef struct ca_tuning {
+    int32_t batch_mode;   /* chosen CA_BATCH_STAGED or CA_BATCH_FUSED */
+    int32_t hyp_threads;  /* chosen threads per hypothesis */
+    int32_t wave_frames;  /* chosen frames per wave (fused) */
+    int32_t n_tried;      /* configurations timed */
+    float ms;             /* chosen configuration */
+    float ms_staged;      /* fastest staged configuration */
+    float ms_fused;       /* fastest fused configuration */
+    float ms_untuned;     /* the configuration CA_BATCH_AUTO used before tuning */
+} ca_tuning;
+
+/* Autotuner.  Runs the batch (arguments as in ca_estimate) under every launch
+ * configuration that leaves the results unchanged -- staged or fused launch,
+ * 1/2/4/8 threads per hypothesis, and for the fused launch the frames per
+ * wave -- times each, and remembers the fastest for later CA_BATCH_AUTO calls
+ * on batches of the same shape (B, the list of resolutions, N, K, hypotheses,
+ * hypothesis mode, which frames have masks).  Synchronous; overwrites out_dev
+ * and the masks; *out (may be NULL) receives the outcome.  The parameters
+ * that do change results (N, K, hypotheses) are the caller's to choose. */
+ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                  ca_result *out_dev, void *stream, ca_tuning *out);
+
+/* A captured estimate: the launch(es) of one batch -- fixed frame buffers,
+ * masks, keys, parameters and output -- recorded once in a CUDA graph with
+ * the plan's own tables, descriptors and workspace, then replayed by
+ * ca_plan_launch as a single graph launch.  New frame contents are picked up
+ * by each launch; changing a pointer, key or parameter needs a new plan.
+ * The plan records the handle's launch configuration (tuned or explicit) at
+ * creation.  Launches of one plan must not overlap on the GPU (they share
+ * the plan's workspace); different plans are independent.  The plan must be
+ * destroyed before its handle. */
+typedef struct ca_plan ca_plan;
+ca_status ca_plan_create(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                         ca_result *out_dev, ca_plan **out);
+ca_status ca_plan_launch(ca_plan *plan, void *stream);
+ca_status ca_plan_destroy(ca_plan *plan);
 
 /* Writes the content-area masks of B results (Sec. 1.1, Fig. 1): pixel (x, y)
  * is 1 iff (x-cx)^2 + (y-cy)^2 <= r^2 in binary32 (each operation rounded, no
@@ -185,7 +235,9 @@ ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, in
                       uint8_t *masks_host);
 
 /* Waits for `stream` and reports any asynchronous device error raised by the
- * handle's kernels (including a bounded wait that gave up). */
+ * handle's kernels: CA_ERR_CUDA, or CA_ERR_TIMEOUT when a bounded wait of the
+ * fused kernel gave up (its results are then not valid; the handle re-arms
+ * itself and stays usable). */
 ca_status ca_sync(ca_handle *h, void *stream);
 
 /* Debug capture of the intermediate values of subsequent calls: 0 = off,
@@ -223,9 +275,10 @@ uint64_t ca_launch_count(const ca_handle *h);
 ca_status ca_set_timing(ca_handle *h, int on);
 
 /* Sums of the recorded kernel durations in milliseconds since the last read:
- * ms[0] strip scoring, ms[1] circle fitting, ms[2] mask writing; counts[i] =
- * launches timed.  Waits for the recorded events, then clears them. */
-ca_status ca_kernel_times(ca_handle *h, double ms[3], int32_t counts[3]);
+ * ms[0] strip scoring, ms[1] circle fitting, ms[2] mask writing, ms[3] the
+ * fused kernel (all three phases); counts[i] = launches timed.  Waits for the
+ * recorded events, then clears them. */
+ca_status ca_kernel_times(ca_handle *h, double ms[4], int32_t counts[4]);
 
 const char *ca_status_string(ca_status s);
 const char *ca_last_error(const ca_handle *h);

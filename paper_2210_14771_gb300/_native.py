@@ -12,6 +12,7 @@ CA_HYP_RANDOM, CA_HYP_EXHAUSTIVE = 0, 1
 CA_NORM_2N, CA_NORM_NK, CA_NORM_RAW = 0, 1, 2
 CA_SCORER_HAND, CA_SCORER_LEARNED, CA_SCORER_LEARNED_FALLBACK = 0, 1, 2
 CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
+CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
 
 
@@ -23,13 +24,20 @@ class CaParams(C.Structure):
         ("t_cs", C.c_float), ("t_px", C.c_float), ("t_ri", C.c_float), ("r_min", C.c_float),
         ("r_max", C.c_float), ("d_max", C.c_float), ("sup_px", C.c_int32),
         ("hyp_mode", C.c_int32), ("score_norm", C.c_int32), ("sobel_norm", C.c_int32),
-        ("scorer_mode", C.c_int32), ("hyp_threads", C.c_int32), ("seed", C.c_uint64),
+        ("scorer_mode", C.c_int32), ("hyp_threads", C.c_int32), ("batch_mode", C.c_int32),
+        ("wave_frames", C.c_int32), ("seed", C.c_uint64),
     ]
 
 
 class CaFrame(C.Structure):
     _fields_ = [("rgb_dev", C.c_void_p), ("mask_dev", C.c_void_p), ("H", C.c_int32),
                 ("W", C.c_int32), ("pitch", C.c_int64), ("frame_key", C.c_uint64)]
+
+
+class CaTuning(C.Structure):
+    _fields_ = [("batch_mode", C.c_int32), ("hyp_threads", C.c_int32),
+                ("wave_frames", C.c_int32), ("n_tried", C.c_int32), ("ms", C.c_float),
+                ("ms_staged", C.c_float), ("ms_fused", C.c_float), ("ms_untuned", C.c_float)]
 
 
 class CaResult(C.Structure):
@@ -50,6 +58,12 @@ SIGNATURES = [
                                       C.c_void_p]),
     ("ca_estimate_static", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _P(C.c_uint64),
                                      _P(CaParams), C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ca_tune", C.c_int, [C.c_void_p, _P(CaFrame), C.c_int, _P(CaParams), C.c_void_p,
+                          C.c_void_p, _P(CaTuning)]),
+    ("ca_plan_create", C.c_int, [C.c_void_p, _P(CaFrame), C.c_int, _P(CaParams), C.c_void_p,
+                                 _P(C.c_void_p)]),
+    ("ca_plan_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("ca_plan_destroy", C.c_int, [C.c_void_p]),
     ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,

@@ -73,8 +73,12 @@ class ContentArea:
         h = C.c_void_p()
         N.check(N.lib().ca_create(C.byref(h), device))
         self._h = h
+        self._plans = []
 
     def close(self):
+        for pl in getattr(self, "_plans", []):
+            pl.close()
+        self._plans = []
         if getattr(self, "_h", None):
             N.lib().ca_destroy(self._h)
             self._h = None
@@ -115,6 +119,13 @@ class ContentArea:
                 C.c_void_p(results.data_ptr()),
                 C.c_void_p(masks.data_ptr()) if masks is not None else None, st))
             return results, masks
+        arr, B, masks, results = self._descriptors(frames, keys, masks, results)
+        self._check(N.lib().ca_estimate(self._h, arr, B, C.byref(p),
+                                        C.c_void_p(results.data_ptr()), st))
+        return results, masks
+
+    def _descriptors(self, frames, keys, masks, results):
+        """ca_frame array for a list of (H, W, 3) uint8 CUDA tensors."""
         frames = list(frames)
         B = len(frames)
         if masks is True:
@@ -126,13 +137,42 @@ class ContentArea:
             assert f.dtype == torch.uint8 and f.is_cuda and f.dim() == 3 and f.shape[2] == 3
             assert f.stride(2) == 1 and f.stride(1) == 3
             arr[i].rgb_dev = f.data_ptr()
-            arr[i].mask_dev = masks[i].data_ptr() if masks is not None else None
+            arr[i].mask_dev = (masks[i].data_ptr() if masks is not None and masks[i] is not None
+                               else None)
             arr[i].H, arr[i].W = int(f.shape[0]), int(f.shape[1])
             arr[i].pitch = int(f.stride(0))
             arr[i].frame_key = int(keys[i]) if keys is not None else i
-        self._check(N.lib().ca_estimate(self._h, arr, B, C.byref(p),
-                                        C.c_void_p(results.data_ptr()), st))
-        return results, masks
+        return arr, B, masks, results
+
+    # ------------------------------------------------------------ batching --
+    def tune(self, frames, p=None, keys=None, masks=None, results=None, stream=None) -> dict:
+        """ca_tune: time the result-preserving launch configurations on this
+        batch (list of (H, W, 3) tensors) and remember the fastest."""
+        p = p or params()
+        if isinstance(frames, torch.Tensor):
+            frames = list(frames)
+            if isinstance(masks, torch.Tensor):
+                masks = list(masks)
+        arr, B, masks, results = self._descriptors(frames, keys, masks, results)
+        t = N.CaTuning()
+        self._check(N.lib().ca_tune(self._h, arr, B, C.byref(p), C.c_void_p(results.data_ptr()),
+                                    _stream_ptr(stream, self.device), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in N.CaTuning._fields_}
+
+    def plan(self, frames, p=None, keys=None, masks=None, results=None) -> "Plan":
+        """ca_plan_create: capture the estimate of this batch in a CUDA graph."""
+        p = p or params()
+        if isinstance(frames, torch.Tensor):
+            frames = list(frames)
+            if isinstance(masks, torch.Tensor):
+                masks = list(masks)
+        arr, B, masks, results = self._descriptors(frames, keys, masks, results)
+        h = C.c_void_p()
+        self._check(N.lib().ca_plan_create(self._h, arr, B, C.byref(p),
+                                           C.c_void_p(results.data_ptr()), C.byref(h)))
+        pl = Plan(self, h, frames, masks, results)
+        self._plans.append(pl)
+        return pl
 
     def mask(self, results: torch.Tensor, sizes, masks=None, stream=None):
         """Content-area masks of results (Sec. 1.1): sizes = [(H, W), ...]."""
@@ -177,10 +217,10 @@ class ContentArea:
 
     def kernel_times(self):
         """{kernel: (total ms, launches)} since the last read (CUDA events)."""
-        ms = (C.c_double * 3)()
-        cnt = (C.c_int32 * 3)()
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int32 * 4)()
         self._check(N.lib().ca_kernel_times(self._h, ms, cnt))
-        return {name: (ms[i], cnt[i]) for i, name in enumerate(("strips", "fit", "mask"))}
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(("strips", "fit", "mask", "fused"))}
 
     # --------------------------------------------------------------- debug --
     def set_debug(self, level: int):
@@ -216,3 +256,27 @@ class ContentArea:
         u16 = raw[:2 * (N.LUT_G + N.LUT_T + N.LUT_I)].view(np.uint16)
         rows = raw[2 * (N.LUT_G + N.LUT_T + N.LUT_I):].view(np.int32)
         return (u16[:N.LUT_G], u16[N.LUT_G:N.LUT_G + N.LUT_T], u16[N.LUT_G + N.LUT_T:], rows)
+
+
+class Plan:
+    """A captured estimate (ca_plan): `launch()` replays one CUDA graph.  Holds
+    references to the frames, masks and results it was captured with."""
+
+    def __init__(self, owner: ContentArea, h, frames, masks, results):
+        self.owner, self._h = owner, h
+        self.frames, self.masks, self.results = frames, masks, results
+
+    def launch(self, stream=None):
+        self.owner._check(N.lib().ca_plan_launch(self._h, _stream_ptr(stream, self.owner.device)))
+        return self.results, self.masks
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().ca_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

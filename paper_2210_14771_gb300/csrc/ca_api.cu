@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -23,6 +24,13 @@ struct Staging {
     size_t cap = 0;
     cudaEvent_t ev = nullptr;
     bool used = false;
+};
+
+// How one call is launched (results do not depend on it).
+struct LaunchCfg {
+    int mode = CA_BATCH_STAGED;   // CA_BATCH_STAGED or CA_BATCH_FUSED
+    int T = 1;                    // threads per hypothesis
+    int wave = 1;                 // fused: frames per wave
 };
 
 struct LutKey {
@@ -74,10 +82,25 @@ struct ca_handle {
     int strip_blocks_per_sm = 0;
     size_t strip_blocks_smem = 0;
 
-    // kernel timing: event pairs per kernel kind (0 strips, 1 fit, 2 mask)
+    // kernel timing: event pairs per kernel kind (0 strips, 1 fit, 2 mask, 3 fused)
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[3];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[4];
+
+    // launch configurations found by ca_tune, by shape of batch
+    std::map<uint64_t, LaunchCfg> tuned;
+    // live plans (their fused-kernel error words are read by ca_sync)
+    std::set<ca_plan *> plans;
+};
+
+struct ca_plan {
+    ca_handle *h = nullptr;
+    uint16_t *d_luts = nullptr;
+    void *d_block = nullptr;
+    Workspace ws;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;   // kernel launches per replay
 };
 
 namespace {
@@ -261,6 +284,8 @@ ca_status ensure_workspace(ca_handle *h, int B, int n_tiles, size_t hyp_records)
         if ((st = grow(h, &h->ws.done, 0, (size_t)nb, true)) != CA_OK) return st;
         if ((st = grow(h, &h->ws.n_hyps, 0, (size_t)nb, true)) != CA_OK) return st;
         if ((st = grow(h, &h->ws.n_cands, 0, (size_t)nb, true)) != CA_OK) return st;
+        if ((st = grow(h, &h->ws.sync, 0, sync_words(nb), true)) != CA_OK) return st;
+        h->ws.sync_frames = nb;
         h->ws_frames = nb;
         h->ws_tiles = 0;   // force tiles realloc with the new frame count
     }
@@ -296,6 +321,18 @@ ca_status take_staging(ca_handle *h, size_t bytes, Staging **out) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Hypotheses per frame: n_hyps, or every triple of N*K slots in exhaustive mode.
+long long hyps_per_frame(const ca_params &p) {
+    if (p.hyp_mode == CA_HYP_EXHAUSTIVE) {
+        const long long nk = (long long)p.n_strips * p.cands_per_strip;
+        return std::max(1LL, nk * (nk - 1) * (nk - 2) / 6);
+    }
+    return p.n_hyps;
+}
+
+// Bound on each wait of the fused kernel (ns); waits normally last microseconds.
+constexpr uint64_t kWaitNs = 2000000000ull;
+
 ca_status ensure_luts(ca_handle *h, const ca_params &p, cudaStream_t stream) {
     LutKey k;
     k.t_g = p.t_g; k.t_theta = p.t_theta_deg; k.t_iota = p.t_iota; k.sobel_norm = p.sobel_norm;
@@ -329,7 +366,7 @@ ca_status mark_last(ca_handle *h, cudaStream_t stream) {
     return CA_OK;
 }
 
-DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int B) {
+DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T) {
     DevParams P;
     std::memset(&P, 0, sizeof(P));
     P.N = p.n_strips;
@@ -346,15 +383,10 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int B) 
     P.score_den = 32768.0 * norm;
     P.qg_sat = h->qg_sat;
     P.io_cut = iota_cut(h->li_host, P.T_ps);
-    long long nh = p.n_hyps;
-    if (p.hyp_mode == CA_HYP_EXHAUSTIVE) {
-        const long long nk = (long long)P.N * P.K;
-        nh = std::max(1LL, nk * (nk - 1) * (nk - 2) / 6);
-    }
-    P.NH = (int)nh;
-    P.hyp_threads = choose_hyp_threads(p.hyp_threads, B, nh, h->sm_count);
+    P.NH = (int)hyps_per_frame(p);
+    P.hyp_threads = T;
     const long long per_tile = kHypTile / P.hyp_threads;
-    P.n_tiles = (int)((nh + per_tile - 1) / per_tile);
+    P.n_tiles = (int)((P.NH + per_tile - 1) / per_tile);
     P.t_ri = p.t_ri;
     P.r_min = p.r_min;
     P.r_max = p.r_max;
@@ -364,35 +396,74 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int B) 
     return P;
 }
 
-// Shared by ca_estimate and ca_mask: one staging block with the frame table,
-// the strip-row tables and the mask-unit prefix.
+// FNV-1a hash of what the launch configuration of a call may depend on.
+uint64_t shape_key(const ca_frame *frames, int B, const ca_params &p) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            x ^= (v >> (8 * i)) & 0xff;
+            x *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)B);
+    mix((uint64_t)p.n_strips);
+    mix((uint64_t)p.cands_per_strip);
+    mix((uint64_t)hyps_per_frame(p));
+    mix((uint64_t)p.refine_iters);
+    for (int i = 0; i < B; ++i)
+        mix(((uint64_t)frames[i].H << 32) | ((uint64_t)frames[i].W << 1) | (frames[i].mask_dev != nullptr));
+    return x;
+}
+
+int default_wave(const ca_handle *h, int B, const ca_params &p, int T) {
+    // about two resident CTAs' worth of strip items per wave
+    DevParams P{};
+    P.N = p.n_strips;
+    P.K = p.cands_per_strip;
+    const int spf = strip_items_of(p.n_strips, p.cands_per_strip);
+    const int resident = h->sm_count * 4;
+    (void)T;
+    return std::max(1, std::min(B, (2 * resident + spf - 1) / spf));
+}
+
+// Launch configuration of a call: explicit fields of p first, then what
+// ca_tune found for this shape, then the defaults.
+LaunchCfg choose_cfg(const ca_handle *h, const ca_frame *frames, int B, const ca_params &p) {
+    LaunchCfg c;
+    const LaunchCfg *t = nullptr;
+    if (p.batch_mode == CA_BATCH_AUTO) {
+        auto it = h->tuned.find(shape_key(frames, B, p));
+        if (it != h->tuned.end()) t = &it->second;
+    }
+    c.mode = p.batch_mode != CA_BATCH_AUTO ? p.batch_mode : t ? t->mode : CA_BATCH_STAGED;
+    c.T = p.hyp_threads ? p.hyp_threads
+        : (t && t->mode == c.mode) ? t->T
+        : choose_hyp_threads(0, B, hyps_per_frame(p), h->sm_count);
+    c.wave = p.wave_frames > 0 ? std::min(p.wave_frames, B)
+           : (t && t->mode == c.mode) ? t->wave : default_wave(h, B, p, c.T);
+    return c;
+}
+
+// Host image of a call's descriptor block: frames | strip rows | segments.
 struct CallBlock {
-    DevFrame *d_frames;
-    int32_t *d_rows;
-    int total_units;
-    int max_w;
+    std::vector<unsigned char> host;
+    size_t off_rows = 0, off_segs = 0;
+    int total_units = 0, n_segs = 0, total_items = 0;
 };
 
-ca_status upload_frames(ca_handle *h, const ca_frame *frames, int B, int N, float alpha,
-                        cudaStream_t stream, CallBlock *cb) {
+void build_block(const ca_frame *frames, int B, int N, float alpha, const DevParams *P,
+                 const LaunchCfg &cfg, CallBlock &cb) {
     // distinct heights -> one strip-row table each
     std::map<int, int> row_off;
     int n_rows = 0;
     if (N > 0)
         for (int i = 0; i < B; ++i)
             if (!row_off.count(frames[i].H)) { row_off[frames[i].H] = n_rows; n_rows += N; }
-    const size_t off_rows = align_up(sizeof(DevFrame) * B, 256);
-    const size_t bytes = off_rows + sizeof(int32_t) * std::max(n_rows, 1);
-    Staging *s;
-    ca_status st = take_staging(h, bytes, &s);
-    if (st != CA_OK) return st;
-    DevFrame *hf = (DevFrame *)s->host;
-    int32_t *hr = (int32_t *)((char *)s->host + off_rows);
-    for (auto &kv : row_off) strip_rows(kv.first, N, alpha, hr + kv.second);
-    int units = 0, max_w = 0;
+    std::vector<DevFrame> df((size_t)B);
+    int units = 0, mitems = 0;
     for (int i = 0; i < B; ++i) {
         const ca_frame &f = frames[i];
-        DevFrame d;
+        DevFrame &d = df[i];
         std::memset(&d, 0, sizeof(d));
         d.rgb = f.rgb_dev;
         d.mask = f.mask_dev;
@@ -402,20 +473,49 @@ ca_status upload_frames(ca_handle *h, const ca_frame *frames, int B, int N, floa
         d.W = f.W;
         d.rows_off = N > 0 ? row_off[f.H] : 0;
         d.unit_off = units;
+        d.mitem_off = mitems;
         d.vec_ok = ((uintptr_t)f.rgb_dev % 16 == 0) && (f.pitch % 16 == 0) && (f.W % 16 == 0);
         d.mask_vec_ok = f.mask_dev && ((uintptr_t)f.mask_dev % 16 == 0) && (f.W % 16 == 0);
-        if (f.mask_dev) units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
-        max_w = std::max(max_w, f.W);
-        hf[i] = d;
+        if (f.mask_dev) {
+            units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
+            mitems += mask_items_of(f.H);
+        }
     }
-    CA_CUDA(h, cudaMemcpyAsync(s->dev, s->host, bytes, cudaMemcpyHostToDevice, stream));
-    CA_CUDA(h, cudaEventRecord(s->ev, stream));
-    s->used = true;
-    cb->d_frames = (DevFrame *)s->dev;
-    cb->d_rows = (int32_t *)((char *)s->dev + off_rows);
-    cb->total_units = units;
-    cb->max_w = max_w;
-    return CA_OK;
+    // fused launch: software pipeline over waves of frames -- step t holds the
+    // strips of wave t, the fit of wave t-1 and the masks of wave t-2
+    std::vector<BatchSeg> segs;
+    int items = 0;
+    if (P && cfg.mode == CA_BATCH_FUSED) {
+        const int wave = std::max(1, cfg.wave);
+        const int nw = (B + wave - 1) / wave;
+        const int spf = strip_items_of(P->N, P->K);
+        auto add = [&](int phase, int w) {
+            const int f0 = w * wave, f1 = std::min(B, f0 + wave);
+            int cnt = 0;
+            if (phase == kPhaseStrips) cnt = (f1 - f0) * spf;
+            else if (phase == kPhaseFit) cnt = (f1 - f0) * P->n_tiles;
+            else cnt = (f1 < B ? df[f1].mitem_off : mitems) - df[f0].mitem_off;
+            if (cnt <= 0) return;
+            segs.push_back(BatchSeg{items, phase, f0, f1});
+            items += cnt;
+        };
+        for (int t = 0; t < nw + 2; ++t) {
+            if (t < nw) add(kPhaseStrips, t);
+            if (t >= 1 && t - 1 < nw) add(kPhaseFit, t - 1);
+            if (t >= 2 && t - 2 < nw) add(kPhaseMask, t - 2);
+        }
+    }
+    cb.off_rows = align_up(sizeof(DevFrame) * B, 256);
+    cb.off_segs = align_up(cb.off_rows + sizeof(int32_t) * std::max(n_rows, 1), 256);
+    const size_t bytes = cb.off_segs + sizeof(BatchSeg) * std::max<size_t>(segs.size(), 1);
+    cb.host.assign(bytes, 0);
+    std::memcpy(cb.host.data(), df.data(), sizeof(DevFrame) * B);
+    int32_t *hr = (int32_t *)(cb.host.data() + cb.off_rows);
+    for (auto &kv : row_off) strip_rows(kv.first, N, alpha, hr + kv.second);
+    if (!segs.empty()) std::memcpy(cb.host.data() + cb.off_segs, segs.data(), sizeof(BatchSeg) * segs.size());
+    cb.total_units = units;
+    cb.n_segs = (int)segs.size();
+    cb.total_items = items;
 }
 
 int mask_grid(const ca_handle *h, int units) {
@@ -451,25 +551,9 @@ void time_end(ca_handle *h, int kind, cudaEvent_t begin, cudaStream_t s) {
     h->timed[kind].emplace_back(begin, e);
 }
 
-ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
-                        ca_result *out_dev, cudaStream_t stream) {
-    ca_status st = check_params(h, p);
-    if (st != CA_OK) return st;
-    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
-    if (B == 0) return CA_OK;
-    if (!frames || !out_dev) return fail(h, CA_ERR_INVALID_ARG, "frames or out_dev is NULL");
-    for (int i = 0; i < B; ++i)
-        if ((st = check_frame(h, frames[i], i)) != CA_OK) return st;
-    CA_CUDA(h, cudaSetDevice(h->device));
-    if ((st = order_after_last(h, stream)) != CA_OK) return st;
-    if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
-    CallBlock cb;
-    if ((st = upload_frames(h, frames, B, p->n_strips, p->alpha, stream, &cb)) != CA_OK) return st;
-    const DevParams P = make_params(h, *p, cb.max_w, B);
-    const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
-    if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
-
-    // strips: enough CTAs to fill the GPU, each CTA loops over strips
+// Shared-memory attributes and occupancies the launches need, set outside
+// any stream capture.
+ca_status prepare_kernels(ca_handle *h, const DevParams &P, const LaunchCfg &cfg, int *grid_out) {
     const size_t smem = strips_smem_bytes(P);
     if (h->strip_blocks_smem != smem) {
         int nb = 0;
@@ -478,29 +562,120 @@ ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_pa
         h->strip_blocks_per_sm = std::max(1, nb);
         h->strip_blocks_smem = smem;
     }
-    // one half-strip per quad of warps (K = 2) or per warp (K > 2); CTAs beyond
-    // the resident ones wait for a free slot, which balances uneven half-strips
+    *grid_out = 0;
+    if (cfg.mode == CA_BATCH_FUSED)
+        *grid_out = h->sm_count * batch_blocks_per_sm(P.hyp_threads, batch_smem_bytes(P));
+    return CA_OK;
+}
+
+// Queues the kernels of one call.  `timed`: record kernel events.
+ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32_t *d_rows,
+                      const BatchSeg *d_segs, const CallBlock &cb, const DevParams &P,
+                      const LaunchCfg &cfg, int fused_grid, const uint16_t *d_luts,
+                      const Workspace &ws, ca_result *out, cudaStream_t stream, bool timed,
+                      int *kernels) {
+    cudaError_t e;
+    *kernels = 0;
+    if (cfg.mode == CA_BATCH_FUSED) {
+        const int grid = std::max(1, std::min(fused_grid, cb.total_items));
+        cudaEvent_t t0 = timed ? time_begin(h, stream) : nullptr;
+        e = launch_batch(d_frames, B, d_rows, P, d_luts, ws, out, d_segs, cb.n_segs,
+                         cb.total_items, grid, kWaitNs, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_batch launch");
+        time_end(h, 3, t0, stream);
+        *kernels = 1;
+        return CA_OK;
+    }
+    // strips: one half-strip per quad of warps (K = 2) or per warp (K > 2);
+    // CTAs beyond the resident ones wait for a free slot, which balances
+    // uneven half-strips
     const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
-    cudaEvent_t t0 = time_begin(h, stream);
-    cudaError_t e = launch_strips(cb.d_frames, B, cb.d_rows, P, h->d_luts, h->ws.slots, sgrid, stream);
+    cudaEvent_t t0 = timed ? time_begin(h, stream) : nullptr;
+    e = launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
     time_end(h, 0, t0, stream);
-    t0 = time_begin(h, stream);
-    e = launch_fit(cb.d_frames, B, P, h->ws.slots, h->ws, out_dev, stream);
+    t0 = timed ? time_begin(h, stream) : nullptr;
+    e = launch_fit(d_frames, B, P, ws.slots, ws, out, stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_fit launch");
     time_end(h, 1, t0, stream);
-    h->launches += 2;
+    *kernels = 2;
     if (cb.total_units > 0) {
-        t0 = time_begin(h, stream);
-        e = launch_mask(cb.d_frames, B, out_dev, cb.total_units, mask_grid(h, cb.total_units), stream);
+        t0 = timed ? time_begin(h, stream) : nullptr;
+        e = launch_mask(d_frames, B, out, cb.total_units, mask_grid(h, cb.total_units), stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "k_mask launch");
         time_end(h, 2, t0, stream);
-        h->launches += 1;
+        *kernels = 3;
     }
+    return CA_OK;
+}
+
+ca_status check_call(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                     const void *out_dev) {
+    ca_status st = check_params(h, p);
+    if (st != CA_OK) return st;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return CA_OK;
+    if (!frames || !out_dev) return fail(h, CA_ERR_INVALID_ARG, "frames or out_dev is NULL");
+    for (int i = 0; i < B; ++i)
+        if ((st = check_frame(h, frames[i], i)) != CA_OK) return st;
+    if (p->batch_mode < CA_BATCH_AUTO || p->batch_mode > CA_BATCH_FUSED)
+        return fail(h, CA_ERR_INVALID_ARG, "bad batch_mode %d", p->batch_mode);
+    if (p->wave_frames < 0) return fail(h, CA_ERR_INVALID_ARG, "wave_frames < 0");
+    if (p->batch_mode == CA_BATCH_FUSED && h->debug > 0 && false)
+        return fail(h, CA_ERR_INVALID_ARG, "unreachable");
+    return CA_OK;
+}
+
+ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                       ca_result *out_dev, cudaStream_t stream, const LaunchCfg &cfg) {
+    CA_CUDA(h, cudaSetDevice(h->device));
+    ca_status st;
+    if ((st = order_after_last(h, stream)) != CA_OK) return st;
+    if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
+    int max_w = 0;
+    for (int i = 0; i < B; ++i) max_w = std::max(max_w, frames[i].W);
+    const DevParams P = make_params(h, *p, max_w, cfg.T);
+    CallBlock cb;
+    build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb);
+    Staging *sg;
+    if ((st = take_staging(h, cb.host.size(), &sg)) != CA_OK) return st;
+    std::memcpy(sg->host, cb.host.data(), cb.host.size());
+    CA_CUDA(h, cudaMemcpyAsync(sg->dev, sg->host, cb.host.size(), cudaMemcpyHostToDevice, stream));
+    CA_CUDA(h, cudaEventRecord(sg->ev, stream));
+    sg->used = true;
+    const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
+    if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
+    int fgrid = 0;
+    if ((st = prepare_kernels(h, P, cfg, &fgrid)) != CA_OK) return st;
+    const unsigned char *dev = (const unsigned char *)sg->dev;
+    int k = 0;
+    st = launch_call(h, (const DevFrame *)dev, B, (const int32_t *)(dev + cb.off_rows),
+                     (const BatchSeg *)(dev + cb.off_segs), cb, P, cfg, fgrid, h->d_luts, h->ws,
+                     out_dev, stream, true, &k);
+    if (st != CA_OK) return st;
+    h->launches += k;
     h->last_B = B;
     h->last_NK = P.N * P.K;
     h->last_hyp_stride = P.NH;
     return mark_last(h, stream);
+}
+
+ca_status estimate_impl(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                        ca_result *out_dev, cudaStream_t stream) {
+    ca_status st = check_call(h, frames, B, p, out_dev);
+    if (st != CA_OK || B == 0) return st;
+    return estimate_cfg(h, frames, B, p, out_dev, stream, choose_cfg(h, frames, B, *p));
+}
+
+// Reads (and clears) the fused kernel's error word of a workspace.
+ca_status check_sync_word(ca_handle *h, const Workspace &ws) {
+    if (!ws.sync) return CA_OK;
+    uint32_t err = 0;
+    CA_CUDA(h, cudaMemcpy(&err, ws.sync + 2, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err == 0) return CA_OK;
+    // a wait gave up: the counters of that call are inconsistent; re-arm all
+    CA_CUDA(h, cudaMemset(ws.sync, 0, sizeof(uint32_t) * sync_words(ws.sync_frames)));
+    return fail(h, CA_ERR_TIMEOUT, "a wait of the fused kernel gave up (flags 0x%x)", err);
 }
 
 }  // namespace
@@ -562,6 +737,7 @@ ca_status ca_create(ca_handle **out, int device) {
 
 ca_status ca_destroy(ca_handle *h) {
     if (!h) return CA_ERR_INVALID_ARG;
+    if (!h->plans.empty()) return fail(h, CA_ERR_STATE, "destroy the handle's plans first");
     cudaSetDevice(h->device);
     if (h->has_last) cudaEventSynchronize(h->last_ev);
     for (auto &s : h->ring) {
@@ -578,6 +754,7 @@ ca_status ca_destroy(ca_handle *h) {
     cudaFree(h->ws.hyps);
     cudaFree(h->ws.n_hyps);
     cudaFree(h->ws.n_cands);
+    cudaFree(h->ws.sync);
     cudaFree(h->e2e_frames);
     cudaFree(h->e2e_masks);
     cudaFree(h->e2e_res);
@@ -618,6 +795,195 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
     return estimate_impl(h, fr.data(), B, p, out_dev, (cudaStream_t)stream);
 }
 
+ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                  ca_result *out_dev, void *stream, ca_tuning *out) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    ca_status st = check_call(h, frames, B, p, out_dev);
+    if (st != CA_OK) return st;
+    if (B == 0) return fail(h, CA_ERR_INVALID_ARG, "nothing to tune (B = 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    ca_params q = *p;
+    q.batch_mode = CA_BATCH_AUTO;
+    const uint64_t key = shape_key(frames, B, q);
+    h->tuned.erase(key);
+    const LaunchCfg untuned = choose_cfg(h, frames, B, q);
+    std::vector<LaunchCfg> cands;
+    const int Ts[4] = {1, 2, 4, 8};
+    for (int T : Ts) cands.push_back(LaunchCfg{CA_BATCH_STAGED, T, 1});
+    for (int T : Ts) {
+        std::vector<int> waves;
+        for (int w = B; w >= 1; w = (w + 1) / 2) {
+            waves.push_back(w);
+            if (w == 1) break;
+        }
+        for (int w : waves) cands.push_back(LaunchCfg{CA_BATCH_FUSED, T, w});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CA_CUDA(h, cudaEventCreate(&e0));
+    CA_CUDA(h, cudaEventCreate(&e1));
+    const bool timing = h->timing;
+    h->timing = false;
+    auto time_cfg = [&](const LaunchCfg &c, float *ms) -> ca_status {
+        ca_status r = estimate_cfg(h, frames, B, &q, out_dev, s, c);   // warm-up
+        if (r != CA_OK) return r;
+        const int reps = 3;
+        CA_CUDA(h, cudaEventRecord(e0, s));
+        for (int i = 0; i < reps && r == CA_OK; ++i) r = estimate_cfg(h, frames, B, &q, out_dev, s, c);
+        if (r != CA_OK) return r;
+        CA_CUDA(h, cudaEventRecord(e1, s));
+        CA_CUDA(h, cudaEventSynchronize(e1));
+        float t = 0.0f;
+        CA_CUDA(h, cudaEventElapsedTime(&t, e0, e1));
+        *ms = t / reps;
+        return check_sync_word(h, h->ws);
+    };
+    ca_tuning res;
+    std::memset(&res, 0, sizeof(res));
+    res.ms_staged = res.ms_fused = 1e30f;
+    LaunchCfg best;
+    float best_ms = 1e30f;
+    for (const LaunchCfg &c : cands) {
+        float ms = 0.0f;
+        if ((st = time_cfg(c, &ms)) != CA_OK) break;
+        res.n_tried += 1;
+        if (c.mode == CA_BATCH_STAGED) res.ms_staged = std::min(res.ms_staged, ms);
+        else res.ms_fused = std::min(res.ms_fused, ms);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    float ms_u = 0.0f;
+    if (st == CA_OK) st = time_cfg(untuned, &ms_u);
+    h->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CA_OK) return st;
+    h->tuned[key] = best;
+    res.batch_mode = best.mode;
+    res.hyp_threads = best.T;
+    res.wave_frames = best.wave;
+    res.ms = best_ms;
+    res.ms_untuned = ms_u;
+    if (out) *out = res;
+    return CA_OK;
+}
+
+ca_status ca_plan_destroy(ca_plan *pl) {
+    if (!pl) return CA_ERR_INVALID_ARG;
+    ca_handle *h = pl->h;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    cudaFree(pl->d_luts);
+    cudaFree(pl->d_block);
+    cudaFree(pl->ws.slots);
+    cudaFree(pl->ws.tiles);
+    cudaFree(pl->ws.best);
+    cudaFree(pl->ws.done);
+    cudaFree(pl->ws.hyps);
+    cudaFree(pl->ws.n_hyps);
+    cudaFree(pl->ws.n_cands);
+    cudaFree(pl->ws.sync);
+    h->plans.erase(pl);
+    delete pl;
+    return CA_OK;
+}
+
+ca_status ca_plan_create(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                         ca_result *out_dev, ca_plan **out) {
+    if (!h || !out) return CA_ERR_INVALID_ARG;
+    *out = nullptr;
+    ca_status st = check_call(h, frames, B, p, out_dev);
+    if (st != CA_OK) return st;
+    if (B == 0) return fail(h, CA_ERR_INVALID_ARG, "empty plan (B = 0)");
+    if (h->debug) return fail(h, CA_ERR_STATE, "plans do not capture debug records");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    const LaunchCfg cfg = choose_cfg(h, frames, B, *p);
+    // tables of the plan's own (host-built as for any call)
+    std::vector<uint16_t> luts((size_t)kLutG + kLutT + kLutI), dev_tab(kDevTableU16);
+    int qg_sat = kLutG - 1;
+    build_luts(*p, luts.data(), &qg_sat);
+    pack_device_tables(luts.data(), qg_sat, dev_tab.data());
+    // make_params reads the handle's table state: point it at these tables
+    const int saved_qg = h->qg_sat;
+    uint16_t saved_li[kLutI];
+    std::memcpy(saved_li, h->li_host, sizeof(saved_li));
+    h->qg_sat = qg_sat;
+    std::memcpy(h->li_host, luts.data() + kLutG + kLutT, sizeof(h->li_host));
+    int max_w = 0;
+    for (int i = 0; i < B; ++i) max_w = std::max(max_w, frames[i].W);
+    const DevParams P = make_params(h, *p, max_w, cfg.T);
+    h->qg_sat = saved_qg;
+    std::memcpy(h->li_host, saved_li, sizeof(saved_li));
+    CallBlock cb;
+    build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb);
+
+    ca_plan *pl = new ca_plan();
+    pl->h = h;
+    h->plans.insert(pl);
+    auto bail = [&](ca_status r) {
+        ca_plan_destroy(pl);
+        return r;
+    };
+    auto cu = [&](cudaError_t e, const char *what) {
+        return e == cudaSuccess ? CA_OK : cuda_fail(h, e, what);
+    };
+    const size_t nb = (size_t)B;
+    if ((st = cu(cudaMalloc(&pl->d_luts, sizeof(uint16_t) * kDevTableU16), "plan tables")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->d_block, cb.host.size()), "plan block")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.slots, sizeof(CandSlot) * nb * kMaxSlots), "plan slots")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.tiles, sizeof(TileRec) * nb * P.n_tiles), "plan tiles")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.best, sizeof(unsigned long long) * nb), "plan best")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.done, sizeof(uint32_t) * nb), "plan done")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.n_hyps, sizeof(int32_t) * nb), "plan counts")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.n_cands, sizeof(int32_t) * nb), "plan counts")) != CA_OK ||
+        (st = cu(cudaMalloc(&pl->ws.sync, sizeof(uint32_t) * sync_words(B)), "plan sync")) != CA_OK)
+        return bail(st);
+    pl->ws.sync_frames = B;
+    if ((st = cu(cudaMemcpy(pl->d_luts, dev_tab.data(), sizeof(uint16_t) * kDevTableU16,
+                            cudaMemcpyHostToDevice), "plan tables")) != CA_OK ||
+        (st = cu(cudaMemcpy(pl->d_block, cb.host.data(), cb.host.size(), cudaMemcpyHostToDevice),
+                 "plan block")) != CA_OK ||
+        (st = cu(cudaMemset(pl->ws.best, 0, sizeof(unsigned long long) * nb), "plan")) != CA_OK ||
+        (st = cu(cudaMemset(pl->ws.done, 0, sizeof(uint32_t) * nb), "plan")) != CA_OK ||
+        (st = cu(cudaMemset(pl->ws.sync, 0, sizeof(uint32_t) * sync_words(B)), "plan")) != CA_OK)
+        return bail(st);
+    int fgrid = 0;
+    if ((st = prepare_kernels(h, P, cfg, &fgrid)) != CA_OK) return bail(st);
+    if (cfg.mode == CA_BATCH_STAGED) mask_grid(h, cb.total_units);   // occupancy query now
+    cudaStream_t cs = nullptr;
+    if ((st = cu(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "plan stream")) != CA_OK)
+        return bail(st);
+    const unsigned char *dev = (const unsigned char *)pl->d_block;
+    st = cu(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st == CA_OK) {
+        int k = 0;
+        st = launch_call(h, (const DevFrame *)dev, B, (const int32_t *)(dev + cb.off_rows),
+                         (const BatchSeg *)(dev + cb.off_segs), cb, P, cfg, fgrid, pl->d_luts,
+                         pl->ws, out_dev, cs, false, &k);
+        pl->kernels = k;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        pl->graph = g;
+        if (st == CA_OK) st = cu(e, "end capture");
+    }
+    cudaStreamDestroy(cs);
+    if (st == CA_OK)
+        st = cu(cudaGraphInstantiate(&pl->exec, pl->graph, 0), "graph instantiate");
+    if (st != CA_OK) return bail(st);
+    *out = pl;
+    return CA_OK;
+}
+
+ca_status ca_plan_launch(ca_plan *pl, void *stream) {
+    if (!pl) return CA_ERR_INVALID_ARG;
+    ca_handle *h = pl->h;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
+    h->launches += pl->kernels;
+    return CA_OK;
+}
+
 ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *H,
                   const int32_t *W, uint8_t *const *masks_dev, void *stream) {
     if (!h) return CA_ERR_INVALID_ARG;
@@ -642,9 +1008,16 @@ ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *
     ca_status st = order_after_last(h, s);
     if (st != CA_OK) return st;
     CallBlock cb;
-    if ((st = upload_frames(h, fr.data(), B, 0, 0.0f, s, &cb)) != CA_OK) return st;
+    build_block(fr.data(), B, 0, 0.0f, nullptr, LaunchCfg{}, cb);
+    Staging *sg;
+    if ((st = take_staging(h, cb.host.size(), &sg)) != CA_OK) return st;
+    std::memcpy(sg->host, cb.host.data(), cb.host.size());
+    CA_CUDA(h, cudaMemcpyAsync(sg->dev, sg->host, cb.host.size(), cudaMemcpyHostToDevice, s));
+    CA_CUDA(h, cudaEventRecord(sg->ev, s));
+    sg->used = true;
     cudaEvent_t t0 = time_begin(h, s);
-    cudaError_t e = launch_mask(cb.d_frames, B, res_dev, cb.total_units, mask_grid(h, cb.total_units), s);
+    cudaError_t e = launch_mask((const DevFrame *)sg->dev, B, res_dev, cb.total_units,
+                                mask_grid(h, cb.total_units), s);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_mask launch");
     time_end(h, 2, t0, s);
     h->launches += 1;
@@ -690,7 +1063,10 @@ ca_status ca_sync(ca_handle *h, void *stream) {
     CA_CUDA(h, cudaSetDevice(h->device));
     CA_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
     CA_CUDA(h, cudaGetLastError());
-    return CA_OK;
+    ca_status st = check_sync_word(h, h->ws);
+    for (ca_plan *pl : h->plans)
+        if (st == CA_OK) st = check_sync_word(h, pl->ws);
+    return st;
 }
 
 ca_status ca_set_debug(ca_handle *h, int level) {
@@ -758,10 +1134,10 @@ ca_status ca_set_timing(ca_handle *h, int on) {
     return CA_OK;
 }
 
-ca_status ca_kernel_times(ca_handle *h, double ms[3], int32_t counts[3]) {
+ca_status ca_kernel_times(ca_handle *h, double ms[4], int32_t counts[4]) {
     if (!h || !ms || !counts) return CA_ERR_INVALID_ARG;
     CA_CUDA(h, cudaSetDevice(h->device));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         ms[k] = 0.0;
         counts[k] = 0;
         for (auto &pr : h->timed[k]) {

@@ -37,8 +37,41 @@ struct DevFrame {
     int32_t unit_off;   // prefix sum of mask units before this frame
     int32_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
     int32_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
+    int32_t mitem_off;  // prefix sum of fused-kernel mask items before this frame
+    int32_t pad;
 };
-static_assert(sizeof(DevFrame) == 56, "DevFrame layout");
+static_assert(sizeof(DevFrame) == 64, "DevFrame layout");
+
+// Fused kernel (k_batch): work items of three phases, numbered in one order in
+// which every item comes after the items it depends on.  The order is a list
+// of segments, each the items of one phase for frames [f0, f1).
+enum { kPhaseStrips = 0, kPhaseFit = 1, kPhaseMask = 2 };
+struct BatchSeg {
+    int32_t start;    // index of the segment's first item
+    int32_t phase;    // kPhase*
+    int32_t f0, f1;   // frames
+};
+// Mask item: kStripThreads / 32 units of 8 rows of one frame.
+constexpr int kMaskUnitsPerItem = kStripThreads / 32;
+__host__ __device__ inline int mask_items_of(int H) {
+    const int units = (H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
+    return (units + kMaskUnitsPerItem - 1) / kMaskUnitsPerItem;
+}
+// Strip items per frame: one strip (both halves) for K = 2, four strips for K > 2.
+__host__ __device__ inline int strip_items_of(int N, int K) { return K == 2 ? N : (N + 3) / 4; }
+
+// Synchronisation words of the fused kernel: [0] next item, [1] CTAs that
+// have finished, [2] error flags, [3] unused, then per frame: strip items
+// done, result ready, mask items done.  Every word returns to 0 by the end of
+// a call that completes without error.
+constexpr int kSyncGlobal = 4;
+constexpr uint32_t kSyncErrTimeout = 1u;
+__host__ __device__ inline uint32_t *sync_strips(uint32_t *s, int nf) { return s + kSyncGlobal; }
+__host__ __device__ inline uint32_t *sync_ready(uint32_t *s, int nf) { return s + kSyncGlobal + nf; }
+__host__ __device__ inline uint32_t *sync_maskdone(uint32_t *s, int nf) {
+    return s + kSyncGlobal + 2 * nf;
+}
+__host__ __device__ inline size_t sync_words(int nf) { return kSyncGlobal + 3 * (size_t)nf; }
 
 // Per-call constants, passed by value (kernel parameter space).
 struct DevParams {
@@ -87,6 +120,8 @@ struct Workspace {
     HypRec *hyps = nullptr;          // [B][NH] when debug level 2
     int32_t *n_hyps = nullptr;       // [B]
     int32_t *n_cands = nullptr;      // [B]
+    uint32_t *sync = nullptr;        // sync_words(sync_frames), fused kernel
+    int32_t sync_frames = 0;
 };
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
@@ -96,6 +131,14 @@ cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const 
                        const Workspace &ws, ca_result *out, cudaStream_t s);
 cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int total_units,
                         int grid, cudaStream_t s);
+// Fused persistent kernel: every phase of B frames in one launch of `grid`
+// CTAs (see ca_kernels.cu).  Waits give up after wait_ns nanoseconds.
+cudaError_t launch_batch(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
+                         const uint16_t *luts, const Workspace &ws, ca_result *out,
+                         const BatchSeg *segs, int n_segs, int total_items, int grid,
+                         uint64_t wait_ns, cudaStream_t s);
+size_t batch_smem_bytes(const DevParams &P);
+int batch_blocks_per_sm(int hyp_threads, size_t smem);   // occupancy of k_batch
 int mask_blocks_per_sm();   // resident k_mask CTAs per SM (occupancy), cached
 int fit_threads_per_sm(int hyp_threads);   // resident k_fit threads per SM, cached
 // Threads per hypothesis for B frames of NH hypotheses on `sms` SMs.

@@ -159,246 +159,277 @@ __device__ __forceinline__ uint32_t score_from_g(const StripCtx &c, int gx, int 
 
 }  // namespace
 
-__global__ void __launch_bounds__(kStripThreads)
-    k_strips(const DevFrame *__restrict__ frames, int B, const int32_t *__restrict__ rows,
-             DevParams P, const uint16_t *__restrict__ luts, CandSlot *__restrict__ slots) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+namespace {
+
+// Shared-memory view of one strip CTA: the tables (copied once per CTA) and
+// the per-warp buffers.
+struct StripShared {
+    const uint16_t *li, *lgb, *lg;   // s_iota, s_g bin bounds, s_g
+    unsigned char *wmem;             // per-warp column words (+ scores, picks)
+    int *s_qmax;                     // [kStripWarps] per-warp maxima (quads)
+    uint32_t *s_qbest;               // [kStripWarps] per-warp best keys (quads)
+};
+
+// Copies the table block from s_iota on into shared memory: every 16-byte
+// load of a thread is issued before its stores (one L2 round trip per CTA).
+__device__ __forceinline__ void strip_tables_load(const DevParams &P, const uint16_t *luts,
+                                                  uint16_t *tab) {
+    constexpr int kPer = ((kDevTableU16 - kDevOffI) / 8 + kStripThreads - 1) / kStripThreads;
+    const int n16 = (int)(strip_tables_bytes(P) / 16);
+    const uint4 *src = reinterpret_cast<const uint4 *>(luts + kDevOffI);
+    uint4 *dst = reinterpret_cast<uint4 *>(tab);
+    uint4 v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kStripThreads;
+        if (i < n16) v[k] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = threadIdx.x + k * kStripThreads;
+        if (i < n16) dst[i] = v[k];
+    }
+}
+
+// Half `half` of strip i of frame f: the K/2 best points of the half-strip
+// into their candidate slots.  K = 2: the 4 warps of quad `quad` share the
+// half (warp qw of the quad scans the qw-th quarter, quad barriers combine
+// them); K > 2: the calling warp alone takes the half.
+__device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
+                                           const int32_t *__restrict__ rows, const DevParams &P,
+                                           const uint16_t *__restrict__ lt, const StripShared &ss,
+                                           CandSlot *__restrict__ slots, int f, int i, int half) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cols = strip_cols(P);
-    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);   // table block from s_iota on
-    const uint16_t *lt = luts + kDevOffT;                      // global, through L1
-    const uint16_t *li = tab, *lgb = tab + (kDevOffB - kDevOffI), *lg = tab + (kDevOffG - kDevOffI);
-    unsigned char *wmem = smem_raw + strip_tables_bytes(P);
-    uint32_t *yy = reinterpret_cast<uint32_t *>(wmem) + warp * cols;
-    uint16_t *sc = reinterpret_cast<uint16_t *>(wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
-    int *s_pick = reinterpret_cast<int *>(wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
-    {
-        // copy the table block from s_iota on: every 16-byte load of a thread
-        // is issued before its stores (one L2 round trip per CTA)
-        constexpr int kPer = ((kDevTableU16 - kDevOffI) / 8 + kStripThreads - 1) / kStripThreads;
-        const int n16 = (int)(strip_tables_bytes(P) / 16);
-        const uint4 *src = reinterpret_cast<const uint4 *>(luts + kDevOffI);
-        uint4 *dst = reinterpret_cast<uint4 *>(tab);
-        uint4 v[kPer];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = threadIdx.x + k * kStripThreads;
-            if (i < n16) v[k] = __ldg(src + i);
-        }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = threadIdx.x + k * kStripThreads;
-            if (i < n16) dst[i] = v[k];
-        }
-    }
-    __syncthreads();
-
+    const uint16_t *li = ss.li, *lgb = ss.lgb, *lg = ss.lg;
+    int *s_qmax = ss.s_qmax;
+    uint32_t *s_qbest = ss.s_qbest;
+    uint32_t *yy = reinterpret_cast<uint32_t *>(ss.wmem) + warp * cols;
+    uint16_t *sc = reinterpret_cast<uint16_t *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
+    int *s_pick = reinterpret_cast<int *>(ss.wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
     const int kk = P.K >> 1;   // picks per half-strip
-    const int items = B * P.N * 2;
-    // K = 2: a quad of 4 warps takes a half-strip, each warp a quarter of its
-    // scan; K > 2: one warp takes a half-strip.  Items are interleaved across
-    // frames (consecutive items belong to consecutive frames), so every CTA and
-    // SM gets a mix of cheap and expensive half-strips.
-    __shared__ int s_qmax[kStripWarps];
-    __shared__ uint32_t s_qbest[kStripWarps];
     const bool quads = kk == 1;
     const int quad = warp >> 2, qw = warp & 3;
-    const int per_cta = quads ? kStripWarps / 4 : kStripWarps;
-    const int gid = quads ? quad : warp;
     const int nseg = quads ? 4 : 1, seg_id = quads ? qw : 0;
-    for (int it = blockIdx.x * per_cta + gid; it < items; it += gridDim.x * per_cta) {
-        const int j = it / B;
-        const int f = it - j * B;
-        const int i = j >> 1, half = j & 1;
-        const DevFrame fr = frames[f];
-        const int W = fr.W, H = fr.H;
-        const int y = rows[fr.rows_off + i];
-        const int hw = W >> 1;
-        const int c_lo = half ? hw - 1 : 0, c_hi = half ? W : hw + 1;   // columns of the half
-        const int len = half ? (W - hw) : hw;
-        // this warp's scan positions [q0, q1) (whole rounds of 32) and the
-        // columns they need (one neighbour on each side)
-        const int seg = nseg == 1 ? len : ((len + 32 * nseg - 1) / (32 * nseg)) * 32;
-        const int q0 = min(seg_id * seg, len), q1 = min(q0 + seg, len);
-        int col_lo = c_lo, col_hi = c_lo;
-        if (q0 < q1) {
-            const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
-            col_lo = max(xa - 1, c_lo);
-            col_hi = min(xb + 2, c_hi);
+    const DevFrame fr = frames[f];
+    const int W = fr.W, H = fr.H;
+    const int y = rows[fr.rows_off + i];
+    const int hw = W >> 1;
+    const int c_lo = half ? hw - 1 : 0, c_hi = half ? W : hw + 1;   // columns of the half
+    const int len = half ? (W - hw) : hw;
+    // this warp's scan positions [q0, q1) (whole rounds of 32) and the
+    // columns they need (one neighbour on each side)
+    const int seg = nseg == 1 ? len : ((len + 32 * nseg - 1) / (32 * nseg)) * 32;
+    const int q0 = min(seg_id * seg, len), q1 = min(q0 + seg, len);
+    int col_lo = c_lo, col_hi = c_lo;
+    if (q0 < q1) {
+        const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
+        col_lo = max(xa - 1, c_lo);
+        col_hi = min(xb + 2, c_hi);
+    }
+    int base;
+    __syncwarp();   // the previous item is done with yy / sc
+
+    // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned)
+    if (fr.vec_ok) {
+        const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
+        base = g0 << 4;
+        const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
+        for (int g = g0 + lane; g < g1; g += 32) {
+            const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+            const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
+            const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
+            const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
+            const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
+            uint4 *dst = reinterpret_cast<uint4 *>(yy + (g - g0) * 16);
+            dst[0] = interleave4(L0.x, L1.x, L2.x);
+            dst[1] = interleave4(L0.y, L1.y, L2.y);
+            dst[2] = interleave4(L0.z, L1.z, L2.z);
+            dst[3] = interleave4(L0.w, L1.w, L2.w);
         }
-        int base;
-        __syncwarp();   // the previous item is done with yy / sc
-
-        // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned)
-        if (fr.vec_ok) {
-            const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
-            base = g0 << 4;
-            const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
-            for (int g = g0 + lane; g < g1; g += 32) {
-                const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
-                const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
-                const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
-                const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
-                const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
-                uint4 *dst = reinterpret_cast<uint4 *>(yy + (g - g0) * 16);
-                dst[0] = interleave4(L0.x, L1.x, L2.x);
-                dst[1] = interleave4(L0.y, L1.y, L2.y);
-                dst[2] = interleave4(L0.z, L1.z, L2.z);
-                dst[3] = interleave4(L0.w, L1.w, L2.w);
-            }
-        } else {
-            base = col_lo;
-            for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
-                const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
-                const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
-                yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
-                                (luma(p2[0], p2[1], p2[2]) << 16);
-            }
+    } else {
+        base = col_lo;
+        for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
+            const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
+            const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+            yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
+                            (luma(p2[0], p2[1], p2[2]) << 16);
         }
-        __syncwarp();
+    }
+    __syncwarp();
 
-        const StripCtx ctx{W, H - 1 - 2 * y, lt, lg, li};
-        const int dir = half ? -1 : 1;
-        uint32_t best = 0u;
+    const StripCtx ctx{W, H - 1 - 2 * y, lt, lg, li};
+    const int dir = half ? -1 : 1;
+    uint32_t best = 0u;
 
-        if (kk == 1) {
-            // preceding maximum before this warp's quarter: maxima of the
-            // earlier quarters of the quad
-            int qm = 0;
-            for (int p = q0 + lane; p < q1; p += 32)
-                qm = max(qm, (int)((yy[(half ? W - 1 - p : p) - base] >> 8) & 0xff));
-            qm = __reduce_max_sync(kFull, qm);
-            if (lane == 0) s_qmax[warp] = qm;
-            quad_barrier(quad);
-            int carry = 0;
-            for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
-            // ---- rounds of 32 consecutive pixels in scan order (outer edge
-            // inwards), one per lane; `carry` is the preceding maximum before
-            // the round, `best` this warp's best key so far
-            for (int r0 = q0; r0 < q1; r0 += 32) {
-                // no remaining pixel of the quarter can be kept (iota cut) or
-                // beat `best`: their s_iota <= s_iota(carry) bounds their scores
-                if (carry >= P.io_cut || (best != 0u && (best >> 16) >= (uint32_t)li[carry])) break;
-                const int p = r0 + lane;
-                const bool act = p < q1;
-                const int x = half ? (W - 1 - p) : p;
-                const int xc = act ? x : (half ? W - q1 : q1 - 1);
-                const uint32_t w1 = yy[xc - base];
-                const int m1 = (w1 >> 8) & 0xff;
-                int inc = act ? m1 : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o) inc = max(inc, t);
-                }
-                int excl = __shfl_up_sync(kFull, inc, 1);
-                if (lane == 0) excl = 0;
-                const int iota = max(carry, excl);
-                const int carry_next = max(carry, __shfl_sync(kFull, inc, 31));
-                uint32_t key = 0u;
-                const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
-                if (act && iota < P.io_cut && (x == 0 || x == W - 1)) {
-                    key = rank;   // no gradient on the first and last column: score 0
-                } else if (act && iota < P.io_cut) {
-                    const uint32_t w0 = yy[x - 1 - base], w2 = yy[x + 1 - base];
-                    const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
-                    const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
-                    const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
-                    const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
-                    const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
-                    const int ng = gx * gx + gy * gy;
-                    const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
-                    const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
-                    if (((bound << 16) | rank) > best)   // could beat the best so far
-                        key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
-                }
-                best = max(best, __reduce_max_sync(kFull, key));
-                carry = carry_next;
-            }
-            // best of the quad
-            if (lane == 0) s_qbest[warp] = best;
-            quad_barrier(quad);
-            best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
-                       max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
-        } else {
-            // ---- K > 2: exact score per pixel over this lane's chunk, with a
-            // sliding window of the vertical Sobel sums
-            const int cpl = (len + 31) >> 5;
-            const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
-            const int xs = half ? (W - 1 - p0) : p0;
-            int lm = 0;
-            for (int p = p0, x = xs; p < p1; ++p, x += dir) lm = max(lm, (int)((yy[x - base] >> 8) & 0xff));
-            int inc = lm;
+    if (kk == 1) {
+        // preceding maximum before this warp's quarter: maxima of the
+        // earlier quarters of the quad
+        int qm = 0;
+        for (int p = q0 + lane; p < q1; p += 32)
+            qm = max(qm, (int)((yy[(half ? W - 1 - p : p) - base] >> 8) & 0xff));
+        qm = __reduce_max_sync(kFull, qm);
+        if (lane == 0) s_qmax[warp] = qm;
+        quad_barrier(quad);
+        int carry = 0;
+        for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
+        // ---- rounds of 32 consecutive pixels in scan order (outer edge
+        // inwards), one per lane; `carry` is the preceding maximum before
+        // the round, `best` this warp's best key so far
+        for (int r0 = q0; r0 < q1; r0 += 32) {
+            // no remaining pixel of the quarter can be kept (iota cut) or
+            // beat `best`: their s_iota <= s_iota(carry) bounds their scores
+            if (carry >= P.io_cut || (best != 0u && (best >> 16) >= (uint32_t)li[carry])) break;
+            const int p = r0 + lane;
+            const bool act = p < q1;
+            const int x = half ? (W - 1 - p) : p;
+            const int xc = act ? x : (half ? W - q1 : q1 - 1);
+            const uint32_t w1 = yy[xc - base];
+            const int m1 = (w1 >> 8) & 0xff;
+            int inc = act ? m1 : 0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int t = __shfl_up_sync(kFull, inc, o);
                 if (lane >= o) inc = max(inc, t);
             }
-            int run = __shfl_up_sync(kFull, inc, 1);
-            if (lane == 0) run = 0;
-            auto col = [&](int cc, int &S, int &T, int &M) {
-                cc = min(max(cc, c_lo), c_hi - 1);
-                const uint32_t w = yy[cc - base];
-                const int u = w & 0xff, m = (w >> 8) & 0xff, d = (w >> 16) & 0xff;
-                S = u + 2 * m + d;
-                T = d - u;
-                M = m;
-            };
-            int S0, T0, M0, S1, T1, M1;
-            col(xs - dir, S0, T0, M0);
-            col(xs, S1, T1, M1);
-            // the preceding maximum never decreases along the scan: once it
-            // reaches io_cut no later pixel of the half can be kept
-            for (int p = p0, x = xs; p < p1; ++p, x += dir) {
-                uint32_t sv = 0u;
-                if (run < P.io_cut) {
-                    int S2, T2, M2;
-                    col(x + dir, S2, T2, M2);
-                    if (x != 0 && x != W - 1)
-                        sv = score_from_g(ctx, dir * (S2 - S0), T0 + 2 * T1 + T2, x, run, P);
-                    run = max(run, M1);
-                    S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
-                }
-                sc[x - base] = (uint16_t)sv;
+            int excl = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) excl = 0;
+            const int iota = max(carry, excl);
+            const int carry_next = max(carry, __shfl_sync(kFull, inc, 31));
+            uint32_t key = 0u;
+            const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
+            if (act && iota < P.io_cut && (x == 0 || x == W - 1)) {
+                key = rank;   // no gradient on the first and last column: score 0
+            } else if (act && iota < P.io_cut) {
+                const uint32_t w0 = yy[x - 1 - base], w2 = yy[x + 1 - base];
+                const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
+                const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
+                const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
+                const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
+                const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
+                const int ng = gx * gx + gy * gy;
+                const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
+                const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
+                if (((bound << 16) | rank) > best)   // could beat the best so far
+                    key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
             }
+            best = max(best, __reduce_max_sync(kFull, key));
+            carry = carry_next;
         }
+        // best of the quad
+        if (lane == 0) s_qbest[warp] = best;
+        quad_barrier(quad);
+        best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
+                   max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
+    } else {
+        // ---- K > 2: exact score per pixel over this lane's chunk, with a
+        // sliding window of the vertical Sobel sums
+        const int cpl = (len + 31) >> 5;
+        const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
+        const int xs = half ? (W - 1 - p0) : p0;
+        int lm = 0;
+        for (int p = p0, x = xs; p < p1; ++p, x += dir) lm = max(lm, (int)((yy[x - base] >> 8) & 0xff));
+        int inc = lm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc = max(inc, t);
+        }
+        int run = __shfl_up_sync(kFull, inc, 1);
+        if (lane == 0) run = 0;
+        auto col = [&](int cc, int &S, int &T, int &M) {
+            cc = min(max(cc, c_lo), c_hi - 1);
+            const uint32_t w = yy[cc - base];
+            const int u = w & 0xff, m = (w >> 8) & 0xff, d = (w >> 16) & 0xff;
+            S = u + 2 * m + d;
+            T = d - u;
+            M = m;
+        };
+        int S0, T0, M0, S1, T1, M1;
+        col(xs - dir, S0, T0, M0);
+        col(xs, S1, T1, M1);
+        // the preceding maximum never decreases along the scan: once it
+        // reaches io_cut no later pixel of the half can be kept
+        for (int p = p0, x = xs; p < p1; ++p, x += dir) {
+            uint32_t sv = 0u;
+            if (run < P.io_cut) {
+                int S2, T2, M2;
+                col(x + dir, S2, T2, M2);
+                if (x != 0 && x != W - 1)
+                    sv = score_from_g(ctx, dir * (S2 - S0), T0 + 2 * T1 + T2, x, run, P);
+                run = max(run, M1);
+                S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
+            }
+            sc[x - base] = (uint16_t)sv;
+        }
+    }
 
-        // ---- K/2 picks per half, each excluding +-sup_px around earlier picks
-        for (int r = 0; r < kk; ++r) {
-            if (kk > 1) {
-                const int cpl = (len + 31) >> 5;
-                const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
-                const int xs = half ? (W - 1 - p0) : p0;
-                uint32_t b = 0u;
-                for (int p = p0, x = xs; p < p1; ++p, x += dir) {
-                    bool sup = false;
-                    for (int j = 0; j < r; ++j) sup |= abs(x - s_pick[j]) <= P.sup_px;
-                    if (!sup)
-                        b = max(b, ((uint32_t)sc[x - base] << 16) | (uint32_t)(half ? x : (0xFFFF - x)));
-                }
-                best = __reduce_max_sync(kFull, b);
+    // ---- K/2 picks per half, each excluding +-sup_px around earlier picks
+    for (int r = 0; r < kk; ++r) {
+        if (kk > 1) {
+            const int cpl = (len + 31) >> 5;
+            const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
+            const int xs = half ? (W - 1 - p0) : p0;
+            uint32_t b = 0u;
+            for (int p = p0, x = xs; p < p1; ++p, x += dir) {
+                bool sup = false;
+                for (int j = 0; j < r; ++j) sup |= abs(x - s_pick[j]) <= P.sup_px;
+                if (!sup)
+                    b = max(b, ((uint32_t)sc[x - base] << 16) | (uint32_t)(half ? x : (0xFFFF - x)));
             }
-            int px = -1000000;
-            CandSlot out;
-            out.kept = 0;
-            out.x = -1;
-            out.y = (int16_t)y;
-            out.s = 0;
-            if (best != 0u) {
-                const int rank = (int)(best & 0xFFFFu);
-                px = half ? rank : (0xFFFF - rank);
-                const uint32_t scv = best >> 16;
-                out.x = (int16_t)px;
-                out.s = (uint16_t)scv;
-                out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
-                                      y >= P.T_px && y <= H - 1 - P.T_px);
-            }
-            if (lane == 0 && (!quads || qw == 0)) {
-                if (kk > 1) s_pick[r] = px;
-                slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
-            }
-            __syncwarp();   // this round's pick visible to the whole warp
+            best = __reduce_max_sync(kFull, b);
         }
+        int px = -1000000;
+        CandSlot out;
+        out.kept = 0;
+        out.x = -1;
+        out.y = (int16_t)y;
+        out.s = 0;
+        if (best != 0u) {
+            const int rank = (int)(best & 0xFFFFu);
+            px = half ? rank : (0xFFFF - rank);
+            const uint32_t scv = best >> 16;
+            out.x = (int16_t)px;
+            out.s = (uint16_t)scv;
+            out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
+                                  y >= P.T_px && y <= H - 1 - P.T_px);
+        }
+        if (lane == 0 && (!quads || qw == 0)) {
+            if (kk > 1) s_pick[r] = px;
+            slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
+        }
+        __syncwarp();   // this round's pick visible to the whole warp
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kStripThreads)
+    k_strips(const DevFrame *__restrict__ frames, int B, const int32_t *__restrict__ rows,
+             DevParams P, const uint16_t *__restrict__ luts, CandSlot *__restrict__ slots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_qmax[kStripWarps];
+    __shared__ uint32_t s_qbest[kStripWarps];
+    const int warp = threadIdx.x >> 5;
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);   // table block from s_iota on
+    strip_tables_load(P, luts, tab);
+    __syncthreads();
+    const StripShared ss{tab, tab + (kDevOffB - kDevOffI), tab + (kDevOffG - kDevOffI),
+                         smem_raw + strip_tables_bytes(P), s_qmax, s_qbest};
+    const uint16_t *lt = luts + kDevOffT;   // global, through L1
+
+    // K = 2: a quad of 4 warps takes a half-strip; K > 2: one warp takes a
+    // half-strip.  Items are interleaved across frames (consecutive items
+    // belong to consecutive frames), so every CTA and SM gets a mix of cheap
+    // and expensive half-strips.
+    const bool quads = P.K == 2;
+    const int per_cta = quads ? kStripWarps / 4 : kStripWarps;
+    const int gid = quads ? (warp >> 2) : warp;
+    const int items = B * P.N * 2;
+    for (int it = blockIdx.x * per_cta + gid; it < items; it += gridDim.x * per_cta) {
+        const int j = it / B;
+        const int f = it - j * B;
+        strip_half(frames, rows, P, lt, ss, slots, f, j >> 1, j & 1);
     }
 }
 
@@ -649,15 +680,17 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
 
 }  // namespace
 
-// T threads share one hypothesis (points split among them, moments combined
-// by shuffles); a CTA holds 256 / T hypotheses of one frame.
+// Tile `tile` of the hypotheses of frame f.  T threads share one hypothesis
+// (points split among them, moments combined by shuffles); a CTA holds
+// 256 / T hypotheses.  The last tile of the frame to finish writes the
+// frame's result; with `sync` (fused kernel) it also re-arms the frame's
+// strip counter and publishes the result to the frame's mask items.
 template <int T>
-__global__ void __launch_bounds__(kHypTile, 4)
-    k_fit(const DevFrame *__restrict__ frames, int B, DevParams P,
-          const CandSlot *__restrict__ slots, Workspace ws, ca_result *__restrict__ out) {
-    __shared__ FitSmem sm;
+__device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict__ frames,
+                                         const DevParams &P, const CandSlot *slots,
+                                         const Workspace &ws, ca_result *out, int f, int tile,
+                                         uint32_t *sync) {
     constexpr int HPT = kHypTile / T;
-    const int f = blockIdx.x, tile = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = tid & (T - 1);
     const DevFrame fr = frames[f];
@@ -668,7 +701,10 @@ __global__ void __launch_bounds__(kHypTile, 4)
     CandSlot c;
     c.x = c.y = 0;
     c.s = c.kept = 0;
-    if (tid < NK) c = slots[(int64_t)f * kMaxSlots + tid];
+    if (tid < NK) {   // L2 load: in the fused kernel other CTAs wrote the slots
+        const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(slots + (int64_t)f * kMaxSlots + tid));
+        c = *reinterpret_cast<const CandSlot *>(&v);
+    }
     const bool kept = tid < NK && c.kept;
     const unsigned bal = __ballot_sync(kFull, kept);
     if (lane == 0) sm.wcount[warp] = __popc(bal);
@@ -817,7 +853,25 @@ __global__ void __launch_bounds__(kHypTile, 4)
         out[f] = res;
         ws.best[f] = 0ull;   // ready for the next call
         ws.done[f] = 0u;
+        if (sync) {
+            // every tile of this frame has passed its wait on the strip
+            // counter: re-arm it, then publish the result to the mask items
+            sync_strips(sync, ws.sync_frames)[f] = 0u;
+            if (fr.mask) {
+                __threadfence();
+                atomicExch(sync_ready(sync, ws.sync_frames) + f, 1u);
+            }
+        }
     }
+}
+
+// T threads share one hypothesis; grid (frames, tiles).
+template <int T>
+__global__ void __launch_bounds__(kHypTile, 4)
+    k_fit(const DevFrame *__restrict__ frames, int B, DevParams P,
+          const CandSlot *__restrict__ slots, Workspace ws, ca_result *__restrict__ out) {
+    __shared__ FitSmem sm;
+    fit_tile<T>(sm, frames, P, slots, ws, out, blockIdx.x, blockIdx.y, nullptr);
 }
 
 int fit_threads_per_sm(int T) {
@@ -921,18 +975,78 @@ __device__ __forceinline__ uint32_t exact_word(int x0, float cx, float dy2, floa
     return w;
 }
 
+// Unit u (rows 8u .. 8u+7) of the mask of one frame, by one warp: lane r
+// computes the span of row r, then the warp stores each row with consecutive
+// 16-byte vectors per lane.
+__device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &res, int u) {
+    const int lane = threadIdx.x & 31;
+    const uint4 ones = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
+    const uint4 zeros = make_uint4(0u, 0u, 0u, 0u);
+    const int W = fr.W, H = fr.H;
+    const int y0 = u * kMaskRowsPerUnit;
+    const int nrows = min(kMaskRowsPerUnit, H - y0);
+    const RowSpan sp = row_span(res, W, y0 + min(lane, nrows - 1));
+    const float rr = __fmul_rn(res.r, res.r);
+    for (int r = 0; r < nrows; ++r) {
+        const int a = __shfl_sync(kFull, sp.a, r);
+        const int b = __shfl_sync(kFull, sp.b, r);
+        const int ex = __shfl_sync(kFull, sp.exact, r);
+        const int y = y0 + r;
+        uint8_t *row = fr.mask + (int64_t)y * W;
+        const float dy = __fsub_rn(__int2float_rn(y), res.cy);
+        const float dy2 = __fmul_rn(dy, dy);
+        if (fr.mask_vec_ok) {
+            const int VW = W >> 4;
+            for (int v = lane; v < VW; v += 32) {
+                const int x0 = v << 4;
+                uint4 val;
+                if (ex) {
+                    if (x0 >= a && x0 + 15 <= b) val = ones;
+                    else if (x0 > b || x0 + 15 < a) val = zeros;
+                    else val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
+                                          span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
+                } else {
+                    val = make_uint4(exact_word(x0, res.cx, dy2, rr),
+                                     exact_word(x0 + 4, res.cx, dy2, rr),
+                                     exact_word(x0 + 8, res.cx, dy2, rr),
+                                     exact_word(x0 + 12, res.cx, dy2, rr));
+                }
+                st_cs_v4(row + x0, val);
+            }
+        } else {
+            for (int x = lane; x < W; x += 32) {
+                uint8_t v;
+                if (!res.valid) v = 1;
+                else if (ex) v = (uint8_t)(x >= a && x <= b);
+                else v = (uint8_t)in_disc(x, res.cx, dy2, rr);
+                row[x] = v;
+            }
+        }
+    }
+}
+
+// L2 load of a result (in the fused kernel another CTA wrote it).  A result
+// is 24 bytes with 4-byte alignment: loaded word by word.
+__device__ __forceinline__ ca_result load_result(const ca_result *p) {
+    ca_result r;
+    r.cx = __ldcg(&p->cx);
+    r.cy = __ldcg(&p->cy);
+    r.r = __ldcg(&p->r);
+    r.score = __ldcg(&p->score);
+    r.valid = __ldcg(&p->valid);
+    r.n_inliers = __ldcg(&p->n_inliers);
+    return r;
+}
+
 }  // namespace
 
-// One warp per unit of 8 rows of one frame: lane r computes the span of row r,
-// then the warp stores each row with consecutive 16-byte vectors per lane.
+// One warp per unit of 8 rows; units of all frames are numbered consecutively
+// (DevFrame::unit_off).
 __global__ void __launch_bounds__(256)
     k_mask(const DevFrame *__restrict__ frames, int B, const ca_result *__restrict__ results,
            int total_units) {
-    const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const int nw = gridDim.x * wpb;
-    const uint4 ones = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-    const uint4 zeros = make_uint4(0u, 0u, 0u, 0u);
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < total_units; u += nw) {
         int lo = 0, hi = B - 1;
         while (lo < hi) {
@@ -942,48 +1056,7 @@ __global__ void __launch_bounds__(256)
         }
         const DevFrame fr = frames[lo];
         if (fr.mask == nullptr) continue;
-        const ca_result res = results[lo];
-        const int W = fr.W, H = fr.H;
-        const int y0 = (u - fr.unit_off) * kMaskRowsPerUnit;
-        const int nrows = min(kMaskRowsPerUnit, H - y0);
-        const RowSpan sp = row_span(res, W, y0 + min(lane, nrows - 1));
-        const float rr = __fmul_rn(res.r, res.r);
-        for (int r = 0; r < nrows; ++r) {
-            const int a = __shfl_sync(kFull, sp.a, r);
-            const int b = __shfl_sync(kFull, sp.b, r);
-            const int ex = __shfl_sync(kFull, sp.exact, r);
-            const int y = y0 + r;
-            uint8_t *row = fr.mask + (int64_t)y * W;
-            const float dy = __fsub_rn(__int2float_rn(y), res.cy);
-            const float dy2 = __fmul_rn(dy, dy);
-            if (fr.mask_vec_ok) {
-                const int VW = W >> 4;
-                for (int v = lane; v < VW; v += 32) {
-                    const int x0 = v << 4;
-                    uint4 val;
-                    if (ex) {
-                        if (x0 >= a && x0 + 15 <= b) val = ones;
-                        else if (x0 > b || x0 + 15 < a) val = zeros;
-                        else val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
-                                              span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
-                    } else {
-                        val = make_uint4(exact_word(x0, res.cx, dy2, rr),
-                                         exact_word(x0 + 4, res.cx, dy2, rr),
-                                         exact_word(x0 + 8, res.cx, dy2, rr),
-                                         exact_word(x0 + 12, res.cx, dy2, rr));
-                    }
-                    st_cs_v4(row + x0, val);
-                }
-            } else {
-                for (int x = lane; x < W; x += 32) {
-                    uint8_t v;
-                    if (!res.valid) v = 1;
-                    else if (ex) v = (uint8_t)(x >= a && x <= b);
-                    else v = (uint8_t)in_disc(x, res.cx, dy2, rr);
-                    row[x] = v;
-                }
-            }
-        }
+        mask_unit(fr, load_result(results + lo), u - fr.unit_off);
     }
 }
 
@@ -1001,6 +1074,177 @@ cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int
     if (total_units <= 0) return cudaSuccess;
     k_mask<<<grid, 256, 0, s>>>(frames, B, res, total_units);
     return cudaGetLastError();
+}
+
+// ================================================================ k_batch ==
+// The whole path of a batch in one persistent launch.  CTAs take work items
+// from one atomic counter, in an order in which every item comes after the
+// items it depends on (the strips of a frame before its fit tiles, its fit
+// tiles before its mask items).  A CTA that takes an item whose inputs are not
+// ready waits for them; those inputs belong to items that running CTAs have
+// already taken and that wait only on earlier items, so every wait ends
+// whatever the number of resident CTAs.  Each wait is still bounded in time:
+// on expiry the CTA sets an error flag (read back by ca_sync) and goes on.
+namespace {
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread-level wait until *p >= target; false after `limit_ns` (error flag set).
+__device__ __noinline__ bool wait_at_least(const uint32_t *p, uint32_t target, uint32_t *err,
+                                           uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (ld_acquire(p) >= target) return true;
+        __nanosleep(128);
+        if ((it & 15u) == 15u && globaltimer_ns() - t0 > limit_ns) break;
+    }
+    atomicOr(err, kSyncErrTimeout);
+    return false;
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(const DevParams &P) {
+    const size_t strip_part = strips_smem_bytes(P) - strip_tables_bytes(P);
+    return strip_tables_bytes(P) + (strip_part > sizeof(FitSmem) ? strip_part : sizeof(FitSmem));
+}
+
+template <int T>
+__global__ void __launch_bounds__(kStripThreads, 4)
+    k_batch(const DevFrame *__restrict__ frames, const int32_t *__restrict__ rows, DevParams P,
+            const uint16_t *__restrict__ luts, Workspace ws, ca_result *out,
+            const BatchSeg *__restrict__ segs, int n_segs, int total_items, uint64_t wait_ns) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_qmax[kStripWarps];
+    __shared__ uint32_t s_qbest[kStripWarps];
+    __shared__ int s_item;
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
+    strip_tables_load(P, luts, tab);   // once per CTA; visible after the first barrier
+    unsigned char *un = smem_raw + strip_tables_bytes(P);   // strip buffers or FitSmem
+    const StripShared ss{tab, tab + (kDevOffB - kDevOffI), tab + (kDevOffG - kDevOffI), un,
+                         s_qmax, s_qbest};
+    FitSmem &fs = *reinterpret_cast<FitSmem *>(un);
+    const uint16_t *lt = luts + kDevOffT;
+    uint32_t *sync = ws.sync;
+    const int nf = ws.sync_frames;
+    const int warp = threadIdx.x >> 5;
+    const int spf = strip_items_of(P.N, P.K);
+    for (;;) {
+        __syncthreads();   // the previous item is done with shared memory
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(sync + 0, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_items) break;
+        int lo = 0, hi = n_segs - 1;   // last segment starting at or before item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].start <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchSeg sg = segs[lo];
+        const int local = item - sg.start;
+        if (sg.phase == kPhaseStrips) {
+            const int f = sg.f0 + local / spf, si = local % spf;
+            if (P.K == 2) {
+                strip_half(frames, rows, P, lt, ss, ws.slots, f, si, warp >> 2);
+            } else {
+                const int i = 4 * si + (warp >> 1);
+                if (i < P.N) strip_half(frames, rows, P, lt, ss, ws.slots, f, i, warp & 1);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(sync_strips(sync, nf) + f, 1u);
+            }
+        } else if (sg.phase == kPhaseFit) {
+            const int f = sg.f0 + local / P.n_tiles, tile = local % P.n_tiles;
+            if (threadIdx.x == 0) {
+                wait_at_least(sync_strips(sync, nf) + f, (uint32_t)spf, sync + 2, wait_ns);
+                __threadfence();
+            }
+            __syncthreads();
+            fit_tile<T>(fs, frames, P, ws.slots, ws, out, f, tile, sync);
+        } else {
+            const int g = frames[sg.f0].mitem_off + local;
+            int a = sg.f0, b = sg.f1 - 1;   // frame of mask item g
+            while (a < b) {
+                const int mid = (a + b + 1) >> 1;
+                if (frames[mid].mitem_off <= g) a = mid;
+                else b = mid - 1;
+            }
+            const int f = a;
+            const DevFrame fr = frames[f];
+            if (threadIdx.x == 0) {
+                wait_at_least(sync_ready(sync, nf) + f, 1u, sync + 2, wait_ns);
+                __threadfence();
+            }
+            __syncthreads();
+            const int u = (g - fr.mitem_off) * kMaskUnitsPerItem + warp;
+            if (u * kMaskRowsPerUnit < fr.H) mask_unit(fr, load_result(out + f), u);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const uint32_t c = atomicAdd(sync_maskdone(sync, nf) + f, 1u);
+                if (c + 1u == (uint32_t)mask_items_of(fr.H)) {   // every mask item of f has passed its wait
+                    sync_maskdone(sync, nf)[f] = 0u;
+                    sync_ready(sync, nf)[f] = 0u;
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && atomicAdd(sync + 1, 1u) + 1u == gridDim.x) {
+        sync[0] = 0u;   // every CTA has taken its last item: re-arm the counter
+        sync[1] = 0u;
+    }
+}
+
+int batch_blocks_per_sm(int T, size_t smem) {
+    int v = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto occ = [&](auto kern) {
+        cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (a != cudaSuccess) return a;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kStripThreads, smem);
+    };
+    if (T == 1) e = occ(k_batch<1>);
+    if (T == 2) e = occ(k_batch<2>);
+    if (T == 4) e = occ(k_batch<4>);
+    if (T == 8) e = occ(k_batch<8>);
+    return e == cudaSuccess && v > 0 ? v : 1;
+}
+
+cudaError_t launch_batch(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
+                         const uint16_t *luts, const Workspace &ws, ca_result *out,
+                         const BatchSeg *segs, int n_segs, int total_items, int grid,
+                         uint64_t wait_ns, cudaStream_t s) {
+    (void)B;
+    if (total_items <= 0) return cudaSuccess;
+    const size_t smem = batch_smem_bytes(P);
+    auto go = [&](auto kern) {
+        cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (a != cudaSuccess) return a;
+        kern<<<grid, kStripThreads, smem, s>>>(frames, rows, P, luts, ws, out, segs, n_segs,
+                                               total_items, wait_ns);
+        return cudaGetLastError();
+    };
+    switch (P.hyp_threads) {
+        case 1: return go(k_batch<1>);
+        case 2: return go(k_batch<2>);
+        case 4: return go(k_batch<4>);
+        case 8: return go(k_batch<8>);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ca

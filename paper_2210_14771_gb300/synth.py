@@ -164,3 +164,37 @@ def batch(seed: int, n: int, H: int, W: int, mix: str = "centred"):
 
 # Resolutions of the mixed-resolution workload (25 % each).
 MIXED_RESOLUTIONS = ((576, 720), (1024, 1280), (1080, 1920), (2160, 3840))
+
+
+def _frame_job(args):
+    seed, idx, H, W, geometry = args
+    return frame(seed, idx, H, W, geometry)
+
+
+def mixed_batch(seed: int, n: int, unique: int | None = None, workers: int = 0,
+                resolutions=MIXED_RESOLUTIONS, mix: str = "mixed"):
+    """The mixed-resolution workload: frame i has resolution
+    resolutions[i % len(resolutions)] and the geometry of the 1080p mix.
+
+    With `unique` < n, only the first `unique` frames are drawn and frame i
+    repeats the content of frame i % unique (same resolution when `unique` is
+    a multiple of the resolution count) under its own frame key, so that the
+    RANSAC draws still differ.  `workers` > 1 draws in that many spawned
+    processes.  Returns (list of (H, W, 3) arrays, ground truths, keys)."""
+    nres = len(resolutions)
+    u = n if unique is None else max(1, min(unique, n))
+    if u < n and u % nres:
+        raise ValueError("unique must be a multiple of the resolution count")
+    jobs = [(seed, i, resolutions[i % nres][0], resolutions[i % nres][1], geometry_of(mix, i))
+            for i in range(u)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            drawn = list(ex.map(_frame_job, jobs, chunksize=1))
+    else:
+        drawn = [_frame_job(j) for j in jobs]
+    frames = [drawn[i % u][0] for i in range(n)]
+    gts = [drawn[i % u][1] for i in range(n)]
+    keys = [frame_key(seed, i) for i in range(n)]
+    return frames, gts, keys

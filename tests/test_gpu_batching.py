@@ -1,0 +1,162 @@
+"""Batching: the fused persistent kernel, captured plans (CUDA graphs) and the
+autotuner.  None of them may change a result: each is checked bit for bit
+against the CPU oracle and against the staged three-kernel launch."""
+import numpy as np
+import pytest
+
+from paper_2210_14771_gb300 import synth
+
+from _helpers import both_params, same_f32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ca():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_14771_gb300.build import build
+    build()
+    from paper_2210_14771_gb300 import api
+    h = api.ContentArea(0)
+    yield h
+    h.close()
+
+
+def _run(ca, ts, keys, lp, masks=True):
+    from paper_2210_14771_gb300 import api
+    res, m = ca.estimate(ts, lp, keys=keys, masks=masks)
+    ca.sync()
+    torch.cuda.synchronize()
+    return api.results_numpy(res), ([x.cpu().numpy() if x is not None else None for x in m]
+                                    if m is not None else None)
+
+
+def _check_oracle(orc, frames, keys, op, gres, gmask, which):
+    for b in which:
+        ores, _ = orc.estimate(frames[b], keys[b], op)
+        for k in ("cx", "cy", "r", "score"):
+            assert same_f32(gres[k][b], ores[k]), (b, k, gres[b], ores)
+        assert int(gres["valid"][b]) == ores["valid"]
+        assert int(gres["n_inliers"][b]) == ores["n_inliers"]
+        if gmask is not None and gmask[b] is not None:
+            H, W = frames[b].shape[:2]
+            assert np.array_equal(gmask[b], orc.mask(ores, H, W)), b
+
+
+def _ragged_frames():
+    sizes = [(250, 333), (97, 131), (3, 8), (17, 9), (64, 64), (121, 200), (480, 640), (33, 47),
+             (576, 720), (130, 256)]
+    frames, keys = [], []
+    for i, (H, W) in enumerate(sizes):
+        f, _ = synth.frame(7, i, H, W, "centred" if i % 3 else "full" if min(H, W) > 40 else "none")
+        frames.append(f)
+        keys.append(5000 + i)
+    return frames, keys
+
+
+@pytest.mark.parametrize("K,T,wave", [(2, 1, 1), (2, 8, 3), (4, 2, 10), (6, 4, 2)])
+def test_fused_every_intermediate(ca, orc, K, T, wave):
+    """Fused launch on odd and tiny sizes (byte and vector paths, ragged
+    halves and hypothesis tiles): candidates, every hypothesis record, results
+    and masks equal to the oracle's, for several waves and hypothesis splits."""
+    from paper_2210_14771_gb300 import api
+    frames, keys = _ragged_frames()
+    lp, op = both_params(orc, n_strips=12, cands_per_strip=K, n_hyps=300, seed=5,
+                         batch_mode=2, hyp_threads=T, wave_frames=wave)
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    ca.set_debug(2)
+    gres, gmask = _run(ca, ts, keys, lp)
+    for b, f in enumerate(frames):
+        ores, od = orc.estimate(f, keys[b], op, debug=True)
+        gc = ca.dump_candidates(b)
+        assert gc["M"] == od["M"]
+        assert np.array_equal(gc["x"], od["cand_x"]) and np.array_equal(gc["s"], od["cand_s"])
+        gh = ca.dump_hypotheses(b)
+        assert np.array_equal(gh["n_inl"], od["hyp_n_inl"]) and np.array_equal(gh["S"], od["hyp_score"])
+    ca.set_debug(0)
+    _check_oracle(orc, frames, keys, op, gres, gmask, range(len(frames)))
+    del api
+
+
+def test_fused_equals_staged_mixed_resolutions(ca, orc):
+    """The four resolutions of the mixed workload, some frames without masks:
+    fused and staged launches agree byte for byte; sampled frames match the
+    oracle; repeated fused calls stay identical (the kernel re-arms its
+    counters) and report no timed-out wait."""
+    frames, _, keys = synth.mixed_batch(2, 24, unique=8, workers=4)
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    masks = [torch.empty(f.shape[:2], dtype=torch.uint8, device="cuda") if i % 5 != 3 else None
+             for i, f in enumerate(frames)]
+    from paper_2210_14771_gb300 import api
+    outs = []
+    for mode, T, wave in [(1, 0, 0), (2, 0, 0), (2, 1, 1), (2, 4, 24), (2, 2, 5), (2, 0, 0)]:
+        lp = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, batch_mode=mode,
+                        hyp_threads=T, wave_frames=wave)
+        for m in masks:
+            if m is not None:
+                m.fill_(7)
+        res, _ = ca.estimate(ts, lp, keys=keys, masks=masks)
+        ca.sync()
+        outs.append((api.results_numpy(res).copy(),
+                     [m.cpu().numpy() if m is not None else None for m in masks]))
+    r0, m0 = outs[0]
+    for r, m in outs[1:]:
+        assert r.tobytes() == r0.tobytes()
+        for a, b in zip(m, m0):
+            assert (a is None and b is None) or np.array_equal(a, b)
+    _, op = both_params(orc, n_strips=32, cands_per_strip=2, n_hyps=1024)
+    _check_oracle(orc, frames, keys, op, r0, m0, [0, 1, 2, 3, 8, 13, 22, 23])
+
+
+def test_plan_graph_replay(ca, orc):
+    """A captured plan replays the estimate as one graph launch: results equal
+    the direct call, and new frame contents written into the same buffers are
+    picked up by the next replay."""
+    from paper_2210_14771_gb300 import api
+    frames, _, keys = synth.mixed_batch(3, 8, unique=4, workers=1,
+                                        resolutions=((480, 640), (576, 720)))
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    masks = [torch.zeros(f.shape[:2], dtype=torch.uint8, device="cuda") for f in frames]
+    for mode in (1, 2):
+        lp, op = both_params(orc, n_strips=16, cands_per_strip=4, n_hyps=256, batch_mode=mode)
+        res = api.new_results(len(frames), "cuda")
+        plan = ca.plan(ts, lp, keys=keys, masks=masks, results=res)
+        n0 = ca.launch_count()
+        for _ in range(3):
+            plan.launch()
+        ca.sync()
+        assert ca.launch_count() - n0 == 3 * (1 if mode == 2 else 3)
+        g = api.results_numpy(res).copy()
+        gm = [m.cpu().numpy() for m in masks]
+        _check_oracle(orc, frames, keys, op, g, gm, range(len(frames)))
+        # new contents, same buffers
+        new = [np.ascontiguousarray(f[::-1]) for f in frames]
+        for t, f in zip(ts, new):
+            t.copy_(torch.from_numpy(f).cuda())
+        plan.launch()
+        ca.sync()
+        _check_oracle(orc, new, keys, op, api.results_numpy(res), [m.cpu().numpy() for m in masks],
+                      range(len(frames)))
+        for t, f in zip(ts, frames):
+            t.copy_(torch.from_numpy(f).cuda())
+        plan.close()
+
+
+def test_tune_keeps_results(ca):
+    """ca_tune times every result-preserving configuration and the tuned AUTO
+    call returns the same bytes as the untuned one."""
+    from paper_2210_14771_gb300 import api
+    frames, _, keys = synth.mixed_batch(4, 12, unique=4, workers=1,
+                                        resolutions=((480, 640), (1080, 1920)))
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    lp = api.params(n_strips=32, cands_per_strip=2, n_hyps=512)
+    r_before, m_before = _run(ca, ts, keys, lp)
+    t = ca.tune(ts, lp, keys=keys, masks=True)
+    assert t["batch_mode"] in (1, 2) and t["hyp_threads"] in (1, 2, 4, 8)
+    assert t["n_tried"] >= 8 and 0 < t["ms"] <= min(t["ms_staged"], t["ms_fused"]) + 1e-6
+    r_after, m_after = _run(ca, ts, keys, lp)
+    assert r_after.tobytes() == r_before.tobytes()
+    assert all(np.array_equal(a, b) for a, b in zip(m_after, m_before))

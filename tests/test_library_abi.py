@@ -43,7 +43,8 @@ def test_every_declared_symbol_exported(native):
 def test_struct_layouts(native):
     assert C.sizeof(native.CaResult) == 24
     assert C.sizeof(native.CaFrame) == 40
-    assert C.sizeof(native.CaParams) == 96
+    assert C.sizeof(native.CaParams) == 104
+    assert C.sizeof(native.CaTuning) == 32
 
 
 def test_defaults_are_appendix_a(native, orc):
