@@ -76,6 +76,17 @@ def lib():
         L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_uint64,
                                    P(OrcParams), P(OrcResult), P(OrcDebug)]
         L.orc_mask.argtypes = [P(OrcResult), C.c_int, C.c_int, C.c_void_p]
+        L.orc_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_int,
+                              C.c_uint64, P(OrcParams), P(OrcResult), P(OrcDebug)]
+        L.orc_bf16.argtypes = [C.c_float]
+        L.orc_bf16.restype = C.c_float
+        L.orc_sc_offsets.argtypes = [C.c_void_p]
+        L.orc_sc_features.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.orc_sc_forward.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                     C.c_void_p, C.c_void_p]
+        L.orc_sc_loss_grad.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                       C.c_float, C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_sc_loss_grad.restype = C.c_double
         _lib = L
     return _lib
 
@@ -245,3 +256,78 @@ def mask(result, H, W):
     out = np.zeros((H, W), np.uint8)
     lib().orc_mask(C.byref(res), H, W, _ptr(out))
     return out
+
+
+def fit(xs, ys, ss, H, W, frame_key=0, p=None):
+    """Sec. 2.2.5 on a given candidate list (pixel x, y and Q15 scores)."""
+    p = p or params()
+    xs = np.ascontiguousarray(xs, np.int16)
+    ys = np.ascontiguousarray(ys, np.int16)
+    ss = np.ascontiguousarray(ss, np.uint16)
+    res = OrcResult()
+    if lib().orc_fit(_ptr(xs), _ptr(ys), _ptr(ss), len(xs), H, W, frame_key, C.byref(p),
+                     C.byref(res), None) != 0:
+        raise ValueError("bad fit arguments")
+    return dict(cx=res.cx, cy=res.cy, r=res.r, score=res.score, valid=res.valid,
+                n_inliers=res.n_inliers)
+
+
+# ------------------------------------------------------- learned scorer --
+SC_CIN, SC_CH, SC_K, SC_NPARAM = 14, 32, 7, 17601
+SC_EXACT, SC_MIXED = 0, 1
+
+
+def bf16(v):
+    return np.float32(lib().orc_bf16(float(v)))
+
+
+def sc_offsets():
+    out = np.zeros(8, np.int32)
+    lib().orc_sc_offsets(_ptr(out))
+    return dict(zip(("W1", "b1", "W2", "b2", "W3", "b3", "wh", "bh"), (int(v) for v in out)))
+
+
+def _strip(rgb3):
+    s = np.ascontiguousarray(rgb3, np.uint8)
+    assert s.ndim == 3 and s.shape[0] == 3 and s.shape[2] == 3
+    return s
+
+
+def sc_features(rgb3, y, H, mixed=True):
+    s = _strip(rgb3)
+    W = s.shape[1]
+    out = np.zeros((W, SC_CIN), np.float64)
+    lib().orc_sc_features(_ptr(s), W, int(y), int(H), 1 if mixed else 0, _ptr(out))
+    return out
+
+
+def sc_forward(rgb3, y, H, prm, mode=SC_MIXED, acts=False):
+    """Logits (W,) of one strip; with acts=True also (features, a1, a2, a3)."""
+    s = _strip(rgb3)
+    W = s.shape[1]
+    prm = np.ascontiguousarray(prm, np.float32)
+    assert prm.size == SC_NPARAM
+    lg = np.zeros(W, np.float64)
+    ac = np.zeros(W * SC_CIN + 3 * W * SC_CH, np.float64) if acts else None
+    if lib().orc_sc_forward(_ptr(s), W, int(y), int(H), _ptr(prm), mode, _ptr(lg),
+                            _ptr(ac) if acts else None) != 0:
+        raise ValueError("bad scorer arguments")
+    if not acts:
+        return lg
+    f = ac[:W * SC_CIN].reshape(W, SC_CIN)
+    a = [ac[W * SC_CIN + l * W * SC_CH: W * SC_CIN + (l + 1) * W * SC_CH].reshape(W, SC_CH)
+         for l in range(3)]
+    return lg, (f, *a)
+
+
+def sc_loss_grad(rgb3, y, H, labels, prm, pos_weight=1.0, mode=SC_MIXED):
+    """(loss, gradient) of one strip: summed weighted cross-entropy."""
+    s = _strip(rgb3)
+    W = s.shape[1]
+    prm = np.ascontiguousarray(prm, np.float32)
+    lab = np.ascontiguousarray(labels, np.uint8)
+    assert lab.size == W and prm.size == SC_NPARAM
+    g = np.zeros(SC_NPARAM, np.float64)
+    loss = lib().orc_sc_loss_grad(_ptr(s), W, int(y), int(H), _ptr(lab), float(pos_weight),
+                                  _ptr(prm), mode, _ptr(g))
+    return loss, g

@@ -411,6 +411,22 @@ int orc_estimate(const uint8_t *rgb, int H, int W, int64_t pitch, uint64_t frame
     uint16_t *cs = (uint16_t *)malloc(sizeof(uint16_t) * cap);
     int32_t M = 0;
     orc_candidates(rgb, H, W, pitch, p, cap, cx16, cy16, cs, &M);
+    int rc = orc_fit(cx16, cy16, cs, M, H, W, frame_key, p, res, dbg);
+    free(cx16);
+    free(cy16);
+    free(cs);
+    return rc;
+}
+
+/* Sec. 2.2.5 from the candidate list on: RANSAC, refits, scores, filters,
+ * best circle and the t_cs acceptance. */
+int orc_fit(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_t M, int H,
+            int W, uint64_t frame_key, const orc_params *p, orc_result *res, orc_debug *dbg) {
+    memset(res, 0, sizeof(*res));
+    int N = p->n_strips, K = p->cands_per_strip;
+    if (W < 8 || H < 3 || N < 1 || K < 2 || (K & 1) || N * K > 256 || M < 0 || M > N * K)
+        return -1;
+    int cap = N * K;
     if (dbg) {
         if (dbg->n_cands) *dbg->n_cands = M;
         for (int j = 0; j < M && j < dbg->cand_cap; ++j) {
@@ -509,7 +525,7 @@ int orc_estimate(const uint8_t *rgb, int H, int W, int64_t pitch, uint64_t frame
         res->n_inliers = bestn;
         res->valid = bestS >= T_cs;
     }
-    free(cx16); free(cy16); free(cs); free(X); free(Y); free(flag); free(IX); free(IY);
+    free(X); free(Y); free(flag); free(IX); free(IY);
     return 0;
 }
 

@@ -125,6 +125,38 @@ float orc_i128_to_f32(int64_t hi, uint64_t lo);
 int orc_estimate(const uint8_t *rgb, int H, int W, int64_t pitch, uint64_t frame_key,
                  const orc_params *p, orc_result *res, orc_debug *dbg);
 
+/* The fitting part of the pipeline (Sec. 2.2.5) on a given candidate list
+ * (pixel coordinates and Q15 scores, in order): same steps and outputs as
+ * orc_estimate after its candidate stage. */
+int orc_fit(const int16_t *xs, const int16_t *ys, const uint16_t *ss, int32_t M, int H, int W,
+            uint64_t frame_key, const orc_params *p, orc_result *res, orc_debug *dbg);
+
+/* ---- Learned edge scorer (1-D CNN over strip profiles; see
+ * ca_scorer_oracle.c).  Parameters: one flat binary32 vector of
+ * ORC_SC_NPARAM values, W1[32][14][7], b1[32], W2[32][32][7], b2[32],
+ * W3[32][32][7], b3[32], wh[32], bh. */
+enum { ORC_SC_CIN = 14, ORC_SC_CH = 32, ORC_SC_K = 7, ORC_SC_NPARAM = 17601 };
+enum { ORC_SC_EXACT = 0, ORC_SC_MIXED = 1 };
+
+/* bfloat16 round-to-nearest-even of a binary32 value. */
+float orc_bf16(float v);
+
+/* Offsets of W1, b1, W2, b2, W3, b3, wh, bh in the parameter vector. */
+void orc_sc_offsets(int32_t out[8]);
+
+/* Column features of a strip (rgb3: rows y-1, y, y+1, each W x 3 bytes). */
+void orc_sc_features(const uint8_t *rgb3, int W, int y, int H, int mixed, double *feat);
+
+/* Logits of the W columns; acts (optional) receives features (W x 14) and
+ * the activations a1, a2, a3 (W x 32 each). */
+int orc_sc_forward(const uint8_t *rgb3, int W, int y, int H, const float *prm, int mode,
+                   double *logits, double *acts);
+
+/* Weighted cross-entropy of the strip's columns against labels (0/1), and
+ * its gradient, added into grads (ORC_SC_NPARAM doubles). */
+double orc_sc_loss_grad(const uint8_t *rgb3, int W, int y, int H, const uint8_t *labels,
+                        float pos_weight, const float *prm, int mode, double *grads);
+
 /* Content-area mask of a result: disc intersected with the rectangle, or the
  * whole rectangle when the circle is not valid.  H*W bytes, 0/1. */
 void orc_mask(const orc_result *res, int H, int W, uint8_t *out);
