@@ -218,6 +218,72 @@ ca_status ca_plan_create(ca_handle *h, const ca_frame *frames, int B, const ca_p
 ca_status ca_plan_launch(ca_plan *plan, void *stream);
 ca_status ca_plan_destroy(ca_plan *plan);
 
+/* ---- Learned edge scorer (Sec. 2.2.4: a learned alternative to the
+ * handcrafted edge score; here a 1-D network over strip profiles).
+ *
+ * Per strip column x (the strip's rows y-1, y, y+1), 14 features: luma, R, G,
+ * B of each row as (v - 128) / 128, then (x - (W-1)/2) / W and (y - (H-1)/2)
+ * / H.  Three convolutions of kernel 7 with 32 output channels and ReLU
+ * ("same" zero padding; conv[x][co] = b[co] + sum_{ci,t} W[co][ci][t]
+ * in[x + t - 3][ci]), a 1x1 head logit = bh + wh . a3 and p = sigmoid(logit).
+ * Weights and activations are rounded to bfloat16, sums accumulate in f32 on
+ * the tensor cores.  The edge score of a column is round(32768 p).
+ *
+ * Parameters: CA_SCORER_NPARAM binary32 values in the order W1[32][14][7],
+ * b1[32], W2[32][32][7], b2[32], W3[32][32][7], b3[32], wh[32], bh.
+ *
+ * With scorer_mode LEARNED the candidates of every half-strip come from the
+ * learned scores (same pick rule, K <= 16); with LEARNED_FALLBACK a half-strip
+ * whose best learned score is below 16384 (p < 1/2) keeps its handcrafted
+ * candidates.  Either mode needs parameters (init, set or load) first. */
+#define CA_SCORER_NPARAM 17601
+
+/* Training hyper-parameters: SGD with momentum on the weighted binary
+ * cross-entropy of the columns, mean over the columns of the step. */
+typedef struct ca_train_params {
+    float lr;          /* step size */
+    float momentum;    /* momentum of the SGD update */
+    float pos_weight;  /* loss weight of edge columns (label 1); others weigh 1 */
+    int32_t apply;     /* 0: compute the gradient only (no update) */
+} ca_train_params;
+
+/* Random initial parameters (He-normal convolution weights, zero biases,
+ * head bias -3), seeded; resets the momentum. */
+ca_status ca_scorer_init(ca_handle *h, uint64_t seed);
+/* Copies n = CA_SCORER_NPARAM parameters in / out (host memory); set resets
+ * the momentum. */
+ca_status ca_scorer_set_params(ca_handle *h, const float *params, size_t n);
+ca_status ca_scorer_get_params(ca_handle *h, float *params, size_t n);
+/* Checkpoint: parameters and momentum in a small binary file (magic "CASC",
+ * version, count, then binary32 values). */
+ca_status ca_scorer_save(ca_handle *h, const char *path);
+ca_status ca_scorer_load(ca_handle *h, const char *path);
+
+/* Network on n stand-alone strips: strips_dev = n x 3 x W x 3 bytes (rows
+ * y-1, y, y+1 of each strip, packed RGB), ys_dev = n middle-row indices in
+ * frames of height H.  Writes the n x W logits (f32) and/or Q15 scores (either
+ * may be NULL).  Queued on `stream`. */
+ca_status ca_scorer_forward(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev, int n,
+                            int W, int H, float *logits_dev, uint16_t *scores_dev, void *stream);
+
+/* One training step on the strips idx_dev[0..n-1] (or 0..n-1 when idx_dev is
+ * NULL) of a strip set as in ca_scorer_forward, with labels_dev = per strip W
+ * bytes (1 = edge column).  Runs the forward pass, the loss and its gradient
+ * with the library's kernels and, if tp->apply, the SGD update.  Synchronous.
+ * loss_host (may be NULL): the summed loss of the step; grads_host (may be
+ * NULL): the summed gradient (CA_SCORER_NPARAM values, before the 1/columns
+ * scaling of the update). */
+ca_status ca_scorer_step(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev,
+                         const uint8_t *labels_dev, const int32_t *idx_dev, int n, int W, int H,
+                         const ca_train_params *tp, float *loss_host, float *grads_host);
+
+/* Training loop: `epochs` passes over the n strips in minibatches of `batch`
+ * strips, shuffled per epoch by `seed`.  epoch_loss_host (may be NULL)
+ * receives the mean loss per column of each epoch.  Synchronous. */
+ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev,
+                          const uint8_t *labels_dev, int n, int W, int H, const ca_train_params *tp,
+                          int epochs, int batch, uint64_t seed, float *epoch_loss_host);
+
 /* Writes the content-area masks of B results (Sec. 1.1, Fig. 1): pixel (x, y)
  * is 1 iff (x-cx)^2 + (y-cy)^2 <= r^2 in binary32 (each operation rounded, no
  * fused multiply-add), or 1 everywhere when valid == 0.  res_dev: device array
@@ -259,7 +325,10 @@ enum {
      * s_theta table (8193), s_iota table (256), then int32 strip rows for
      * H = frame (pass the frame height as `frame`); host computation only,
      * h may be NULL and no device is needed */
-    CA_DUMP_TABLES = 3
+    CA_DUMP_TABLES = 3,
+    /* per frame: N x W uint16 learned scores of the last call (learned
+     * scorer modes only) */
+    CA_DUMP_LEARNED = 4
 };
 
 /* Copies debug data of frame `frame` of the last ca_estimate call (synchronises
@@ -276,9 +345,10 @@ ca_status ca_set_timing(ca_handle *h, int on);
 
 /* Sums of the recorded kernel durations in milliseconds since the last read:
  * ms[0] strip scoring, ms[1] circle fitting, ms[2] mask writing, ms[3] the
- * fused kernel (all three phases); counts[i] = launches timed.  Waits for the
- * recorded events, then clears them. */
-ca_status ca_kernel_times(ca_handle *h, double ms[4], int32_t counts[4]);
+ * fused kernel (all three phases), ms[4] the learned scorer's network;
+ * counts[i] = launches timed.  Waits for the recorded events, then clears
+ * them. */
+ca_status ca_kernel_times(ca_handle *h, double ms[5], int32_t counts[5]);
 
 const char *ca_status_string(ca_status s);
 const char *ca_last_error(const ca_handle *h);

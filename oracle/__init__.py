@@ -76,6 +76,9 @@ def lib():
         L.orc_estimate.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_uint64,
                                    P(OrcParams), P(OrcResult), P(OrcDebug)]
         L.orc_mask.argtypes = [P(OrcResult), C.c_int, C.c_int, C.c_void_p]
+        L.orc_learned_candidates.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64,
+                                             P(OrcParams), C.c_void_p, C.c_int, C.c_int,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_int,
                               C.c_uint64, P(OrcParams), P(OrcResult), P(OrcDebug)]
         L.orc_bf16.argtypes = [C.c_float]
@@ -148,6 +151,33 @@ def strip_scores(frame, row, p=None):
 def score_exact(gx, gy, cx2, cy2, iota, p=None):
     p = p or params()
     return lib().orc_score_exact(int(gx), int(gy), int(cx2), int(cy2), int(iota), C.byref(p))
+
+
+def learned_candidates(frame, learned, fallback, p=None):
+    """Candidates from learned Q15 pixel scores (N x W), with or without the
+    handcrafted fallback of unsure half-strips."""
+    f = _frame(frame)
+    H, W = f.shape[:2]
+    p = p or params()
+    lq = np.ascontiguousarray(learned, np.uint16)
+    assert lq.shape == (p.n_strips, W)
+    cap = p.n_strips * p.cands_per_strip
+    xs = np.zeros(cap, np.int16)
+    ys = np.zeros(cap, np.int16)
+    ss = np.zeros(cap, np.uint16)
+    M = C.c_int32(0)
+    if lib().orc_learned_candidates(_ptr(f), H, W, W * 3, C.byref(p), _ptr(lq),
+                                    1 if fallback else 0, cap, _ptr(xs), _ptr(ys), _ptr(ss),
+                                    C.byref(M)) != 0:
+        raise ValueError("bad candidate arguments")
+    m = M.value
+    return xs[:m].copy(), ys[:m].copy(), ss[:m].copy()
+
+
+def sc_q15(logits):
+    """Learned Q15 score of logits: round(32768 sigmoid(l))."""
+    l = np.asarray(logits, np.float64)
+    return np.floor(32768.0 / (1.0 + np.exp(-l)) + 0.5).astype(np.uint16)
 
 
 def candidates(frame, p=None):

@@ -208,8 +208,45 @@ int orc_strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int row,
  * each excluding pixels within sup_px of an earlier pick of that half; equal
  * scores go to the outermost pixel.  Then the paper's filter: drop points
  * closer than t_px to the image edge or scoring below t_ps. */
-int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
-                   int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M) {
+/* Best K/2 points of one half-strip [x0, x1) by the key (score, outer rank),
+ * each at least sup_px + 1 away from the earlier ones (Sec. 2.2.5: the best
+ * pixel of each half; K/2 > 1 is this project's extension).  Appends the
+ * kept ones (t_px / t_ps filter) to xs/ys/ss; returns the first pick's score
+ * (or -1 if the half is empty). */
+static int pick_half(const uint16_t *s, int x0, int x1, int half, int y, int H, int W,
+                     const orc_params *p, int cap, int16_t *xs, int16_t *ys, uint16_t *ss,
+                     int *m, int32_t *picks) {
+    uint32_t T_ps = (uint32_t)ceil((double)p->t_ps * 32768.0);
+    int T_px = (int)ceil((double)p->t_px);
+    int np = 0, first = -1;
+    for (int r = 0; r < p->cands_per_strip / 2; ++r) {
+        int best = -1;
+        uint32_t bestkey = 0;
+        for (int x = x0; x < x1; ++x) {
+            int sup = 0;
+            for (int j = 0; j < np; ++j)
+                if (abs(x - picks[j]) <= p->sup_px) sup = 1;
+            if (sup) continue;
+            uint32_t rank = half ? (uint32_t)x : (uint32_t)(0xFFFF - x);
+            uint32_t key = ((uint32_t)s[x] << 16) | rank;
+            if (best < 0 || key > bestkey) { best = x; bestkey = key; }
+        }
+        if (best < 0) break;
+        if (r == 0) first = s[best];
+        picks[np++] = best;
+        int keep = s[best] >= T_ps && best >= T_px && best <= W - 1 - T_px &&
+                   y >= T_px && y <= H - 1 - T_px;
+        if (keep) {
+            if (*m < cap) { xs[*m] = (int16_t)best; ys[*m] = (int16_t)y; ss[*m] = s[best]; }
+            ++*m;
+        }
+    }
+    return first;
+}
+
+static int candidates_impl(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                           const uint16_t *learned, int fallback, int cap, int16_t *xs,
+                           int16_t *ys, uint16_t *ss, int32_t *M) {
     int N = p->n_strips, K = p->cands_per_strip;
     if (N < 1 || K < 2 || (K & 1)) return -1;
     int32_t *rows = (int32_t *)malloc(sizeof(int32_t) * N);
@@ -220,41 +257,40 @@ int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_pa
     uint16_t *lut_i = (uint16_t *)malloc(sizeof(uint16_t) * ORC_LUT_I);
     orc_build_luts(p, lut_g, lut_t, lut_i);
     orc_strip_rows(H, N, p->alpha, rows);
-    uint32_t T_ps = (uint32_t)ceil((double)p->t_ps * 32768.0);
-    int T_px = (int)ceil((double)p->t_px);
     int hw = W / 2, m = 0;
     for (int i = 0; i < N; ++i) {
         int y = rows[i];
         strip_scores(rgb, H, W, pitch, y, lut_g, lut_t, lut_i, s, NULL, NULL, NULL);
         for (int half = 0; half < 2; ++half) {
             int x0 = half ? hw : 0, x1 = half ? W : hw;
-            int np = 0;
-            for (int r = 0; r < K / 2; ++r) {
-                int best = -1;
-                uint32_t bestkey = 0;
-                for (int x = x0; x < x1; ++x) {
-                    int sup = 0;
-                    for (int j = 0; j < np; ++j)
-                        if (abs(x - picks[j]) <= p->sup_px) sup = 1;
-                    if (sup) continue;
-                    uint32_t rank = half ? (uint32_t)x : (uint32_t)(0xFFFF - x);
-                    uint32_t key = ((uint32_t)s[x] << 16) | rank;
-                    if (best < 0 || key > bestkey) { best = x; bestkey = key; }
-                }
-                if (best < 0) break;
-                picks[np++] = best;
-                int keep = s[best] >= T_ps && best >= T_px && best <= W - 1 - T_px &&
-                           y >= T_px && y <= H - 1 - T_px;
-                if (keep) {
-                    if (m < cap) { xs[m] = (int16_t)best; ys[m] = (int16_t)y; ss[m] = s[best]; }
-                    ++m;
-                }
+            if (learned) {
+                /* learned scores; with the fallback, a half whose best
+                 * learned score is below one half (16384 in Q15) takes the
+                 * handcrafted points instead */
+                int m0 = m;
+                int first = pick_half(learned + (size_t)i * W, x0, x1, half, y, H, W, p, cap,
+                                      xs, ys, ss, &m, picks);
+                if (!fallback || first >= 16384) continue;
+                m = m0;
             }
+            pick_half(s, x0, x1, half, y, H, W, p, cap, xs, ys, ss, &m, picks);
         }
     }
     *M = m;
     free(rows); free(s); free(picks); free(lut_g); free(lut_t); free(lut_i);
     return 0;
+}
+
+int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                   int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M) {
+    return candidates_impl(rgb, H, W, pitch, p, NULL, 0, cap, xs, ys, ss, M);
+}
+
+int orc_learned_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                           const uint16_t *learned, int fallback, int cap, int16_t *xs,
+                           int16_t *ys, uint16_t *ss, int32_t *M) {
+    if (!learned) return -1;
+    return candidates_impl(rgb, H, W, pitch, p, learned, fallback, cap, xs, ys, ss, M);
 }
 
 /* ------------------------------------------------------- Philox4x32-10 -- */

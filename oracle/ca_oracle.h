@@ -102,6 +102,14 @@ double orc_score_exact(int gx, int gy, int cx2, int cy2, int iota, const orc_par
 int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
                    int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M);
 
+/* Candidates from learned per-pixel Q15 scores (learned: N x W, strip by
+ * strip), picked by the same rule; with `fallback`, a half-strip whose best
+ * learned score is below 16384 (probability one half) takes the handcrafted
+ * points of that half instead. */
+int orc_learned_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                           const uint16_t *learned, int fallback, int cap, int16_t *xs,
+                           int16_t *ys, uint16_t *ss, int32_t *M);
+
 /* Philox4x32-10 (Salmon et al., SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 

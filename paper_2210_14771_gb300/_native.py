@@ -13,6 +13,8 @@ CA_NORM_2N, CA_NORM_NK, CA_NORM_RAW = 0, 1, 2
 CA_SCORER_HAND, CA_SCORER_LEARNED, CA_SCORER_LEARNED_FALLBACK = 0, 1, 2
 CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
 CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
+CA_DUMP_LEARNED = 4
+CA_SCORER_NPARAM = 17601
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
 
 
@@ -40,6 +42,11 @@ class CaTuning(C.Structure):
                 ("ms_staged", C.c_float), ("ms_fused", C.c_float), ("ms_untuned", C.c_float)]
 
 
+class CaTrainParams(C.Structure):
+    _fields_ = [("lr", C.c_float), ("momentum", C.c_float), ("pos_weight", C.c_float),
+                ("apply", C.c_int32)]
+
+
 class CaResult(C.Structure):
     _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("r", C.c_float), ("score", C.c_float),
                 ("valid", C.c_int32), ("n_inliers", C.c_int32)]
@@ -64,6 +71,19 @@ SIGNATURES = [
                                  _P(C.c_void_p)]),
     ("ca_plan_launch", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ca_plan_destroy", C.c_int, [C.c_void_p]),
+    ("ca_scorer_init", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("ca_scorer_set_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("ca_scorer_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("ca_scorer_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ca_scorer_load", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ca_scorer_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ca_scorer_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int, C.c_int, C.c_int, _P(CaTrainParams), _P(C.c_float),
+                                 C.c_void_p]),
+    ("ca_scorer_train", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                  C.c_int, _P(CaTrainParams), C.c_int, C.c_int, C.c_uint64,
+                                  C.c_void_p]),
     ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,

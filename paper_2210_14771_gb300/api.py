@@ -217,10 +217,83 @@ class ContentArea:
 
     def kernel_times(self):
         """{kernel: (total ms, launches)} since the last read (CUDA events)."""
-        ms = (C.c_double * 4)()
-        cnt = (C.c_int32 * 4)()
+        ms = (C.c_double * 5)()
+        cnt = (C.c_int32 * 5)()
         self._check(N.lib().ca_kernel_times(self._h, ms, cnt))
-        return {name: (ms[i], cnt[i]) for i, name in enumerate(("strips", "fit", "mask", "fused"))}
+        names = ("strips", "fit", "mask", "fused", "scorer")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(names)}
+
+    # ------------------------------------------------------ learned scorer --
+    def scorer_init(self, seed: int = 0):
+        self._check(N.lib().ca_scorer_init(self._h, seed))
+
+    def scorer_set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(N.lib().ca_scorer_set_params(self._h, p.ctypes.data_as(C.c_void_p), p.size))
+
+    def scorer_get_params(self) -> np.ndarray:
+        p = np.zeros(N.CA_SCORER_NPARAM, np.float32)
+        self._check(N.lib().ca_scorer_get_params(self._h, p.ctypes.data_as(C.c_void_p), p.size))
+        return p
+
+    def scorer_save(self, path: str):
+        self._check(N.lib().ca_scorer_save(self._h, path.encode()))
+
+    def scorer_load(self, path: str):
+        self._check(N.lib().ca_scorer_load(self._h, path.encode()))
+
+    @staticmethod
+    def _strip_args(strips, ys):
+        assert strips.dtype == torch.uint8 and strips.is_cuda and strips.is_contiguous()
+        assert strips.dim() == 4 and strips.shape[1] == 3 and strips.shape[3] == 3
+        assert ys.dtype == torch.int32 and ys.is_cuda and ys.is_contiguous()
+        return int(strips.shape[0]), int(strips.shape[2])
+
+    def scorer_forward(self, strips, ys, H: int, stream=None):
+        """Logits and Q15 scores (n, W) of stand-alone strips (n, 3, W, 3)."""
+        n, W = self._strip_args(strips, ys)
+        logits = torch.empty((n, W), dtype=torch.float32, device=strips.device)
+        scores = torch.empty((n, W), dtype=torch.int16, device=strips.device)
+        self._check(N.lib().ca_scorer_forward(
+            self._h, C.c_void_p(strips.data_ptr()), C.c_void_p(ys.data_ptr()), n, W, H,
+            C.c_void_p(logits.data_ptr()), C.c_void_p(scores.data_ptr()),
+            _stream_ptr(stream, strips.device)))
+        return logits, scores
+
+    def scorer_step(self, strips, ys, labels, H: int, idx=None, lr=0.0, momentum=0.9,
+                    pos_weight=1.0, apply=False, want_grads=True):
+        """One training step; returns (summed loss, summed gradient or None)."""
+        n, W = self._strip_args(strips, ys)
+        if idx is not None:
+            assert idx.dtype == torch.int32 and idx.is_cuda
+            n = int(idx.numel())
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1 if apply else 0)
+        loss = C.c_float(0.0)
+        g = np.zeros(N.CA_SCORER_NPARAM, np.float32) if want_grads else None
+        self._check(N.lib().ca_scorer_step(
+            self._h, C.c_void_p(strips.data_ptr()), C.c_void_p(ys.data_ptr()),
+            C.c_void_p(labels.data_ptr()), C.c_void_p(idx.data_ptr()) if idx is not None else None,
+            n, W, H, C.byref(tp), C.byref(loss),
+            g.ctypes.data_as(C.c_void_p) if g is not None else None))
+        return float(loss.value), g
+
+    def scorer_train(self, strips, ys, labels, H: int, epochs=1, batch=64, seed=0, lr=0.05,
+                     momentum=0.9, pos_weight=20.0):
+        """ca_scorer_train; returns the mean loss per column of each epoch."""
+        n, W = self._strip_args(strips, ys)
+        assert labels.dtype == torch.uint8 and labels.shape == (n, W)
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1)
+        out = np.zeros(max(epochs, 1), np.float32)
+        self._check(N.lib().ca_scorer_train(
+            self._h, C.c_void_p(strips.data_ptr()), C.c_void_p(ys.data_ptr()),
+            C.c_void_p(labels.data_ptr()), n, W, H, C.byref(tp), epochs, batch, seed,
+            out.ctypes.data_as(C.c_void_p)))
+        return out[:epochs]
+
+    def dump_learned(self, frame: int, n_strips: int, W: int):
+        """Learned Q15 scores (N, W) of one frame of the last call."""
+        raw = self._dump(N.CA_DUMP_LEARNED, frame, None, 2 * n_strips * W)
+        return raw.view(np.uint16).reshape(n_strips, W)
 
     # --------------------------------------------------------------- debug --
     def set_debug(self, level: int):

@@ -31,6 +31,7 @@ struct LaunchCfg {
     int mode = CA_BATCH_STAGED;   // CA_BATCH_STAGED or CA_BATCH_FUSED
     int T = 1;                    // threads per hypothesis
     int wave = 1;                 // fused: frames per wave
+    int scorer = CA_SCORER_HAND;  // learned modes always run staged
 };
 
 struct LutKey {
@@ -85,7 +86,25 @@ struct ca_handle {
     // kernel timing: event pairs per kernel kind (0 strips, 1 fit, 2 mask, 3 fused)
     bool timing = false;
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[4];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed[5];
+
+    // learned scorer: f32 parameters and momentum, packed bf16 weight block,
+    // per-CTA gradient partials, learned pixel scores of the last call
+    struct {
+        bool ready = false;
+        float *params = nullptr, *mom = nullptr, *partial = nullptr, *grads = nullptr,
+              *losses = nullptr;
+        unsigned char *block = nullptr;
+        uint32_t *err = nullptr;
+        int32_t *idx = nullptr;
+        size_t idx_cap = 0, losses_cap = 0;
+        uint16_t *scores = nullptr;
+        size_t scores_cap = 0;
+        int partial_n = 0;
+        int last_N = 0;
+        std::vector<int64_t> last_pix_off;
+        std::vector<int32_t> last_W;
+    } sc;
 
     // launch configurations found by ca_tune, by shape of batch
     std::map<uint64_t, LaunchCfg> tuned;
@@ -234,8 +253,16 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
     if (p->hyp_threads != 0 && p->hyp_threads != 1 && p->hyp_threads != 2 &&
         p->hyp_threads != 4 && p->hyp_threads != 8)
         return fail(h, CA_ERR_INVALID_ARG, "hyp_threads %d not in {0, 1, 2, 4, 8}", p->hyp_threads);
-    if (p->scorer_mode != CA_SCORER_HAND)
-        return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs learned weights", p->scorer_mode);
+    if (p->scorer_mode < CA_SCORER_HAND || p->scorer_mode > CA_SCORER_LEARNED_FALLBACK)
+        return fail(h, CA_ERR_INVALID_ARG, "bad scorer_mode %d", p->scorer_mode);
+    if (p->scorer_mode != CA_SCORER_HAND) {
+        if (!h || !h->sc.ready)
+            return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs scorer parameters "
+                        "(ca_scorer_init / set_params / load)", p->scorer_mode);
+        if (p->cands_per_strip / 2 > kScMaxPicks)
+            return fail(h, CA_ERR_INVALID_ARG, "learned scorer: cands_per_strip <= %d",
+                        2 * kScMaxPicks);
+    }
     const float fs[] = {p->alpha, p->t_g, p->t_theta_deg, p->t_iota, p->t_ps, p->t_cs,
                         p->t_px, p->t_ri, p->r_min, p->r_max, p->d_max};
     for (float v : fs)
@@ -441,6 +468,8 @@ LaunchCfg choose_cfg(const ca_handle *h, const ca_frame *frames, int B, const ca
         : choose_hyp_threads(0, B, hyps_per_frame(p), h->sm_count);
     c.wave = p.wave_frames > 0 ? std::min(p.wave_frames, B)
            : (t && t->mode == c.mode) ? t->wave : default_wave(h, B, p, c.T);
+    c.scorer = p.scorer_mode;
+    if (c.scorer != CA_SCORER_HAND) c.mode = CA_BATCH_STAGED;   // the scorer runs between phases
     return c;
 }
 
@@ -449,6 +478,8 @@ struct CallBlock {
     std::vector<unsigned char> host;
     size_t off_rows = 0, off_segs = 0;
     int total_units = 0, n_segs = 0, total_items = 0;
+    int sc_segs = 0;       // learned scorer segments
+    int64_t sc_pix = 0;    // learned scorer pixel scores
 };
 
 void build_block(const ca_frame *frames, int B, int N, float alpha, const DevParams *P,
@@ -460,7 +491,8 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
         for (int i = 0; i < B; ++i)
             if (!row_off.count(frames[i].H)) { row_off[frames[i].H] = n_rows; n_rows += N; }
     std::vector<DevFrame> df((size_t)B);
-    int units = 0, mitems = 0;
+    int units = 0, mitems = 0, sc_segs = 0;
+    int64_t sc_pix = 0;
     for (int i = 0; i < B; ++i) {
         const ca_frame &f = frames[i];
         DevFrame &d = df[i];
@@ -476,6 +508,10 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
         d.mitem_off = mitems;
         d.vec_ok = ((uintptr_t)f.rgb_dev % 16 == 0) && (f.pitch % 16 == 0) && (f.W % 16 == 0);
         d.mask_vec_ok = f.mask_dev && ((uintptr_t)f.mask_dev % 16 == 0) && (f.W % 16 == 0);
+        d.sc_seg_off = sc_segs;
+        d.sc_pix_off = (int32_t)sc_pix;
+        sc_segs += N * ((f.W + kScSegOut - 1) / kScSegOut);
+        sc_pix += (int64_t)N * f.W;
         if (f.mask_dev) {
             units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
             mitems += mask_items_of(f.H);
@@ -516,6 +552,8 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
     cb.total_units = units;
     cb.n_segs = (int)segs.size();
     cb.total_items = items;
+    cb.sc_segs = sc_segs;
+    cb.sc_pix = sc_pix;
 }
 
 int mask_grid(const ca_handle *h, int units) {
@@ -590,21 +628,44 @@ ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32
     // CTAs beyond the resident ones wait for a free slot, which balances
     // uneven half-strips
     const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
-    cudaEvent_t t0 = timed ? time_begin(h, stream) : nullptr;
-    e = launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
-    time_end(h, 0, t0, stream);
+    cudaEvent_t t0 = nullptr;
+    if (cfg.scorer != CA_SCORER_LEARNED) {
+        t0 = timed ? time_begin(h, stream) : nullptr;
+        e = launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
+        time_end(h, 0, t0, stream);
+        *kernels += 1;
+    }
+    if (cfg.scorer != CA_SCORER_HAND) {
+        // learned scores of every strip column, then the picks per half-strip
+        ScSource src{};
+        src.frames = d_frames;
+        src.B = B;
+        src.rows = d_rows;
+        src.N = P.N;
+        const int grid = std::max(1, std::min(cb.sc_segs, h->sm_count * sc_infer_blocks_per_sm()));
+        t0 = timed ? time_begin(h, stream) : nullptr;
+        e = sc_launch_infer(src, h->sc.block, h->sc.scores, nullptr, cb.sc_segs, h->sc.err, grid,
+                            stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_infer launch");
+        time_end(h, 4, t0, stream);
+        const int pgrid = std::max(1, std::min((2 * B * P.N + 7) / 8, h->sm_count * 8));
+        e = sc_launch_pick(d_frames, B, d_rows, P, h->sc.scores,
+                           cfg.scorer == CA_SCORER_LEARNED_FALLBACK, ws.slots, pgrid, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_pick launch");
+        *kernels += 2;
+    }
     t0 = timed ? time_begin(h, stream) : nullptr;
     e = launch_fit(d_frames, B, P, ws.slots, ws, out, stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_fit launch");
     time_end(h, 1, t0, stream);
-    *kernels = 2;
+    *kernels += 1;
     if (cb.total_units > 0) {
         t0 = timed ? time_begin(h, stream) : nullptr;
         e = launch_mask(d_frames, B, out, cb.total_units, mask_grid(h, cb.total_units), stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "k_mask launch");
         time_end(h, 2, t0, stream);
-        *kernels = 3;
+        *kernels += 1;
     }
     return CA_OK;
 }
@@ -645,6 +706,20 @@ ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_par
     sg->used = true;
     const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
     if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
+    if (cfg.scorer != CA_SCORER_HAND) {
+        if (cb.sc_pix > INT32_MAX) return fail(h, CA_ERR_INVALID_ARG, "batch too large for the scorer");
+        if ((size_t)cb.sc_pix > h->sc.scores_cap) {
+            if ((st = grow(h, &h->sc.scores, 0, (size_t)cb.sc_pix, false)) != CA_OK) return st;
+            h->sc.scores_cap = (size_t)cb.sc_pix;
+        }
+        h->sc.last_N = P.N;
+        h->sc.last_pix_off.assign((size_t)B, 0);
+        h->sc.last_W.assign((size_t)B, 0);
+        for (int i = 0; i < B; ++i) {
+            h->sc.last_pix_off[i] = ((const DevFrame *)cb.host.data())[i].sc_pix_off;
+            h->sc.last_W[i] = frames[i].W;
+        }
+    }
     int fgrid = 0;
     if ((st = prepare_kernels(h, P, cfg, &fgrid)) != CA_OK) return st;
     const unsigned char *dev = (const unsigned char *)sg->dev;
@@ -755,6 +830,15 @@ ca_status ca_destroy(ca_handle *h) {
     cudaFree(h->ws.n_hyps);
     cudaFree(h->ws.n_cands);
     cudaFree(h->ws.sync);
+    cudaFree(h->sc.params);
+    cudaFree(h->sc.mom);
+    cudaFree(h->sc.partial);
+    cudaFree(h->sc.grads);
+    cudaFree(h->sc.losses);
+    cudaFree(h->sc.block);
+    cudaFree(h->sc.err);
+    cudaFree(h->sc.idx);
+    cudaFree(h->sc.scores);
     cudaFree(h->e2e_frames);
     cudaFree(h->e2e_masks);
     cudaFree(h->e2e_res);
@@ -793,6 +877,270 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
         fr[i].frame_key = keys ? keys[i] : (uint64_t)i;
     }
     return estimate_impl(h, fr.data(), B, p, out_dev, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------ learned scorer --
+namespace {
+
+ca_status sc_alloc(ca_handle *h) {
+    auto &S = h->sc;
+    if (S.params) return CA_OK;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    S.partial_n = h->sm_count;   // one partial slice per training CTA (one CTA per SM)
+    CA_CUDA(h, cudaMalloc(&S.params, sizeof(float) * kScNParam));
+    CA_CUDA(h, cudaMalloc(&S.mom, sizeof(float) * kScNParam));
+    CA_CUDA(h, cudaMalloc(&S.grads, sizeof(float) * kScNParam));
+    CA_CUDA(h, cudaMalloc(&S.partial, sizeof(float) * kScPartialStride * (size_t)S.partial_n));
+    CA_CUDA(h, cudaMalloc(&S.block, kScBlockBytes));
+    CA_CUDA(h, cudaMalloc(&S.err, sizeof(uint32_t)));
+    CA_CUDA(h, cudaMemset(S.partial, 0, sizeof(float) * kScPartialStride * (size_t)S.partial_n));
+    CA_CUDA(h, cudaMemset(S.block, 0, kScBlockBytes));
+    CA_CUDA(h, cudaMemset(S.err, 0, sizeof(uint32_t)));
+    return CA_OK;
+}
+
+// Uploads parameters (and zero momentum) and packs the weight block.
+ca_status sc_upload(ca_handle *h, const float *params, const float *mom) {
+    ca_status st = sc_alloc(h);
+    if (st != CA_OK) return st;
+    auto &S = h->sc;
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    CA_CUDA(h, cudaMemcpy(S.params, params, sizeof(float) * kScNParam, cudaMemcpyHostToDevice));
+    if (mom) CA_CUDA(h, cudaMemcpy(S.mom, mom, sizeof(float) * kScNParam, cudaMemcpyHostToDevice));
+    else CA_CUDA(h, cudaMemset(S.mom, 0, sizeof(float) * kScNParam));
+    CA_CUDA(h, sc_launch_pack(S.params, S.block, nullptr));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    S.ready = true;
+    return CA_OK;
+}
+
+ca_status sc_check_err(ca_handle *h) {
+    uint32_t e = 0;
+    CA_CUDA(h, cudaMemcpy(&e, h->sc.err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) {
+        CA_CUDA(h, cudaMemset(h->sc.err, 0, sizeof(uint32_t)));
+        return fail(h, CA_ERR_TIMEOUT, "a tensor-core wait of the scorer gave up (flags 0x%x)", e);
+    }
+    return CA_OK;
+}
+
+uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double gauss(uint64_t &st) {   // Box-Muller from two uniforms in (0, 1)
+    const double u1 = ((double)(splitmix64(st) >> 11) + 0.5) / 9007199254740992.0;
+    const double u2 = ((double)(splitmix64(st) >> 11) + 0.5) / 9007199254740992.0;
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+ca_status check_strips(ca_handle *h, const uint8_t *strips, const int32_t *ys, int n, int W, int H) {
+    if (!strips || !ys) return fail(h, CA_ERR_INVALID_ARG, "strips or ys is NULL");
+    if (n < 0 || W < 1 || W > kMaxDim || H < 3 || H > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "bad strip set (n %d, W %d, H %d)", n, W, H);
+    if (!h->sc.ready) return fail(h, CA_ERR_STATE, "scorer has no parameters");
+    return CA_OK;
+}
+
+int sc_segs_of(int n, int W) { return n * ((W + kScSegOut - 1) / kScSegOut); }
+
+// Forward + loss + gradient partials of n strips, then the reduction (and the
+// update when tp->apply).  Queued on `s`.
+ca_status sc_step_async(ca_handle *h, const uint8_t *strips, const int32_t *ys,
+                        const uint8_t *labels, const int32_t *idx, int n, int W, int H,
+                        const ca_train_params &tp, float *loss_dev, float *grads_dev,
+                        cudaStream_t s) {
+    auto &S = h->sc;
+    ScSource src{};
+    src.strips = strips;
+    src.ys = ys;
+    src.idx = idx;
+    src.n = n;
+    src.W = W;
+    src.H = H;
+    const int segs = sc_segs_of(n, W);
+    const int grid = std::max(1, std::min(segs, S.partial_n));
+    cudaError_t e = sc_launch_train(src, labels, tp.pos_weight, S.block, S.partial, segs, S.err,
+                                    grid, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_train launch");
+    const float scale = 1.0f / (float)((double)n * W);
+    e = sc_launch_sgd(S.params, S.mom, S.partial, grid, scale, tp.lr, tp.momentum, tp.apply,
+                      grads_dev, loss_dev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_sgd launch");
+    h->launches += 2;
+    if (tp.apply) {
+        e = sc_launch_pack(S.params, S.block, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_pack launch");
+        h->launches += 1;
+    }
+    return CA_OK;
+}
+
+}  // namespace
+
+ca_status ca_scorer_init(ca_handle *h, uint64_t seed) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    std::vector<float> p(kScNParam, 0.0f);
+    uint64_t st = seed ^ 0x5CA1AB1E5EEDull;
+    auto fill = [&](int off, int count, double stdv) {
+        for (int i = 0; i < count; ++i) p[off + i] = (float)(stdv * gauss(st));
+    };
+    fill(kScPW1, kScPB1 - kScPW1, std::sqrt(2.0 / (kScCin * kScTaps)));
+    fill(kScPW2, kScPB2 - kScPW2, std::sqrt(2.0 / (kScCh * kScTaps)));
+    fill(kScPW3, kScPB3 - kScPW3, std::sqrt(2.0 / (kScCh * kScTaps)));
+    fill(kScPWh, kScCh, std::sqrt(1.0 / kScCh));
+    p[kScPBh] = -3.0f;
+    return sc_upload(h, p.data(), nullptr);
+}
+
+ca_status ca_scorer_set_params(ca_handle *h, const float *params, size_t n) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (!params || n != (size_t)kScNParam)
+        return fail(h, CA_ERR_INVALID_ARG, "scorer parameters: need %d values", kScNParam);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(params[i])) return fail(h, CA_ERR_INVALID_ARG, "non-finite parameter %zu", i);
+    return sc_upload(h, params, nullptr);
+}
+
+ca_status ca_scorer_get_params(ca_handle *h, float *params, size_t n) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (!params || n != (size_t)kScNParam)
+        return fail(h, CA_ERR_INVALID_ARG, "scorer parameters: need %d values", kScNParam);
+    if (!h->sc.ready) return fail(h, CA_ERR_STATE, "scorer has no parameters");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    CA_CUDA(h, cudaMemcpy(params, h->sc.params, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return CA_OK;
+}
+
+ca_status ca_scorer_save(ca_handle *h, const char *path) {
+    if (!h || !path) return CA_ERR_INVALID_ARG;
+    if (!h->sc.ready) return fail(h, CA_ERR_STATE, "scorer has no parameters");
+    std::vector<float> p(kScNParam), m(kScNParam);
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    CA_CUDA(h, cudaMemcpy(p.data(), h->sc.params, sizeof(float) * kScNParam, cudaMemcpyDeviceToHost));
+    CA_CUDA(h, cudaMemcpy(m.data(), h->sc.mom, sizeof(float) * kScNParam, cudaMemcpyDeviceToHost));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(h, CA_ERR_INVALID_ARG, "cannot write %s", path);
+    const uint32_t hdr[4] = {0x43534143u /* "CASC" */, 1u, (uint32_t)kScNParam, 2u};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size() &&
+              std::fwrite(m.data(), sizeof(float), m.size(), f) == m.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? CA_OK : fail(h, CA_ERR_INVALID_ARG, "short write to %s", path);
+}
+
+ca_status ca_scorer_load(ca_handle *h, const char *path) {
+    if (!h || !path) return CA_ERR_INVALID_ARG;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(h, CA_ERR_INVALID_ARG, "cannot read %s", path);
+    uint32_t hdr[4] = {0, 0, 0, 0};
+    std::vector<float> p(kScNParam), m(kScNParam);
+    bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 0x43534143u && hdr[1] == 1u &&
+              hdr[2] == (uint32_t)kScNParam && hdr[3] == 2u &&
+              std::fread(p.data(), sizeof(float), p.size(), f) == p.size() &&
+              std::fread(m.data(), sizeof(float), m.size(), f) == m.size();
+    std::fclose(f);
+    if (!ok) return fail(h, CA_ERR_INVALID_ARG, "%s is not a scorer checkpoint", path);
+    return sc_upload(h, p.data(), m.data());
+}
+
+ca_status ca_scorer_forward(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev, int n,
+                            int W, int H, float *logits_dev, uint16_t *scores_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips(h, strips_dev, ys_dev, n, W, H);
+    if (st != CA_OK || n == 0) return st;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = order_after_last(h, s)) != CA_OK) return st;
+    ScSource src{};
+    src.strips = strips_dev;
+    src.ys = ys_dev;
+    src.n = n;
+    src.W = W;
+    src.H = H;
+    const int segs = sc_segs_of(n, W);
+    const int grid = std::max(1, std::min(segs, h->sm_count * sc_infer_blocks_per_sm()));
+    cudaEvent_t t0 = time_begin(h, s);
+    cudaError_t e = sc_launch_infer(src, h->sc.block, scores_dev, logits_dev, segs, h->sc.err,
+                                    grid, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_infer launch");
+    time_end(h, 4, t0, s);
+    h->launches += 1;
+    return mark_last(h, s);
+}
+
+ca_status ca_scorer_step(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev,
+                         const uint8_t *labels_dev, const int32_t *idx_dev, int n, int W, int H,
+                         const ca_train_params *tp, float *loss_host, float *grads_host) {
+    if (!h || !tp) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips(h, strips_dev, ys_dev, n, W, H);
+    if (st != CA_OK) return st;
+    if (!labels_dev || n == 0) return fail(h, CA_ERR_INVALID_ARG, "no labels or no strips");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    if (!h->sc.losses) {
+        CA_CUDA(h, cudaMalloc(&h->sc.losses, sizeof(float) * 1024));
+        h->sc.losses_cap = 1024;
+    }
+    if ((st = sc_step_async(h, strips_dev, ys_dev, labels_dev, idx_dev, n, W, H, *tp,
+                            h->sc.losses, grads_host ? h->sc.grads : nullptr, nullptr)) != CA_OK)
+        return st;
+    CA_CUDA(h, cudaDeviceSynchronize());
+    if ((st = sc_check_err(h)) != CA_OK) return st;
+    if (loss_host) CA_CUDA(h, cudaMemcpy(loss_host, h->sc.losses, sizeof(float), cudaMemcpyDeviceToHost));
+    if (grads_host)
+        CA_CUDA(h, cudaMemcpy(grads_host, h->sc.grads, sizeof(float) * kScNParam, cudaMemcpyDeviceToHost));
+    return CA_OK;
+}
+
+ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev,
+                          const uint8_t *labels_dev, int n, int W, int H, const ca_train_params *tp,
+                          int epochs, int batch, uint64_t seed, float *epoch_loss_host) {
+    if (!h || !tp) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips(h, strips_dev, ys_dev, n, W, H);
+    if (st != CA_OK) return st;
+    if (!labels_dev || n == 0 || epochs < 0 || batch < 1)
+        return fail(h, CA_ERR_INVALID_ARG, "bad training arguments");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    const int steps = (n + batch - 1) / batch;
+    if ((size_t)n > h->sc.idx_cap) {
+        if ((st = grow(h, &h->sc.idx, 0, (size_t)n, false)) != CA_OK) return st;
+        h->sc.idx_cap = (size_t)n;
+    }
+    if ((size_t)steps > h->sc.losses_cap) {
+        if ((st = grow(h, &h->sc.losses, 0, (size_t)steps, false)) != CA_OK) return st;
+        h->sc.losses_cap = (size_t)steps;
+    }
+    std::vector<int32_t> order((size_t)n);
+    std::vector<float> losses((size_t)steps);
+    uint64_t rs = seed ^ 0x7EA1C0DEull;
+    cudaStream_t s = nullptr;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = 0; i < n; ++i) order[i] = i;
+        for (int i = n - 1; i > 0; --i) std::swap(order[i], order[splitmix64(rs) % (uint64_t)(i + 1)]);
+        CA_CUDA(h, cudaMemcpy(h->sc.idx, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+        for (int k = 0; k < steps; ++k) {
+            const int cnt = std::min(batch, n - k * batch);
+            if ((st = sc_step_async(h, strips_dev, ys_dev, labels_dev, h->sc.idx + (size_t)k * batch,
+                                    cnt, W, H, *tp, h->sc.losses + k, nullptr, s)) != CA_OK)
+                return st;
+        }
+        CA_CUDA(h, cudaMemcpy(losses.data(), h->sc.losses, sizeof(float) * steps, cudaMemcpyDeviceToHost));
+        if ((st = sc_check_err(h)) != CA_OK) return st;
+        if (epoch_loss_host) {
+            double t = 0.0;
+            for (float v : losses) t += v;
+            epoch_loss_host[ep] = (float)(t / ((double)n * W));
+        }
+    }
+    CA_CUDA(h, cudaDeviceSynchronize());
+    return CA_OK;
 }
 
 ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
@@ -1066,6 +1414,7 @@ ca_status ca_sync(ca_handle *h, void *stream) {
     ca_status st = check_sync_word(h, h->ws);
     for (ca_plan *pl : h->plans)
         if (st == CA_OK) st = check_sync_word(h, pl->ws);
+    if (st == CA_OK && h->sc.err) st = sc_check_err(h);
     return st;
 }
 
@@ -1095,7 +1444,7 @@ ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p, v
     }
     if (!h) return CA_ERR_INVALID_ARG;
     if (frame < 0 || frame >= h->last_B) return fail(h, CA_ERR_INVALID_ARG, "bad frame index");
-    if (h->debug < 1) return fail(h, CA_ERR_STATE, "debug capture is off");
+    if (h->debug < 1 && what != CA_DUMP_LEARNED) return fail(h, CA_ERR_STATE, "debug capture is off");
     CA_CUDA(h, cudaSetDevice(h->device));
     if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
     if (what == CA_DUMP_CANDIDATES) {
@@ -1123,6 +1472,16 @@ ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p, v
         if (written) *written = need;
         return CA_OK;
     }
+    if (what == CA_DUMP_LEARNED) {
+        if (frame >= (int)h->sc.last_W.size() || h->sc.last_N == 0)
+            return fail(h, CA_ERR_STATE, "the last call did not use the learned scorer");
+        const size_t cnt = (size_t)h->sc.last_N * h->sc.last_W[frame];
+        if (bytes < 2 * cnt) return fail(h, CA_ERR_INVALID_ARG, "buffer too small (%zu)", 2 * cnt);
+        CA_CUDA(h, cudaMemcpy(host_buf, h->sc.scores + h->sc.last_pix_off[frame],
+                              2 * cnt, cudaMemcpyDeviceToHost));
+        if (written) *written = 2 * cnt;
+        return CA_OK;
+    }
     return fail(h, CA_ERR_INVALID_ARG, "unknown dump %d", what);
 }
 
@@ -1134,10 +1493,10 @@ ca_status ca_set_timing(ca_handle *h, int on) {
     return CA_OK;
 }
 
-ca_status ca_kernel_times(ca_handle *h, double ms[4], int32_t counts[4]) {
+ca_status ca_kernel_times(ca_handle *h, double ms[5], int32_t counts[5]) {
     if (!h || !ms || !counts) return CA_ERR_INVALID_ARG;
     CA_CUDA(h, cudaSetDevice(h->device));
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         ms[k] = 0.0;
         counts[k] = 0;
         for (auto &pr : h->timed[k]) {

@@ -35,10 +35,11 @@ struct DevFrame {
     int32_t H, W;
     int32_t rows_off;   // offset of this frame's strip rows in the rows table
     int32_t unit_off;   // prefix sum of mask units before this frame
-    int32_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
-    int32_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
+    int16_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
+    int16_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
     int32_t mitem_off;  // prefix sum of fused-kernel mask items before this frame
-    int32_t pad;
+    int32_t sc_seg_off; // learned scorer: prefix sum of its segments before this frame
+    int32_t sc_pix_off; // learned scorer: offset of this frame's N x W pixel scores
 };
 static_assert(sizeof(DevFrame) == 64, "DevFrame layout");
 
@@ -123,6 +124,53 @@ struct Workspace {
     uint32_t *sync = nullptr;        // sync_words(sync_frames), fused kernel
     int32_t sync_frames = 0;
 };
+
+// ---- Learned edge scorer (ca_scorer.cu): 1-D CNN over strip profiles.
+constexpr int kScCin = 14, kScCh = 32, kScTaps = 7;
+constexpr int kScHalo = 9;                       // 3 layers x 3 columns of context
+constexpr int kScSegOut = 512 - 2 * kScHalo;     // output columns per 512-column segment
+constexpr int kScNParam = 17601;                 // flat parameter count (see ca.h)
+constexpr int kScMaxPicks = 8;                   // K/2 limit with the learned scorer
+constexpr uint32_t kScErrTimeout = 2u;
+// parameter offsets in the flat vector: W1[32][14][7], b1, W2[32][32][7], b2, W3, b3, wh, bh
+constexpr int kScPW1 = 0, kScPB1 = 3136, kScPW2 = 3168, kScPB2 = 10336, kScPW3 = 10368,
+              kScPB3 = 17536, kScPWh = 17568, kScPBh = 17600;
+// packed device weight block (bytes): bf16 B operands of the forward convolutions
+// ([tap x input chunk][32 out][8 in]), of the input-gradient convolutions of
+// layers 2-3 ([tap x output chunk][32 in][8 out], taps reversed), then floats
+constexpr int kScOffW1f = 0, kScOffW2f = 7168, kScOffW3f = 21504, kScOffW2b = 35840,
+              kScOffW3b = 50176, kScOffVec = 64512;
+constexpr int kScFwdBytes = 35840, kScVecBytes = 528, kScBlockBytes = 65040;
+constexpr int kScPartialStride = 17664;          // per-CTA gradient partials (+ loss at kScNParam)
+
+// Rows of the strips a scorer launch reads: either frames (rows from the
+// strip-row table) or stand-alone strips (3 rows x W x 3 bytes each).
+struct ScSource {
+    const DevFrame *frames;   // frames mode
+    int B;
+    const int32_t *rows;
+    int N;
+    const uint8_t *strips;    // strips mode (frames == nullptr)
+    const int32_t *ys;        // middle row of each strip in its frame
+    const int32_t *idx;       // strips mode: optional index list of the strips to use
+    int n, W, H;
+};
+
+cudaError_t sc_launch_pack(const float *params, unsigned char *block, cudaStream_t s);
+size_t sc_infer_smem();
+int sc_infer_blocks_per_sm();
+cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uint16_t *scores,
+                            float *logits, int total_segs, uint32_t *err, int grid, cudaStream_t s);
+cudaError_t sc_launch_pick(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
+                           const uint16_t *scores, int fallback, CandSlot *slots, int grid,
+                           cudaStream_t s);
+size_t sc_train_smem();
+cudaError_t sc_launch_train(const ScSource &src, const uint8_t *labels, float pos_weight,
+                            const unsigned char *block, float *partial, int total_segs,
+                            uint32_t *err, int grid, cudaStream_t s);
+cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
+                          float lr, float momentum, int apply, float *grads_out, float *loss_out,
+                          cudaStream_t s);
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
 cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,

@@ -1,0 +1,864 @@
+// ca_scorer.cu -- learned edge scorer: a 1-D convolutional network over strip
+// profiles (the learned variant of Sec. 2.2.4, here with 1-D convolutions over
+// 3-row strips), run on the 5th-generation tensor cores (tcgen05) with bf16
+// operands and f32 accumulators in tensor memory.
+//
+// Network, per strip column x (W columns, "same" zero padding):
+//   features f[x] (14): luma, R, G, B of rows y-1, y, y+1 as (v - 128) / 128,
+//                       then (x - (W-1)/2) / W and (y - (H-1)/2) / H
+//   a1 = relu(conv7(f,  W1) + b1), a2 = relu(conv7(a1, W2) + b2),
+//   a3 = relu(conv7(a2, W3) + b3)          (32 channels, kernel 7 each)
+//   logit = bh + wh . a3,  p = sigmoid(logit)
+// with conv7(in, W)[x][co] = sum_{ci,t} W[co][ci][t] in[x + t - 3][ci].
+// Activations and weights are stored in bf16, every sum accumulates in f32.
+//
+// Layout.  A strip is processed in segments of 512 consecutive columns (4
+// tiles of 128), of which the middle 494 are outputs: three layers of kernel
+// 7 need 9 columns of context on each side.  Activations of a segment live in
+// shared memory as "planes": plane c holds channels 8c..8c+7 of every column,
+// one 16-byte row per column, with 8 zero guard rows at both ends.  A tile of
+// 128 columns and 16 channels is then a K-major tcgen05 operand (core
+// matrices of 8 columns x 8 channels = 128 contiguous bytes; SBO = 128 bytes
+// between 8-column groups, LBO = one plane between channel groups), and the
+// column shift t - 3 of a convolution tap is only a 16-byte offset of the
+// operand's start address: the 7 taps need no im2col copy.  The same planes
+// read as MN-major operands (channels contiguous, columns as K) give the
+// weight gradients: dW[co][ci][t] = sum_x dz[x][co] a[x + t - 3][ci].
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "ca_internal.h"
+
+namespace ca {
+
+namespace {
+
+constexpr int kCin = kScCin, kCh = kScCh, kTaps = kScTaps;
+constexpr int kTile = 128, kSegTiles = 4, kSegRows = kTile * kSegTiles;
+constexpr int kGuard = 8;
+constexpr int kPlaneBytes = (kSegRows + 2 * kGuard) * 16;
+
+// smem descriptors (no swizzle): start, LBO (K direction), SBO (M/N direction)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: bf16 A and B, f32 D
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{.reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier; false
+// (error flag set) if it does not complete within ~2 s.
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, uint32_t *err) {
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255u) == 255u) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) break;
+        }
+    }
+    if (err) atomicOr(err, kScErrTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// One-shot bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on `bar` (which must expect the bytes).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 32 consecutive f32 columns of the calling warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ uint32_t tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    // whole warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    return 0;
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// Writes the 32 values of a row into 4 planes (bf16).
+__device__ __forceinline__ void store_row32(unsigned char *planes, int row, const float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint4 q;
+        q.x = pack_bf16(v[8 * c + 0], v[8 * c + 1]);
+        q.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+        q.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+        q.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(planes + c * kPlaneBytes + (kGuard + row) * 16) = q;
+    }
+}
+
+__device__ __forceinline__ void load_row32(const unsigned char *planes, int row, float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(planes + c * kPlaneBytes + (kGuard + row) * 16);
+        v[8 * c + 0] = bf16_lo(q.x); v[8 * c + 1] = bf16_hi(q.x);
+        v[8 * c + 2] = bf16_lo(q.y); v[8 * c + 3] = bf16_hi(q.y);
+        v[8 * c + 4] = bf16_lo(q.z); v[8 * c + 5] = bf16_hi(q.z);
+        v[8 * c + 6] = bf16_lo(q.w); v[8 * c + 7] = bf16_hi(q.w);
+    }
+}
+
+// Sum over the warp of each of 32 per-lane values: lane c receives channel c.
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < o; ++k) {
+            const float send = upper ? v[k] : v[k + o];
+            const float keep = upper ? v[k + o] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ float luma_f(uint32_t r, uint32_t g, uint32_t b) {
+    return (float)((int)((77u * r + 150u * g + 29u * b + 128u) >> 8) - 128) * (1.0f / 128.0f);
+}
+
+// Column features of a segment: rows r in [0, 512) <-> columns b0 + r; two
+// planes (14 features + 2 zero channels), zero outside [0, W).
+__device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t *row0,
+                                               const uint8_t *row1, const uint8_t *row2, int W,
+                                               int y, int H, int b0) {
+    const float yf = __fdiv_rn(__fsub_rn((float)y, __fmul_rn(0.5f, (float)(H - 1))), (float)H);
+    const float xc = __fmul_rn(0.5f, (float)(W - 1));
+    const float Wf = (float)W;
+    for (int r = threadIdx.x; r < kSegRows; r += blockDim.x) {
+        const int x = b0 + r;
+        uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
+        if (x >= 0 && x < W) {
+            float f[16];
+            const uint8_t *p[3] = {row0 + 3 * x, row1 + 3 * x, row2 + 3 * x};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint32_t R = p[k][0], G = p[k][1], B = p[k][2];
+                f[4 * k + 0] = luma_f(R, G, B);
+                f[4 * k + 1] = (float)((int)R - 128) * (1.0f / 128.0f);
+                f[4 * k + 2] = (float)((int)G - 128) * (1.0f / 128.0f);
+                f[4 * k + 3] = (float)((int)B - 128) * (1.0f / 128.0f);
+            }
+            f[12] = __fdiv_rn(__fsub_rn((float)x, xc), Wf);
+            f[13] = yf;
+            f[14] = f[15] = 0.0f;
+            q0 = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                            pack_bf16(f[6], f[7]));
+            q1 = make_uint4(pack_bf16(f[8], f[9]), pack_bf16(f[10], f[11]), pack_bf16(f[12], f[13]),
+                            pack_bf16(f[14], f[15]));
+        }
+        *reinterpret_cast<uint4 *>(x0 + (kGuard + r) * 16) = q0;
+        *reinterpret_cast<uint4 *>(x0 + kPlaneBytes + (kGuard + r) * 16) = q1;
+    }
+}
+
+// Issues one convolution of a segment (single thread): for each tile j and
+// tap t, MMAs over channel pairs of planes; D of tile j = columns 32 j.
+//   in: planes of the input (n_in_chunks = 2 or 4), w: weight chunks
+//   [t * n_in_chunks + c][32 out][8 in] (512 bytes each).
+__device__ __forceinline__ void issue_conv(uint32_t tmem, const unsigned char *in, int n_in_chunks,
+                                           const unsigned char *w) {
+    constexpr uint32_t idesc = idesc_bf16(128, 32, false, false);
+    const uint32_t a0 = smem_u32(in), w0 = smem_u32(w);
+    for (int j = 0; j < kSegTiles; ++j)
+        for (int t = 0; t < kTaps; ++t)
+            for (int q = 0; q < n_in_chunks / 2; ++q) {
+                const uint32_t a = a0 + 2 * q * kPlaneBytes + (kGuard + kTile * j + t - 3) * 16;
+                const uint32_t b = w0 + (t * n_in_chunks + 2 * q) * 512;
+                mma_bf16(tmem + 32 * j, sdesc(a, kPlaneBytes, 128), sdesc(b, 512, 128), idesc,
+                         (t | q) != 0);
+            }
+}
+
+struct ScVec {   // float part of the weight block
+    float b[3][kCh];
+    float whq[kCh];   // head weights rounded to bf16
+    float bh;
+    float pad[3];
+};
+static_assert(sizeof(ScVec) == kScVecBytes, "vector block size");
+
+// Epilogue helper: the 32 accumulator channels of row r (= 128 j + 32 warp + lane).
+__device__ __forceinline__ void acc_row(uint32_t tmem, int j, float (&v)[32]) {
+    const int warp = threadIdx.x >> 5;
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * j, v);
+}
+
+// Where segment g of a launch reads and writes.
+struct SegInfo {
+    const uint8_t *r0;   // row y-1 of the strip (rows y, y+1 follow at `pitch`)
+    int64_t pitch;
+    int W, H, y;
+    int s0, s1;          // output columns [s0, s1)
+    int64_t out;         // index of column 0 of the strip in the per-column outputs
+    int strip;           // strips mode: index of the strip in the source
+};
+
+__device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
+    SegInfo si;
+    if (src.frames) {
+        int lo = 0, hi = src.B - 1;   // frame of segment g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (src.frames[mid].sc_seg_off <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const DevFrame &fr = src.frames[lo];
+        const int nseg = (fr.W + kScSegOut - 1) / kScSegOut;
+        const int local = g - fr.sc_seg_off;
+        const int i = local / nseg, s = local - i * nseg;
+        si.y = src.rows[fr.rows_off + i];
+        si.W = fr.W;
+        si.H = fr.H;
+        si.pitch = fr.pitch;
+        si.r0 = fr.rgb + (int64_t)(si.y - 1) * fr.pitch;
+        si.s0 = s * kScSegOut;
+        si.out = (int64_t)fr.sc_pix_off + (int64_t)i * fr.W;
+        si.strip = -1;
+    } else {
+        const int nseg = (src.W + kScSegOut - 1) / kScSegOut;
+        const int j = g / nseg, s = g - j * nseg;
+        const int id = src.idx ? src.idx[j] : j;
+        si.y = src.ys[id];
+        si.W = src.W;
+        si.H = src.H;
+        si.pitch = (int64_t)src.W * 3;
+        si.r0 = src.strips + (int64_t)id * 3 * si.pitch;
+        si.s0 = s * kScSegOut;
+        si.out = (int64_t)j * src.W;
+        si.strip = id;
+    }
+    si.s1 = min(si.W, si.s0 + kScSegOut);
+    return si;
+}
+
+// Common prologue of the scorer kernels: zero guard rows of `n_planes`
+// planes from `sm`, init the barriers, allocate TMEM, start the weight copy.
+__device__ __forceinline__ uint32_t sc_prologue(unsigned char *sm, int n_planes, uint64_t *bar_w,
+                                                uint64_t *bar_m, uint32_t *tslot, uint32_t ncols,
+                                                unsigned char *wdst, const unsigned char *wsrc,
+                                                uint32_t wbytes, void *vdst, const void *vsrc) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < n_planes * kGuard * 2; i += blockDim.x) {
+        const int plane = i / (2 * kGuard), g = i % (2 * kGuard);
+        const int row = g < kGuard ? g : kSegRows + g;   // rows [0, 8) and [520, 528)
+        *reinterpret_cast<uint4 *>(sm + plane * kPlaneBytes + row * 16) = make_uint4(0, 0, 0, 0);
+    }
+    if (tid == 0) {
+        bar_init(bar_w, 1);
+        bar_init(bar_m, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, ncols);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+        bar_expect_tx(bar_w, wbytes + kScVecBytes);
+        bulk_g2s(wdst, wsrc, wbytes, bar_w);
+        bulk_g2s(vdst, vsrc, kScVecBytes, bar_w);
+    }
+    return *tslot;
+}
+
+}  // namespace
+
+// ============================================================ inference ==
+// One CTA (4 warps) per 512-column segment at a time, 2 CTAs per SM.  Output:
+// the Q15 score round(32768 p) of every output column, and the logit when
+// `logits` is set.
+constexpr int kInfThreads = 128;
+constexpr size_t kInfSmem = 6 * (size_t)kPlaneBytes + kScFwdBytes + kScVecBytes + 64;
+
+__global__ void __launch_bounds__(kInfThreads, 2)
+    k_sc_infer(ScSource src, const unsigned char *__restrict__ wblock, uint16_t *__restrict__ scores,
+               float *__restrict__ logits, int total_segs, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *X0 = sm;                       // 2 planes: features
+    unsigned char *A = sm + 2 * kPlaneBytes;      // 4 planes: a1, then a2 (in place)
+    unsigned char *Wf = A + 4 * kPlaneBytes;
+    ScVec *vec = reinterpret_cast<ScVec *>(Wf + kScFwdBytes);
+    uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kScVecBytes);
+    uint64_t *bar_m = bar_w + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t tmem = sc_prologue(sm, 6, bar_w, bar_m, tslot, 128, Wf, wblock + kScOffW1f,
+                                      kScFwdBytes, vec, wblock + kScOffVec);
+    bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
+    uint32_t phase = 0;
+
+    for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
+        const SegInfo si = seg_info(src, g);
+        const int b0 = si.s0 - kScHalo;
+        __syncthreads();   // the previous segment is done with A and X0
+        build_features(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        for (int l = 0; l < 3; ++l) {
+            if (tid == 0) {
+                const int woff = l == 0 ? 0 : (l == 1 ? kScOffW2f : kScOffW3f) - kScOffW1f;
+                issue_conv(tmem, l == 0 ? X0 : A, l == 0 ? 2 : 4, Wf + woff);
+                mma_commit(bar_m);
+            }
+            const bool ok = bar_wait(bar_m, phase, err);
+            phase ^= 1u;
+            tc_after_sync();
+            if (__syncthreads_or(!ok)) { abort = true; break; }
+            for (int j = 0; j < kSegTiles; ++j) {
+                float v[32];
+                acc_row(tmem, j, v);
+                const int r = kTile * j + 32 * warp + (tid & 31);
+                const int x = b0 + r;
+                const bool inside = x >= 0 && x < si.W;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float z = __fadd_rn(v[c], vec->b[l][c]);
+                    v[c] = inside && z > 0.0f ? __bfloat162float(__float2bfloat16_rn(z)) : 0.0f;
+                }
+                if (l < 2) {
+                    store_row32(A, r, v);   // every MMA reading A has completed
+                } else if (x >= si.s0 && x < si.s1) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) acc = __fadd_rn(acc, __fmul_rn(vec->whq[c], v[c]));
+                    const float lg = __fadd_rn(vec->bh, acc);
+                    const float p = 1.0f / (1.0f + expf(-lg));
+                    const int q = min(32768, max(0, __float2int_rn(p * 32768.0f)));
+                    if (scores) scores[si.out + x] = (uint16_t)q;
+                    if (logits) logits[si.out + x] = lg;
+                }
+            }
+            fence_async_smem();
+            tc_before_sync();
+            __syncthreads();
+            tc_after_sync();
+        }
+    }
+    __syncthreads();
+    if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
+        mma_commit(bar_m);
+        bar_wait(bar_m, phase, nullptr);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 128);
+}
+
+size_t sc_infer_smem() { return kInfSmem; }
+
+int sc_infer_blocks_per_sm() {
+    static int nb = [] {
+        int v = 0;
+        if (cudaFuncSetAttribute(k_sc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kInfSmem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sc_infer, kInfThreads, kInfSmem) !=
+                cudaSuccess)
+            v = 1;
+        return v < 1 ? 1 : (v > 2 ? 2 : v);   // TMEM: 128 columns per CTA
+    }();
+    return nb;
+}
+
+cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uint16_t *scores,
+                            float *logits, int total_segs, uint32_t *err, int grid, cudaStream_t s) {
+    if (total_segs <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_sc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kInfSmem);
+    if (e != cudaSuccess) return e;
+    k_sc_infer<<<grid, kInfThreads, kInfSmem, s>>>(src, block, scores, logits, total_segs, err);
+    return cudaGetLastError();
+}
+
+// ============================================================= training ==
+// One CTA (4 warps, one per SM) per segment, segments assigned statically
+// (g = blockIdx.x + k gridDim.x) so that every run sums the same gradient
+// terms in the same order.  Per segment: forward (features -> a1 -> a2 ->
+// head), loss and its gradient at the logits, then for layers 3, 2, 1 the
+// weight gradient (tcgen05, MN-major operands: M = 64 output channels of
+// which 32 are real, N = input channels, K = 16 columns per MMA, one
+// accumulator per tap) and, for layers 3 and 2, the input gradient (a
+// forward convolution of the gradient planes with the reversed, transposed
+// weights).  The sums of the CTA go to its own slice of `partial`.
+constexpr int kTrainThreads = 128;
+constexpr int kTrainPlanes = 14;   // D (4) | A1 (4) | A2 (4) | X0 (2)
+constexpr size_t kTrainSmem = (size_t)kTrainPlanes * kPlaneBytes + (kScBlockBytes - kScVecBytes) +
+                              kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float);
+constexpr int kDwCol = 128;        // TMEM columns of the weight-gradient accumulators (7 x 32)
+
+namespace {
+
+// Weight-gradient MMAs of one layer: for every tap t, dW_t[co][ci] +=
+// sum_x dz[x][co] in[x + t - 3][ci] over the 512 rows of the segment.
+__device__ __forceinline__ void issue_dw(uint32_t tmem, const unsigned char *dz,
+                                         const unsigned char *in, int n_in) {
+    const uint32_t idesc = idesc_bf16(64, 8 * n_in, true, true);
+    const uint32_t a0 = smem_u32(dz), b0 = smem_u32(in);
+    for (int t = 0; t < kTaps; ++t)
+        for (int k = 0; k < kSegRows / 16; ++k) {
+            const uint32_t a = a0 + (kGuard + 16 * k) * 16;
+            const uint32_t b = b0 + (kGuard + 16 * k + t - 3) * 16;
+            mma_bf16(tmem + kDwCol + 32 * t, sdesc(a, 128, kPlaneBytes), sdesc(b, 128, kPlaneBytes),
+                     idesc, k != 0);
+        }
+}
+
+// Adds the weight gradient of a layer into the CTA's partial sums.  An M = 64
+// accumulator keeps rows 16q .. 16q+15 in lanes 0-15 of TMEM lane quarter q:
+// output channels 0-15 are read by warp 0 and 16-31 by warp 1.
+__device__ __forceinline__ void flush_dw(uint32_t tmem, float *part, int off, int n_in_real) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp >= 2) return;
+    const int co = 16 * warp + lane;
+    for (int t = 0; t < kTaps; ++t) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + kDwCol + 32 * t, v);
+        if (lane < 16) {
+#pragma unroll
+            for (int ci = 0; ci < 32; ++ci)
+                if (ci < n_in_real) {
+                    float *q = part + off + (co * n_in_real + ci) * kTaps + t;
+                    *q = __fadd_rn(*q, v[ci]);
+                }
+        }
+    }
+}
+
+// Sums a per-thread 32-vector over the CTA (fixed order) into part[off + c].
+__device__ __forceinline__ void flush_vec32(float (&v)[32], float *red, float *part, int off) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float w = warp_transpose_sum(v);
+    red[warp * 32 + lane] = w;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = 0.0f;
+        for (int k = 0; k < kTrainThreads / 32; ++k) t = __fadd_rn(t, red[k * 32 + threadIdx.x]);
+        part[off + threadIdx.x] = __fadd_rn(part[off + threadIdx.x], t);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+    k_sc_train(ScSource src, const uint8_t *__restrict__ labels, float pos_weight,
+               const unsigned char *__restrict__ wblock, float *__restrict__ partial,
+               int total_segs, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *D = sm;                          // gradient planes; planes 4-7 read as M padding
+    unsigned char *A1 = sm + 4 * kPlaneBytes;
+    unsigned char *A2 = sm + 8 * kPlaneBytes;
+    unsigned char *X0 = sm + 12 * kPlaneBytes;
+    unsigned char *Wall = sm + kTrainPlanes * kPlaneBytes;
+    ScVec *vec = reinterpret_cast<ScVec *>(Wall + (kScBlockBytes - kScVecBytes));
+    uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kScVecBytes);
+    uint64_t *bar_m = bar_w + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
+    float *red = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(bar_w) + 64);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem = sc_prologue(sm, kTrainPlanes, bar_w, bar_m, tslot, 512, Wall, wblock,
+                                      kScBlockBytes - kScVecBytes, vec, wblock + kScOffVec);
+    bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
+    float *part = partial + (size_t)blockIdx.x * kScPartialStride;
+    uint32_t phase = 0;
+    const unsigned char *Wf1 = Wall + kScOffW1f, *Wf2 = Wall + kScOffW2f, *Wf3 = Wall + kScOffW3f;
+    const unsigned char *Wb2 = Wall + kScOffW2b, *Wb3 = Wall + kScOffW3b;
+
+    auto mma_sync_point = [&]() {   // st.shared visible to MMAs, TMEM reads done
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+    };
+    // a wait that gave up ends the CTA's work (uniformly: the flag is reduced
+    // over the CTA), so a fault shows as one ~2 s wait, not one per MMA batch
+    auto wait_mma = [&]() {
+        const bool ok = bar_wait(bar_m, phase, err);
+        phase ^= 1u;
+        tc_after_sync();
+        if (__syncthreads_or(!ok)) abort = true;
+        return !abort;
+    };
+
+    for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
+        const SegInfo si = seg_info(src, g);
+        const int b0 = si.s0 - kScHalo;
+        const uint8_t *lab = labels + (int64_t)si.strip * si.W;
+        __syncthreads();
+        build_features(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
+        mma_sync_point();
+
+        // ---- forward: layers 1 and 2
+        for (int l = 0; l < 2; ++l) {
+            if (tid == 0) {
+                issue_conv(tmem, l == 0 ? X0 : A1, l == 0 ? 2 : 4, l == 0 ? Wf1 : Wf2);
+                mma_commit(bar_m);
+            }
+            if (!wait_mma()) break;
+            unsigned char *dst = l == 0 ? A1 : A2;
+            for (int j = 0; j < kSegTiles; ++j) {
+                float v[32];
+                acc_row(tmem, j, v);
+                const int r = kTile * j + 32 * warp + lane, x = b0 + r;
+                const bool inside = x >= 0 && x < si.W;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float z = __fadd_rn(v[c], vec->b[l][c]);
+                    v[c] = inside && z > 0.0f ? __bfloat162float(__float2bfloat16_rn(z)) : 0.0f;
+                }
+                store_row32(dst, r, v);
+            }
+            mma_sync_point();
+        }
+        // ---- layer 3, head, loss; gradient at the logits and at z3
+        if (abort) break;
+        if (tid == 0) {
+            issue_conv(tmem, A2, 4, Wf3);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        {
+            float gwh[32], gb3[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) gwh[c] = gb3[c] = 0.0f;
+            float gbh = 0.0f, loss = 0.0f;
+            for (int j = 0; j < kSegTiles; ++j) {
+                float v[32];
+                acc_row(tmem, j, v);
+                const int r = kTile * j + 32 * warp + lane, x = b0 + r;
+                const bool inside = x >= 0 && x < si.W;
+                float acc = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float z = __fadd_rn(v[c], vec->b[2][c]);
+                    v[c] = inside && z > 0.0f ? __bfloat162float(__float2bfloat16_rn(z)) : 0.0f;
+                    acc = __fadd_rn(acc, __fmul_rn(vec->whq[c], v[c]));
+                }
+                float dl = 0.0f;
+                if (x >= si.s0 && x < si.s1) {
+                    const float lg = __fadd_rn(vec->bh, acc);
+                    const float y = lab[x] ? 1.0f : 0.0f, w = lab[x] ? pos_weight : 1.0f;
+                    const float p = 1.0f / (1.0f + expf(-lg));
+                    dl = __fmul_rn(w, __fsub_rn(p, y));
+                    const float sp = lg > 0.0f ? lg + log1pf(expf(-lg)) : log1pf(expf(lg));
+                    loss = __fadd_rn(loss, __fmul_rn(w, __fsub_rn(sp, __fmul_rn(y, lg))));
+                }
+                gbh = __fadd_rn(gbh, dl);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    gwh[c] = __fadd_rn(gwh[c], __fmul_rn(dl, v[c]));
+                    const float dz = v[c] > 0.0f
+                                         ? __bfloat162float(__float2bfloat16_rn(__fmul_rn(dl, vec->whq[c])))
+                                         : 0.0f;
+                    gb3[c] = __fadd_rn(gb3[c], dz);
+                    v[c] = dz;
+                }
+                store_row32(D, r, v);
+            }
+            flush_vec32(gwh, red, part, kScPWh);
+            flush_vec32(gb3, red + 128, part, kScPB3);
+            gbh = warp_sum(gbh);
+            loss = warp_sum(loss);
+            if (lane == 0) { red[256 + 2 * warp] = gbh; red[256 + 2 * warp + 1] = loss; }
+            __syncthreads();
+            if (tid == 0) {
+                float a = 0.0f, b = 0.0f;
+                for (int k = 0; k < kTrainThreads / 32; ++k) {
+                    a = __fadd_rn(a, red[256 + 2 * k]);
+                    b = __fadd_rn(b, red[256 + 2 * k + 1]);
+                }
+                part[kScPBh] = __fadd_rn(part[kScPBh], a);
+                part[kScNParam] = __fadd_rn(part[kScNParam], b);
+            }
+        }
+        mma_sync_point();
+        // ---- layers 3 and 2: weight gradient and input gradient
+        for (int l = 2; l >= 1; --l) {
+            const unsigned char *in = l == 2 ? A2 : A1;
+            if (tid == 0) {
+                issue_conv(tmem, D, 4, l == 2 ? Wb3 : Wb2);   // input gradient, columns [0, 128)
+                issue_dw(tmem, D, in, 4);
+                mma_commit(bar_m);
+            }
+            if (!wait_mma()) break;
+            flush_dw(tmem, part, l == 2 ? kScPW3 : kScPW2, kCh);
+            float gb[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) gb[c] = 0.0f;
+            for (int j = 0; j < kSegTiles; ++j) {
+                float v[32], a[32];
+                acc_row(tmem, j, v);
+                const int r = kTile * j + 32 * warp + lane;
+                load_row32(in, r, a);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    v[c] = a[c] > 0.0f ? __bfloat162float(__float2bfloat16_rn(v[c])) : 0.0f;
+                    gb[c] = __fadd_rn(gb[c], v[c]);
+                }
+                store_row32(D, r, v);   // every MMA reading D has completed
+            }
+            __syncthreads();
+            flush_vec32(gb, red, part, l == 2 ? kScPB2 : kScPB1);
+            mma_sync_point();
+        }
+        // ---- layer 1: weight gradient only
+        if (abort) break;
+        if (tid == 0) {
+            issue_dw(tmem, D, X0, 2);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        flush_dw(tmem, part, kScPW1, kScCin);
+        tc_before_sync();
+    }
+    __syncthreads();
+    if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
+        mma_commit(bar_m);
+        bar_wait(bar_m, phase, nullptr);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 512);
+}
+
+size_t sc_train_smem() { return kTrainSmem; }
+
+cudaError_t sc_launch_train(const ScSource &src, const uint8_t *labels, float pos_weight,
+                            const unsigned char *block, float *partial, int total_segs,
+                            uint32_t *err, int grid, cudaStream_t s) {
+    if (total_segs <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_sc_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTrainSmem);
+    if (e != cudaSuccess) return e;
+    k_sc_train<<<grid, kTrainThreads, kTrainSmem, s>>>(src, labels, pos_weight, block, partial,
+                                                      total_segs, err);
+    return cudaGetLastError();
+}
+
+// =============================================================== picks ==
+// One warp per half-strip: K/2 best learned scores with the suppression
+// window; a half whose best learned score is under 16384 (p < 1/2) keeps the
+// handcrafted points already in its slots when `fallback` is set.
+__global__ void __launch_bounds__(256)
+    k_sc_pick(const DevFrame *__restrict__ frames, int B, const int32_t *__restrict__ rows,
+              DevParams P, const uint16_t *__restrict__ scores, int fallback,
+              CandSlot *__restrict__ slots) {
+    const int lane = threadIdx.x & 31;
+    const int items = B * P.N * 2;
+    const int kk = P.K >> 1;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items;
+         it += (gridDim.x * blockDim.x) >> 5) {
+        const int f = it / (2 * P.N), j = it - f * 2 * P.N;
+        const int i = j >> 1, half = j & 1;
+        const DevFrame fr = frames[f];
+        const int W = fr.W, H = fr.H, hw = W >> 1;
+        const int x0 = half ? hw : 0, x1 = half ? W : hw;
+        const int y = rows[fr.rows_off + i];
+        const uint16_t *s = scores + fr.sc_pix_off + (int64_t)i * W;
+        int picks[kScMaxPicks];
+        for (int r = 0; r < kk; ++r) {
+            uint32_t b = 0u;
+            for (int x = x0 + lane; x < x1; x += 32) {
+                bool sup = false;
+                for (int q = 0; q < r; ++q) sup |= abs(x - picks[q]) <= P.sup_px;
+                if (!sup) b = max(b, ((uint32_t)s[x] << 16) | (uint32_t)(half ? x : (0xFFFF - x)));
+            }
+            b = __reduce_max_sync(0xffffffffu, b);
+            const int rank = (int)(b & 0xFFFFu);
+            const int px = b == 0u ? -1000000 : (half ? rank : (0xFFFF - rank));
+            const uint32_t scv = b >> 16;
+            if (r == 0 && fallback && scv < 16384u) break;   // keep the handcrafted points
+            picks[r] = px;
+            if (lane == 0) {
+                CandSlot out;
+                out.x = (int16_t)(b == 0u ? -1 : px);
+                out.y = (int16_t)y;
+                out.s = (uint16_t)scv;
+                out.kept = (uint16_t)(b != 0u && scv >= P.T_ps && px >= P.T_px &&
+                                      px <= W - 1 - P.T_px && y >= P.T_px && y <= H - 1 - P.T_px);
+                slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
+            }
+        }
+    }
+}
+
+cudaError_t sc_launch_pick(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
+                           const uint16_t *scores, int fallback, CandSlot *slots, int grid,
+                           cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    k_sc_pick<<<grid, 256, 0, s>>>(frames, B, rows, P, scores, fallback, slots);
+    return cudaGetLastError();
+}
+
+// ============================================================= weights ==
+// Packs the f32 parameters into the device weight block: the bf16 B operands
+// of the forward convolutions and of the input-gradient convolutions, the
+// biases, the bf16-rounded head weights and the head bias.
+__global__ void k_sc_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kScNParam) return;
+    const float w = prm[p];
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    ScVec *vec = reinterpret_cast<ScVec *>(blk + kScOffVec);
+    auto put = [&](int off) { *reinterpret_cast<__nv_bfloat16 *>(blk + off) = wb; };
+    if (p < kScPB1) {                           // W1[co][ci][t], 2 input chunks per tap
+        const int co = p / (kScCin * kTaps), ci = (p / kTaps) % kScCin, t = p % kTaps;
+        put(kScOffW1f + ((t * 2 + ci / 8) * 32 + co) * 16 + (ci % 8) * 2);
+    } else if (p < kScPW2) {
+        vec->b[0][p - kScPB1] = w;
+    } else if (p < kScPB2 || (p >= kScPW3 && p < kScPB3)) {   // W2 / W3 [co][ci][t]
+        const bool l3 = p >= kScPW3;
+        const int q = p - (l3 ? kScPW3 : kScPW2);
+        const int co = q / (kCh * kTaps), ci = (q / kTaps) % kCh, t = q % kTaps;
+        put((l3 ? kScOffW3f : kScOffW2f) + ((t * 4 + ci / 8) * 32 + co) * 16 + (ci % 8) * 2);
+        // input gradient: da[x][ci] = sum dz[x + t' - 3][co] W[co][ci][6 - t']
+        put((l3 ? kScOffW3b : kScOffW2b) + (((kTaps - 1 - t) * 4 + co / 8) * 32 + ci) * 16 +
+            (co % 8) * 2);
+    } else if (p < kScPW3) {
+        vec->b[1][p - kScPB2] = w;
+    } else if (p < kScPWh) {
+        vec->b[2][p - kScPB3] = w;
+    } else if (p < kScPBh) {
+        vec->whq[p - kScPWh] = __bfloat162float(wb);
+    } else {
+        vec->bh = w;
+    }
+}
+
+cudaError_t sc_launch_pack(const float *params, unsigned char *block, cudaStream_t s) {
+    k_sc_pack<<<(kScNParam + 255) / 256, 256, 0, s>>>(params, block);
+    return cudaGetLastError();
+}
+
+// Sums the per-CTA gradient partials in a fixed order (and clears them), then
+// optionally takes an SGD step with momentum:
+//   v = momentum v + scale g,  w = w - lr v.
+__global__ void k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, float *__restrict__ part,
+                         int n_part, float scale, float lr, float momentum, int apply,
+                         float *__restrict__ grads_out, float *__restrict__ loss_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > kScNParam) return;
+    float g = 0.0f;
+    for (int c = 0; c < n_part; ++c) {
+        float *q = part + (size_t)c * kScPartialStride + p;
+        g = __fadd_rn(g, *q);
+        *q = 0.0f;
+    }
+    if (p == kScNParam) {   // loss slot
+        if (loss_out) *loss_out = g;
+        return;
+    }
+    if (grads_out) grads_out[p] = g;
+    if (apply) {
+        const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), __fmul_rn(scale, g));
+        mom[p] = v;
+        prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+    }
+}
+
+cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
+                          float lr, float momentum, int apply, float *grads_out, float *loss_out,
+                          cudaStream_t s) {
+    k_sc_sgd<<<(kScNParam + 1 + 255) / 256, 256, 0, s>>>(params, mom, partial, n_partials, scale,
+                                                          lr, momentum, apply, grads_out, loss_out);
+    return cudaGetLastError();
+}
+
+}  // namespace ca

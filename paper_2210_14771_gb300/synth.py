@@ -198,3 +198,112 @@ def mixed_batch(seed: int, n: int, unique: int | None = None, workers: int = 0,
     gts = [drawn[i % u][1] for i in range(n)]
     keys = [frame_key(seed, i) for i in range(n)]
     return frames, gts, keys
+
+
+_GRAMS = {}
+
+
+def _grams(H, W):
+    """Bicubic weights of both axes with their Gram matrices and column sums."""
+    if (H, W) not in _GRAMS:
+        wy, wx = _cubic_weights(H, 8), _cubic_weights(W, 8)
+        y64, x64 = wy.astype(np.float64), wx.astype(np.float64)
+        _GRAMS[(H, W)] = (wy, wx, y64.T @ y64, x64.T @ x64, y64.sum(0), x64.sum(0))
+    return _GRAMS[(H, W)]
+
+
+def training_strip(seed: int, idx: int, H: int, W: int, geometry: str = "mixed"):
+    """One labelled training strip: rows y-1, y, y+1 (3, W, 3) of a scene drawn
+    like `frame` (same geometry classes and appearance), its middle row y and
+    per-column labels: 1 within 2 px of a crossing of the true circle with
+    row y, else 0.  Only the three rows are rendered."""
+    rng = np.random.default_rng([0x57A1, seed & 0xFFFFFFFF, idx & 0xFFFFFFFF, H, W])
+    kind = geometry_of(geometry, idx) if geometry == "mixed" else geometry
+    base = kind
+    if kind == "hard":
+        base = "clipped" if rng.uniform() < 0.5 else "full"
+    y = int(rng.integers(1, H - 1))
+    ys = np.array([y - 1, y, y + 1], np.float32)
+    mean = rng.uniform(80, 200)
+    tint = rng.uniform(-15, 15, size=3)
+    gains = rng.uniform(0.8, 1.2, size=3)
+    g = rng.standard_normal((8, 8)).astype(np.float32)
+    wy, wx, gy, gx, sy, sx = _grams(H, W)
+    tex = wy[y - 1:y + 2] @ g @ wx.T
+    # standard deviation of the whole frame's texture, from 8x8 Gram matrices
+    g64 = g.astype(np.float64)
+    m1 = float(sy @ g64 @ sx) / (H * W)
+    m2 = float(np.trace(g64.T @ gy @ g64 @ gx)) / (H * W)
+    sd = math.sqrt(max(m2 - m1 * m1, 0.0)) or 1.0
+    tex = tex * np.float32(25.0 / sd)
+    noise_in = rng.standard_normal((3, W, 3), dtype=np.float32) * 2.0
+    interior = (mean + tint[None, None, :]).astype(np.float32) + \
+        tex[:, :, None] * gains[None, None, :].astype(np.float32) + noise_in
+    level = rng.uniform(0, 15)
+    border = level + rng.standard_normal((3, W, 3), dtype=np.float32) * 3.0
+    labels = np.zeros(W, np.uint8)
+    if base == "none":
+        img = interior
+    else:
+        cx, cy, r = _draw_circle(rng, base, H, W)
+        xs = np.arange(W, dtype=np.float32)[None, :]
+        d = np.sqrt((xs - np.float32(cx)) ** 2 + (ys[:, None] - np.float32(cy)) ** 2)
+        if kind == "hard":
+            vig = 1.0 - 0.5 * np.minimum(d / np.float32(r), 1.0) ** 2
+            interior = interior * vig[:, :, None]
+            for _ in range(int(rng.integers(1, 3))):
+                ang = rng.uniform(0, 2 * math.pi)
+                pr = rng.uniform(0.08, 0.2) * min(H, W)
+                px, py = cx + r * math.cos(ang), cy + r * math.sin(ang)
+                dp = np.sqrt((xs - np.float32(px)) ** 2 + (ys[:, None] - np.float32(py)) ** 2)
+                beta = np.clip((pr + 1 - dp) / 2, 0, 1)[:, :, None]
+                interior = interior * (1 - beta) + rng.uniform(10, 30) * beta
+            for _ in range(int(rng.integers(1, 5))):
+                ang = rng.uniform(0, 2 * math.pi)
+                rad = r * math.sqrt(rng.uniform(0.0, 0.9))
+                px, py = cx + rad * math.cos(ang), cy + rad * math.sin(ang)
+                br = rng.uniform(5, 30)
+                dp = np.sqrt((xs - np.float32(px)) ** 2 + (ys[:, None] - np.float32(py)) ** 2)
+                beta = np.clip((br + 1 - dp) / 2, 0, 1)[:, :, None]
+                interior = interior * (1 - beta) + 255.0 * beta
+        a = np.clip((np.float32(r) + 1.0 - d) / 2.0, 0.0, 1.0)[:, :, None]
+        img = interior * a + border * (1.0 - a)
+        dy = y - cy
+        if abs(dy) <= r:
+            h = math.sqrt(r * r - dy * dy)
+            for xc in (cx - h, cx + h):
+                lo, hi = int(math.ceil(xc - 2.0)), int(math.floor(xc + 2.0))
+                lo, hi = max(lo, 0), min(hi, W - 1)
+                if lo <= hi:
+                    labels[lo:hi + 1] = 1
+    out = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    return out, y, labels
+
+
+def _strip_job(args):
+    seed, i0, i1, H, W, geometry = args
+    n = i1 - i0
+    s = np.empty((n, 3, W, 3), np.uint8)
+    ys = np.empty(n, np.int32)
+    lab = np.empty((n, W), np.uint8)
+    for k in range(n):
+        s[k], ys[k], lab[k] = training_strip(seed, i0 + k, H, W, geometry)
+    return s, ys, lab
+
+
+def training_strips(seed: int, n: int, H: int = 1080, W: int = 1920, geometry: str = "mixed",
+                    workers: int = 0):
+    """n labelled strips: (strips (n, 3, W, 3) uint8, ys (n,) int32, labels (n, W) uint8)."""
+    chunk = 256
+    jobs = [(seed, i, min(n, i + chunk), H, W, geometry) for i in range(0, n, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_strip_job, jobs))
+    else:
+        parts = [_strip_job(j) for j in jobs]
+    if not parts:
+        return (np.empty((0, 3, W, 3), np.uint8), np.empty(0, np.int32), np.empty((0, W), np.uint8))
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+            np.concatenate([p[2] for p in parts]))

@@ -1,0 +1,169 @@
+"""Learned edge scorer on the GPU (tcgen05 forward and backward) against the
+CPU oracle of the same network.
+
+Tolerances.  The oracle forms every convolution sum exactly (binary64) and
+rounds it once to binary32; the tensor cores accumulate the same bf16
+products in binary32 in their own order, a relative difference of about
+224 * 2^-24 of the sum of |terms|.  That difference flips the bf16 rounding
+of an activation (one step = 2^-8 relative) about once in 300 activations;
+a logit depends on ~900 activations of the three layers, so a few flips of
+~1e-3 each reach it: 0.03 absolute is ten times that.  The gradient passes
+through three more bf16 roundings (one per layer), so each parameter block
+is compared to 5 % of its largest entry, with a cosine similarity of the
+whole gradient of at least 0.999.  The picks and the circle fit, given the
+same learned scores, are exact (integer and binary32 decisions taken the
+same way on both sides) and compared bit for bit.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2210_14771_gb300 import synth
+
+from _helpers import both_params, same_f32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+LOGIT_TOL = 0.03
+
+
+@pytest.fixture(scope="module")
+def ca():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_14771_gb300.build import build
+    build()
+    from paper_2210_14771_gb300 import api
+    h = api.ContentArea(0)
+    yield h
+    h.close()
+
+
+def _params(seed, scale=0.08):
+    import oracle as orc
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(orc.SC_NPARAM) * scale).astype(np.float32)
+    off = orc.sc_offsets()
+    p[off["bh"]] = -1.0
+    return p
+
+
+def _strips(seed, n, W, H):
+    s, ys, lab = synth.training_strips(seed, n, H, W)
+    return s, ys, lab
+
+
+def _to_dev(s, ys, lab):
+    return (torch.from_numpy(s).cuda(), torch.from_numpy(ys.astype(np.int32)).cuda(),
+            torch.from_numpy(lab).cuda())
+
+
+@pytest.mark.parametrize("W", [1920, 700, 37])
+def test_forward_matches_oracle(ca, orc, W):
+    H = 1080 if W >= 700 else 64
+    p = _params(1)
+    ca.scorer_set_params(p)
+    s, ys, lab = _strips(2, 5, W, H)
+    ds, dy, _ = _to_dev(s, ys, lab)
+    lg, sc = ca.scorer_forward(ds, dy, H)
+    torch.cuda.synchronize()
+    ca.sync()
+    lg = lg.cpu().numpy()
+    worst = 0.0
+    for k in range(len(s)):
+        ref = orc.sc_forward(s[k], ys[k], H, p, mode=orc.SC_MIXED)
+        d = np.abs(lg[k] - ref)
+        worst = max(worst, float(d.max()))
+        assert d.max() <= LOGIT_TOL, (k, int(d.argmax()), float(d.max()))
+        q = sc[k].cpu().numpy().view(np.uint16).astype(np.int64)
+        assert np.abs(q - orc.sc_q15(lg[k]).astype(np.int64)).max() <= 1
+    print("max |logit - oracle| =", worst)
+
+
+def test_gradient_matches_oracle(ca, orc):
+    W, H = 700, 480
+    p = _params(3, 0.1)
+    ca.scorer_set_params(p)
+    s, ys, lab = _strips(4, 6, W, H)
+    ds, dy, dl = _to_dev(s, ys, lab)
+    pw = 8.0
+    loss, g = ca.scorer_step(ds, dy, dl, H, pos_weight=pw, apply=False)
+    ref = np.zeros(orc.SC_NPARAM)
+    ref_loss = 0.0
+    for k in range(len(s)):
+        lk, gk = orc.sc_loss_grad(s[k], ys[k], H, lab[k], p, pos_weight=pw, mode=orc.SC_MIXED)
+        ref += gk
+        ref_loss += lk
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    off = orc.sc_offsets()
+    bounds = list(off.items()) + [("end", orc.SC_NPARAM)]
+    for (name, a), (_, b) in zip(bounds[:-1], bounds[1:]):
+        gb, rb = g[a:b].astype(np.float64), ref[a:b]
+        assert np.abs(gb - rb).max() <= 0.05 * np.abs(rb).max() + 1e-6, name
+    cos = float(g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)))
+    assert cos >= 0.999, cos
+
+
+def test_training_is_deterministic_and_lowers_the_loss(ca):
+    W, H = 1920, 1080
+    s, ys, lab = _strips(5, 512, W, H)
+    ds, dy, dl = _to_dev(s, ys, lab)
+    runs = []
+    for _ in range(2):
+        ca.scorer_init(7)
+        losses = ca.scorer_train(ds, dy, dl, H, epochs=4, batch=64, seed=1, lr=0.05,
+                                 momentum=0.9, pos_weight=20.0)
+        runs.append((losses, ca.scorer_get_params()))
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][0], runs[1][0])
+    losses = runs[0][0]
+    assert losses[-1] < 0.7 * losses[0], losses
+
+
+def test_save_load_roundtrip(ca):
+    p = _params(9)
+    ca.scorer_set_params(p)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "scorer.bin")
+        ca.scorer_save(path)
+        ca.scorer_set_params(_params(10))
+        ca.scorer_load(path)
+    assert np.array_equal(ca.scorer_get_params(), p)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_learned_pipeline_parity(ca, orc, mode):
+    """Learned scores of every strip column within tolerance of the oracle's;
+    given those scores, the candidates (with the fallback of unsure
+    half-strips), the fitted circle and the mask equal the oracle's."""
+    from paper_2210_14771_gb300 import api
+    p = _params(11, 0.1)
+    ca.scorer_set_params(p)
+    frames, _, keys = synth.batch(12, 4, 480, 640, "mixed")
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=4, n_hyps=256, seed=3, scorer_mode=mode)
+    ca.set_debug(1)
+    res, masks = ca.estimate(torch.from_numpy(frames).cuda(), lp, keys=keys, masks=True)
+    ca.sync()
+    gres = api.results_numpy(res)
+    gm = masks.cpu().numpy()
+    rows = orc.strip_rows(480, 16)
+    for b in range(len(frames)):
+        learned = ca.dump_learned(b, 16, 640)
+        for i, y in enumerate(rows):
+            ref = orc.sc_forward(frames[b][y - 1:y + 2], y, 480, p, mode=orc.SC_MIXED)
+            dq = np.abs(learned[i].astype(np.int64) - orc.sc_q15(ref).astype(np.int64))
+            # Q15 step of the sigmoid at the logit tolerance: 32768 * 0.25 * 0.03
+            assert dq.max() <= 250, (b, i, int(dq.max()))
+        xs, ys_, ss = orc.learned_candidates(frames[b], learned, fallback=(mode == 2), p=op)
+        gc = ca.dump_candidates(b)
+        assert np.array_equal(gc["x"], xs) and np.array_equal(gc["y"], ys_)
+        assert np.array_equal(gc["s"], ss)
+        want = orc.fit(xs, ys_, ss, 480, 640, keys[b], op)
+        for k in ("cx", "cy", "r", "score"):
+            assert same_f32(gres[k][b], want[k]), (b, k)
+        assert int(gres["valid"][b]) == want["valid"] and int(gres["n_inliers"][b]) == want["n_inliers"]
+        assert np.array_equal(gm[b], orc.mask(want, 480, 640))
+    ca.set_debug(0)
