@@ -33,6 +33,9 @@ METRIC = "1080p frames/s (batched, whole hot path)"
 PAPER_CONTEXT = {"ms_per_frame": 0.129, "hardware": "NVIDIA GeForce GTX 980 Ti",
                  "source": "Table 1 (handcrafted variant)"}
 MIXED = dict(B=512, seed=2, unique=128)   # 4 resolutions, 25 % each
+LEARNED = dict(seed=3, train_strips=200000, epochs=3, frames=256, unique=64, eval_frames=64)
+SERVING = dict(seed=4, streams=32, budget=4 << 30, n_strips=32, n_hyps=1024, realtime_frames=90,
+               saturation_frames=60)
 ROTATE_INPUTS = 4   # resident copies of the batch, used in turn (1.6 GB > L2)
 ROTATE_MASKS = 2
 
@@ -47,6 +50,8 @@ def parse():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batching", action="store_true")
+    ap.add_argument("--skip-learned", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -260,6 +265,129 @@ def batching_leg(ca, mixed, p_ref, stream, steps, warmup):
     return out
 
 
+# MACs per strip column: forward (3 convolutions + head), and a training step
+# (forward, input gradients of layers 3 and 2, weight gradients of all three)
+SC_FWD_MACS = 14 * 7 * 32 + 2 * 32 * 7 * 32 + 32
+SC_TRAIN_MACS = SC_FWD_MACS + 2 * 32 * 7 * 32 + (14 * 7 * 32 + 2 * 32 * 7 * 32)
+
+
+def learned_leg(ca, data, stream, steps):
+    """The learned scorer: trained on the GPU by the library's own kernels on
+    LEARNED["train_strips"] labelled 1080p strips, then run fused before
+    RANSAC (with the handcrafted fallback) on 256 1080p frames; accuracy
+    against the generator's ground truth, with and without the network."""
+    import numpy as np
+    import torch
+    from paper_2210_14771_gb300 import api, metrics
+    (s, ys, lab), (frames, gts, keys) = data
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, W, H = len(s), 1920, 1080
+    ds, dy, dl = (torch.from_numpy(s).to(dev), torch.from_numpy(ys).to(dev),
+                  torch.from_numpy(lab).to(dev))
+    ca.scorer_init(0)
+    ep = LEARNED["epochs"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ca.scorer_train(ds, dy, dl, H, epochs=ep, batch=64, seed=1, lr=0.05, momentum=0.9,
+                             pos_weight=20.0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    hbm_peak, _ = peaks()
+    tc_peak, tc_kind = tensor_peak()
+    out = {"train": {"strips": n, "epochs": ep, "batch": 64, "seconds": el,
+                     "strips_per_s": n * ep / el,
+                     "tflops": n * ep * W * 2 * SC_TRAIN_MACS / el / 1e12,
+                     "loss_per_epoch": [float(v) for v in losses]}}
+    fr = torch.from_numpy(np.stack(frames)).to(dev)
+    B = fr.shape[0]
+    masks = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+    p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=2)
+    for _ in range(3):
+        ca.estimate(fr, p, keys=keys, masks=masks)
+    torch.cuda.synchronize()
+    ca.kernel_times()
+    ca.set_timing(True)
+    total, per = timed_loop(stream, steps, lambda k: ca.estimate(fr, p, keys=keys, masks=masks))
+    ca.set_timing(False)
+    ca.sync()
+    kt = ca.kernel_times()
+    sc_ms = kt["scorer"][0] / max(1, kt["scorer"][1])
+    flops = B * 32 * W * 2 * SC_FWD_MACS
+    out["infer"] = {"frames": B, "frames_per_s": B * steps / (total / 1e3),
+                    "ms_per_call": total / steps, "scorer_ms": sc_ms,
+                    "scorer_share": kt["scorer"][0] / max(1e-9, sum(v[0] for v in kt.values())),
+                    "roofline": {"bound": "tensor", "kernel": "k_sc_infer",
+                                 "achieved": flops / (sc_ms / 1e3) / 1e12, "peak": tc_peak,
+                                 "unit": "TFLOP/s", "peak_kind": tc_kind,
+                                 "frac": flops / (sc_ms / 1e3) / 1e12 / tc_peak}}
+    # accuracy on a sample of the frames: handcrafted, learned, learned + fallback
+    sample = list(range(0, B, max(1, B // LEARNED["eval_frames"])))[:LEARNED["eval_frames"]]
+    sub = [fr[i] for i in sample]
+    acc = {}
+    for mode, name in ((0, "hand"), (1, "learned"), (2, "learned_fallback")):
+        q = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=mode)
+        ca.set_debug(1)
+        _, m = ca.estimate(sub, q, keys=[keys[i] for i in sample], masks=True)
+        ca.sync()
+        hits, nh = [], []
+        for j, i in enumerate(sample):
+            g = gts[i]
+            c = ca.dump_candidates(j)
+            if g["kind"] != "none" and len(c["x"]):
+                d = np.abs(np.hypot(c["x"] - g["cx"], c["y"] - g["cy"]) - g["r"])
+                hits.append(float((d <= 3.0).mean()))
+            nh.append(metrics.normalised_hausdorff(m[j].cpu().numpy().astype(bool),
+                                                   metrics.gt_mask(g, H, W)))
+        ca.set_debug(0)
+        acc[name] = {"candidate_hit_rate_3px": float(np.mean(hits)), **metrics.summarise(nh)}
+    out["accuracy"] = acc
+    return out
+
+
+def serving_leg(ca, streams):
+    """32 synthetic video streams (four resolutions, Poisson arrivals at 30-60
+    fps, drifting circles with scope changes) served with continuous batching
+    under a 4 GB admission budget, against the same load served one frame per
+    launch (max_batch 1); then all frames at once (saturation)."""
+    from paper_2210_14771_gb300 import api, serve
+    p = api.params(n_strips=SERVING["n_strips"], cands_per_strip=2, n_hyps=SERVING["n_hyps"])
+    banks = serve.pinned_banks(streams)
+    out = {"streams": len(streams), "budget_bytes": SERVING["budget"],
+           "resolutions": sorted({"%dx%d" % (s.W, s.H) for s in streams}),
+           "offered_fps": float(sum(s.fps for s in streams))}
+    n_rt = SERVING["realtime_frames"]
+    for name, mb in (("continuous_batching", 64), ("one_frame_per_launch", 1)):
+        srv = serve.Server(ca, p, mem_budget=SERVING["budget"], max_streams=len(streams),
+                           max_batch=mb)
+        recs, wall = serve.run_load(srv, streams, banks, n_rt, realtime=True)
+        srv.close()
+        out[name] = serve.summarise(recs, wall)
+    srv = serve.Server(ca, p, mem_budget=SERVING["budget"], max_streams=len(streams), max_batch=64)
+    recs, wall = serve.run_load(srv, streams, banks, SERVING["saturation_frames"], realtime=False)
+    srv.close()
+    out["saturation"] = serve.summarise(recs, wall)
+    return out
+
+
+def tensor_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        if "bf16_tflops_sustained" in d:
+            return d["bf16_tflops_sustained"], "measured (sustained)"
+    return 1700.0, "fallback (sustained)"
+
+
+def learned_data(rank):
+    from paper_2210_14771_gb300 import synth
+    w = min(16, os.cpu_count() or 1)
+    strips = synth.training_strips(LEARNED["seed"] + 1000 * rank, LEARNED["train_strips"], 1080,
+                                   1920, "mixed", workers=w)
+    fb = synth.mixed_batch(LEARNED["seed"] + 1 + 1000 * rank, LEARNED["frames"],
+                           unique=LEARNED["unique"], workers=w, resolutions=((1080, 1920),))
+    return strips, fb
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -272,6 +400,11 @@ def run_ours(args):
     # inputs first: the mixed workload is drawn in spawned processes
     frames, gts, keys = make_workload(rank)
     mixed = None
+    ldata = learned_data(rank) if not args.skip_learned else None
+    vstreams = None
+    if not args.skip_serving:
+        vstreams = synth.video_streams(SERVING["seed"] + 1000 * rank, SERVING["streams"], bank=6,
+                                       workers=min(16, os.cpu_count() or 1))
     if not args.skip_batching:
         mixed = synth.mixed_batch(MIXED["seed"] + 1000 * rank, MIXED["B"], unique=MIXED["unique"],
                                   workers=min(16, os.cpu_count() or 1))
@@ -384,6 +517,10 @@ def run_ours(args):
     batching = None
     if mixed is not None:
         batching = batching_leg(ca, mixed, p, stream, max(5, min(args.steps, 20)), args.warmup)
+    learned = None
+    if ldata is not None:
+        learned = learned_leg(ca, ldata, stream, max(3, min(args.steps, 10)))
+    serving = serving_leg(ca, vstreams) if vstreams is not None else None
     clk = clocks.stop()
 
     # ---- roofline: the step is one fused kernel per graph launch
@@ -442,7 +579,7 @@ def run_ours(args):
                  "ms_per_frame": ms_per_step / B},
         "tuning": tuning, "kernels": kern,
         "staged": {"ms_per_call": staged_ms / staged_steps, "results_equal": bool(same_staged)},
-        "plain": plain, "batching": batching,
+        "plain": plain, "batching": batching, "learned": learned, "serving": serving,
         "accuracy": {"vs": "generator ground truth", **acc},
         "paper_context": PAPER_CONTEXT,
     }

@@ -141,6 +141,19 @@ ca_status ca_estimate_uniform(ca_handle *h, const uint8_t *frames_dev, int B, in
                               const uint64_t *keys, const ca_params *p, ca_result *out_dev,
                               uint8_t *masks_dev, void *stream);
 
+/* Tracked estimate (video): the previous estimate of a frame's track is used
+ * for the current one, as the paper's discussion suggests (Sec. 4): when the
+ * track's previous result (state_dev[track[i]]) was accepted (valid), its
+ * circle joins RANSAC as one more hypothesis, index n_hyps after the random
+ * ones, refined and scored like them (ties still go to the lowest index).
+ * After the call state_dev[track[i]] holds frame i's result.  state_dev:
+ * device array of n_tracks results (zero = no previous circle); track: host
+ * array of B indices in [0, n_tracks), or -1 for an untracked frame; a track
+ * may appear once per call.  Otherwise as ca_estimate. */
+ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                              ca_result *state_dev, const int32_t *track, int n_tracks,
+                              ca_result *out_dev, void *stream);
+
 /* Allocation-free estimate, for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a packaging variant of
  * ca_estimate_uniform (same arguments and results, bit for bit) with no handle.
@@ -283,6 +296,84 @@ ca_status ca_scorer_step(ca_handle *h, const uint8_t *strips_dev, const int32_t 
 ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t *ys_dev,
                           const uint8_t *labels_dev, int n, int W, int H, const ca_train_params *tp,
                           int epochs, int batch, uint64_t seed, float *epoch_loss_host);
+
+/* ---- Serving (no counterpart in the paper, which estimates one frame at a
+ * time): frames of many video streams under continuous batching.
+ *
+ * A request is one frame of one stream.  ca_server_submit admits it when its
+ * device buffers (the frame, and its mask when masks are kept) fit the
+ * server's memory budget -- else CA_ERR_ADMISSION, and the caller submits it
+ * again once results have been polled -- and queues its copy to the device.
+ * Every ca_server_poll launches the admitted frames (at most one per stream
+ * and max_batch per launch, oldest first) as one tracked estimate without
+ * waiting for more frames or for earlier launches to finish, and returns the
+ * results that have completed.  Each stream's previous result stays on the
+ * device and, with `track`, its circle joins the stream's next RANSAC
+ * (ca_estimate_tracked).  A stream's frames are estimated in submission
+ * order, so a frame's result is the same whether its stream is served alone
+ * or among others.  Times are seconds of ca_server_now()'s clock. */
+typedef struct ca_server ca_server;
+
+typedef struct ca_server_config {
+    ca_params params;    /* estimation parameters of every frame */
+    size_t mem_budget;   /* device bytes for the buffers of admitted frames */
+    int32_t max_streams; /* stream ids 0 .. max_streams-1 */
+    int32_t max_batch;   /* frames per launch */
+    int32_t track;       /* 1: previous circle of each stream as an extra hypothesis */
+    int32_t want_masks;  /* 1: write each frame's mask (copied to the host buffer
+                            given at submit, if any) */
+} ca_server_config;
+
+typedef struct ca_server_result {
+    uint64_t ticket;     /* from ca_server_submit */
+    int32_t stream_id;
+    int32_t pad;
+    uint64_t frame_key;
+    ca_result result;
+    double t_arrival;    /* as given at submit */
+    double t_submit;     /* admitted */
+    double t_launch;     /* its launch was queued */
+    double t_done;       /* seen complete by a poll */
+} ca_server_result;
+
+/* Monotonic clock of the server, in seconds. */
+double ca_server_now(void);
+
+/* Creates a server on the handle's device (the current device) with its own
+ * streams, a device pool of cfg->mem_budget bytes and the per-stream state.
+ * The handle must outlive the server. */
+ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server **out);
+
+/* Admits frame (H x W x 3 bytes of host memory; pinned memory makes the copy
+ * asynchronous) of stream `stream_id` with RANSAC key `frame_key` and arrival
+ * time `t_arrival`.  The frame buffer (and mask_host, H x W bytes or NULL)
+ * must stay valid and unchanged until the frame's result has been polled.
+ * Returns CA_ERR_ADMISSION, with nothing queued, when the budget is full. */
+ca_status ca_server_submit(ca_server *s, int stream_id, const uint8_t *frame_host, int H, int W,
+                           uint64_t frame_key, double t_arrival, uint8_t *mask_host,
+                           uint64_t *ticket);
+
+/* Launches what is admitted and returns up to `max` finished results (in
+ * completion order).  wait != 0: if nothing has finished, blocks until the
+ * oldest launch completes. */
+ca_status ca_server_poll(ca_server *s, int wait, ca_server_result *out, int max, int *n_done);
+
+/* Bytes of the pool in use, admitted frames not yet launched, launches queued. */
+ca_status ca_server_stats(const ca_server *s, size_t *bytes_in_use, int32_t *pending,
+                          int32_t *launches_in_flight);
+
+/* Waits for the server's work and frees it. */
+ca_status ca_server_destroy(ca_server *s);
+
+/* The server's admission allocator on its own (host bookkeeping only, no
+ * device memory): first-fit offsets in [0, bytes), aligned to `align`,
+ * adjacent free blocks merged.  CA_ERR_ADMISSION when no block fits. */
+typedef struct ca_pool ca_pool;
+ca_status ca_pool_create(size_t bytes, size_t align, ca_pool **out);
+ca_status ca_pool_alloc(ca_pool *p, size_t bytes, size_t *offset);
+ca_status ca_pool_free(ca_pool *p, size_t offset);
+ca_status ca_pool_stats(const ca_pool *p, size_t *used, size_t *largest_free);
+ca_status ca_pool_destroy(ca_pool *p);
 
 /* Writes the content-area masks of B results (Sec. 1.1, Fig. 1): pixel (x, y)
  * is 1 iff (x-cx)^2 + (y-cy)^2 <= r^2 in binary32 (each operation rounded, no

@@ -81,6 +81,9 @@ def lib():
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_int,
                               C.c_uint64, P(OrcParams), P(OrcResult), P(OrcDebug)]
+        L.orc_fit_prior.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int,
+                                    C.c_int, C.c_uint64, P(OrcParams), C.c_void_p, P(OrcResult),
+                                    P(OrcDebug)]
         L.orc_bf16.argtypes = [C.c_float]
         L.orc_bf16.restype = C.c_float
         L.orc_sc_offsets.argtypes = [C.c_void_p]
@@ -239,6 +242,14 @@ def i128_to_f32(v: int) -> np.float32:
     return np.float32(lib().orc_i128_to_f32(hi, v & ((1 << 64) - 1)))
 
 
+def estimate_tracked(frame, frame_key, p, prior):
+    """Whole pipeline with the previous circle (cx, cy, r) as an extra
+    hypothesis, or None for none."""
+    xs, ys, ss = candidates(frame, p)
+    H, W = np.shape(frame)[:2]
+    return fit(xs, ys, ss, H, W, frame_key, p, prior)
+
+
 def estimate(frame, frame_key=0, p=None, debug=False, hyp_cap=None):
     """Run the whole pipeline on one frame.  Returns (result dict, debug dict)."""
     f = _frame(frame)
@@ -288,15 +299,17 @@ def mask(result, H, W):
     return out
 
 
-def fit(xs, ys, ss, H, W, frame_key=0, p=None):
-    """Sec. 2.2.5 on a given candidate list (pixel x, y and Q15 scores)."""
+def fit(xs, ys, ss, H, W, frame_key=0, p=None, prior=None):
+    """Sec. 2.2.5 on a given candidate list (pixel x, y and Q15 scores); with
+    `prior` (cx, cy, r) the previous circle is one more hypothesis."""
     p = p or params()
     xs = np.ascontiguousarray(xs, np.int16)
     ys = np.ascontiguousarray(ys, np.int16)
     ss = np.ascontiguousarray(ss, np.uint16)
     res = OrcResult()
-    if lib().orc_fit(_ptr(xs), _ptr(ys), _ptr(ss), len(xs), H, W, frame_key, C.byref(p),
-                     C.byref(res), None) != 0:
+    pr = np.ascontiguousarray(prior, np.float32) if prior is not None else None
+    if lib().orc_fit_prior(_ptr(xs), _ptr(ys), _ptr(ss), len(xs), H, W, frame_key, C.byref(p),
+                           _ptr(pr) if pr is not None else None, C.byref(res), None) != 0:
         raise ValueError("bad fit arguments")
     return dict(cx=res.cx, cy=res.cy, r=res.r, score=res.score, valid=res.valid,
                 n_inliers=res.n_inliers)

@@ -458,6 +458,15 @@ int orc_estimate(const uint8_t *rgb, int H, int W, int64_t pitch, uint64_t frame
  * best circle and the t_cs acceptance. */
 int orc_fit(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_t M, int H,
             int W, uint64_t frame_key, const orc_params *p, orc_result *res, orc_debug *dbg) {
+    return orc_fit_prior(cx16, cy16, cs, M, H, W, frame_key, p, NULL, res, dbg);
+}
+
+/* The same with the previous frame's circle (pixel coordinates cx, cy, r) as
+ * one more hypothesis after the random ones, the use of the previous
+ * estimate that Sec. 4 suggests; prior == NULL: none. */
+int orc_fit_prior(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_t M,
+                  int H, int W, uint64_t frame_key, const orc_params *p, const float *prior,
+                  orc_result *res, orc_debug *dbg) {
     memset(res, 0, sizeof(*res));
     int N = p->n_strips, K = p->cands_per_strip;
     if (W < 8 || H < 3 || N < 1 || K < 2 || (K & 1) || N * K > 256 || M < 0 || M > N * K)
@@ -482,7 +491,8 @@ int orc_fit(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_
     int64_t NH = 0;
     if (M >= 3)
         NH = p->hyp_mode == ORC_HYP_EXHAUSTIVE ? (int64_t)M * (M - 1) * (M - 2) / 6 : p->n_hyps;
-    if (dbg && dbg->n_hyps) *dbg->n_hyps = (int32_t)NH;
+    int64_t NH_all = NH + ((prior && M >= 3) ? 1 : 0);
+    if (dbg && dbg->n_hyps) *dbg->n_hyps = (int32_t)NH_all;
 
     uint8_t *flag = (uint8_t *)malloc((size_t)cap + 1);
     int32_t *IX = (int32_t *)malloc(sizeof(int32_t) * cap);
@@ -497,8 +507,18 @@ int orc_fit(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_
     uint32_t bestS = 0;
     float bestc[3] = {0, 0, 0};
     int32_t bestn = 0;
-    for (int64_t h = 0; h < NH; ++h) {
+    for (int64_t h = 0; h < NH_all; ++h) {
         int32_t t[3];
+        float c[3];
+        int ok;
+        if (h == NH) {
+            /* the previous circle, in the origin-relative coordinates */
+            t[0] = t[1] = t[2] = -1;
+            c[0] = prior[0] - (float)ox;
+            c[1] = prior[1] - (float)oy;
+            c[2] = prior[2];
+            ok = 1;
+        } else {
         if (p->hyp_mode == ORC_HYP_EXHAUSTIVE) {
             t[0] = ti; t[1] = tj; t[2] = tk;
             if (++tk == M) { if (++tj == M - 1) { ++ti; tj = ti + 1; } tk = tj + 1; }
@@ -511,8 +531,8 @@ int orc_fit(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, int32_
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
         if (s1 > s2) { tmp = s1; s1 = s2; s2 = tmp; }
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
-        float c[3];
-        int ok = orc_circumcircle(X[s0], Y[s0], X[s1], Y[s1], X[s2], Y[s2], c);
+        ok = orc_circumcircle(X[s0], Y[s0], X[s1], Y[s1], X[s2], Y[s2], c);
+        }
         int32_t n_inl = 0;
         uint32_t S = 0;
         int pass = 0;

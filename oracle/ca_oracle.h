@@ -165,6 +165,13 @@ int orc_sc_forward(const uint8_t *rgb3, int W, int y, int H, const float *prm, i
 double orc_sc_loss_grad(const uint8_t *rgb3, int W, int y, int H, const uint8_t *labels,
                         float pos_weight, const float *prm, int mode, double *grads);
 
+/* orc_fit with the previous frame's circle (cx, cy, r in pixel coordinates)
+ * as one more hypothesis, index n_hyps (Sec. 4: using the previous
+ * estimate); prior == NULL is orc_fit. */
+int orc_fit_prior(const int16_t *xs, const int16_t *ys, const uint16_t *ss, int32_t M, int H,
+                  int W, uint64_t frame_key, const orc_params *p, const float *prior,
+                  orc_result *res, orc_debug *dbg);
+
 /* Content-area mask of a result: disc intersected with the rectangle, or the
  * whole rectangle when the circle is not valid.  H*W bytes, 0/1. */
 void orc_mask(const orc_result *res, int H, int W, uint8_t *out);

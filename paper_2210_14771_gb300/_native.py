@@ -52,6 +52,17 @@ class CaResult(C.Structure):
                 ("valid", C.c_int32), ("n_inliers", C.c_int32)]
 
 
+class CaServerConfig(C.Structure):
+    _fields_ = [("params", CaParams), ("mem_budget", C.c_size_t), ("max_streams", C.c_int32),
+                ("max_batch", C.c_int32), ("track", C.c_int32), ("want_masks", C.c_int32)]
+
+
+class CaServerResult(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("stream_id", C.c_int32), ("pad", C.c_int32),
+                ("frame_key", C.c_uint64), ("result", CaResult), ("t_arrival", C.c_double),
+                ("t_submit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double)]
+
+
 # (name, restype, argtypes) of every exported function, in header order.
 _P = C.POINTER
 SIGNATURES = [
@@ -63,6 +74,8 @@ SIGNATURES = [
     ("ca_estimate_uniform", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                       _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    ("ca_estimate_tracked", C.c_int, [C.c_void_p, _P(CaFrame), C.c_int, _P(CaParams), C.c_void_p,
+                                      _P(C.c_int32), C.c_int, C.c_void_p, C.c_void_p]),
     ("ca_estimate_static", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _P(C.c_uint64),
                                      _P(CaParams), C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ca_tune", C.c_int, [C.c_void_p, _P(CaFrame), C.c_int, _P(CaParams), C.c_void_p,
@@ -84,6 +97,19 @@ SIGNATURES = [
     ("ca_scorer_train", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                   C.c_int, _P(CaTrainParams), C.c_int, C.c_int, C.c_uint64,
                                   C.c_void_p]),
+    ("ca_server_now", C.c_double, []),
+    ("ca_server_create", C.c_int, [C.c_void_p, _P(CaServerConfig), _P(C.c_void_p)]),
+    ("ca_server_submit", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_uint64,
+                                   C.c_double, C.c_void_p, _P(C.c_uint64)]),
+    ("ca_server_poll", C.c_int, [C.c_void_p, C.c_int, _P(CaServerResult), C.c_int,
+                                 _P(C.c_int)]),
+    ("ca_server_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int32), _P(C.c_int32)]),
+    ("ca_server_destroy", C.c_int, [C.c_void_p]),
+    ("ca_pool_create", C.c_int, [C.c_size_t, C.c_size_t, _P(C.c_void_p)]),
+    ("ca_pool_alloc", C.c_int, [C.c_void_p, C.c_size_t, _P(C.c_size_t)]),
+    ("ca_pool_free", C.c_int, [C.c_void_p, C.c_size_t]),
+    ("ca_pool_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_size_t)]),
+    ("ca_pool_destroy", C.c_int, [C.c_void_p]),
     ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,

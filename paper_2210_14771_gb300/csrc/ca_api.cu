@@ -393,7 +393,7 @@ ca_status mark_last(ca_handle *h, cudaStream_t stream) {
     return CA_OK;
 }
 
-DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T) {
+DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T, bool track = false) {
     DevParams P;
     std::memset(&P, 0, sizeof(P));
     P.N = p.n_strips;
@@ -411,9 +411,10 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T) 
     P.qg_sat = h->qg_sat;
     P.io_cut = iota_cut(h->li_host, P.T_ps);
     P.NH = (int)hyps_per_frame(p);
+    P.track = track ? 1 : 0;
     P.hyp_threads = T;
     const long long per_tile = kHypTile / P.hyp_threads;
-    P.n_tiles = (int)((P.NH + per_tile - 1) / per_tile);
+    P.n_tiles = (int)((P.NH + P.track + per_tile - 1) / per_tile);
     P.t_ri = p.t_ri;
     P.r_min = p.r_min;
     P.r_max = p.r_max;
@@ -480,10 +481,11 @@ struct CallBlock {
     int total_units = 0, n_segs = 0, total_items = 0;
     int sc_segs = 0;       // learned scorer segments
     int64_t sc_pix = 0;    // learned scorer pixel scores
+    size_t off_track = 0;  // tracked call: [B] track indices
 };
 
 void build_block(const ca_frame *frames, int B, int N, float alpha, const DevParams *P,
-                 const LaunchCfg &cfg, CallBlock &cb) {
+                 const LaunchCfg &cfg, CallBlock &cb, const int32_t *track = nullptr) {
     // distinct heights -> one strip-row table each
     std::map<int, int> row_off;
     int n_rows = 0;
@@ -543,8 +545,10 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
     }
     cb.off_rows = align_up(sizeof(DevFrame) * B, 256);
     cb.off_segs = align_up(cb.off_rows + sizeof(int32_t) * std::max(n_rows, 1), 256);
-    const size_t bytes = cb.off_segs + sizeof(BatchSeg) * std::max<size_t>(segs.size(), 1);
+    cb.off_track = align_up(cb.off_segs + sizeof(BatchSeg) * std::max<size_t>(segs.size(), 1), 256);
+    const size_t bytes = cb.off_track + (track ? sizeof(int32_t) * B : 0);
     cb.host.assign(bytes, 0);
+    if (track) std::memcpy(cb.host.data() + cb.off_track, track, sizeof(int32_t) * B);
     std::memcpy(cb.host.data(), df.data(), sizeof(DevFrame) * B);
     int32_t *hr = (int32_t *)(cb.host.data() + cb.off_rows);
     for (auto &kv : row_off) strip_rows(kv.first, N, alpha, hr + kv.second);
@@ -688,24 +692,30 @@ ca_status check_call(ca_handle *h, const ca_frame *frames, int B, const ca_param
 }
 
 ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
-                       ca_result *out_dev, cudaStream_t stream, const LaunchCfg &cfg) {
+                       ca_result *out_dev, cudaStream_t stream, const LaunchCfg &cfg,
+                       const int32_t *track = nullptr, ca_result *state_dev = nullptr) {
     CA_CUDA(h, cudaSetDevice(h->device));
     ca_status st;
     if ((st = order_after_last(h, stream)) != CA_OK) return st;
     if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
     int max_w = 0;
     for (int i = 0; i < B; ++i) max_w = std::max(max_w, frames[i].W);
-    const DevParams P = make_params(h, *p, max_w, cfg.T);
+    const DevParams P = make_params(h, *p, max_w, cfg.T, track != nullptr);
     CallBlock cb;
-    build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb);
+    build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb, track);
     Staging *sg;
     if ((st = take_staging(h, cb.host.size(), &sg)) != CA_OK) return st;
     std::memcpy(sg->host, cb.host.data(), cb.host.size());
     CA_CUDA(h, cudaMemcpyAsync(sg->dev, sg->host, cb.host.size(), cudaMemcpyHostToDevice, stream));
     CA_CUDA(h, cudaEventRecord(sg->ev, stream));
     sg->used = true;
-    const size_t hyp_rec = h->debug >= 2 ? (size_t)B * P.NH : 0;
+    const size_t hyp_rec = h->debug >= 2 ? (size_t)B * (P.NH + P.track) : 0;
     if ((st = ensure_workspace(h, B, P.n_tiles, hyp_rec)) != CA_OK) return st;
+    Workspace ws = h->ws;
+    if (track) {
+        ws.track = (const int32_t *)((const unsigned char *)sg->dev + cb.off_track);
+        ws.state = state_dev;
+    }
     if (cfg.scorer != CA_SCORER_HAND) {
         if (cb.sc_pix > INT32_MAX) return fail(h, CA_ERR_INVALID_ARG, "batch too large for the scorer");
         if ((size_t)cb.sc_pix > h->sc.scores_cap) {
@@ -725,13 +735,13 @@ ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_par
     const unsigned char *dev = (const unsigned char *)sg->dev;
     int k = 0;
     st = launch_call(h, (const DevFrame *)dev, B, (const int32_t *)(dev + cb.off_rows),
-                     (const BatchSeg *)(dev + cb.off_segs), cb, P, cfg, fgrid, h->d_luts, h->ws,
+                     (const BatchSeg *)(dev + cb.off_segs), cb, P, cfg, fgrid, h->d_luts, ws,
                      out_dev, stream, true, &k);
     if (st != CA_OK) return st;
     h->launches += k;
     h->last_B = B;
     h->last_NK = P.N * P.K;
-    h->last_hyp_stride = P.NH;
+    h->last_hyp_stride = P.NH + P.track;
     return mark_last(h, stream);
 }
 
@@ -1330,6 +1340,27 @@ ca_status ca_plan_launch(ca_plan *pl, void *stream) {
     CA_CUDA(h, cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
     h->launches += pl->kernels;
     return CA_OK;
+}
+
+ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
+                              ca_result *state_dev, const int32_t *track, int n_tracks,
+                              ca_result *out_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    ca_status st = check_call(h, frames, B, p, out_dev);
+    if (st != CA_OK || B == 0) return st;
+    if (!state_dev || !track || n_tracks < 1)
+        return fail(h, CA_ERR_INVALID_ARG, "tracked call needs state, tracks and n_tracks");
+    std::vector<char> seen((size_t)n_tracks, 0);
+    for (int i = 0; i < B; ++i) {
+        if (track[i] < -1 || track[i] >= n_tracks)
+            return fail(h, CA_ERR_INVALID_ARG, "frame %d: track %d outside [-1, %d)", i, track[i], n_tracks);
+        if (track[i] >= 0) {
+            if (seen[track[i]]) return fail(h, CA_ERR_INVALID_ARG, "track %d twice in one call", track[i]);
+            seen[track[i]] = 1;
+        }
+    }
+    return estimate_cfg(h, frames, B, p, out_dev, (cudaStream_t)stream, choose_cfg(h, frames, B, *p),
+                        track, state_dev);
 }
 
 ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *H,

@@ -87,7 +87,7 @@ struct DevParams {
     int32_t max_w;       // widest frame of the call (shared-memory sizing)
     int32_t hyp_threads; // threads per hypothesis in k_fit: 1, 2, 4 or 8
     int32_t io_cut;      // preceding maxima >= io_cut have s_iota < T_ps: never kept
-    int32_t pad;
+    int32_t track;       // 1: tracked call (previous circles as extra hypotheses)
 };
 
 // A candidate slot (8 bytes): x, y, Q15 score, kept flag.
@@ -123,6 +123,8 @@ struct Workspace {
     int32_t *n_cands = nullptr;      // [B]
     uint32_t *sync = nullptr;        // sync_words(sync_frames), fused kernel
     int32_t sync_frames = 0;
+    const int32_t *track = nullptr;  // tracked call: [B] track of each frame (-1: none)
+    ca_result *state = nullptr;      // tracked call: per-track previous result
 };
 
 // ---- Learned edge scorer (ca_scorer.cu): 1-D CNN over strip profiles.

@@ -67,6 +67,19 @@ __device__ __forceinline__ int qmag(int ng, int qsat) {
     return r;
 }
 
+// L2 load of a result (other CTAs may have written it during the kernel).  A
+// result is 24 bytes with 4-byte alignment: loaded word by word.
+__device__ __forceinline__ ca_result load_result(const ca_result *p) {
+    ca_result r;
+    r.cx = __ldcg(&p->cx);
+    r.cy = __ldcg(&p->cy);
+    r.r = __ldcg(&p->r);
+    r.score = __ldcg(&p->score);
+    r.valid = __ldcg(&p->valid);
+    r.n_inliers = __ldcg(&p->n_inliers);
+    return r;
+}
+
 }  // namespace
 
 // ============================================================== k_strips ==
@@ -728,10 +741,21 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
 
     long long NH = 0;
     if (M >= 3) NH = P.hyp_mode == CA_HYP_EXHAUSTIVE ? (long long)M * (M - 1) * (M - 2) / 6 : P.NH;
+    // tracked call: the previous circle of the frame's track, when it was
+    // accepted, is one more hypothesis (index NH), refined and scored like
+    // the others
+    int trk = -1;
+    ca_result prior;
+    prior.valid = 0;
+    if (P.track) {
+        trk = ws.track[f];
+        if (trk >= 0) prior = load_result(ws.state + trk);
+    }
+    const long long NH_all = NH + ((M >= 3 && prior.valid) ? 1 : 0);
     const long long h = (long long)tile * HPT + tid / T;
     if (P.debug >= 1 && tile == 0 && tid == 0) {
         ws.n_cands[f] = M;
-        ws.n_hyps[f] = (int)NH;
+        ws.n_hyps[f] = (int)NH_all;
     }
 
     unsigned long long key = 0ull;
@@ -739,7 +763,14 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
     int n_fin = 0;
     uint32_t S_fin = 0u;
     int t0 = 0, t1 = 0, t2 = 0, pass = 0;
-    if (h < NH) {   // uniform across the T threads of a group
+    if (h < NH_all) {   // uniform across the T threads of a group
+        bool have_circle;
+        if (h == NH) {
+            c0 = Circle{__fsub_rn(prior.cx, __int2float_rn(ox)), __fsub_rn(prior.cy, __int2float_rn(oy)),
+                        prior.r};
+            t0 = t1 = t2 = -1;
+            have_circle = true;
+        } else {
         if (P.hyp_mode == CA_HYP_EXHAUSTIVE) {
             unrank_triple(h, M, t0, t1, t2);
         } else {
@@ -760,8 +791,10 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
         if (s1 > s2) { tmp = s1; s1 = s2; s2 = tmp; }
         if (s0 > s1) { tmp = s0; s0 = s1; s1 = tmp; }
-        if (circumcircle(sm.pt[s0].X, sm.pt[s0].Y, sm.pt[s1].X, sm.pt[s1].Y, sm.pt[s2].X,
-                         sm.pt[s2].Y, c0)) {
+        have_circle = circumcircle(sm.pt[s0].X, sm.pt[s0].Y, sm.pt[s1].X, sm.pt[s1].Y,
+                                   sm.pt[s2].X, sm.pt[s2].Y, c0);
+        }
+        if (have_circle) {
             uint32_t bits[8 / T];
 #pragma unroll
             for (int w = 0; w < 8 / T; ++w) bits[w] = 0u;
@@ -801,7 +834,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
             rec.i0 = t0; rec.i1 = t1; rec.i2 = t2;
             rec.n_inl = n_fin; rec.S = S_fin; rec.pass = pass;
             rec.cx = c0.cx; rec.cy = c0.cy; rec.r = c0.r;
-            ws.hyps[(int64_t)f * P.NH + h] = rec;
+            ws.hyps[(int64_t)f * (P.NH + P.track) + h] = rec;
         }
     }
 
@@ -851,6 +884,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
             res.valid = S >= P.T_cs ? 1 : 0;
         }
         out[f] = res;
+        if (trk >= 0) ws.state[trk] = res;   // every tile of the frame has read the prior
         ws.best[f] = 0ull;   // ready for the next call
         ws.done[f] = 0u;
         if (sync) {
@@ -1023,19 +1057,6 @@ __device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &r
             }
         }
     }
-}
-
-// L2 load of a result (in the fused kernel another CTA wrote it).  A result
-// is 24 bytes with 4-byte alignment: loaded word by word.
-__device__ __forceinline__ ca_result load_result(const ca_result *p) {
-    ca_result r;
-    r.cx = __ldcg(&p->cx);
-    r.cy = __ldcg(&p->cy);
-    r.r = __ldcg(&p->r);
-    r.score = __ldcg(&p->score);
-    r.valid = __ldcg(&p->valid);
-    r.n_inliers = __ldcg(&p->n_inliers);
-    return r;
 }
 
 }  // namespace

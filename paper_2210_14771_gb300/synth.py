@@ -307,3 +307,84 @@ def training_strips(seed: int, n: int, H: int = 1080, W: int = 1920, geometry: s
         return (np.empty((0, 3, W, 3), np.uint8), np.empty(0, np.int32), np.empty((0, W), np.uint8))
     return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
             np.concatenate([p[2] for p in parts]))
+
+
+class VideoStream:
+    """A synthetic endoscopic video stream: its frames are windows of a larger
+    scene that drift by at most 2 px per frame (the scope moving), with a
+    scope change -- a new scene -- with probability 1 % per frame, and arrive
+    as a Poisson process of `fps` frames per second.  Only `bank` distinct
+    frames are rendered; frame k shows frame k mod bank of the walk, so the
+    stream can be served for any length with bounded memory (the walk is a
+    there-and-back path, so consecutive frames stay within 2 px)."""
+
+    MARGIN = 48
+
+    def __init__(self, seed: int, sid: int, H: int, W: int, fps: float, bank: int = 8,
+                 geometry: str | None = None):
+        self.seed, self.sid, self.H, self.W, self.fps = seed, sid, H, W, fps
+        rng = np.random.default_rng([0x5E7, seed & 0xFFFFFFFF, sid])
+        geo = geometry or ("centred", "clipped", "full", "hard")[sid % 4]
+        M = self.MARGIN
+        scenes, k = [], 0
+        half = max(1, bank // 2)
+        offs, which = [], []
+        ox = oy = 0
+        for i in range(half):
+            if i == 0 or rng.uniform() < 0.01:
+                scenes.append(frame(seed, (sid << 16) | k, H + 2 * M, W + 2 * M, geo))
+                k += 1
+                ox = oy = 0
+            else:
+                ox = int(np.clip(ox + rng.integers(-2, 3), -M + 2, M - 2))
+                oy = int(np.clip(oy + rng.integers(-2, 3), -M + 2, M - 2))
+            offs.append((ox, oy))
+            which.append(len(scenes) - 1)
+        path = list(range(half)) + list(range(half - 1, -1, -1))   # there and back
+        self.frames, self.gts = [], []
+        for j in path[:bank]:
+            img, gt = scenes[which[j]]
+            ox, oy = offs[j]
+            x0, y0 = M + ox, M + oy
+            self.frames.append(np.ascontiguousarray(img[y0:y0 + H, x0:x0 + W]))
+            g = dict(gt)
+            if g["kind"] != "none":
+                g["cx"] -= x0
+                g["cy"] -= y0
+                g["valid"] = gt_valid(g["cx"], g["cy"], g["r"], H, W)
+            self.gts.append(g)
+        self._rng = np.random.default_rng([0xA77, seed & 0xFFFFFFFF, sid])
+
+    def arrivals(self, n: int) -> np.ndarray:
+        """Arrival times (s, from 0) of the first n frames."""
+        return np.cumsum(self._rng.exponential(1.0 / self.fps, size=n))
+
+    def frame(self, k: int):
+        return self.frames[k % len(self.frames)], self.gts[k % len(self.gts)]
+
+    def key(self, k: int) -> int:
+        return frame_key((self.seed << 8) | self.sid, k)
+
+
+SERVING_RESOLUTIONS = MIXED_RESOLUTIONS
+
+
+def _stream_job(args):
+    seed, sid, H, W, fps, bank = args
+    return VideoStream(seed, sid, H, W, fps, bank)
+
+
+def video_streams(seed: int, n: int, resolutions=SERVING_RESOLUTIONS, bank: int = 8,
+                  workers: int = 0):
+    """n streams with resolutions drawn from `resolutions` and rates U[30, 60] fps."""
+    rng = np.random.default_rng([0x57E, seed & 0xFFFFFFFF])
+    jobs = []
+    for sid in range(n):
+        H, W = resolutions[int(rng.integers(0, len(resolutions)))]
+        jobs.append((seed, sid, H, W, float(rng.uniform(30.0, 60.0)), bank))
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_stream_job, jobs))
+    return [_stream_job(j) for j in jobs]

@@ -167,3 +167,55 @@ def test_learned_pipeline_parity(ca, orc, mode):
         assert int(gres["valid"][b]) == want["valid"] and int(gres["n_inliers"][b]) == want["n_inliers"]
         assert np.array_equal(gm[b], orc.mask(want, 480, 640))
     ca.set_debug(0)
+
+
+def _hit_rate(xs, ys, gt, tol=3.0):
+    """Fraction of candidates within tol pixels of the true circle."""
+    if gt["kind"] == "none" or len(xs) == 0:
+        return None
+    d = np.abs(np.hypot(xs - gt["cx"], ys - gt["cy"]) - gt["r"])
+    return float((d <= tol).mean())
+
+
+def test_trained_network_gains_over_handcrafted(ca):
+    """What the learned part buys: trained on the GPU (own kernels) on 8192
+    labelled 1080p strips, then run on 48 held-out 1080p frames of the
+    geometry mix.  Candidates land on the true boundary far more often, no
+    more frames are missed (normalised Hausdorff > 15 px, Sec. 2.3) and at
+    least as many content areas are within 5 px of the truth.  The mean
+    distance is printed, not asserted: on a few dozen frames it is decided by
+    single ill-conditioned frames (a clipped circle whose border is two thin
+    corner slivers), where the confident learned scores let a circle through
+    the short arcs pass t_cs that the handcrafted scores leave below it."""
+    from paper_2210_14771_gb300 import api, metrics
+    s, ys, lab = synth.training_strips(100, 8192, 1080, 1920, "mixed", workers=4)
+    ds, dy, dl = _to_dev(s, ys, lab)
+    ca.scorer_init(1)
+    losses = ca.scorer_train(ds, dy, dl, 1080, epochs=6, batch=64, seed=3, lr=0.05, momentum=0.9,
+                             pos_weight=20.0)
+    assert losses[-1] < 0.5 * losses[0]
+    frames, gts, keys = synth.mixed_batch(200, 48, workers=4, resolutions=((1080, 1920),))
+    fr = [torch.from_numpy(f).cuda() for f in frames]
+    out = {}
+    for mode in (0, 1, 2):
+        p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=mode)
+        ca.set_debug(1)
+        _, m = ca.estimate(fr, p, keys=keys, masks=True)
+        ca.sync()
+        hits, nh = [], []
+        for b in range(len(fr)):
+            c = ca.dump_candidates(b)
+            h = _hit_rate(c["x"].astype(float), c["y"].astype(float), gts[b])
+            if h is not None:
+                hits.append(h)
+            nh.append(metrics.normalised_hausdorff(m[b].cpu().numpy().astype(bool),
+                                                   metrics.gt_mask(gts[b], 1080, 1920)))
+        nh = np.asarray(nh)
+        out[mode] = dict(hit=float(np.mean(hits)), mean_nh=float(nh.mean()),
+                         miss=float((nh > 15).mean()), within5=float((nh <= 5).mean()))
+    ca.set_debug(0)
+    print("hand %s | learned %s | learned+fallback %s" % (out[0], out[1], out[2]))
+    assert out[1]["hit"] >= out[0]["hit"] + 0.15
+    for mode in (1, 2):
+        assert out[mode]["miss"] <= out[0]["miss"]
+        assert out[mode]["within5"] >= out[0]["within5"]

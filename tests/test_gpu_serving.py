@@ -1,0 +1,133 @@
+"""Tracked estimation and the serving loop on the GPU.
+
+The tracked call must equal the oracle's tracked fit (the previous circle of
+the stream as one more hypothesis) bit for bit along a whole stream; the
+server must give every frame the result it gets when its stream is served
+alone, whatever the mix, batch sizes and admission refusals around it.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2210_14771_gb300 import synth
+
+from _helpers import both_params, same_f32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SMALL = ((240, 320), (288, 360), (480, 640))
+
+
+@pytest.fixture(scope="module")
+def ca():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_14771_gb300.build import build
+    build()
+    from paper_2210_14771_gb300 import api
+    h = api.ContentArea(0)
+    yield h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def streams():
+    return synth.video_streams(5, 6, resolutions=SMALL, bank=6)
+
+
+def _oracle_chain(orc, stream, n, op):
+    out, prior = [], None
+    for k in range(n):
+        f, _ = stream.frame(k)
+        r = orc.estimate_tracked(f, stream.key(k), op, prior)
+        out.append(r)
+        prior = (r["cx"], r["cy"], r["r"]) if r["valid"] else None
+    return out
+
+
+def _same(g, o):
+    return (all(same_f32(g[i], o[k]) for i, k in enumerate(("cx", "cy", "r", "score")))
+            and int(g[4]) == o["valid"] and int(g[5]) == o["n_inliers"])
+
+
+def test_tracked_estimate_matches_oracle(ca, orc, streams):
+    from paper_2210_14771_gb300 import _native as N, api
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4)
+    n = 6
+    want = [_oracle_chain(orc, s, n, op) for s in streams]
+    state = torch.zeros((len(streams), 6), dtype=torch.float32, device="cuda")
+    for k in range(n):
+        ts = [torch.from_numpy(s.frame(k)[0]).cuda() for s in streams]
+        arr, B, _, res = ca._descriptors(ts, [s.key(k) for s in streams], None, None)
+        track = (C.c_int32 * B)(*range(B))
+        ca._check(N.lib().ca_estimate_tracked(ca._h, arr, B, C.byref(lp),
+                                              C.c_void_p(state.data_ptr()), track, B,
+                                              C.c_void_p(res.data_ptr()),
+                                              api._stream_ptr(None, ca.device)))
+        ca.sync()
+        g = api.results_numpy(res)
+        for i in range(B):
+            assert _same(tuple(g[i]), want[i][k]), (i, k, g[i], want[i][k])
+
+
+def _serve(ca, streams, banks, n, sids, max_batch, budget, p):
+    from paper_2210_14771_gb300 import serve
+    srv = serve.Server(ca, p, mem_budget=budget, max_streams=len(streams), max_batch=max_batch)
+    recs, _ = serve.run_load(srv, streams, banks, n, realtime=False, sids=sids)
+    srv.close()
+    return {(r["stream"], r["index"]): r["result"] for r in recs}
+
+
+def test_server_result_same_alone_and_in_the_mix(ca, orc, streams):
+    from paper_2210_14771_gb300 import api, serve
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4)
+    banks = serve.pinned_banks(streams)
+    n = 8
+    mix = _serve(ca, streams, banks, n, None, 4, 1 << 30, lp)
+    # a budget of about two frames forces admission refusals and retries
+    tight = _serve(ca, streams, banks, n, None, 3, 2 * 480 * 640 * 3 + 4096, lp)
+    assert mix == tight
+    for s in range(len(streams)):
+        alone = _serve(ca, streams, banks, n, [s], 64, 1 << 28, lp)
+        assert all(alone[(s, k)] == mix[(s, k)] for k in range(n)), s
+    want = _oracle_chain(orc, streams[2], n, op)
+    assert all(_same(mix[(2, k)], want[k]) for k in range(n))
+    del api
+
+
+def test_admission_refuses_beyond_the_budget(ca, streams):
+    from paper_2210_14771_gb300 import serve
+    s = streams[0]
+    fb = s.H * s.W * 3
+    srv = serve.Server(ca, None, mem_budget=2 * ((fb + 255) // 256 * 256), max_streams=6)
+    f = torch.from_numpy(s.frames[0]).pin_memory()
+    t0 = srv.submit(0, f, 1, srv.now())
+    t1 = srv.submit(1, f, 2, srv.now())
+    assert t0 is not None and t1 is not None
+    assert srv.submit(2, f, 3, srv.now()) is None          # budget full
+    got = []
+    while len(got) < 2:
+        got += srv.poll(wait=True)
+    assert srv.stats()["bytes_in_use"] == 0
+    assert srv.submit(2, f, 3, srv.now()) is not None      # admitted once memory is free
+    while not srv.poll(wait=True):
+        pass
+    srv.close()
+
+
+def test_realtime_serving_latency(ca, streams):
+    """Poisson arrivals at 30-60 fps per stream: every frame is served and the
+    tail latency stays far below a frame interval."""
+    from paper_2210_14771_gb300 import api, serve
+    p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024)
+    srv = serve.Server(ca, p, mem_budget=1 << 30, max_streams=len(streams))
+    banks = serve.pinned_banks(streams)
+    recs, wall = serve.run_load(srv, streams, banks, 15, realtime=True)
+    srv.close()
+    st = serve.summarise(recs, wall)
+    print("serving:", st)
+    assert st["frames"] == 15 * len(streams)
+    assert st["p99_ms"] < 20.0
