@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--skip-batching", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--learned-strips", type=int, default=None,
+                    help="training strips of the learned leg (default 200000)")
+    ap.add_argument("--learned-epochs", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -378,8 +381,12 @@ def tensor_peak():
     return 1700.0, "fallback (sustained)"
 
 
-def learned_data(rank):
+def learned_data(rank, args):
     from paper_2210_14771_gb300 import synth
+    if args.learned_strips:
+        LEARNED["train_strips"] = args.learned_strips
+    if args.learned_epochs:
+        LEARNED["epochs"] = args.learned_epochs
     w = min(16, os.cpu_count() or 1)
     strips = synth.training_strips(LEARNED["seed"] + 1000 * rank, LEARNED["train_strips"], 1080,
                                    1920, "mixed", workers=w)
@@ -400,7 +407,7 @@ def run_ours(args):
     # inputs first: the mixed workload is drawn in spawned processes
     frames, gts, keys = make_workload(rank)
     mixed = None
-    ldata = learned_data(rank) if not args.skip_learned else None
+    ldata = learned_data(rank, args) if not args.skip_learned else None
     vstreams = None
     if not args.skip_serving:
         vstreams = synth.video_streams(SERVING["seed"] + 1000 * rank, SERVING["streams"], bank=6,
