@@ -399,8 +399,15 @@ ca_status ca_sync(ca_handle *h, void *stream);
 
 /* Debug capture of the intermediate values of subsequent calls: 0 = off,
  * 1 = candidates, 2 = candidates and per-hypothesis records.  Capturing costs
- * extra device memory and writes; results are unchanged. */
+ * extra device memory and writes; results are unchanged.  Level 3 (level 2
+ * plus a test of the failure path): the fused launch withholds the signals
+ * that release its mask work, so those waits run out after the wait limit and
+ * the call reports CA_ERR_TIMEOUT through ca_sync; its masks are not valid. */
 ca_status ca_set_debug(ca_handle *h, int level);
+
+/* Bound on each dependency wait of the fused launch (nanoseconds, 1 ms to
+ * 60 s; default 2 s).  Waits normally last microseconds. */
+ca_status ca_set_wait_limit(ca_handle *h, uint64_t ns);
 
 enum {
     /* per frame: int32 M, int32 n_slots(=N*K), then n_slots records of

@@ -116,6 +116,7 @@ SIGNATURES = [
                               _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p]),
     ("ca_sync", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ca_set_debug", C.c_int, [C.c_void_p, C.c_int]),
+    ("ca_set_wait_limit", C.c_int, [C.c_void_p, C.c_uint64]),
     ("ca_debug_dump", C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(CaParams), C.c_void_p,
                                 C.c_size_t, _P(C.c_size_t)]),
     ("ca_launch_count", C.c_uint64, [C.c_void_p]),

@@ -299,6 +299,9 @@ class ContentArea:
     def set_debug(self, level: int):
         self._check(N.lib().ca_set_debug(self._h, level))
 
+    def set_wait_limit(self, ns: int):
+        self._check(N.lib().ca_set_wait_limit(self._h, ns))
+
     def _dump(self, what, frame, p, nbytes):
         buf = np.zeros(nbytes, np.uint8)
         written = C.c_size_t(0)

@@ -51,6 +51,7 @@ struct ca_handle {
     std::string err;
     int debug = 0;
     uint64_t launches = 0;
+    uint64_t wait_ns = 2000000000ull;   // bound on each wait of the fused kernel
 
     // score tables on the device: [s_g][s_theta][s_iota]
     uint16_t *d_luts = nullptr;
@@ -357,8 +358,7 @@ long long hyps_per_frame(const ca_params &p) {
     return p.n_hyps;
 }
 
-// Bound on each wait of the fused kernel (ns); waits normally last microseconds.
-constexpr uint64_t kWaitNs = 2000000000ull;
+
 
 ca_status ensure_luts(ca_handle *h, const ca_params &p, cudaStream_t stream) {
     LutKey k;
@@ -509,10 +509,12 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
         d.unit_off = units;
         d.mitem_off = mitems;
         d.vec_ok = ((uintptr_t)f.rgb_dev % 16 == 0) && (f.pitch % 16 == 0) && (f.W % 16 == 0);
-        d.mask_vec_ok = f.mask_dev && ((uintptr_t)f.mask_dev % 16 == 0) && (f.W % 16 == 0);
+        d.mask_vec_ok = !f.mask_dev ? 0
+                      : ((uintptr_t)f.mask_dev % 32 == 0 && f.W % 32 == 0) ? 2
+                      : ((uintptr_t)f.mask_dev % 16 == 0 && f.W % 16 == 0) ? 1 : 0;
         d.sc_seg_off = sc_segs;
         d.sc_pix_off = (int32_t)sc_pix;
-        sc_segs += N * ((f.W + kScSegOut - 1) / kScSegOut);
+        sc_segs += N * ((f.W + kScSegOutInfer - 1) / kScSegOutInfer);
         sc_pix += (int64_t)N * f.W;
         if (f.mask_dev) {
             units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
@@ -622,7 +624,7 @@ ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32
         const int grid = std::max(1, std::min(fused_grid, cb.total_items));
         cudaEvent_t t0 = timed ? time_begin(h, stream) : nullptr;
         e = launch_batch(d_frames, B, d_rows, P, d_luts, ws, out, d_segs, cb.n_segs,
-                         cb.total_items, grid, kWaitNs, stream);
+                         cb.total_items, grid, h->wait_ns, stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "k_batch launch");
         time_end(h, 3, t0, stream);
         *kernels = 1;
@@ -955,7 +957,7 @@ ca_status check_strips(ca_handle *h, const uint8_t *strips, const int32_t *ys, i
     return CA_OK;
 }
 
-int sc_segs_of(int n, int W) { return n * ((W + kScSegOut - 1) / kScSegOut); }
+int sc_segs_of(int n, int W, int out) { return n * ((W + out - 1) / out); }
 
 // Forward + loss + gradient partials of n strips, then the reduction (and the
 // update when tp->apply).  Queued on `s`.
@@ -971,7 +973,7 @@ ca_status sc_step_async(ca_handle *h, const uint8_t *strips, const int32_t *ys,
     src.n = n;
     src.W = W;
     src.H = H;
-    const int segs = sc_segs_of(n, W);
+    const int segs = sc_segs_of(n, W, kScSegOutTrain);
     const int grid = std::max(1, std::min(segs, S.partial_n));
     cudaError_t e = sc_launch_train(src, labels, tp.pos_weight, S.block, S.partial, segs, S.err,
                                     grid, s);
@@ -1073,7 +1075,7 @@ ca_status ca_scorer_forward(ca_handle *h, const uint8_t *strips_dev, const int32
     src.n = n;
     src.W = W;
     src.H = H;
-    const int segs = sc_segs_of(n, W);
+    const int segs = sc_segs_of(n, W, kScSegOutInfer);
     const int grid = std::max(1, std::min(segs, h->sm_count * sc_infer_blocks_per_sm()));
     cudaEvent_t t0 = time_begin(h, s);
     cudaError_t e = sc_launch_infer(src, h->sc.block, scores_dev, logits_dev, segs, h->sc.err,
@@ -1451,8 +1453,17 @@ ca_status ca_sync(ca_handle *h, void *stream) {
 
 ca_status ca_set_debug(ca_handle *h, int level) {
     if (!h) return CA_ERR_INVALID_ARG;
-    if (level < 0 || level > 2) return fail(h, CA_ERR_INVALID_ARG, "debug level %d", level);
+    if (level < 0 || level > 3) return fail(h, CA_ERR_INVALID_ARG, "debug level %d", level);
     h->debug = level;
+    return CA_OK;
+}
+
+ca_status ca_set_wait_limit(ca_handle *h, uint64_t ns) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (ns < 1000000ull || ns > 60000000000ull)
+        return fail(h, CA_ERR_INVALID_ARG, "wait limit %llu ns outside [1 ms, 60 s]",
+                    (unsigned long long)ns);
+    h->wait_ns = ns;
     return CA_OK;
 }
 

@@ -36,7 +36,7 @@ struct DevFrame {
     int32_t rows_off;   // offset of this frame's strip rows in the rows table
     int32_t unit_off;   // prefix sum of mask units before this frame
     int16_t vec_ok;     // 1: rgb, pitch and 3W are multiples of 16 bytes
-    int16_t mask_vec_ok;// 1: mask pointer and W are multiples of 16 bytes
+    int16_t mask_vec_ok;// 2: mask pointer and W multiples of 32 bytes, 1: of 16, 0: neither
     int32_t mitem_off;  // prefix sum of fused-kernel mask items before this frame
     int32_t sc_seg_off; // learned scorer: prefix sum of its segments before this frame
     int32_t sc_pix_off; // learned scorer: offset of this frame's N x W pixel scores
@@ -130,7 +130,9 @@ struct Workspace {
 // ---- Learned edge scorer (ca_scorer.cu): 1-D CNN over strip profiles.
 constexpr int kScCin = 14, kScCh = 32, kScTaps = 7;
 constexpr int kScHalo = 9;                       // 3 layers x 3 columns of context
-constexpr int kScSegOut = 512 - 2 * kScHalo;     // output columns per 512-column segment
+constexpr int kScInferTiles = 3, kScTrainTiles = 4;   // 128-column tiles per segment
+constexpr int kScSegOutInfer = 128 * kScInferTiles - 2 * kScHalo;   // output columns per segment
+constexpr int kScSegOutTrain = 128 * kScTrainTiles - 2 * kScHalo;
 constexpr int kScNParam = 17601;                 // flat parameter count (see ca.h)
 constexpr int kScMaxPicks = 8;                   // K/2 limit with the learned scorer
 constexpr uint32_t kScErrTimeout = 2u;

@@ -891,7 +891,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
             // every tile of this frame has passed its wait on the strip
             // counter: re-arm it, then publish the result to the mask items
             sync_strips(sync, ws.sync_frames)[f] = 0u;
-            if (fr.mask) {
+            if (fr.mask && P.debug < 3) {   // debug level 3 withholds it (tests the bounded waits)
                 __threadfence();
                 atomicExch(sync_ready(sync, ws.sync_frames) + f, 1u);
             }

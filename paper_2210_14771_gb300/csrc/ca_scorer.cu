@@ -36,9 +36,21 @@ namespace ca {
 namespace {
 
 constexpr int kCin = kScCin, kCh = kScCh, kTaps = kScTaps;
-constexpr int kTile = 128, kSegTiles = 4, kSegRows = kTile * kSegTiles;
+constexpr int kTile = 128;
 constexpr int kGuard = 8;
-constexpr int kPlaneBytes = (kSegRows + 2 * kGuard) * 16;
+
+// Segment geometry: TILES tiles of 128 columns, of which all but 9 columns of
+// context at each end are outputs.
+template <int TILES>
+struct SegGeom {
+    static constexpr int kTiles = TILES;
+    static constexpr int kRows = kTile * TILES;
+    static constexpr int kPlane = (kRows + 2 * kGuard) * 16;   // bytes of one channel plane
+    static constexpr int kOut = kRows - 2 * kScHalo;
+};
+using SegI = SegGeom<kScInferTiles>;   // inference
+using SegT = SegGeom<kScTrainTiles>;   // training
+static_assert(SegI::kOut == kScSegOutInfer && SegT::kOut == kScSegOutTrain, "segment sizes");
 
 // smem descriptors (no swizzle): start, LBO (K direction), SBO (M/N direction)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -166,6 +178,7 @@ __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w 
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
 // Writes the 32 values of a row into 4 planes (bf16).
+template <class G>
 __device__ __forceinline__ void store_row32(unsigned char *planes, int row, const float (&v)[32]) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -174,14 +187,15 @@ __device__ __forceinline__ void store_row32(unsigned char *planes, int row, cons
         q.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
         q.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
         q.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
-        *reinterpret_cast<uint4 *>(planes + c * kPlaneBytes + (kGuard + row) * 16) = q;
+        *reinterpret_cast<uint4 *>(planes + c * G::kPlane + (kGuard + row) * 16) = q;
     }
 }
 
+template <class G>
 __device__ __forceinline__ void load_row32(const unsigned char *planes, int row, float (&v)[32]) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(planes + c * kPlaneBytes + (kGuard + row) * 16);
+        const uint4 q = *reinterpret_cast<const uint4 *>(planes + c * G::kPlane + (kGuard + row) * 16);
         v[8 * c + 0] = bf16_lo(q.x); v[8 * c + 1] = bf16_hi(q.x);
         v[8 * c + 2] = bf16_lo(q.y); v[8 * c + 3] = bf16_hi(q.y);
         v[8 * c + 4] = bf16_lo(q.z); v[8 * c + 5] = bf16_hi(q.z);
@@ -211,13 +225,14 @@ __device__ __forceinline__ float luma_f(uint32_t r, uint32_t g, uint32_t b) {
 
 // Column features of a segment: rows r in [0, 512) <-> columns b0 + r; two
 // planes (14 features + 2 zero channels), zero outside [0, W).
+template <class G>
 __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t *row0,
                                                const uint8_t *row1, const uint8_t *row2, int W,
                                                int y, int H, int b0) {
     const float yf = __fdiv_rn(__fsub_rn((float)y, __fmul_rn(0.5f, (float)(H - 1))), (float)H);
     const float xc = __fmul_rn(0.5f, (float)(W - 1));
     const float Wf = (float)W;
-    for (int r = threadIdx.x; r < kSegRows; r += blockDim.x) {
+    for (int r = threadIdx.x; r < G::kRows; r += blockDim.x) {
         const int x = b0 + r;
         uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
         if (x >= 0 && x < W) {
@@ -240,7 +255,7 @@ __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t 
                             pack_bf16(f[14], f[15]));
         }
         *reinterpret_cast<uint4 *>(x0 + (kGuard + r) * 16) = q0;
-        *reinterpret_cast<uint4 *>(x0 + kPlaneBytes + (kGuard + r) * 16) = q1;
+        *reinterpret_cast<uint4 *>(x0 + G::kPlane + (kGuard + r) * 16) = q1;
     }
 }
 
@@ -248,17 +263,23 @@ __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t 
 // tap t, MMAs over channel pairs of planes; D of tile j = columns 32 j.
 //   in: planes of the input (n_in_chunks = 2 or 4), w: weight chunks
 //   [t * n_in_chunks + c][32 out][8 in] (512 bytes each).
-__device__ __forceinline__ void issue_conv(uint32_t tmem, const unsigned char *in, int n_in_chunks,
+template <class G, int NIN>
+__device__ __forceinline__ void issue_conv(uint32_t tmem, const unsigned char *in,
                                            const unsigned char *w) {
+    // base descriptors; an operand's start address is bits 0-13 (16-byte
+    // units), so a byte offset d moves it by adding d >> 4
     constexpr uint32_t idesc = idesc_bf16(128, 32, false, false);
-    const uint32_t a0 = smem_u32(in), w0 = smem_u32(w);
-    for (int j = 0; j < kSegTiles; ++j)
+    const uint64_t da = sdesc(smem_u32(in) + (kGuard - 3) * 16, G::kPlane, 128);
+    const uint64_t db = sdesc(smem_u32(w), 512, 128);
+#pragma unroll
+    for (int j = 0; j < G::kTiles; ++j)
+#pragma unroll
         for (int t = 0; t < kTaps; ++t)
-            for (int q = 0; q < n_in_chunks / 2; ++q) {
-                const uint32_t a = a0 + 2 * q * kPlaneBytes + (kGuard + kTile * j + t - 3) * 16;
-                const uint32_t b = w0 + (t * n_in_chunks + 2 * q) * 512;
-                mma_bf16(tmem + 32 * j, sdesc(a, kPlaneBytes, 128), sdesc(b, 512, 128), idesc,
-                         (t | q) != 0);
+#pragma unroll
+            for (int q = 0; q < NIN / 2; ++q) {
+                const uint32_t ao = (2 * q * G::kPlane + (kTile * j + t) * 16) >> 4;
+                const uint32_t bo = ((t * NIN + 2 * q) * 512) >> 4;
+                mma_bf16(tmem + 32 * j, da + ao, db + bo, idesc, (t | q) != 0);
             }
 }
 
@@ -270,10 +291,11 @@ struct ScVec {   // float part of the weight block
 };
 static_assert(sizeof(ScVec) == kScVecBytes, "vector block size");
 
-// Epilogue helper: the 32 accumulator channels of row r (= 128 j + 32 warp + lane).
+// Epilogue helper: the 32 accumulator channels of row r = 128 j + 32 q + lane,
+// q = warp % 4 (a warp can only read its own quarter of the TMEM lanes).
 __device__ __forceinline__ void acc_row(uint32_t tmem, int j, float (&v)[32]) {
-    const int warp = threadIdx.x >> 5;
-    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * j, v);
+    const int q = (threadIdx.x >> 5) & 3;
+    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * j, v);
 }
 
 // Where segment g of a launch reads and writes.
@@ -286,6 +308,7 @@ struct SegInfo {
     int strip;           // strips mode: index of the strip in the source
 };
 
+template <class G>
 __device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
     SegInfo si;
     if (src.frames) {
@@ -296,7 +319,7 @@ __device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
             else hi = mid - 1;
         }
         const DevFrame &fr = src.frames[lo];
-        const int nseg = (fr.W + kScSegOut - 1) / kScSegOut;
+        const int nseg = (fr.W + G::kOut - 1) / G::kOut;
         const int local = g - fr.sc_seg_off;
         const int i = local / nseg, s = local - i * nseg;
         si.y = src.rows[fr.rows_off + i];
@@ -304,11 +327,11 @@ __device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
         si.H = fr.H;
         si.pitch = fr.pitch;
         si.r0 = fr.rgb + (int64_t)(si.y - 1) * fr.pitch;
-        si.s0 = s * kScSegOut;
+        si.s0 = s * G::kOut;
         si.out = (int64_t)fr.sc_pix_off + (int64_t)i * fr.W;
         si.strip = -1;
     } else {
-        const int nseg = (src.W + kScSegOut - 1) / kScSegOut;
+        const int nseg = (src.W + G::kOut - 1) / G::kOut;
         const int j = g / nseg, s = g - j * nseg;
         const int id = src.idx ? src.idx[j] : j;
         si.y = src.ys[id];
@@ -316,16 +339,17 @@ __device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
         si.H = src.H;
         si.pitch = (int64_t)src.W * 3;
         si.r0 = src.strips + (int64_t)id * 3 * si.pitch;
-        si.s0 = s * kScSegOut;
+        si.s0 = s * G::kOut;
         si.out = (int64_t)j * src.W;
         si.strip = id;
     }
-    si.s1 = min(si.W, si.s0 + kScSegOut);
+    si.s1 = min(si.W, si.s0 + G::kOut);
     return si;
 }
 
 // Common prologue of the scorer kernels: zero guard rows of `n_planes`
 // planes from `sm`, init the barriers, allocate TMEM, start the weight copy.
+template <class G>
 __device__ __forceinline__ uint32_t sc_prologue(unsigned char *sm, int n_planes, uint64_t *bar_w,
                                                 uint64_t *bar_m, uint32_t *tslot, uint32_t ncols,
                                                 unsigned char *wdst, const unsigned char *wsrc,
@@ -333,8 +357,8 @@ __device__ __forceinline__ uint32_t sc_prologue(unsigned char *sm, int n_planes,
     const int tid = threadIdx.x, warp = tid >> 5;
     for (int i = tid; i < n_planes * kGuard * 2; i += blockDim.x) {
         const int plane = i / (2 * kGuard), g = i % (2 * kGuard);
-        const int row = g < kGuard ? g : kSegRows + g;   // rows [0, 8) and [520, 528)
-        *reinterpret_cast<uint4 *>(sm + plane * kPlaneBytes + row * 16) = make_uint4(0, 0, 0, 0);
+        const int row = g < kGuard ? g : G::kRows + g;   // rows [0, 8) and [520, 528)
+        *reinterpret_cast<uint4 *>(sm + plane * G::kPlane + row * 16) = make_uint4(0, 0, 0, 0);
     }
     if (tid == 0) {
         bar_init(bar_w, 1);
@@ -359,31 +383,31 @@ __device__ __forceinline__ uint32_t sc_prologue(unsigned char *sm, int n_planes,
 // One CTA (4 warps) per 512-column segment at a time, 2 CTAs per SM.  Output:
 // the Q15 score round(32768 p) of every output column, and the logit when
 // `logits` is set.
-constexpr int kInfThreads = 128;
-constexpr size_t kInfSmem = 6 * (size_t)kPlaneBytes + kScFwdBytes + kScVecBytes + 64;
+constexpr int kInfThreads = 256;   // 8 warps: two per TMEM lane quarter
+constexpr size_t kInfSmem = 6 * (size_t)SegI::kPlane + kScFwdBytes + kScVecBytes + 64;
 
-__global__ void __launch_bounds__(kInfThreads, 2)
+__global__ void __launch_bounds__(kInfThreads, 3)
     k_sc_infer(ScSource src, const unsigned char *__restrict__ wblock, uint16_t *__restrict__ scores,
                float *__restrict__ logits, int total_segs, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *X0 = sm;                       // 2 planes: features
-    unsigned char *A = sm + 2 * kPlaneBytes;      // 4 planes: a1, then a2 (in place)
-    unsigned char *Wf = A + 4 * kPlaneBytes;
+    unsigned char *A = sm + 2 * SegI::kPlane;      // 4 planes: a1, then a2 (in place)
+    unsigned char *Wf = A + 4 * SegI::kPlane;
     ScVec *vec = reinterpret_cast<ScVec *>(Wf + kScFwdBytes);
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kScVecBytes);
     uint64_t *bar_m = bar_w + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t tmem = sc_prologue(sm, 6, bar_w, bar_m, tslot, 128, Wf, wblock + kScOffW1f,
+    const uint32_t tmem = sc_prologue<SegI>(sm, 6, bar_w, bar_m, tslot, 128, Wf, wblock + kScOffW1f,
                                       kScFwdBytes, vec, wblock + kScOffVec);
     bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
     uint32_t phase = 0;
 
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
-        const SegInfo si = seg_info(src, g);
+        const SegInfo si = seg_info<SegI>(src, g);
         const int b0 = si.s0 - kScHalo;
         __syncthreads();   // the previous segment is done with A and X0
-        build_features(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
+        build_features<SegI>(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
         fence_async_smem();
         tc_before_sync();
         __syncthreads();
@@ -391,30 +415,42 @@ __global__ void __launch_bounds__(kInfThreads, 2)
         for (int l = 0; l < 3; ++l) {
             if (tid == 0) {
                 const int woff = l == 0 ? 0 : (l == 1 ? kScOffW2f : kScOffW3f) - kScOffW1f;
-                issue_conv(tmem, l == 0 ? X0 : A, l == 0 ? 2 : 4, Wf + woff);
+                if (l == 0) issue_conv<SegI, 2>(tmem, X0, Wf + woff);
+                else issue_conv<SegI, 4>(tmem, A, Wf + woff);
                 mma_commit(bar_m);
             }
             const bool ok = bar_wait(bar_m, phase, err);
             phase ^= 1u;
             tc_after_sync();
             if (__syncthreads_or(!ok)) { abort = true; break; }
-            for (int j = 0; j < kSegTiles; ++j) {
+            for (int j = warp >> 2; j < SegI::kTiles; j += 2) {   // warp w: tiles w/4, w/4 + 2
                 float v[32];
                 acc_row(tmem, j, v);
-                const int r = kTile * j + 32 * warp + (tid & 31);
+                const int r = kTile * j + 32 * (warp & 3) + (tid & 31);
                 const int x = b0 + r;
                 const bool inside = x >= 0 && x < si.W;
+                // relu(z) rounded to bf16, two channels per conversion (ReLU and
+                // rounding commute); zero outside the strip
+                uint32_t w[16];
+                const float *bl = vec->b[l];
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float z = __fadd_rn(v[c], vec->b[l][c]);
-                    v[c] = inside && z > 0.0f ? __bfloat162float(__float2bfloat16_rn(z)) : 0.0f;
+                for (int c = 0; c < 16; ++c) {
+                    const float z0 = fmaxf(__fadd_rn(v[2 * c], bl[2 * c]), 0.0f);
+                    const float z1 = fmaxf(__fadd_rn(v[2 * c + 1], bl[2 * c + 1]), 0.0f);
+                    w[c] = inside ? pack_bf16(z0, z1) : 0u;
                 }
-                if (l < 2) {
-                    store_row32(A, r, v);   // every MMA reading A has completed
+                if (l < 2) {   // every MMA reading A has completed: overwrite in place
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        *reinterpret_cast<uint4 *>(A + c * SegI::kPlane + (kGuard + r) * 16) =
+                            make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
                 } else if (x >= si.s0 && x < si.s1) {
                     float acc = 0.0f;
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) acc = __fadd_rn(acc, __fmul_rn(vec->whq[c], v[c]));
+                    for (int c = 0; c < 16; ++c) {
+                        acc = __fadd_rn(acc, __fmul_rn(vec->whq[2 * c], bf16_lo(w[c])));
+                        acc = __fadd_rn(acc, __fmul_rn(vec->whq[2 * c + 1], bf16_hi(w[c])));
+                    }
                     const float lg = __fadd_rn(vec->bh, acc);
                     const float p = 1.0f / (1.0f + expf(-lg));
                     const int q = min(32768, max(0, __float2int_rn(p * 32768.0f)));
@@ -440,14 +476,16 @@ __global__ void __launch_bounds__(kInfThreads, 2)
 size_t sc_infer_smem() { return kInfSmem; }
 
 int sc_infer_blocks_per_sm() {
+    // shared memory per SM (each CTA also reserves 1 KB), at most 4 CTAs for
+    // the 512 TMEM columns (128 each)
     static int nb = [] {
-        int v = 0;
-        if (cudaFuncSetAttribute(k_sc_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kInfSmem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_sc_infer, kInfThreads, kInfSmem) !=
+        int dev = 0, smem_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
                 cudaSuccess)
-            v = 1;
-        return v < 1 ? 1 : (v > 2 ? 2 : v);   // TMEM: 128 columns per CTA
+            return 1;
+        const int v = smem_sm / (int)(kInfSmem + 1024);
+        return v < 1 ? 1 : (v > 4 ? 4 : v);
     }();
     return nb;
 }
@@ -474,50 +512,74 @@ cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uin
 // weights).  The sums of the CTA go to its own slice of `partial`.
 constexpr int kTrainThreads = 128;
 constexpr int kTrainPlanes = 14;   // D (4) | A1 (4) | A2 (4) | X0 (2)
-constexpr size_t kTrainSmem = (size_t)kTrainPlanes * kPlaneBytes + (kScBlockBytes - kScVecBytes) +
-                              kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float);
+constexpr size_t kTrainStageBytes = (size_t)kTaps * 32 * 32 * sizeof(float);   // one layer's dW
+constexpr size_t kTrainSmem = (size_t)kTrainPlanes * SegT::kPlane + (kScBlockBytes - kScVecBytes) +
+                              kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float) + kTrainStageBytes;
 constexpr int kDwCol = 128;        // TMEM columns of the weight-gradient accumulators (7 x 32)
 
 namespace {
 
 // Weight-gradient MMAs of one layer: for every tap t, dW_t[co][ci] +=
 // sum_x dz[x][co] in[x + t - 3][ci] over the 512 rows of the segment.
+template <class G>
 __device__ __forceinline__ void issue_dw(uint32_t tmem, const unsigned char *dz,
                                          const unsigned char *in, int n_in) {
     const uint32_t idesc = idesc_bf16(64, 8 * n_in, true, true);
-    const uint32_t a0 = smem_u32(dz), b0 = smem_u32(in);
+    const uint64_t da = sdesc(smem_u32(dz) + kGuard * 16, 128, G::kPlane);
+    const uint64_t db = sdesc(smem_u32(in) + (kGuard - 3) * 16, 128, G::kPlane);
     for (int t = 0; t < kTaps; ++t)
-        for (int k = 0; k < kSegRows / 16; ++k) {
-            const uint32_t a = a0 + (kGuard + 16 * k) * 16;
-            const uint32_t b = b0 + (kGuard + 16 * k + t - 3) * 16;
-            mma_bf16(tmem + kDwCol + 32 * t, sdesc(a, 128, kPlaneBytes), sdesc(b, 128, kPlaneBytes),
+#pragma unroll 4
+        for (int k = 0; k < G::kRows / 16; ++k)
+            mma_bf16(tmem + kDwCol + 32 * t, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k + t),
                      idesc, k != 0);
-        }
 }
 
-// Adds the weight gradient of a layer into the CTA's partial sums.  An M = 64
-// accumulator keeps rows 16q .. 16q+15 in lanes 0-15 of TMEM lane quarter q:
-// output channels 0-15 are read by warp 0 and 16-31 by warp 1.
-__device__ __forceinline__ void flush_dw(uint32_t tmem, float *part, int off, int n_in_real) {
+// Adds the weight gradient of a layer into the CTA's partial sums (layout
+// [t][co][ci] per layer; written instead of added on the CTA's first
+// segment).  An M = 64 accumulator keeps rows 16q .. 16q+15 in lanes 0-15 of
+// TMEM lane quarter q: output channels 0-15 are read by warp 0 and 16-31 by
+// warp 1 into shared memory, then every thread adds its share with 16-byte
+// loads and stores.
+__device__ __forceinline__ void flush_dw(uint32_t tmem, float *stage, float *part, int off,
+                                         int n_in_real, bool first) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp >= 2) return;
-    const int co = 16 * warp + lane;
-    for (int t = 0; t < kTaps; ++t) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + kDwCol + 32 * t, v);
-        if (lane < 16) {
+    if (warp < 2) {
+        const int co = 16 * warp + lane;
+        for (int t = 0; t < kTaps; ++t) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + kDwCol + 32 * t, v);
+            if (lane < 16) {
+                float *row = stage + (t * 32 + co) * n_in_real;
 #pragma unroll
-            for (int ci = 0; ci < 32; ++ci)
-                if (ci < n_in_real) {
-                    float *q = part + off + (co * n_in_real + ci) * kTaps + t;
-                    *q = __fadd_rn(*q, v[ci]);
-                }
+                for (int ci = 0; ci < 32; ++ci)
+                    if (ci < n_in_real) row[ci] = v[ci];
+            }
         }
     }
+    __syncthreads();
+    const int n4 = kTaps * 32 * n_in_real / 4;
+    float4 *dst = reinterpret_cast<float4 *>(part + off);
+    const float4 *src = reinterpret_cast<const float4 *>(stage);
+    for (int i = threadIdx.x; i < n4; i += 2 * kTrainThreads) {
+        const int j = i + kTrainThreads;
+        float4 a = src[i], b = j < n4 ? src[j] : make_float4(0, 0, 0, 0);
+        if (!first) {
+            const float4 pa = dst[i];
+            const float4 pb = j < n4 ? dst[j] : make_float4(0, 0, 0, 0);
+            a = make_float4(__fadd_rn(pa.x, a.x), __fadd_rn(pa.y, a.y), __fadd_rn(pa.z, a.z),
+                            __fadd_rn(pa.w, a.w));
+            b = make_float4(__fadd_rn(pb.x, b.x), __fadd_rn(pb.y, b.y), __fadd_rn(pb.z, b.z),
+                            __fadd_rn(pb.w, b.w));
+        }
+        dst[i] = a;
+        if (j < n4) dst[j] = b;
+    }
+    __syncthreads();
 }
 
 // Sums a per-thread 32-vector over the CTA (fixed order) into part[off + c].
-__device__ __forceinline__ void flush_vec32(float (&v)[32], float *red, float *part, int off) {
+__device__ __forceinline__ void flush_vec32(float (&v)[32], float *red, float *part, int off,
+                                            bool first) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float w = warp_transpose_sum(v);
     red[warp * 32 + lane] = w;
@@ -525,7 +587,7 @@ __device__ __forceinline__ void flush_vec32(float (&v)[32], float *red, float *p
     if (threadIdx.x < 32) {
         float t = 0.0f;
         for (int k = 0; k < kTrainThreads / 32; ++k) t = __fadd_rn(t, red[k * 32 + threadIdx.x]);
-        part[off + threadIdx.x] = __fadd_rn(part[off + threadIdx.x], t);
+        part[off + threadIdx.x] = first ? t : __fadd_rn(part[off + threadIdx.x], t);
     }
     __syncthreads();
 }
@@ -544,17 +606,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                int total_segs, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *D = sm;                          // gradient planes; planes 4-7 read as M padding
-    unsigned char *A1 = sm + 4 * kPlaneBytes;
-    unsigned char *A2 = sm + 8 * kPlaneBytes;
-    unsigned char *X0 = sm + 12 * kPlaneBytes;
-    unsigned char *Wall = sm + kTrainPlanes * kPlaneBytes;
+    unsigned char *A1 = sm + 4 * SegT::kPlane;
+    unsigned char *A2 = sm + 8 * SegT::kPlane;
+    unsigned char *X0 = sm + 12 * SegT::kPlane;
+    unsigned char *Wall = sm + kTrainPlanes * SegT::kPlane;
     ScVec *vec = reinterpret_cast<ScVec *>(Wall + (kScBlockBytes - kScVecBytes));
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kScVecBytes);
     uint64_t *bar_m = bar_w + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
     float *red = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(bar_w) + 64);
+    float *stage = red + 3 * 4 * 32;   // 16-byte aligned
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tmem = sc_prologue(sm, kTrainPlanes, bar_w, bar_m, tslot, 512, Wall, wblock,
+    const uint32_t tmem = sc_prologue<SegT>(sm, kTrainPlanes, bar_w, bar_m, tslot, 512, Wall, wblock,
                                       kScBlockBytes - kScVecBytes, vec, wblock + kScOffVec);
     bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
     float *part = partial + (size_t)blockIdx.x * kScPartialStride;
@@ -579,22 +642,24 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     };
 
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
-        const SegInfo si = seg_info(src, g);
+        const SegInfo si = seg_info<SegT>(src, g);
         const int b0 = si.s0 - kScHalo;
         const uint8_t *lab = labels + (int64_t)si.strip * si.W;
+        const bool first = g == (int)blockIdx.x;   // the CTA's first segment writes its partials
         __syncthreads();
-        build_features(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
+        build_features<SegT>(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
         mma_sync_point();
 
         // ---- forward: layers 1 and 2
         for (int l = 0; l < 2; ++l) {
             if (tid == 0) {
-                issue_conv(tmem, l == 0 ? X0 : A1, l == 0 ? 2 : 4, l == 0 ? Wf1 : Wf2);
+                if (l == 0) issue_conv<SegT, 2>(tmem, X0, Wf1);
+                else issue_conv<SegT, 4>(tmem, A1, Wf2);
                 mma_commit(bar_m);
             }
             if (!wait_mma()) break;
             unsigned char *dst = l == 0 ? A1 : A2;
-            for (int j = 0; j < kSegTiles; ++j) {
+            for (int j = 0; j < SegT::kTiles; ++j) {
                 float v[32];
                 acc_row(tmem, j, v);
                 const int r = kTile * j + 32 * warp + lane, x = b0 + r;
@@ -604,14 +669,14 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                     const float z = __fadd_rn(v[c], vec->b[l][c]);
                     v[c] = inside && z > 0.0f ? __bfloat162float(__float2bfloat16_rn(z)) : 0.0f;
                 }
-                store_row32(dst, r, v);
+                store_row32<SegT>(dst, r, v);
             }
             mma_sync_point();
         }
         // ---- layer 3, head, loss; gradient at the logits and at z3
         if (abort) break;
         if (tid == 0) {
-            issue_conv(tmem, A2, 4, Wf3);
+            issue_conv<SegT, 4>(tmem, A2, Wf3);
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
@@ -620,7 +685,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
 #pragma unroll
             for (int c = 0; c < 32; ++c) gwh[c] = gb3[c] = 0.0f;
             float gbh = 0.0f, loss = 0.0f;
-            for (int j = 0; j < kSegTiles; ++j) {
+            for (int j = 0; j < SegT::kTiles; ++j) {
                 float v[32];
                 acc_row(tmem, j, v);
                 const int r = kTile * j + 32 * warp + lane, x = b0 + r;
@@ -651,10 +716,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                     gb3[c] = __fadd_rn(gb3[c], dz);
                     v[c] = dz;
                 }
-                store_row32(D, r, v);
+                store_row32<SegT>(D, r, v);
             }
-            flush_vec32(gwh, red, part, kScPWh);
-            flush_vec32(gb3, red + 128, part, kScPB3);
+            flush_vec32(gwh, red, part, kScPWh, first);
+            flush_vec32(gb3, red + 128, part, kScPB3, first);
             gbh = warp_sum(gbh);
             loss = warp_sum(loss);
             if (lane == 0) { red[256 + 2 * warp] = gbh; red[256 + 2 * warp + 1] = loss; }
@@ -665,8 +730,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                     a = __fadd_rn(a, red[256 + 2 * k]);
                     b = __fadd_rn(b, red[256 + 2 * k + 1]);
                 }
-                part[kScPBh] = __fadd_rn(part[kScPBh], a);
-                part[kScNParam] = __fadd_rn(part[kScNParam], b);
+                part[kScPBh] = first ? a : __fadd_rn(part[kScPBh], a);
+                part[kScNParam] = first ? b : __fadd_rn(part[kScNParam], b);
             }
         }
         mma_sync_point();
@@ -674,39 +739,39 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         for (int l = 2; l >= 1; --l) {
             const unsigned char *in = l == 2 ? A2 : A1;
             if (tid == 0) {
-                issue_conv(tmem, D, 4, l == 2 ? Wb3 : Wb2);   // input gradient, columns [0, 128)
-                issue_dw(tmem, D, in, 4);
+                issue_conv<SegT, 4>(tmem, D, l == 2 ? Wb3 : Wb2);   // input gradient, columns [0, 128)
+                issue_dw<SegT>(tmem, D, in, 4);
                 mma_commit(bar_m);
             }
             if (!wait_mma()) break;
-            flush_dw(tmem, part, l == 2 ? kScPW3 : kScPW2, kCh);
+            flush_dw(tmem, stage, part, l == 2 ? kScPW3 : kScPW2, kCh, first);
             float gb[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) gb[c] = 0.0f;
-            for (int j = 0; j < kSegTiles; ++j) {
+            for (int j = 0; j < SegT::kTiles; ++j) {
                 float v[32], a[32];
                 acc_row(tmem, j, v);
                 const int r = kTile * j + 32 * warp + lane;
-                load_row32(in, r, a);
+                load_row32<SegT>(in, r, a);
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     v[c] = a[c] > 0.0f ? __bfloat162float(__float2bfloat16_rn(v[c])) : 0.0f;
                     gb[c] = __fadd_rn(gb[c], v[c]);
                 }
-                store_row32(D, r, v);   // every MMA reading D has completed
+                store_row32<SegT>(D, r, v);   // every MMA reading D has completed
             }
             __syncthreads();
-            flush_vec32(gb, red, part, l == 2 ? kScPB2 : kScPB1);
+            flush_vec32(gb, red, part, l == 2 ? kScPB2 : kScPB1, first);
             mma_sync_point();
         }
         // ---- layer 1: weight gradient only
         if (abort) break;
         if (tid == 0) {
-            issue_dw(tmem, D, X0, 2);
+            issue_dw<SegT>(tmem, D, X0, 2);
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
-        flush_dw(tmem, part, kScPW1, kScCin);
+        flush_dw(tmem, stage, part, kScPW1, kScCin, first);
         tc_before_sync();
     }
     __syncthreads();
@@ -827,20 +892,40 @@ cudaError_t sc_launch_pack(const float *params, unsigned char *block, cudaStream
     return cudaGetLastError();
 }
 
-// Sums the per-CTA gradient partials in a fixed order (and clears them), then
-// optionally takes an SGD step with momentum:
-//   v = momentum v + scale g,  w = w - lr v.
-__global__ void k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, float *__restrict__ part,
-                         int n_part, float scale, float lr, float momentum, int apply,
-                         float *__restrict__ grads_out, float *__restrict__ loss_out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p > kScNParam) return;
+// Sums the per-CTA gradient partials in a fixed order, then optionally takes
+// an SGD step with momentum:  v = momentum v + scale g,  w = w - lr v.
+// Weight blocks of the partials are laid out [t][co][ci]; the parameters are
+// [co][ci][t].  A block reduces 64 parameters with 4 threads each (partials
+// c = q, q + 4, ...), combined in order.
+constexpr int kSgdParams = 64;
+
+__device__ __forceinline__ int partial_index(int p) {
+    auto tr = [](int q, int off, int cin) {
+        const int co = q / (cin * kTaps), ci = (q / kTaps) % cin, t = q % kTaps;
+        return off + (t * 32 + co) * cin + ci;
+    };
+    if (p < kScPB1) return tr(p - kScPW1, kScPW1, kScCin);
+    if (p >= kScPW2 && p < kScPB2) return tr(p - kScPW2, kScPW2, kCh);
+    if (p >= kScPW3 && p < kScPB3) return tr(p - kScPW3, kScPW3, kCh);
+    return p;
+}
+
+__global__ void __launch_bounds__(256)
+    k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ part,
+             int n_part, float scale, float lr, float momentum, int apply,
+             float *__restrict__ grads_out, float *__restrict__ loss_out) {
+    __shared__ float red[4][kSgdParams];
+    const int pl = threadIdx.x % kSgdParams, q = threadIdx.x / kSgdParams;
+    const int p = blockIdx.x * kSgdParams + pl;
     float g = 0.0f;
-    for (int c = 0; c < n_part; ++c) {
-        float *q = part + (size_t)c * kScPartialStride + p;
-        g = __fadd_rn(g, *q);
-        *q = 0.0f;
+    if (p <= kScNParam) {
+        const float *src = part + partial_index(p);
+        for (int c = q; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(src + (size_t)c * kScPartialStride));
     }
+    red[q][pl] = g;
+    __syncthreads();
+    if (q != 0 || p > kScNParam) return;
+    g = __fadd_rn(__fadd_rn(__fadd_rn(red[0][pl], red[1][pl]), red[2][pl]), red[3][pl]);
     if (p == kScNParam) {   // loss slot
         if (loss_out) *loss_out = g;
         return;
@@ -856,8 +941,8 @@ __global__ void k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, float
 cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
                           float lr, float momentum, int apply, float *grads_out, float *loss_out,
                           cudaStream_t s) {
-    k_sc_sgd<<<(kScNParam + 1 + 255) / 256, 256, 0, s>>>(params, mom, partial, n_partials, scale,
-                                                          lr, momentum, apply, grads_out, loss_out);
+    k_sc_sgd<<<(kScNParam + 1 + kSgdParams - 1) / kSgdParams, 256, 0, s>>>(
+        params, mom, partial, n_partials, scale, lr, momentum, apply, grads_out, loss_out);
     return cudaGetLastError();
 }
 

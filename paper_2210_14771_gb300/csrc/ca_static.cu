@@ -150,7 +150,9 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
         d.rows_off = 0;
         d.unit_off = masks_dev ? units_per_frame * i : 0;
         d.vec_ok = ((uintptr_t)d.rgb % 16 == 0) && (W % 16 == 0);
-        d.mask_vec_ok = masks_dev && ((uintptr_t)d.mask % 16 == 0) && (W % 16 == 0);
+        d.mask_vec_ok = !masks_dev ? 0
+                      : ((uintptr_t)d.mask % 32 == 0 && W % 32 == 0) ? 2
+                      : ((uintptr_t)d.mask % 16 == 0 && W % 16 == 0) ? 1 : 0;
     }
 
     DevFrame *d_frames = reinterpret_cast<DevFrame *>(scratch + kOffFrames);

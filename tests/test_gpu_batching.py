@@ -160,3 +160,27 @@ def test_tune_keeps_results(ca):
     r_after, m_after = _run(ca, ts, keys, lp)
     assert r_after.tobytes() == r_before.tobytes()
     assert all(np.array_equal(a, b) for a, b in zip(m_after, m_before))
+
+
+def test_fused_wait_runs_out_reports_timeout_and_recovers(ca, orc):
+    """The failure path of the fused kernel's bounded waits, without any
+    fault: debug level 3 withholds the signals that release the mask work, so
+    those waits run out after the (shortened) limit; ca_sync reports
+    CA_ERR_TIMEOUT, and the next call on the same handle is correct again."""
+    from paper_2210_14771_gb300 import _native as N, api
+    frames, _, keys = synth.batch(31, 4, 240, 320, "centred")
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=128, batch_mode=2)
+    ca.set_wait_limit(50_000_000)
+    ca.set_debug(3)
+    try:
+        ca.estimate(ts, lp, keys=keys, masks=True)
+        with pytest.raises(N.CaError) as ei:
+            ca.sync()
+        assert ei.value.status == N.CA_ERR_TIMEOUT
+    finally:
+        ca.set_debug(0)
+        ca.set_wait_limit(2_000_000_000)
+    gres, gmask = _run(ca, ts, keys, lp)
+    _check_oracle(orc, frames, keys, op, gres, gmask, range(len(frames)))
+    del api
