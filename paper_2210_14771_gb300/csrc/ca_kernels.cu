@@ -240,36 +240,38 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
         col_lo = max(xa - 1, c_lo);
         col_hi = min(xb + 2, c_hi);
     }
-    int base;
+    int base = col_lo;
     __syncwarp();   // the previous item is done with yy / sc
 
     // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned)
-    if (fr.vec_ok) {
-        const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
-        base = g0 << 4;
-        const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
-        for (int g = g0 + lane; g < g1; g += 32) {
-            const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
-            const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
-            const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
-            const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
-            const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
-            uint4 *dst = reinterpret_cast<uint4 *>(yy + (g - g0) * 16);
-            dst[0] = interleave4(L0.x, L1.x, L2.x);
-            dst[1] = interleave4(L0.y, L1.y, L2.y);
-            dst[2] = interleave4(L0.z, L1.z, L2.z);
-            dst[3] = interleave4(L0.w, L1.w, L2.w);
+    auto load_words = [&]() {
+        if (fr.vec_ok) {
+            const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
+            base = g0 << 4;
+            const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
+            for (int g = g0 + lane; g < g1; g += 32) {
+                const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+                const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
+                const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
+                const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
+                const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
+                uint4 *dst = reinterpret_cast<uint4 *>(yy + (g - g0) * 16);
+                dst[0] = interleave4(L0.x, L1.x, L2.x);
+                dst[1] = interleave4(L0.y, L1.y, L2.y);
+                dst[2] = interleave4(L0.z, L1.z, L2.z);
+                dst[3] = interleave4(L0.w, L1.w, L2.w);
+            }
+        } else {
+            base = col_lo;
+            for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
+                const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
+                const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+                yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
+                                (luma(p2[0], p2[1], p2[2]) << 16);
+            }
         }
-    } else {
-        base = col_lo;
-        for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
-            const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
-            const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
-            yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
-                            (luma(p2[0], p2[1], p2[2]) << 16);
-        }
-    }
-    __syncwarp();
+        __syncwarp();
+    };
 
     const StripCtx ctx{W, H - 1 - 2 * y, lt, lg, li};
     const int dir = half ? -1 : 1;
@@ -277,15 +279,36 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
 
     if (kk == 1) {
         // preceding maximum before this warp's quarter: maxima of the
-        // earlier quarters of the quad
+        // earlier quarters of the quad, each from its middle row alone -- a
+        // quarter whose preceding maximum already reaches io_cut keeps no
+        // pixel, and loads nothing more
         int qm = 0;
-        for (int p = q0 + lane; p < q1; p += 32)
-            qm = max(qm, (int)((yy[(half ? W - 1 - p : p) - base] >> 8) & 0xff));
+        if (q0 < q1) {
+            const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
+            const uint8_t *r1 = fr.rgb + (int64_t)y * fr.pitch;
+            if (fr.vec_ok) {
+                for (int g = (xa >> 4) + lane; g <= (xb >> 4); g += 32) {
+                    const uint8_t *p1 = r1 + g * 48;
+                    const uint4 L = luma16(ld_nc_v4(p1), ld_nc_v4(p1 + 16), ld_nc_v4(p1 + 32));
+                    const uint32_t wv[4] = {L.x, L.y, L.z, L.w};
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int x = 16 * g + k;
+                        if (x >= xa && x <= xb)
+                            qm = max(qm, (int)((wv[k >> 2] >> (8 * (k & 3))) & 0xffu));
+                    }
+                }
+            } else {
+                for (int x = xa + lane; x <= xb; x += 32)
+                    qm = max(qm, (int)luma(r1[3 * x], r1[3 * x + 1], r1[3 * x + 2]));
+            }
+        }
         qm = __reduce_max_sync(kFull, qm);
         if (lane == 0) s_qmax[warp] = qm;
         quad_barrier(quad);
         int carry = 0;
         for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
+        if (carry < P.io_cut && q0 < q1) load_words();
         // ---- rounds of 32 consecutive pixels in scan order (outer edge
         // inwards), one per lane; `carry` is the preceding maximum before
         // the round, `best` this warp's best key so far
@@ -335,6 +358,7 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
         best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
                    max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
     } else {
+        load_words();
         // ---- K > 2: exact score per pixel over this lane's chunk, with a
         // sliding window of the vertical Sobel sums
         const int cpl = (len + 31) >> 5;
