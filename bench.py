@@ -138,6 +138,11 @@ def algorithmic_bytes(B, H, W, N, K):
             "fused": B * (9 * N * W + H * W + 24)}
 
 
+def abytes_strips_read(B, W, N):
+    """Strip-row bytes the method reads per batch (3 rows x 3 channels)."""
+    return B * 9 * N * W
+
+
 def kernel_traffic(kernel):
     """DRAM bytes of one launch from a committed ncu capture, if it was taken
     on the current kernel source (else None)."""
@@ -520,6 +525,34 @@ def run_ours(args):
         same = np.array_equal(h_masks.numpy(), m_host) and \
             h_res.numpy().tobytes() == res_host.tobytes()
         e2e["matches_device_path"] = bool(same)
+        # zero-copy variant: the kernels read the strip rows from and write
+        # the masks into the same page-locked host buffers (NVLink-C2C)
+        for _ in range(2):
+            ca.run_host_zero_copy_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
+                                      h_masks.data_ptr())
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            ca.run_host_zero_copy_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
+                                      h_masks.data_ptr())
+        elz = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([elz], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elz = float(t.item())
+        samez = np.array_equal(h_masks.numpy(), m_host) and \
+            h_res.numpy().tobytes() == res_host.tobytes()
+        zc = {"value": B * e_steps * world / elz, "unit": "frames/s",
+              "h2d_bytes_per_step": abytes_strips_read(B, W, WORKLOAD["n_strips"]),
+              "d2h_bytes_per_step": B * (H * W + 24), "ms_per_step": 1e3 * elz / e_steps,
+              "call": "ca_run_host_zero_copy (kernels read strip rows from and write masks to "
+                      "pinned host memory; h2d = strip rows read)",
+              "matches_device_path": bool(samez)}
+        if zc["value"] > e2e["value"]:
+            e2e = dict(zc, copy_path=e2e)
+        else:
+            e2e["zero_copy"] = zc
 
     batching = None
     if mixed is not None:

@@ -391,6 +391,17 @@ ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, in
                       const uint64_t *keys, const ca_params *p, ca_result *res_host,
                       uint8_t *masks_host);
 
+/* End-to-end call on page-locked HOST buffers without copying the frames:
+ * the kernels read the strip rows they need straight from host memory (on
+ * Grace-Blackwell over NVLink-C2C) and write the masks straight into
+ * masks_host; only the B results are copied.  frames_host and masks_host
+ * (when not NULL) must be page-locked (cudaHostAlloc / cudaHostRegister);
+ * otherwise CA_ERR_INVALID_ARG.  Results and masks equal ca_run_host's.
+ * Synchronous. */
+ca_status ca_run_host_zero_copy(ca_handle *h, const uint8_t *frames_host, int B, int H, int W,
+                                const uint64_t *keys, const ca_params *p, ca_result *res_host,
+                                uint8_t *masks_host);
+
 /* Waits for `stream` and reports any asynchronous device error raised by the
  * handle's kernels: CA_ERR_CUDA, or CA_ERR_TIMEOUT when a bounded wait of the
  * fused kernel gave up (its results are then not valid; the handle re-arms

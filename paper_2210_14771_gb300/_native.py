@@ -114,6 +114,8 @@ SIGNATURES = [
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                               _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p]),
+    ("ca_run_host_zero_copy", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                        _P(C.c_uint64), _P(CaParams), C.c_void_p, C.c_void_p]),
     ("ca_sync", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ca_set_debug", C.c_int, [C.c_void_p, C.c_int]),
     ("ca_set_wait_limit", C.c_int, [C.c_void_p, C.c_uint64]),

@@ -206,6 +206,13 @@ class ContentArea:
                                         C.byref(p), C.c_void_p(res_ptr),
                                         C.c_void_p(masks_ptr) if masks_ptr else None))
 
+    def run_host_zero_copy_ptr(self, frames_ptr: int, B, H, W, keys_arr, p, res_ptr: int,
+                               masks_ptr):
+        """ca_run_host_zero_copy on page-locked host buffers of the caller."""
+        self._check(N.lib().ca_run_host_zero_copy(self._h, C.c_void_p(frames_ptr), B, H, W,
+                                                  keys_arr, C.byref(p), C.c_void_p(res_ptr),
+                                                  C.c_void_p(masks_ptr) if masks_ptr else None))
+
     def sync(self, stream=None):
         self._check(N.lib().ca_sync(self._h, _stream_ptr(stream, self.device)))
 

@@ -1439,6 +1439,43 @@ ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, in
     return CA_OK;
 }
 
+ca_status ca_run_host_zero_copy(ca_handle *h, const uint8_t *frames_host, int B, int H, int W,
+                                const uint64_t *keys, const ca_params *p, ca_result *res_host,
+                                uint8_t *masks_host) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return CA_OK;
+    if (!frames_host || !res_host) return fail(h, CA_ERR_INVALID_ARG, "NULL host buffer");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    // both buffers must be page-locked host memory the device can address
+    auto mapped = [&](const void *ptr, void **dev) -> bool {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+        *dev = a.devicePointer;
+        return true;
+    };
+    void *fd = nullptr, *md = nullptr;
+    if (!mapped(frames_host, &fd))
+        return fail(h, CA_ERR_INVALID_ARG, "frames_host is not page-locked host memory");
+    if (masks_host && !mapped(masks_host, &md))
+        return fail(h, CA_ERR_INVALID_ARG, "masks_host is not page-locked host memory");
+    ca_status st;
+    if (!h->e2e_stream) CA_CUDA(h, cudaStreamCreateWithFlags(&h->e2e_stream, cudaStreamNonBlocking));
+    if ((st = grow(h, &h->e2e_res, h->e2e_res_cap, (size_t)B, false)) != CA_OK) return st;
+    h->e2e_res_cap = std::max(h->e2e_res_cap, (size_t)B);
+    cudaStream_t s = h->e2e_stream;
+    st = ca_estimate_uniform(h, (const uint8_t *)fd, B, H, W, keys, p, h->e2e_res, (uint8_t *)md, s);
+    if (st != CA_OK) return st;
+    CA_CUDA(h, cudaMemcpyAsync(res_host, h->e2e_res, sizeof(ca_result) * B,
+                               cudaMemcpyDeviceToHost, s));
+    CA_CUDA(h, cudaStreamSynchronize(s));
+    return CA_OK;
+}
+
 ca_status ca_sync(ca_handle *h, void *stream) {
     if (!h) return CA_ERR_INVALID_ARG;
     CA_CUDA(h, cudaSetDevice(h->device));

@@ -347,6 +347,23 @@ __device__ __forceinline__ SegInfo seg_info(const ScSource &src, int g) {
     return si;
 }
 
+// L2 prefetch (TMA) of the strip rows a segment reads: the bytes of columns
+// [b0, b0 + rows) of rows y-1, y, y+1, shrunk to whole 16-byte blocks inside
+// each row (a hint: the loads of the segment read the same bytes).
+template <class G>
+__device__ __forceinline__ void prefetch_rows(const SegInfo &si) {
+    const int c0 = max(si.s0 - kScHalo, 0), c1 = min(si.s0 - kScHalo + G::kRows, si.W);
+    if (c1 <= c0) return;
+    for (int r = 0; r < 3; ++r) {
+        const uint8_t *row = si.r0 + r * si.pitch;
+        const uintptr_t a = ((uintptr_t)(row + 3 * c0) + 15) & ~(uintptr_t)15;
+        const uintptr_t b = (uintptr_t)(row + 3 * c1) & ~(uintptr_t)15;
+        if (b > a)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                         : "memory");
+    }
+}
+
 // Common prologue of the scorer kernels: zero guard rows of `n_planes`
 // planes from `sm`, init the barriers, allocate TMEM, start the weight copy.
 template <class G>
@@ -406,6 +423,8 @@ __global__ void __launch_bounds__(kInfThreads, 3)
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
         const SegInfo si = seg_info<SegI>(src, g);
         const int b0 = si.s0 - kScHalo;
+        if (tid == 0 && g + (int)gridDim.x < total_segs)   // this CTA's next segment
+            prefetch_rows<SegI>(seg_info<SegI>(src, g + gridDim.x));
         __syncthreads();   // the previous segment is done with A and X0
         build_features<SegI>(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
         fence_async_smem();
@@ -644,6 +663,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
         const SegInfo si = seg_info<SegT>(src, g);
         const int b0 = si.s0 - kScHalo;
+        if (tid == 0 && g + (int)gridDim.x < total_segs)   // this CTA's next segment
+            prefetch_rows<SegT>(seg_info<SegT>(src, g + gridDim.x));
         const uint8_t *lab = labels + (int64_t)si.strip * si.W;
         const bool first = g == (int)blockIdx.x;   // the CTA's first segment writes its partials
         __syncthreads();

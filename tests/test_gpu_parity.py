@@ -198,9 +198,23 @@ def test_mask_call_and_host_path_agree(ca, orc, hd_batch):
     for i in range(6):
         assert torch.equal(masks[i], m2[i])
     hres, hmasks = ca.run_host(frames[:6], lp, keys=keys[:6])
-    from paper_2210_14771_gb300 import api
+    from paper_2210_14771_gb300 import _native as N, api
     assert hres.view(np.uint8).tobytes() == api.results_numpy(res).view(np.uint8).tobytes()
     assert np.array_equal(hmasks, masks.cpu().numpy())
+    # zero-copy: kernels read the frames from and write the masks to
+    # page-locked host memory; same results and masks
+    import ctypes as C
+    hf = torch.from_numpy(np.ascontiguousarray(frames[:6])).pin_memory()
+    hm = torch.zeros((6, 1080, 1920), dtype=torch.uint8).pin_memory()
+    hr = torch.zeros((6, 6), dtype=torch.float32).pin_memory()
+    karr = (C.c_uint64 * 6)(*keys[:6])
+    ca.run_host_zero_copy_ptr(hf.data_ptr(), 6, 1080, 1920, karr, lp, hr.data_ptr(), hm.data_ptr())
+    assert hr.numpy().tobytes() == api.results_numpy(res).tobytes()
+    assert np.array_equal(hm.numpy(), masks.cpu().numpy())
+    pageable = np.ascontiguousarray(frames[:6])
+    with pytest.raises(N.CaError):
+        ca.run_host_zero_copy_ptr(pageable.ctypes.data, 6, 1080, 1920, karr, lp, hr.data_ptr(),
+                                  None)
 
 
 def test_full_rectangle_and_empty_inputs(ca, orc):
