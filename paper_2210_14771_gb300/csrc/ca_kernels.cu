@@ -28,10 +28,11 @@ __device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
     return v;
 }
 
+// 16-byte streaming store.  No memory clobber: nothing in the issuing kernel
+// reads the stored bytes, so the compiler may schedule around it freely.
 __device__ __forceinline__ void st_cs_v4(void *p, uint4 v) {
     asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
-                 "r"(v.z), "r"(v.w)
-                 : "memory");
+                 "r"(v.z), "r"(v.w));
 }
 
 // Integer BT.601 luma on the 0-255 scale.
@@ -1038,8 +1039,6 @@ __device__ __forceinline__ uint32_t exact_word(int x0, float cx, float dy2, floa
 // 16-byte vectors per lane.
 __device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &res, int u) {
     const int lane = threadIdx.x & 31;
-    const uint4 ones = make_uint4(0x01010101u, 0x01010101u, 0x01010101u, 0x01010101u);
-    const uint4 zeros = make_uint4(0u, 0u, 0u, 0u);
     const int W = fr.W, H = fr.H;
     const int y0 = u * kMaskRowsPerUnit;
     const int nrows = min(kMaskRowsPerUnit, H - y0);
@@ -1053,23 +1052,29 @@ __device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &r
         uint8_t *row = fr.mask + (int64_t)y * W;
         const float dy = __fsub_rn(__int2float_rn(y), res.cy);
         const float dy2 = __fmul_rn(dy, dy);
-        if (fr.mask_vec_ok) {
+        if (fr.mask_vec_ok && ex) {
+            // vectors wholly inside [a, b] are ones, wholly outside zeros; the
+            // (at most two) that hold an end are built byte by byte
+            const int VW = W >> 4;
+            const int fa = (a + 15) >> 4, fb = ((b + 1) >> 4) - 1;   // whole vectors inside
+            const int ea = a >> 4, eb = b >> 4;                      // vectors holding an end
+            for (int v = lane; v < VW; v += 32) {
+                const int x0 = v << 4;
+                const uint32_t w = (v >= fa && v <= fb) ? 0x01010101u : 0u;
+                uint4 val = make_uint4(w, w, w, w);
+                if ((v == ea || v == eb) && a <= b && !(v >= fa && v <= fb))
+                    val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
+                                     span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
+                st_cs_v4(row + x0, val);
+            }
+        } else if (fr.mask_vec_ok) {
             const int VW = W >> 4;
             for (int v = lane; v < VW; v += 32) {
                 const int x0 = v << 4;
-                uint4 val;
-                if (ex) {
-                    if (x0 >= a && x0 + 15 <= b) val = ones;
-                    else if (x0 > b || x0 + 15 < a) val = zeros;
-                    else val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
-                                          span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
-                } else {
-                    val = make_uint4(exact_word(x0, res.cx, dy2, rr),
-                                     exact_word(x0 + 4, res.cx, dy2, rr),
-                                     exact_word(x0 + 8, res.cx, dy2, rr),
-                                     exact_word(x0 + 12, res.cx, dy2, rr));
-                }
-                st_cs_v4(row + x0, val);
+                st_cs_v4(row + x0, make_uint4(exact_word(x0, res.cx, dy2, rr),
+                                              exact_word(x0 + 4, res.cx, dy2, rr),
+                                              exact_word(x0 + 8, res.cx, dy2, rr),
+                                              exact_word(x0 + 12, res.cx, dy2, rr)));
             }
         } else {
             for (int x = lane; x < W; x += 32) {
