@@ -252,12 +252,24 @@ ca_status ca_plan_destroy(ca_plan *plan);
 #define CA_SCORER_NPARAM 17601
 
 /* Training hyper-parameters: SGD with momentum on the weighted binary
- * cross-entropy of the columns, mean over the columns of the step. */
+ * cross-entropy of the columns, mean over the columns of the step:
+ *     f = min(1, clip_norm / |g|)   (f = 1 when clip_norm is 0)
+ *     v = momentum v + f g,   w = w - lr_t v
+ * with g the mean gradient of the step and |g| its Euclidean norm over all
+ * CA_SCORER_NPARAM parameters.  lr_t = lr, except in ca_scorer_train with
+ * lr_schedule CA_LR_COSINE: over the T steps of the call, a linear warm-up
+ * lr (t + 1) / U for the first U = clamp(T / 20, 1, 200) steps, then
+ * lr (1 + cos(pi (t - U) / (T - U))) / 2.  Invalid values (non-finite,
+ * momentum outside [0, 1), pos_weight <= 0, clip_norm < 0, unknown schedule)
+ * return CA_ERR_INVALID_ARG. */
+enum { CA_LR_CONSTANT = 0, CA_LR_COSINE = 1 };
 typedef struct ca_train_params {
-    float lr;          /* step size */
-    float momentum;    /* momentum of the SGD update */
-    float pos_weight;  /* loss weight of edge columns (label 1); others weigh 1 */
-    int32_t apply;     /* 0: compute the gradient only (no update) */
+    float lr;            /* step size (peak step size with CA_LR_COSINE) */
+    float momentum;      /* momentum of the SGD update */
+    float pos_weight;    /* loss weight of edge columns (label 1); others weigh 1 */
+    int32_t apply;       /* 0: compute the gradient only (no update) */
+    float clip_norm;     /* > 0: clip the gradient norm of a step to this value */
+    int32_t lr_schedule; /* CA_LR_CONSTANT or CA_LR_COSINE (ca_scorer_train only) */
 } ca_train_params;
 
 /* Random initial parameters (He-normal convolution weights, zero biases,

@@ -15,6 +15,7 @@ CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
 CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
 CA_DUMP_LEARNED = 4
 CA_SCORER_NPARAM = 17601
+CA_LR_CONSTANT, CA_LR_COSINE = 0, 1
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
 
 
@@ -44,7 +45,7 @@ class CaTuning(C.Structure):
 
 class CaTrainParams(C.Structure):
     _fields_ = [("lr", C.c_float), ("momentum", C.c_float), ("pos_weight", C.c_float),
-                ("apply", C.c_int32)]
+                ("apply", C.c_int32), ("clip_norm", C.c_float), ("lr_schedule", C.c_int32)]
 
 
 class CaResult(C.Structure):

@@ -268,13 +268,14 @@ class ContentArea:
         return logits, scores
 
     def scorer_step(self, strips, ys, labels, H: int, idx=None, lr=0.0, momentum=0.9,
-                    pos_weight=1.0, apply=False, want_grads=True):
+                    pos_weight=1.0, apply=False, want_grads=True, clip_norm=0.0):
         """One training step; returns (summed loss, summed gradient or None)."""
         n, W = self._strip_args(strips, ys)
         if idx is not None:
             assert idx.dtype == torch.int32 and idx.is_cuda
             n = int(idx.numel())
-        tp = N.CaTrainParams(lr, momentum, pos_weight, 1 if apply else 0)
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1 if apply else 0, clip_norm,
+                             N.CA_LR_CONSTANT)
         loss = C.c_float(0.0)
         g = np.zeros(N.CA_SCORER_NPARAM, np.float32) if want_grads else None
         self._check(N.lib().ca_scorer_step(
@@ -285,11 +286,13 @@ class ContentArea:
         return float(loss.value), g
 
     def scorer_train(self, strips, ys, labels, H: int, epochs=1, batch=64, seed=0, lr=0.05,
-                     momentum=0.9, pos_weight=20.0):
-        """ca_scorer_train; returns the mean loss per column of each epoch."""
+                     momentum=0.9, pos_weight=20.0, clip_norm=1.0, schedule="cosine"):
+        """ca_scorer_train; returns the mean loss per column of each epoch.
+        schedule: "cosine" (warm-up, then cosine decay of lr) or "constant"."""
         n, W = self._strip_args(strips, ys)
         assert labels.dtype == torch.uint8 and labels.shape == (n, W)
-        tp = N.CaTrainParams(lr, momentum, pos_weight, 1)
+        sched = {"constant": N.CA_LR_CONSTANT, "cosine": N.CA_LR_COSINE}[schedule]
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1, clip_norm, sched)
         out = np.zeros(max(epochs, 1), np.float32)
         self._check(N.lib().ca_scorer_train(
             self._h, C.c_void_p(strips.data_ptr()), C.c_void_p(ys.data_ptr()),

@@ -94,7 +94,7 @@ struct ca_handle {
     struct {
         bool ready = false;
         float *params = nullptr, *mom = nullptr, *partial = nullptr, *grads = nullptr,
-              *losses = nullptr;
+              *losses = nullptr, *norm = nullptr;
         unsigned char *block = nullptr;
         uint32_t *err = nullptr;
         int32_t *idx = nullptr;
@@ -846,6 +846,7 @@ ca_status ca_destroy(ca_handle *h) {
     cudaFree(h->sc.mom);
     cudaFree(h->sc.partial);
     cudaFree(h->sc.grads);
+    cudaFree(h->sc.norm);
     cudaFree(h->sc.losses);
     cudaFree(h->sc.block);
     cudaFree(h->sc.err);
@@ -902,6 +903,7 @@ ca_status sc_alloc(ca_handle *h) {
     CA_CUDA(h, cudaMalloc(&S.params, sizeof(float) * kScNParam));
     CA_CUDA(h, cudaMalloc(&S.mom, sizeof(float) * kScNParam));
     CA_CUDA(h, cudaMalloc(&S.grads, sizeof(float) * kScNParam));
+    CA_CUDA(h, cudaMalloc(&S.norm, sizeof(float) * kScSgdBlocks));
     CA_CUDA(h, cudaMalloc(&S.partial, sizeof(float) * kScPartialStride * (size_t)S.partial_n));
     CA_CUDA(h, cudaMalloc(&S.block, kScBlockBytes));
     CA_CUDA(h, cudaMalloc(&S.err, sizeof(uint32_t)));
@@ -959,6 +961,27 @@ ca_status check_strips(ca_handle *h, const uint8_t *strips, const int32_t *ys, i
 
 int sc_segs_of(int n, int W, int out) { return n * ((W + out - 1) / out); }
 
+ca_status check_train_params(ca_handle *h, const ca_train_params &tp) {
+    if (!std::isfinite(tp.lr) || !std::isfinite(tp.momentum) || !std::isfinite(tp.pos_weight) ||
+        !std::isfinite(tp.clip_norm) || tp.momentum < 0.0f || tp.momentum >= 1.0f ||
+        tp.pos_weight <= 0.0f || tp.clip_norm < 0.0f ||
+        (tp.lr_schedule != CA_LR_CONSTANT && tp.lr_schedule != CA_LR_COSINE))
+        return fail(h, CA_ERR_INVALID_ARG,
+                    "bad training parameters (lr %g, momentum %g, pos_weight %g, clip %g, "
+                    "schedule %d)", tp.lr, tp.momentum, tp.pos_weight, tp.clip_norm, tp.lr_schedule);
+    return CA_OK;
+}
+
+// Step size of step t of T under the call's schedule: constant, or a linear
+// warm-up over U = clamp(T / 20, 1, 200) steps followed by a half cosine to 0.
+float scheduled_lr(const ca_train_params &tp, long long t, long long T) {
+    if (tp.lr_schedule != CA_LR_COSINE) return tp.lr;
+    const long long U = std::max(1LL, std::min(T / 20, 200LL));
+    if (t < U) return (float)((double)tp.lr * (double)(t + 1) / (double)U);
+    const double x = (double)(t - U) / (double)std::max(1LL, T - U);
+    return (float)((double)tp.lr * 0.5 * (1.0 + std::cos(3.141592653589793 * x)));
+}
+
 // Forward + loss + gradient partials of n strips, then the reduction (and the
 // update when tp->apply).  Queued on `s`.
 ca_status sc_step_async(ca_handle *h, const uint8_t *strips, const int32_t *ys,
@@ -980,9 +1003,9 @@ ca_status sc_step_async(ca_handle *h, const uint8_t *strips, const int32_t *ys,
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_train launch");
     const float scale = 1.0f / (float)((double)n * W);
     e = sc_launch_sgd(S.params, S.mom, S.partial, grid, scale, tp.lr, tp.momentum, tp.apply,
-                      grads_dev, loss_dev, s);
+                      tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_sgd launch");
-    h->launches += 2;
+    h->launches += (tp.apply && tp.clip_norm > 0.0f) ? 3 : 2;
     if (tp.apply) {
         e = sc_launch_pack(S.params, S.block, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_pack launch");
@@ -1092,6 +1115,7 @@ ca_status ca_scorer_step(ca_handle *h, const uint8_t *strips_dev, const int32_t 
     if (!h || !tp) return CA_ERR_INVALID_ARG;
     ca_status st = check_strips(h, strips_dev, ys_dev, n, W, H);
     if (st != CA_OK) return st;
+    if ((st = check_train_params(h, *tp)) != CA_OK) return st;
     if (!labels_dev || n == 0) return fail(h, CA_ERR_INVALID_ARG, "no labels or no strips");
     CA_CUDA(h, cudaSetDevice(h->device));
     if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
@@ -1116,6 +1140,7 @@ ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t
     if (!h || !tp) return CA_ERR_INVALID_ARG;
     ca_status st = check_strips(h, strips_dev, ys_dev, n, W, H);
     if (st != CA_OK) return st;
+    if ((st = check_train_params(h, *tp)) != CA_OK) return st;
     if (!labels_dev || n == 0 || epochs < 0 || batch < 1)
         return fail(h, CA_ERR_INVALID_ARG, "bad training arguments");
     CA_CUDA(h, cudaSetDevice(h->device));
@@ -1139,8 +1164,10 @@ ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t
         CA_CUDA(h, cudaMemcpy(h->sc.idx, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
         for (int k = 0; k < steps; ++k) {
             const int cnt = std::min(batch, n - k * batch);
+            ca_train_params tk = *tp;
+            tk.lr = scheduled_lr(*tp, (long long)ep * steps + k, (long long)epochs * steps);
             if ((st = sc_step_async(h, strips_dev, ys_dev, labels_dev, h->sc.idx + (size_t)k * batch,
-                                    cnt, W, H, *tp, h->sc.losses + k, nullptr, s)) != CA_OK)
+                                    cnt, W, H, tk, h->sc.losses + k, nullptr, s)) != CA_OK)
                 return st;
         }
         CA_CUDA(h, cudaMemcpy(losses.data(), h->sc.losses, sizeof(float) * steps, cudaMemcpyDeviceToHost));

@@ -146,6 +146,7 @@ constexpr int kScOffW1f = 0, kScOffW2f = 7168, kScOffW3f = 21504, kScOffW2b = 35
               kScOffW3b = 50176, kScOffVec = 64512;
 constexpr int kScFwdBytes = 35840, kScVecBytes = 528, kScBlockBytes = 65040;
 constexpr int kScPartialStride = 17664;          // per-CTA gradient partials (+ loss at kScNParam)
+constexpr int kScSgdBlocks = 276;                // reduction blocks of 64 parameters (+ loss slot)
 
 // Rows of the strips a scorer launch reads: either frames (rows from the
 // strip-row table) or stand-alone strips (3 rows x W x 3 bytes each).
@@ -172,9 +173,11 @@ size_t sc_train_smem();
 cudaError_t sc_launch_train(const ScSource &src, const uint8_t *labels, float pos_weight,
                             const unsigned char *block, float *partial, int total_segs,
                             uint32_t *err, int grid, cudaStream_t s);
+// One SGD step from the partials (two launches when clip > 0 and apply;
+// gbuf: kScNParam floats, norm_part: kScSgdBlocks floats of scratch).
 cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
-                          float lr, float momentum, int apply, float *grads_out, float *loss_out,
-                          cudaStream_t s);
+                          float lr, float momentum, int apply, float clip, float *gbuf,
+                          float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
 cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,

@@ -917,8 +917,12 @@ cudaError_t sc_launch_pack(const float *params, unsigned char *block, cudaStream
 // an SGD step with momentum:  v = momentum v + scale g,  w = w - lr v.
 // Weight blocks of the partials are laid out [t][co][ci]; the parameters are
 // [co][ci][t].  A block reduces 64 parameters with 4 threads each (partials
-// c = q, q + 4, ...), combined in order.
+// c = q, q + 4, ...), combined in order.  With norm_part set (gradient
+// clipping) it takes no step: it stores the summed gradient in gbuf and the
+// block's sum of squares of the mean gradient in norm_part[block], and
+// k_sc_clip_step takes the step once the whole norm is known.
 constexpr int kSgdParams = 64;
+static_assert(kScSgdBlocks == (kScNParam + 1 + kSgdParams - 1) / kSgdParams, "sgd grid");
 
 __device__ __forceinline__ int partial_index(int p) {
     auto tr = [](int q, int off, int cin) {
@@ -934,7 +938,8 @@ __device__ __forceinline__ int partial_index(int p) {
 __global__ void __launch_bounds__(256)
     k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ part,
              int n_part, float scale, float lr, float momentum, int apply,
-             float *__restrict__ grads_out, float *__restrict__ loss_out) {
+             float *__restrict__ grads_out, float *__restrict__ loss_out,
+             float *__restrict__ gbuf, float *__restrict__ norm_part) {
     __shared__ float red[4][kSgdParams];
     const int pl = threadIdx.x % kSgdParams, q = threadIdx.x / kSgdParams;
     const int p = blockIdx.x * kSgdParams + pl;
@@ -945,25 +950,77 @@ __global__ void __launch_bounds__(256)
     }
     red[q][pl] = g;
     __syncthreads();
-    if (q != 0 || p > kScNParam) return;
     g = __fadd_rn(__fadd_rn(__fadd_rn(red[0][pl], red[1][pl]), red[2][pl]), red[3][pl]);
+    if (norm_part) {   // clipping: squares of the mean gradient, summed in order by thread 0
+        __syncthreads();
+        if (q == 0) {
+            const float m = __fmul_rn(scale, g);
+            red[1][pl] = p < kScNParam ? __fmul_rn(m, m) : 0.0f;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int i = 0; i < kSgdParams; ++i) t = __fadd_rn(t, red[1][i]);
+            norm_part[blockIdx.x] = t;
+        }
+    }
+    if (q != 0 || p > kScNParam) return;
     if (p == kScNParam) {   // loss slot
         if (loss_out) *loss_out = g;
         return;
     }
     if (grads_out) grads_out[p] = g;
-    if (apply) {
+    if (norm_part) {
+        gbuf[p] = g;
+    } else if (apply) {
         const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), __fmul_rn(scale, g));
         mom[p] = v;
         prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
     }
 }
 
+// The clipped step: every block sums the kScSgdBlocks partial squares in the
+// same order (strided per thread, then a fixed tree, so all blocks agree on
+// the norm), f = min(1, clip / |scale g|), then
+// v = momentum v + f (scale g),  w = w - lr v.
+__global__ void __launch_bounds__(kSgdParams)
+    k_sc_clip_step(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ gbuf,
+                   const float *__restrict__ norm_part, float scale, float lr, float momentum,
+                   float clip) {
+    __shared__ float red[kSgdParams];
+    __shared__ float f_s;
+    float t = 0.0f;
+    for (int i = threadIdx.x; i < kScSgdBlocks; i += kSgdParams)
+        t = __fadd_rn(t, __ldcg(norm_part + i));
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = kSgdParams / 2; w > 0; w >>= 1) {   // fixed tree: every block sums alike
+        if (threadIdx.x < w) red[threadIdx.x] = __fadd_rn(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float n = sqrtf(red[0]);
+        f_s = n > clip ? __fdiv_rn(clip, n) : 1.0f;
+    }
+    __syncthreads();
+    const int p = blockIdx.x * kSgdParams + threadIdx.x;
+    if (p >= kScNParam) return;
+    const float m = __fmul_rn(f_s, __fmul_rn(scale, gbuf[p]));
+    const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), m);
+    mom[p] = v;
+    prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+}
+
 cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
-                          float lr, float momentum, int apply, float *grads_out, float *loss_out,
-                          cudaStream_t s) {
-    k_sc_sgd<<<(kScNParam + 1 + kSgdParams - 1) / kSgdParams, 256, 0, s>>>(
-        params, mom, partial, n_partials, scale, lr, momentum, apply, grads_out, loss_out);
+                          float lr, float momentum, int apply, float clip, float *gbuf,
+                          float *norm_part, float *grads_out, float *loss_out, cudaStream_t s) {
+    const bool clipped = apply && clip > 0.0f;
+    k_sc_sgd<<<kScSgdBlocks, 256, 0, s>>>(params, mom, partial, n_partials, scale, lr, momentum,
+                                          apply, grads_out, loss_out, clipped ? gbuf : nullptr,
+                                          clipped ? norm_part : nullptr);
+    if (clipped)
+        k_sc_clip_step<<<kScSgdBlocks, kSgdParams, 0, s>>>(params, mom, gbuf, norm_part, scale, lr,
+                                                           momentum, clip);
     return cudaGetLastError();
 }
 

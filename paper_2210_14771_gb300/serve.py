@@ -136,7 +136,19 @@ def run_load(server: Server, streams, banks, n_frames: int, realtime: bool = Tru
 
 
 def summarise(records, wall):
+    """Throughput and latency (arrival to result) of a run, with the latency
+    split into its parts: arrival to submission (the feeding loop),
+    submission to launch (queued for a batch slot) and launch to result (GPU
+    work and collection)."""
     lat = np.array([r["latency"] for r in records]) * 1e3
-    return {"frames": len(records), "seconds": wall, "frames_per_s": len(records) / wall,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "max_ms": float(lat.max())}
+    part = {
+        "feed": np.array([r["t_submit"] - r["t_arrival"] for r in records]) * 1e3,
+        "queue": np.array([r["t_launch"] - r["t_submit"] for r in records]) * 1e3,
+        "gpu": np.array([r["t_done"] - r["t_launch"] for r in records]) * 1e3,
+    }
+    out = {"frames": len(records), "seconds": wall, "frames_per_s": len(records) / wall,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "max_ms": float(lat.max()), "over_10ms": int((lat > 10.0).sum())}
+    for k, v in part.items():
+        out["p99_%s_ms" % k] = float(np.percentile(v, 99))
+    return out

@@ -112,15 +112,59 @@ def test_training_is_deterministic_and_lowers_the_loss(ca):
     W, H = 1920, 1080
     s, ys, lab = _strips(5, 512, W, H)
     ds, dy, dl = _to_dev(s, ys, lab)
-    runs = []
-    for _ in range(2):
-        ca.scorer_init(7)
-        losses = ca.scorer_train(ds, dy, dl, H, epochs=4, batch=64, seed=1, lr=0.05,
-                                 momentum=0.9, pos_weight=20.0)
-        runs.append((losses, ca.scorer_get_params()))
-    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][0], runs[1][0])
-    losses = runs[0][0]
-    assert losses[-1] < 0.7 * losses[0], losses
+    for sched, clip, bound in (("constant", 0.0, 0.7), ("cosine", 0.2, 0.9)):
+        runs = []
+        for _ in range(2):
+            ca.scorer_init(7)
+            losses = ca.scorer_train(ds, dy, dl, H, epochs=4, batch=64, seed=1, lr=0.05,
+                                     momentum=0.9, pos_weight=20.0, clip_norm=clip,
+                                     schedule=sched)
+            runs.append((losses, ca.scorer_get_params()))
+        assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][0], runs[1][0])
+        losses = runs[0][0]
+        assert losses[-1] < bound * losses[0], (sched, losses)
+
+
+def test_sgd_step_and_gradient_clipping(ca):
+    """One update from fresh momentum is w - lr f g_mean, f = min(1, c / |g_mean|):
+    a clip above the norm leaves the unclipped step bit for bit; a clip at
+    half the norm halves it (to binary32 rounding of the norm)."""
+    W, H = 640, 480
+    s, ys, lab = _strips(11, 16, W, H)
+    ds, dy, dl = _to_dev(s, ys, lab)
+    p0 = _params(12)
+    ca.scorer_set_params(p0)
+    _, g = ca.scorer_step(ds, dy, dl, H, pos_weight=4.0, apply=False)
+    gm = g.astype(np.float64) / (16 * W)
+    norm = float(np.linalg.norm(gm))
+    lr = float(np.float32(1e-2 / np.abs(gm).max()))   # largest step 0.01
+    out = {}
+    for c in (0.0, 4.0 * norm, 0.5 * norm):
+        ca.scorer_set_params(p0)          # also zeroes the momentum
+        ca.scorer_step(ds, dy, dl, H, lr=lr, momentum=0.9, pos_weight=4.0, apply=True,
+                       want_grads=False, clip_norm=c)
+        out[c] = ca.scorer_get_params()
+    assert np.array_equal(out[0.0], out[4.0 * norm])
+    ulp = 2.0 * float(np.spacing(np.float32(np.abs(p0).max())))   # rounding of w - lr v
+    step_full = p0.astype(np.float64) - out[0.0]
+    assert np.allclose(step_full, lr * gm, rtol=1e-5, atol=ulp)
+    step_half = p0.astype(np.float64) - out[0.5 * norm]
+    assert np.allclose(step_half, 0.5 * lr * gm, rtol=1e-4, atol=ulp)
+
+
+def test_training_argument_errors(ca):
+    from paper_2210_14771_gb300 import _native as N
+    W, H = 64, 48
+    s, ys, lab = _strips(13, 4, W, H)
+    ds, dy, dl = _to_dev(s, ys, lab)
+    ca.scorer_set_params(_params(14))
+    for kw in (dict(momentum=1.0), dict(clip_norm=-1.0), dict(pos_weight=0.0),
+               dict(lr=float("nan"))):
+        with pytest.raises(N.CaError) as e:
+            ca.scorer_step(ds, dy, dl, H, apply=True, **kw)
+        assert e.value.status == 1, kw
+    with pytest.raises(KeyError):
+        ca.scorer_train(ds, dy, dl, H, schedule="linear")
 
 
 def test_save_load_roundtrip(ca):

@@ -45,6 +45,38 @@ def test_struct_layouts(native):
     assert C.sizeof(native.CaFrame) == 40
     assert C.sizeof(native.CaParams) == 104
     assert C.sizeof(native.CaTuning) == 32
+    assert C.sizeof(native.CaTrainParams) == 24
+
+
+STRUCTS = (("ca_params", "CaParams"), ("ca_frame", "CaFrame"), ("ca_result", "CaResult"),
+           ("ca_tuning", "CaTuning"), ("ca_train_params", "CaTrainParams"),
+           ("ca_server_config", "CaServerConfig"), ("ca_server_result", "CaServerResult"))
+
+
+def test_binding_structs_match_the_header(native, tmp_path):
+    """Size and every field offset of the ctypes structures equal what a C
+    compiler makes of include/ca.h (gcc, C11)."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ca.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS:
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in getattr(native, pyname)._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, pyname in STRUCTS:
+        cls = getattr(native, pyname)
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
 
 
 def test_defaults_are_appendix_a(native, orc):
@@ -99,3 +131,29 @@ def test_create_without_device_fails_cleanly(native):
     h = C.c_void_p()
     assert native.lib().ca_create(C.byref(h), 0) != 0
     assert not h.value
+
+
+def test_null_handles_and_buffers_are_rejected(native):
+    """Every entry point that takes a handle, plan, server, pool or buffer
+    answers CA_ERR_INVALID_ARG for NULL / zero arguments, queues nothing and
+    does not crash (no device needed: the checks run before any CUDA call)."""
+    L = native.lib()
+    no_args = {"ca_params_default", "ca_create", "ca_server_now", "ca_pool_create",
+               "ca_status_string", "ca_last_error", "ca_launch_count"}
+    tried = 0
+    for name, _, args in native.SIGNATURES:
+        if name in no_args:
+            continue
+        vals = []
+        for a in args:
+            if a in (C.c_int, C.c_int32, C.c_uint64, C.c_size_t):
+                vals.append(0)
+            elif a is C.c_double:
+                vals.append(0.0)
+            else:
+                vals.append(None)
+        assert getattr(L, name)(*vals) == 1, name
+        tried += 1
+    assert tried >= 30
+    assert L.ca_launch_count(None) == 0
+    assert L.ca_last_error(None) is not None
