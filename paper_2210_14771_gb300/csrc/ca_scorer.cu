@@ -224,11 +224,13 @@ __device__ __forceinline__ float luma_f(uint32_t r, uint32_t g, uint32_t b) {
 }
 
 // Column features of a segment: rows r in [0, 512) <-> columns b0 + r; two
-// planes (14 features + 2 zero channels), zero outside [0, W).
+// planes (14 features + 2 zero channels), zero outside [0, W).  Pixel x of
+// row k is read at row_k + 3 x - bias (bias 0 for the strip rows themselves,
+// the staged block's start for a copy in shared memory).
 template <class G>
 __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t *row0,
                                                const uint8_t *row1, const uint8_t *row2, int W,
-                                               int y, int H, int b0) {
+                                               int y, int H, int b0, int bias = 0) {
     const float yf = __fdiv_rn(__fsub_rn((float)y, __fmul_rn(0.5f, (float)(H - 1))), (float)H);
     const float xc = __fmul_rn(0.5f, (float)(W - 1));
     const float Wf = (float)W;
@@ -237,7 +239,8 @@ __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t 
         uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
         if (x >= 0 && x < W) {
             float f[16];
-            const uint8_t *p[3] = {row0 + 3 * x, row1 + 3 * x, row2 + 3 * x};
+            const int o = 3 * x - bias;
+            const uint8_t *p[3] = {row0 + o, row1 + o, row2 + o};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const uint32_t R = p[k][0], G = p[k][1], B = p[k][2];
@@ -364,6 +367,42 @@ __device__ __forceinline__ void prefetch_rows(const SegInfo &si) {
     }
 }
 
+// Staging of a segment's strip bytes in shared memory by cp.async (16-byte
+// asynchronous copies), issued one segment ahead.  Possible when the copies
+// stay inside each row: rows start on 16-byte boundaries and 3 W is a
+// multiple of 16 (then the 16-byte blocks around columns [c0, c1) lie in
+// [row, row + 3 W)).  Row k of the segment lands at stage + k kStageRow.
+constexpr int kStageRow = 1200;   // >= 3 x 384 columns + 30 bytes of alignment, 16 x 75
+
+__device__ __forceinline__ bool stageable(const SegInfo &si) {
+    return (((uintptr_t)si.r0 | (uintptr_t)si.pitch | (uintptr_t)(3 * si.W)) & 15) == 0;
+}
+
+// First byte (a multiple of 16, relative to the row) of the staged block.
+template <class G>
+__device__ __forceinline__ int stage_bias(const SegInfo &si) {
+    return (3 * max(si.s0 - kScHalo, 0)) & ~15;
+}
+
+template <class G>
+__device__ __forceinline__ void stage_rows(unsigned char *stage, const SegInfo &si) {
+    static_assert(3 * G::kRows + 30 <= kStageRow, "a staged row fits its slot");
+    const int c0 = max(si.s0 - kScHalo, 0), c1 = min(si.s0 - kScHalo + G::kRows, si.W);
+    const int a = stage_bias<G>(si), b = (3 * c1 + 15) & ~15;
+    const int nb = c1 > c0 ? (b - a) >> 4 : 0;   // 16-byte blocks per row
+    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) {
+        const int k = i / nb, j = i - k * nb;
+        const uint8_t *src = si.r0 + k * si.pitch + a + 16 * j;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         smem_u32(stage + k * kStageRow + 16 * j)),
+                     "l"(src)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Common prologue of the scorer kernels: zero guard rows of `n_planes`
 // planes from `sm`, init the barriers, allocate TMEM, start the weight copy.
 template <class G>
@@ -419,6 +458,12 @@ __global__ void __launch_bounds__(kInfThreads, 3)
                                       kScFwdBytes, vec, wblock + kScOffVec);
     bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
     uint32_t phase = 0;
+    // Staged strip bytes of the next segment: in the interior rows of the
+    // first a1/a2 plane, free from the end of the last convolution of a
+    // segment until the first epilogue of the next one.
+    static_assert(3 * kStageRow <= SegI::kRows * 16, "staging fits the interior rows of a plane");
+    unsigned char *stage = A + kGuard * 16;
+    bool staged = false;   // this segment's bytes are in `stage`
 
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
         const SegInfo si = seg_info<SegI>(src, g);
@@ -426,7 +471,16 @@ __global__ void __launch_bounds__(kInfThreads, 3)
         if (tid == 0 && g + (int)gridDim.x < total_segs)   // this CTA's next segment
             prefetch_rows<SegI>(seg_info<SegI>(src, g + gridDim.x));
         __syncthreads();   // the previous segment is done with A and X0
-        build_features<SegI>(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y, si.H, b0);
+        if (staged) {
+            stage_wait();
+            __syncthreads();
+            build_features<SegI>(X0, stage, stage + kStageRow, stage + 2 * kStageRow, si.W, si.y,
+                                 si.H, b0, stage_bias<SegI>(si));
+        } else {
+            build_features<SegI>(X0, si.r0, si.r0 + si.pitch, si.r0 + 2 * si.pitch, si.W, si.y,
+                                 si.H, b0);
+        }
+        staged = false;
         fence_async_smem();
         tc_before_sync();
         __syncthreads();
@@ -442,6 +496,13 @@ __global__ void __launch_bounds__(kInfThreads, 3)
             phase ^= 1u;
             tc_after_sync();
             if (__syncthreads_or(!ok)) { abort = true; break; }
+            if (l == 2 && g + (int)gridDim.x < total_segs) {   // the MMAs are done with A
+                const SegInfo sn = seg_info<SegI>(src, g + gridDim.x);
+                if (stageable(sn)) {
+                    stage_rows<SegI>(stage, sn);
+                    staged = true;
+                }
+            }
             for (int j = warp >> 2; j < SegI::kTiles; j += 2) {   // warp w: tiles w/4, w/4 + 2
                 float v[32];
                 acc_row(tmem, j, v);
@@ -483,6 +544,7 @@ __global__ void __launch_bounds__(kInfThreads, 3)
             tc_after_sync();
         }
     }
+    stage_wait();   // no copy outlives the CTA
     __syncthreads();
     if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
         mma_commit(bar_m);
