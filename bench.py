@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-small", action="store_true")
     ap.add_argument("--skip-batching", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
@@ -224,7 +225,68 @@ def plain_leg(ca, p, frames_dev, keys, masks_dev, stream, reps):
             "p99_ms_per_frame": float(np.percentile(lat, 99)), "launches_per_frame": 3}
 
 
-def batching_leg(ca, mixed, p_ref, stream, steps, warmup):
+SMALL = dict(seed=0, B=8, H=480, W=640, mix="centred", n_strips=16, cands_per_strip=4, n_hyps=256)
+
+
+def small_leg(ca, stream, steps, cpu_seconds):
+    """The plain method's small case: 8 frames of 640x480 (N=16, K=4, 256
+    hypotheses), one frame per call (three launches per frame) against all
+    eight in one graph launch; the results of both are compared bit for bit
+    (equal Hausdorff error by construction), and the oracle is timed on the
+    same frames when cpu_seconds > 0."""
+    import numpy as np
+    import torch
+    from paper_2210_14771_gb300 import api, synth
+    frames, _, keys = synth.batch(SMALL["seed"], SMALL["B"], SMALL["H"], SMALL["W"], SMALL["mix"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = api.params(n_strips=SMALL["n_strips"], cands_per_strip=SMALL["cands_per_strip"],
+                   n_hyps=SMALL["n_hyps"])
+    ts = [torch.from_numpy(f).to(dev) for f in frames]
+    ms = [torch.empty(f.shape[:2], dtype=torch.uint8, device=dev) for f in frames]
+    B = len(ts)
+    plain = plain_leg(ca, p, ts, keys, ms, stream, max(3, steps))
+    plain_res = []
+    q = api.params(**{k: getattr(p, k) for k, _ in p._fields_})
+    q.batch_mode = 1
+    for b in range(B):
+        r, _ = ca.estimate([ts[b]], q, keys=[keys[b]], masks=[ms[b]])
+        plain_res.append(api.results_numpy(r)[0].tobytes())
+    plain_masks = [m.clone() for m in ms]
+    ca.tune(ts, p, keys=keys, masks=ms)
+    res = api.new_results(B, dev)
+    plan = ca.plan(ts, p, keys=keys, masks=ms, results=res)
+    for _ in range(3):
+        plan.launch()
+    total, per = timed_loop(stream, steps, lambda k: plan.launch())
+    ca.sync()
+    plan.close()
+    rb = api.results_numpy(res)
+    same = all(rb[b].tobytes() == plain_res[b] for b in range(B)) and \
+        all(torch.equal(a, c) for a, c in zip(ms, plain_masks))
+    byts = B * (9 * SMALL["n_strips"] * SMALL["W"] + SMALL["H"] * SMALL["W"] + 24)
+    out = {"workload": "640x480_x8_centred", "frames": B, "plain": plain,
+           "batched": {"frames_per_s": B * steps / (total / 1e3), "ms_per_call": total / steps,
+                       "p50_ms": float(np.percentile(per, 50)),
+                       "p99_ms": float(np.percentile(per, 99)),
+                       "algorithmic_bytes": byts,
+                       "hbm_frac_of_measured": byts / (total / steps / 1e3) / 1e9 / peaks()[0]},
+           "results_equal": bool(same)}
+    if cpu_seconds > 0:
+        import oracle
+        op = oracle.params(n_strips=SMALL["n_strips"], cands_per_strip=SMALL["cands_per_strip"],
+                           n_hyps=SMALL["n_hyps"])
+        t0 = time.perf_counter()
+        n = 0
+        while n < 4 * B and (n < B or time.perf_counter() - t0 < cpu_seconds):
+            r, _ = oracle.estimate(frames[n % B], keys[n % B], op)
+            oracle.mask(r, SMALL["H"], SMALL["W"])
+            n += 1
+        el = time.perf_counter() - t0
+        out["oracle"] = {"frames_per_s": n / el, "cores": 1, "frames": n}
+    return out
+
+
+def batching_leg(ca, mixed, p_ref, stream, steps, warmup, small_plain=None):
     """512 frames at four resolutions in one persistent, graph-captured launch:
     launch shapes tuned by ca_tune, N/K/NH by the accuracy-constrained sweep
     on a calibration subset; timed against the plain one-frame-per-launch
@@ -261,6 +323,8 @@ def batching_leg(ca, mixed, p_ref, stream, steps, warmup):
     out["batched"], res = run_plan(p_ref, "default")
     out["plain"] = plain_leg(ca, p_ref, ts, mk, ms, stream, 1)
     out["speedup_vs_plain"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
+    if small_plain:
+        out["speedup_vs_640x480_plain"] = out["batched"]["frames_per_s"] / small_plain
     # accuracy-constrained sweep of N, K, NH on a calibration subset
     cal = list(range(0, B, max(1, B // 32)))[:32]
     trials, ref_t, best = tune.sweep(ca, [ts[i] for i in cal], [mg[i] for i in cal],
@@ -561,9 +625,14 @@ def run_ours(args):
         else:
             e2e["zero_copy"] = zc
 
+    small = None
+    if not args.skip_small:
+        small = small_leg(ca, stream, max(5, min(args.steps, 20)),
+                          0.0 if (args.skip_cpu or rank != 0) else 2.0)
     batching = None
     if mixed is not None:
-        batching = batching_leg(ca, mixed, p, stream, max(5, min(args.steps, 20)), args.warmup)
+        batching = batching_leg(ca, mixed, p, stream, max(5, min(args.steps, 20)), args.warmup,
+                                small["plain"]["frames_per_s"] if small else None)
     learned = None
     if ldata is not None:
         learned = learned_leg(ca, ldata, stream, max(3, min(args.steps, 10)))
@@ -626,7 +695,8 @@ def run_ours(args):
                  "ms_per_frame": ms_per_step / B},
         "tuning": tuning, "kernels": kern,
         "staged": {"ms_per_call": staged_ms / staged_steps, "results_equal": bool(same_staged)},
-        "plain": plain, "batching": batching, "learned": learned, "serving": serving,
+        "plain": plain, "small": small, "batching": batching, "learned": learned,
+        "serving": serving,
         "accuracy": {"vs": "generator ground truth", **acc},
         "paper_context": PAPER_CONTEXT,
     }
