@@ -449,7 +449,12 @@ enum {
     CA_DUMP_TABLES = 3,
     /* per frame: N x W uint16 learned scores of the last call (learned
      * scorer modes only) */
-    CA_DUMP_LEARNED = 4
+    CA_DUMP_LEARNED = 4,
+    /* the whole last call (`frame` is not used; needs ca_set_trace and a
+     * fused launch): int32 n_items, int32 0, then n_items records of four
+     * uint64 {t_grab, t_ready, t_end, tag}, see ca_set_trace; a buffer too
+     * small for the records receives the 8-byte header alone */
+    CA_DUMP_TRACE = 5
 };
 
 /* Copies debug data of frame `frame` of the last ca_estimate call (synchronises
@@ -459,6 +464,17 @@ ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p,
 
 /* Number of kernel launches the handle has queued since creation. */
 uint64_t ca_launch_count(const ca_handle *h);
+
+/* Timeline of the fused launch: when on, every later fused call through
+ * ca_estimate, ca_estimate_uniform or ca_estimate_tracked (not plans) records
+ * for each work item (one strip, one tile of hypotheses, or one band of mask
+ * rows, in the order the CTAs take them) four uint64 words: t_grab, the
+ * %globaltimer nanoseconds when a CTA took the item; t_ready, when its
+ * dependency wait ended (t_grab for strips); t_end, when its work ended; and
+ * tag = phase << 48 | SM id << 32 | CTA index (phase 0 strips, 1 fit,
+ * 2 mask).  Read with ca_debug_dump(CA_DUMP_TRACE).  Costs one 32-byte store
+ * per item; results are unchanged. */
+ca_status ca_set_trace(ca_handle *h, int on);
 
 /* Kernel timing: when on, every later ca_estimate / ca_mask call records CUDA
  * events on its stream around each kernel it launches. */

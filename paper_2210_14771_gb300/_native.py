@@ -14,6 +14,7 @@ CA_SCORER_HAND, CA_SCORER_LEARNED, CA_SCORER_LEARNED_FALLBACK = 0, 1, 2
 CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
 CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
 CA_DUMP_LEARNED = 4
+CA_DUMP_TRACE = 5
 CA_SCORER_NPARAM = 17601
 CA_LR_CONSTANT, CA_LR_COSINE = 0, 1
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
@@ -123,6 +124,7 @@ SIGNATURES = [
     ("ca_debug_dump", C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(CaParams), C.c_void_p,
                                 C.c_size_t, _P(C.c_size_t)]),
     ("ca_launch_count", C.c_uint64, [C.c_void_p]),
+    ("ca_set_trace", C.c_int, [C.c_void_p, C.c_int]),
     ("ca_set_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("ca_kernel_times", C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_int32)]),
     ("ca_status_string", C.c_char_p, [C.c_int]),

@@ -16,6 +16,8 @@ from . import _native as N
 RESULT_DTYPE = np.dtype([("cx", "<f4"), ("cy", "<f4"), ("r", "<f4"), ("score", "<f4"),
                          ("valid", "<i4"), ("n_inliers", "<i4")])
 SLOT_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("s", "<u2"), ("kept", "<u2")])
+TRACE_DTYPE = np.dtype([("t_grab", "<u8"), ("t_ready", "<u8"), ("t_end", "<u8"),
+                        ("phase", "<i4"), ("sm", "<i4"), ("cta", "<i4")])
 HYP_DTYPE = np.dtype([("i0", "<i4"), ("i1", "<i4"), ("i2", "<i4"), ("n_inl", "<i4"),
                       ("S", "<u4"), ("pass", "<i4"), ("cx", "<f4"), ("cy", "<f4"),
                       ("r", "<f4")])
@@ -221,6 +223,25 @@ class ContentArea:
 
     def set_timing(self, on: bool):
         self._check(N.lib().ca_set_timing(self._h, 1 if on else 0))
+
+    def set_trace(self, on: bool):
+        """ca_set_trace: record the timeline of later fused calls."""
+        self._check(N.lib().ca_set_trace(self._h, 1 if on else 0))
+
+    def dump_trace(self):
+        """Timeline of the last traced fused call: a structured array with one
+        record per work item (t_grab, t_ready, t_end in ns; phase 0 strips,
+        1 fit, 2 mask; sm; cta), in item order."""
+        hdr = self._dump(N.CA_DUMP_TRACE, 0, None, 8)   # the header sizes the buffer
+        n = int(hdr[:4].view(np.int32)[0])
+        raw = self._dump(N.CA_DUMP_TRACE, 0, None, 8 + 32 * n)
+        w = raw[8:8 + 32 * n].view(np.uint64).reshape(n, 4)
+        out = np.zeros(n, dtype=TRACE_DTYPE)
+        out["t_grab"], out["t_ready"], out["t_end"] = w[:, 0], w[:, 1], w[:, 2]
+        out["phase"] = (w[:, 3] >> np.uint64(48)).astype(np.int32)
+        out["sm"] = ((w[:, 3] >> np.uint64(32)) & np.uint64(0xFFFF)).astype(np.int32)
+        out["cta"] = (w[:, 3] & np.uint64(0xFFFFFFFF)).astype(np.int32)
+        return out
 
     def kernel_times(self):
         """{kernel: (total ms, launches)} since the last read (CUDA events)."""

@@ -52,6 +52,12 @@ struct ca_handle {
     int debug = 0;
     uint64_t launches = 0;
     uint64_t wait_ns = 2000000000ull;   // bound on each wait of the fused kernel
+    // fused-kernel timeline (ca_set_trace): 4 words per work item of the last
+    // traced call
+    bool trace_on = false;
+    unsigned long long *trace_buf = nullptr;
+    size_t trace_cap = 0;   // items
+    int trace_items = 0;    // items of the last call (0: not traced)
 
     // score tables on the device: [s_g][s_theta][s_iota]
     uint16_t *d_luts = nullptr;
@@ -732,6 +738,17 @@ ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_par
             h->sc.last_W[i] = frames[i].W;
         }
     }
+    h->trace_items = 0;
+    if (h->trace_on && cfg.mode == CA_BATCH_FUSED && cb.total_items > 0) {
+        const size_t n = (size_t)cb.total_items;
+        if (n > h->trace_cap) {
+            if ((st = grow(h, &h->trace_buf, 0, 4 * n, true)) != CA_OK) return st;
+            h->trace_cap = n;
+        }
+        ws.trace = h->trace_buf;
+        ws.trace_cap = cb.total_items;
+        h->trace_items = cb.total_items;
+    }
     int fgrid = 0;
     if ((st = prepare_kernels(h, P, cfg, &fgrid)) != CA_OK) return st;
     const unsigned char *dev = (const unsigned char *)sg->dev;
@@ -842,6 +859,7 @@ ca_status ca_destroy(ca_handle *h) {
     cudaFree(h->ws.n_hyps);
     cudaFree(h->ws.n_cands);
     cudaFree(h->ws.sync);
+    cudaFree(h->trace_buf);
     cudaFree(h->sc.params);
     cudaFree(h->sc.mom);
     cudaFree(h->sc.partial);
@@ -1549,6 +1567,24 @@ ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p, v
         return CA_OK;
     }
     if (!h) return CA_ERR_INVALID_ARG;
+    if (what == CA_DUMP_TRACE) {   // the whole last call; `frame` is not used
+        if (h->trace_items == 0)
+            return fail(h, CA_ERR_STATE, "the last call was not a traced fused launch");
+        const size_t rec = 4 * sizeof(unsigned long long) * (size_t)h->trace_items;
+        if (bytes < 8) return fail(h, CA_ERR_INVALID_ARG, "buffer too small (8)");
+        int32_t *hdr = (int32_t *)host_buf;
+        hdr[0] = h->trace_items;
+        hdr[1] = 0;
+        if (bytes < 8 + rec) {   // header only: sizes the buffer
+            if (written) *written = 8;
+            return CA_OK;
+        }
+        CA_CUDA(h, cudaSetDevice(h->device));
+        if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+        CA_CUDA(h, cudaMemcpy((char *)host_buf + 8, h->trace_buf, rec, cudaMemcpyDeviceToHost));
+        if (written) *written = 8 + rec;
+        return CA_OK;
+    }
     if (frame < 0 || frame >= h->last_B) return fail(h, CA_ERR_INVALID_ARG, "bad frame index");
     if (h->debug < 1 && what != CA_DUMP_LEARNED) return fail(h, CA_ERR_STATE, "debug capture is off");
     CA_CUDA(h, cudaSetDevice(h->device));
@@ -1592,6 +1628,12 @@ ca_status ca_debug_dump(ca_handle *h, int what, int frame, const ca_params *p, v
 }
 
 uint64_t ca_launch_count(const ca_handle *h) { return h ? h->launches : 0; }
+
+ca_status ca_set_trace(ca_handle *h, int on) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    h->trace_on = on != 0;
+    return CA_OK;
+}
 
 ca_status ca_set_timing(ca_handle *h, int on) {
     if (!h) return CA_ERR_INVALID_ARG;

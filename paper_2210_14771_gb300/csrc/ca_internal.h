@@ -125,6 +125,8 @@ struct Workspace {
     int32_t sync_frames = 0;
     const int32_t *track = nullptr;  // tracked call: [B] track of each frame (-1: none)
     ca_result *state = nullptr;      // tracked call: per-track previous result
+    unsigned long long *trace = nullptr;   // fused kernel timeline: 4 words per item (or none)
+    int32_t trace_cap = 0;                 // items the trace buffer holds
 };
 
 // ---- Learned edge scorer (ca_scorer.cu): 1-D CNN over strip profiles.

@@ -1195,6 +1195,8 @@ __global__ void __launch_bounds__(kStripThreads, 4)
         __syncthreads();
         const int item = s_item;
         if (item >= total_items) break;
+        uint64_t t_grab = 0, t_ready = 0;
+        if (ws.trace && threadIdx.x == 0) t_grab = t_ready = globaltimer_ns();
         int lo = 0, hi = n_segs - 1;   // last segment starting at or before item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -1221,6 +1223,7 @@ __global__ void __launch_bounds__(kStripThreads, 4)
             if (threadIdx.x == 0) {
                 wait_at_least(sync_strips(sync, nf) + f, (uint32_t)spf, sync + 2, wait_ns);
                 __threadfence();
+                if (ws.trace) t_ready = globaltimer_ns();
             }
             __syncthreads();
             fit_tile<T>(fs, frames, P, ws.slots, ws, out, f, tile, sync);
@@ -1237,6 +1240,7 @@ __global__ void __launch_bounds__(kStripThreads, 4)
             if (threadIdx.x == 0) {
                 wait_at_least(sync_ready(sync, nf) + f, 1u, sync + 2, wait_ns);
                 __threadfence();
+                if (ws.trace) t_ready = globaltimer_ns();
             }
             __syncthreads();
             const int u = (g - fr.mitem_off) * kMaskUnitsPerItem + warp;
@@ -1249,6 +1253,16 @@ __global__ void __launch_bounds__(kStripThreads, 4)
                     sync_ready(sync, nf)[f] = 0u;
                 }
             }
+        }
+        if (ws.trace && threadIdx.x == 0 && item < ws.trace_cap) {   // the item's timeline
+            unsigned long long *tr = ws.trace + 4 * (size_t)item;
+            uint32_t smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            tr[0] = t_grab;
+            tr[1] = t_ready;
+            tr[2] = globaltimer_ns();
+            tr[3] = ((unsigned long long)sg.phase << 48) | ((unsigned long long)smid << 32) |
+                    blockIdx.x;
         }
     }
     if (threadIdx.x == 0 && atomicAdd(sync + 1, 1u) + 1u == gridDim.x) {

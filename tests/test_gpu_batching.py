@@ -184,3 +184,38 @@ def test_fused_wait_runs_out_reports_timeout_and_recovers(ca, orc):
     gres, gmask = _run(ca, ts, keys, lp)
     _check_oracle(orc, frames, keys, op, gres, gmask, range(len(frames)))
     del api
+
+
+def test_fused_trace_records_every_item(ca, orc):
+    """ca_set_trace: one record per work item of the fused call, in the
+    phase counts the batch implies, each with grab <= ready <= end, from the
+    launch's CTAs; results and masks unchanged by tracing."""
+    frames, keys = _ragged_frames()
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    T, N, NH = 2, 16, 200
+    lp, op = both_params(orc, n_strips=N, cands_per_strip=2, n_hyps=NH, batch_mode=2,
+                         hyp_threads=T, wave_frames=3)
+    r0, m0 = _run(ca, ts, keys, lp)
+    ca.set_trace(True)
+    try:
+        r1, m1 = _run(ca, ts, keys, lp)
+        tr = ca.dump_trace()
+    finally:
+        ca.set_trace(False)
+    assert r0.tobytes() == r1.tobytes()
+    assert all(np.array_equal(a, b) for a, b in zip(m0, m1))
+    B = len(frames)
+    n_tiles = -(-NH // (256 // T))
+    mask_items = sum(-(-(-(-f.shape[0] // 8)) // 8) for f in frames)
+    counts = np.bincount(tr["phase"], minlength=3)
+    assert counts.tolist() == [B * N, B * n_tiles, mask_items]
+    assert (tr["t_grab"] <= tr["t_ready"]).all() and (tr["t_ready"] <= tr["t_end"]).all()
+    assert (tr["t_grab"] > 0).all()
+    assert tr["cta"].min() >= 0 and tr["cta"].max() < 152 * 8
+    from paper_2210_14771_gb300 import timeline, _native
+    s = timeline.summarise(tr)
+    assert s["items"] == len(tr) and s["strips"]["n"] == B * N
+    _run(ca, ts, keys, lp)                      # a call without the trace
+    with pytest.raises(_native.CaError) as e:
+        ca.dump_trace()
+    assert e.value.status == _native.CA_ERR_STATE
