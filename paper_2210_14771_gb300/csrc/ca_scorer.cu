@@ -174,6 +174,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// max(a, 0) and max(b, 0) rounded to bf16 (the two commute) in one conversion;
+// a in the low half, as pack_bf16.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float a, float b) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
@@ -509,15 +517,18 @@ __global__ void __launch_bounds__(kInfThreads, 3)
                 const int r = kTile * j + 32 * (warp & 3) + (tid & 31);
                 const int x = b0 + r;
                 const bool inside = x >= 0 && x < si.W;
-                // relu(z) rounded to bf16, two channels per conversion (ReLU and
-                // rounding commute); zero outside the strip
+                // relu(z + b) rounded to bf16, two channels per conversion;
+                // zero outside the strip
                 uint32_t w[16];
                 const float *bl = vec->b[l];
+                if (inside) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const float z0 = fmaxf(__fadd_rn(v[2 * c], bl[2 * c]), 0.0f);
-                    const float z1 = fmaxf(__fadd_rn(v[2 * c + 1], bl[2 * c + 1]), 0.0f);
-                    w[c] = inside ? pack_bf16(z0, z1) : 0u;
+                    for (int c = 0; c < 16; ++c)
+                        w[c] = pack_relu_bf16(__fadd_rn(v[2 * c], bl[2 * c]),
+                                              __fadd_rn(v[2 * c + 1], bl[2 * c + 1]));
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) w[c] = 0u;
                 }
                 if (l < 2) {   // every MMA reading A has completed: overwrite in place
 #pragma unroll
@@ -525,11 +536,12 @@ __global__ void __launch_bounds__(kInfThreads, 3)
                         *reinterpret_cast<uint4 *>(A + c * SegI::kPlane + (kGuard + r) * 16) =
                             make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
                 } else if (x >= si.s0 && x < si.s1) {
+                    // head: fused multiply-adds over the bf16 activations
                     float acc = 0.0f;
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
-                        acc = __fadd_rn(acc, __fmul_rn(vec->whq[2 * c], bf16_lo(w[c])));
-                        acc = __fadd_rn(acc, __fmul_rn(vec->whq[2 * c + 1], bf16_hi(w[c])));
+                        acc = __fmaf_rn(vec->whq[2 * c], bf16_lo(w[c]), acc);
+                        acc = __fmaf_rn(vec->whq[2 * c + 1], bf16_hi(w[c]), acc);
                     }
                     const float lg = __fadd_rn(vec->bh, acc);
                     const float p = 1.0f / (1.0f + expf(-lg));
