@@ -694,8 +694,6 @@ ca_status check_call(ca_handle *h, const ca_frame *frames, int B, const ca_param
     if (p->batch_mode < CA_BATCH_AUTO || p->batch_mode > CA_BATCH_FUSED)
         return fail(h, CA_ERR_INVALID_ARG, "bad batch_mode %d", p->batch_mode);
     if (p->wave_frames < 0) return fail(h, CA_ERR_INVALID_ARG, "wave_frames < 0");
-    if (p->batch_mode == CA_BATCH_FUSED && h->debug > 0 && false)
-        return fail(h, CA_ERR_INVALID_ARG, "unreachable");
     return CA_OK;
 }
 
