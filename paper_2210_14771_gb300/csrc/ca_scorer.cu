@@ -594,7 +594,7 @@ cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uin
 }
 
 // ============================================================= training ==
-// One CTA (4 warps, one per SM) per segment, segments assigned statically
+// One CTA (8 warps, one per SM) per segment, segments assigned statically
 // (g = blockIdx.x + k gridDim.x) so that every run sums the same gradient
 // terms in the same order.  Per segment: forward (features -> a1 -> a2 ->
 // head), loss and its gradient at the logits, then for layers 3, 2, 1 the
@@ -603,7 +603,7 @@ cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uin
 // accumulator per tap) and, for layers 3 and 2, the input gradient (a
 // forward convolution of the gradient planes with the reversed, transposed
 // weights).  The sums of the CTA go to its own slice of `partial`.
-constexpr int kTrainThreads = 128;
+constexpr int kTrainThreads = 256;   // 8 warps: two per TMEM lane quarter
 constexpr int kTrainPlanes = 14;   // D (4) | A1 (4) | A2 (4) | X0 (2)
 constexpr size_t kTrainStageBytes = (size_t)kTaps * 32 * 32 * sizeof(float);   // one layer's dW
 constexpr size_t kTrainSmem = (size_t)kTrainPlanes * SegT::kPlane + (kScBlockBytes - kScVecBytes) +
@@ -754,10 +754,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             }
             if (!wait_mma()) break;
             unsigned char *dst = l == 0 ? A1 : A2;
-            for (int j = 0; j < SegT::kTiles; ++j) {
+            for (int j = warp >> 2; j < SegT::kTiles; j += 2) {   // warp w: tiles w/4, w/4 + 2
                 float v[32];
                 acc_row(tmem, j, v);
-                const int r = kTile * j + 32 * warp + lane, x = b0 + r;
+                const int r = kTile * j + 32 * (warp & 3) + lane, x = b0 + r;
                 const bool inside = x >= 0 && x < si.W;
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
@@ -780,10 +780,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
 #pragma unroll
             for (int c = 0; c < 32; ++c) gwh[c] = gb3[c] = 0.0f;
             float gbh = 0.0f, loss = 0.0f;
-            for (int j = 0; j < SegT::kTiles; ++j) {
+            for (int j = warp >> 2; j < SegT::kTiles; j += 2) {   // warp w: tiles w/4, w/4 + 2
                 float v[32];
                 acc_row(tmem, j, v);
-                const int r = kTile * j + 32 * warp + lane, x = b0 + r;
+                const int r = kTile * j + 32 * (warp & 3) + lane, x = b0 + r;
                 const bool inside = x >= 0 && x < si.W;
                 float acc = 0.0f;
 #pragma unroll
@@ -843,10 +843,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             float gb[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) gb[c] = 0.0f;
-            for (int j = 0; j < SegT::kTiles; ++j) {
+            for (int j = warp >> 2; j < SegT::kTiles; j += 2) {   // warp w: tiles w/4, w/4 + 2
                 float v[32], a[32];
                 acc_row(tmem, j, v);
-                const int r = kTile * j + 32 * warp + lane;
+                const int r = kTile * j + 32 * (warp & 3) + lane;
                 load_row32<SegT>(in, r, a);
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
