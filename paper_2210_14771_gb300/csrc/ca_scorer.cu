@@ -1020,7 +1020,15 @@ __global__ void __launch_bounds__(256)
     float g = 0.0f;
     if (p <= kScNParam) {
         const float *src = part + partial_index(p);
-        for (int c = q; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(src + (size_t)c * kScPartialStride));
+        int c = q;
+        for (; c + 28 < n_part; c += 32) {   // eight loads in flight, added in order
+            float t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = __ldcg(src + (size_t)(c + 4 * u) * kScPartialStride);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) g = __fadd_rn(g, t[u]);
+        }
+        for (; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(src + (size_t)c * kScPartialStride));
     }
     red[q][pl] = g;
     __syncthreads();
