@@ -409,6 +409,10 @@ ca_status ca_run_host(ca_handle *h, const uint8_t *frames_host, int B, int H, in
  * masks_host; only the B results are copied.  frames_host and masks_host
  * (when not NULL) must be page-locked (cudaHostAlloc / cudaHostRegister);
  * otherwise CA_ERR_INVALID_ARG.  Results and masks equal ca_run_host's.
+ * With batch_mode CA_BATCH_AUTO the call runs the fused launch in waves of 4
+ * frames with 8 threads per hypothesis (unless p sets hyp_threads or
+ * wave_frames), so that the mask writes over the link, which bound the call,
+ * start with the first frames and overlap the strip reads of the later ones.
  * Synchronous. */
 ca_status ca_run_host_zero_copy(ca_handle *h, const uint8_t *frames_host, int B, int H, int W,
                                 const uint64_t *keys, const ca_params *p, ca_result *res_host,

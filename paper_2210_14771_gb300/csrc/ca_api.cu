@@ -1489,6 +1489,7 @@ ca_status ca_run_host_zero_copy(ca_handle *h, const uint8_t *frames_host, int B,
     if (B < 0) return fail(h, CA_ERR_INVALID_ARG, "B < 0");
     if (B == 0) return CA_OK;
     if (!frames_host || !res_host) return fail(h, CA_ERR_INVALID_ARG, "NULL host buffer");
+    if (!p) return fail(h, CA_ERR_INVALID_ARG, "params is NULL");
     CA_CUDA(h, cudaSetDevice(h->device));
     // both buffers must be page-locked host memory the device can address
     auto mapped = [&](const void *ptr, void **dev) -> bool {
@@ -1511,7 +1512,15 @@ ca_status ca_run_host_zero_copy(ca_handle *h, const uint8_t *frames_host, int B,
     if ((st = grow(h, &h->e2e_res, h->e2e_res_cap, (size_t)B, false)) != CA_OK) return st;
     h->e2e_res_cap = std::max(h->e2e_res_cap, (size_t)B);
     cudaStream_t s = h->e2e_stream;
-    st = ca_estimate_uniform(h, (const uint8_t *)fd, B, H, W, keys, p, h->e2e_res, (uint8_t *)md, s);
+    // host-resident frames and masks: the device-to-host rate of the link
+    // bounds the call, so mask work should start with the first frames
+    ca_params q = *p;
+    if (q.batch_mode == CA_BATCH_AUTO) {
+        q.batch_mode = CA_BATCH_FUSED;
+        if (q.hyp_threads == 0) q.hyp_threads = 8;
+        if (q.wave_frames <= 0) q.wave_frames = 4;
+    }
+    st = ca_estimate_uniform(h, (const uint8_t *)fd, B, H, W, keys, &q, h->e2e_res, (uint8_t *)md, s);
     if (st != CA_OK) return st;
     CA_CUDA(h, cudaMemcpyAsync(res_host, h->e2e_res, sizeof(ca_result) * B,
                                cudaMemcpyDeviceToHost, s));
