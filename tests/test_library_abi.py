@@ -157,3 +157,54 @@ def test_null_handles_and_buffers_are_rejected(native):
     assert tried >= 30
     assert L.ca_launch_count(None) == 0
     assert L.ca_last_error(None) is not None
+
+
+def test_plain_c_program_links_and_calls_the_library(native, tmp_path):
+    """A C11 program that includes only include/ca.h links against libca.so
+    and calls its device-free entry points: defaults, status strings, the
+    host-built tables (equal to what the binding reads) and the argument
+    checks of a NULL handle."""
+    from paper_2210_14771_gb300.build import LIB
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stdlib.h>
+#include "ca.h"
+int main(void) {
+    ca_params p;
+    ca_params_default(&p);
+    if (p.n_strips != 16 || p.refine_iters != 3) return 1;
+    if (ca_estimate(NULL, NULL, 0, &p, NULL, NULL) != CA_ERR_INVALID_ARG) return 2;
+    if (ca_set_trace(NULL, 1) != CA_ERR_INVALID_ARG) return 3;
+    size_t n = 2 * (5772 + 8193 + 256) + 4 * (size_t)p.n_strips, written = 0;
+    unsigned char *buf = (unsigned char *)malloc(n);
+    if (ca_debug_dump(NULL, CA_DUMP_TABLES, 1080, &p, buf, n, &written) != CA_OK || written != n)
+        return 4;
+    unsigned long long sum = 0;
+    for (size_t i = 0; i < n; ++i) sum = sum * 131u + buf[i];
+    printf("%llu|%s\n", sum, ca_status_string(CA_ERR_TIMEOUT));
+    free(buf);
+    return 0;
+}
+''')
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(LIB)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-l:libca.so",
+                    "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    digest, text = r.stdout.strip().split("|", 1)
+    digest = int(digest)
+    assert text.encode() == native.lib().ca_status_string(4)
+    from paper_2210_14771_gb300 import api
+    p = api.params()
+    nb = 2 * (native.LUT_G + native.LUT_T + native.LUT_I) + 4 * p.n_strips
+    buf = np.zeros(nb, np.uint8)
+    written = C.c_size_t()
+    assert native.lib().ca_debug_dump(None, native.CA_DUMP_TABLES, 1080, C.byref(p),
+                                      buf.ctypes.data_as(C.c_void_p), nb, C.byref(written)) == 0
+    s = 0
+    for b in buf.tolist():
+        s = (s * 131 + b) % (1 << 64)
+    assert s == digest
