@@ -65,6 +65,24 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x of all ranks (the slowest rank's time); x itself when
+    no process group is up."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank processes its own units)."""
+    return units_per_rank_step * steps * world / seconds
+
+
 # ---------------------------------------------------------------- clocks --
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons while running."""
@@ -532,11 +550,8 @@ def run_ours(args):
     ca.sync()
     launches = ca.launch_count() - n0
     last_masks = d_masks_all[(args.steps - 1) % ROTATE_MASKS]
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = B * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = whole_job_rate(B, args.steps, world, total_ms / 1e3)
 
     # ---- accuracy of this batch against the generator's ground truth (Sec. 2.3)
     m_host = last_masks.cpu().numpy()
@@ -585,12 +600,8 @@ def run_ours(args):
         for _ in range(e_steps):
             ca.run_host_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
                             h_masks.data_ptr())
-        el = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": B * e_steps * world / el, "unit": "frames/s",
+        el = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": whole_job_rate(B, e_steps, world, el), "unit": "frames/s",
                "h2d_bytes_per_step": B * H * W * 3, "d2h_bytes_per_step": B * (H * W + 24),
                "ms_per_step": 1e3 * el / e_steps, "call": "ca_run_host (pinned host buffers)"}
         same = np.array_equal(h_masks.numpy(), m_host) and \
@@ -607,14 +618,10 @@ def run_ours(args):
         for _ in range(e_steps):
             ca.run_host_zero_copy_ptr(h_frames.data_ptr(), B, H, W, karr, p, h_res.data_ptr(),
                                       h_masks.data_ptr())
-        elz = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([elz], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            elz = float(t.item())
+        elz = max_over_ranks(time.perf_counter() - t0, dev)
         samez = np.array_equal(h_masks.numpy(), m_host) and \
             h_res.numpy().tobytes() == res_host.tobytes()
-        zc = {"value": B * e_steps * world / elz, "unit": "frames/s",
+        zc = {"value": whole_job_rate(B, e_steps, world, elz), "unit": "frames/s",
               "h2d_bytes_per_step": abytes_strips_read(B, W, WORKLOAD["n_strips"]),
               "d2h_bytes_per_step": B * (H * W + 24), "ms_per_step": 1e3 * elz / e_steps,
               "call": "ca_run_host_zero_copy (kernels read strip rows from and write masks to "
