@@ -205,6 +205,56 @@ def oracle_sample(frames, keys, seconds, min_frames=2):
             return n, el
 
 
+_POOL = {}
+
+
+def _oracle_pool_init(shm_name, shape, keys):
+    from multiprocessing import shared_memory
+    import numpy as np
+    import oracle
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _POOL["shm"] = shm
+    _POOL["frames"] = np.ndarray(shape, dtype=np.uint8, buffer=shm.buf)
+    _POOL["keys"] = keys
+    _POOL["op"] = oracle.params(n_strips=WORKLOAD["n_strips"],
+                                cands_per_strip=WORKLOAD["cands_per_strip"],
+                                n_hyps=WORKLOAD["n_hyps"])
+
+
+def _oracle_pool_run(idx):
+    import oracle
+    fr, keys, op = _POOL["frames"], _POOL["keys"], _POOL["op"]
+    for b in idx:
+        res, _ = oracle.estimate(fr[b], keys[b], op)
+        oracle.mask(res, fr.shape[1], fr.shape[2])
+    return len(idx)
+
+
+def oracle_all_cores(frames, keys, workers, per_worker=32):
+    """The same oracle, frame-parallel over `workers` spawned processes (each
+    single-threaded) on the frames in shared memory; returns (frames done,
+    elapsed seconds) of the timed map, after one warm-up frame per worker."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    shm = shared_memory.SharedMemory(create=True, size=frames.nbytes)
+    try:
+        np.ndarray(frames.shape, dtype=np.uint8, buffer=shm.buf)[:] = frames
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
+                                    initializer=_oracle_pool_init,
+                                    initargs=(shm.name, frames.shape, list(keys))) as ex:
+            list(ex.map(_oracle_pool_run, [[w % len(frames)] for w in range(workers)]))
+            chunks = [[(w * per_worker + k) % len(frames) for k in range(per_worker)]
+                      for w in range(workers)]
+            t0 = time.perf_counter()
+            n = sum(ex.map(_oracle_pool_run, chunks))
+            return n, time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+
+
 # ------------------------------------------------------------- ours --
 def timed_loop(stream, steps, fn):
     """Runs fn(k) for k < steps between CUDA events on `stream`; returns
@@ -220,27 +270,34 @@ def timed_loop(stream, steps, fn):
     return ev[0].elapsed_time(ev[steps]), [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
 
 
-def plain_leg(ca, p, frames_dev, keys, masks_dev, stream, reps):
-    """The plain method: one frame per call (three launches per frame, staged)."""
+def plain_leg(ca, p, frames_dev, keys, masks_dev, stream, reps, batched=None):
+    """The plain method: one frame per call (three launches per frame, staged).
+    With `batched` (the results of the batched call on the same frames, host
+    array) the plain results are compared with them bit for bit: equal results
+    mean equal Hausdorff error against the truth."""
     import numpy as np
     import torch
     from paper_2210_14771_gb300 import api
     q = api.params(**{k: getattr(p, k) for k, _ in p._fields_})
     q.batch_mode = 1
-    res = api.new_results(1, frames_dev[0].device)
+    res = api.new_results(len(frames_dev), frames_dev[0].device)
     lat = []
     pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(len(frames_dev))]
     for _ in range(reps):
         for b, f in enumerate(frames_dev):
             pev[b][0].record(stream)
-            ca.estimate([f], q, keys=[keys[b]], masks=[masks_dev[b]], results=res)
+            ca.estimate([f], q, keys=[keys[b]], masks=[masks_dev[b]], results=res[b:b + 1])
             pev[b][1].record(stream)
         torch.cuda.synchronize()
         lat += [a.elapsed_time(c) for a, c in pev]
-    return {"frames_per_s": len(lat) / (sum(lat) / 1e3),
-            "p50_ms_per_frame": float(np.percentile(lat, 50)),
-            "p99_ms_per_frame": float(np.percentile(lat, 99)), "launches_per_frame": 3}
+    out = {"frames_per_s": len(lat) / (sum(lat) / 1e3),
+           "p50_ms_per_frame": float(np.percentile(lat, 50)),
+           "p99_ms_per_frame": float(np.percentile(lat, 99)), "launches_per_frame": 3}
+    if batched is not None:
+        out["results_equal_to_batched"] = bool(api.results_numpy(res).tobytes() ==
+                                               np.asarray(batched).tobytes())
+    return out
 
 
 SMALL = dict(seed=0, B=8, H=480, W=640, mix="centred", n_strips=16, cands_per_strip=4, n_hyps=256)
@@ -339,7 +396,7 @@ def batching_leg(ca, mixed, p_ref, stream, steps, warmup, small_plain=None):
                 "tune_ms": {k: t[k] for k in ("ms", "ms_staged", "ms_fused", "ms_untuned")}}, res
 
     out["batched"], res = run_plan(p_ref, "default")
-    out["plain"] = plain_leg(ca, p_ref, ts, mk, ms, stream, 1)
+    out["plain"] = plain_leg(ca, p_ref, ts, mk, ms, stream, 1, batched=api.results_numpy(res))
     out["speedup_vs_plain"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
     if small_plain:
         out["speedup_vs_640x480_plain"] = out["batched"]["frames_per_s"] / small_plain
@@ -580,7 +637,9 @@ def run_ours(args):
     plain = None
     if not args.skip_plain:
         plain = plain_leg(ca, p, list(d_frames_all[0]), keys, list(d_masks_all[0]), stream,
-                          max(1, min(args.steps, 3)))
+                          max(1, min(args.steps, 3)), batched=res_host)
+        plain["masks_equal_to_batched"] = bool(np.array_equal(d_masks_all[0].cpu().numpy(),
+                                                              m_host))
 
     # ---- end to end through the C ABI on host buffers (copies inside)
     e2e = None
@@ -679,6 +738,12 @@ def run_ours(args):
         cpu = {"value": n / el, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": "%d frames of the 64-frame 1080p workload (N=32, 1024 hypotheses), "
                          "estimate + mask, one thread" % n}
+        workers = os.cpu_count() or 1
+        na, ela = oracle_all_cores(frames, keys, workers)
+        cpu["all_cores"] = {"value": na / ela, "unit": "frames/s", "cores": workers,
+                            "sample": "%d frames (%d per process) of the same workload, one "
+                                      "single-threaded oracle process per host core" %
+                                      (na, na // workers)}
 
     out = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
