@@ -66,6 +66,11 @@ def lib():
         L.orc_score_exact.restype = C.c_double
         L.orc_candidates.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, P(OrcParams),
                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_candidates_centre.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64,
+                                            P(OrcParams), C.c_int32, C.c_int32, C.c_int,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_prior_centre2.argtypes = [C.c_float, C.c_float, C.c_int, C.c_int, C.c_void_p]
+        L.orc_prior_centre2.restype = None
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
         L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
@@ -183,7 +188,9 @@ def sc_q15(logits):
     return np.floor(32768.0 / (1.0 + np.exp(-l)) + 0.5).astype(np.uint16)
 
 
-def candidates(frame, p=None):
+def candidates(frame, p=None, centre2=None):
+    """Candidates of a frame (Sec. 2.2.3-2.2.5); centre2 = the doubled
+    integer centre (C2x, C2y) of the angle term, default the image centre."""
     f = _frame(frame)
     H, W = f.shape[:2]
     p = p or params()
@@ -192,11 +199,24 @@ def candidates(frame, p=None):
     ys = np.zeros(cap, np.int16)
     ss = np.zeros(cap, np.uint16)
     M = C.c_int32(0)
-    if lib().orc_candidates(_ptr(f), H, W, W * 3, C.byref(p), cap, _ptr(xs), _ptr(ys),
-                            _ptr(ss), C.byref(M)) != 0:
+    if centre2 is None:
+        rc = lib().orc_candidates(_ptr(f), H, W, W * 3, C.byref(p), cap, _ptr(xs), _ptr(ys),
+                                  _ptr(ss), C.byref(M))
+    else:
+        rc = lib().orc_candidates_centre(_ptr(f), H, W, W * 3, C.byref(p), int(centre2[0]),
+                                         int(centre2[1]), cap, _ptr(xs), _ptr(ys), _ptr(ss),
+                                         C.byref(M))
+    if rc != 0:
         raise ValueError("bad candidate arguments")
     m = M.value
     return xs[:m].copy(), ys[:m].copy(), ss[:m].copy()
+
+
+def prior_centre2(cx, cy, H, W):
+    """Doubled integer centre of a prior circle centre (orc_prior_centre2)."""
+    out = np.zeros(2, np.int32)
+    lib().orc_prior_centre2(C.c_float(cx), C.c_float(cy), H, W, _ptr(out))
+    return int(out[0]), int(out[1])
 
 
 def philox(ctr, key):
@@ -242,11 +262,13 @@ def i128_to_f32(v: int) -> np.float32:
     return np.float32(lib().orc_i128_to_f32(hi, v & ((1 << 64) - 1)))
 
 
-def estimate_tracked(frame, frame_key, p, prior):
+def estimate_tracked(frame, frame_key, p, prior, prior_centre=False):
     """Whole pipeline with the previous circle (cx, cy, r) as an extra
-    hypothesis, or None for none."""
-    xs, ys, ss = candidates(frame, p)
+    hypothesis, or None for none; with prior_centre, the angle term of the
+    candidate scores also points at the previous circle's centre."""
     H, W = np.shape(frame)[:2]
+    c2 = prior_centre2(prior[0], prior[1], H, W) if (prior_centre and prior is not None) else None
+    xs, ys, ss = candidates(frame, p, c2)
     return fit(xs, ys, ss, H, W, frame_key, p, prior)
 
 

@@ -130,11 +130,14 @@ double orc_score_exact(int gx, int gy, int cx2, int cy2, int iota, const orc_par
 
 /* Sec. 2.2.3 for the strip centred on `row`: Sobel gradient g on the middle
  * row (y down, g pointing dark -> bright, zero on the first and last column),
- * angle to the vector c towards the image centre, preceding maximum iota of the
- * middle row scanned from the outer image edge (exclusive of the pixel), and
- * the quantised product score s_q in Q15. */
+ * angle to the vector c from the pixel towards the centre (c2x0 / 2, c2y0 / 2)
+ * -- the image centre ((W-1)/2, (H-1)/2) unless a prior centre is given --
+ * as the doubled integer vector (c2x0 - 2x, c2y0 - 2 row), preceding maximum
+ * iota of the middle row scanned from the outer image edge (exclusive of the
+ * pixel), and the quantised product score s_q in Q15. */
 static void strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int row,
                          const uint16_t *lut_g, const uint16_t *lut_t, const uint16_t *lut_i,
+                         int c2x0, int c2y0,
                          uint16_t *s_out, int32_t *gx_out, int32_t *gy_out, uint8_t *iota_out) {
     int32_t *Y = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)W);
     uint8_t *iota = (uint8_t *)malloc((size_t)W);
@@ -165,7 +168,7 @@ static void strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int ro
             gx = (Yu[x + 1] + 2 * Ym[x + 1] + Yd[x + 1]) - (Yu[x - 1] + 2 * Ym[x - 1] + Yd[x - 1]);
             gy = (Yd[x - 1] + 2 * Yd[x] + Yd[x + 1]) - (Yu[x - 1] + 2 * Yu[x] + Yu[x + 1]);
         }
-        int cx2 = W - 1 - 2 * x, cy2 = H - 1 - 2 * row;
+        int cx2 = c2x0 - 2 * x, cy2 = c2y0 - 2 * row;
         int64_t ng = (int64_t)gx * gx + (int64_t)gy * gy;
         int64_t nc = (int64_t)cx2 * cx2 + (int64_t)cy2 * cy2;
         uint32_t s = 0;
@@ -198,7 +201,8 @@ int orc_strip_scores(const uint8_t *rgb, int H, int W, int64_t pitch, int row,
     uint16_t *lut_t = (uint16_t *)malloc(sizeof(uint16_t) * ORC_LUT_T);
     uint16_t *lut_i = (uint16_t *)malloc(sizeof(uint16_t) * ORC_LUT_I);
     orc_build_luts(p, lut_g, lut_t, lut_i);
-    strip_scores(rgb, H, W, pitch, row, lut_g, lut_t, lut_i, s_out, gx_out, gy_out, iota_out);
+    strip_scores(rgb, H, W, pitch, row, lut_g, lut_t, lut_i, W - 1, H - 1, s_out, gx_out, gy_out,
+                 iota_out);
     free(lut_g); free(lut_t); free(lut_i);
     return 0;
 }
@@ -245,8 +249,8 @@ static int pick_half(const uint16_t *s, int x0, int x1, int half, int y, int H, 
 }
 
 static int candidates_impl(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
-                           const uint16_t *learned, int fallback, int cap, int16_t *xs,
-                           int16_t *ys, uint16_t *ss, int32_t *M) {
+                           const uint16_t *learned, int fallback, int c2x0, int c2y0, int cap,
+                           int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M) {
     int N = p->n_strips, K = p->cands_per_strip;
     if (N < 1 || K < 2 || (K & 1)) return -1;
     int32_t *rows = (int32_t *)malloc(sizeof(int32_t) * N);
@@ -260,7 +264,7 @@ static int candidates_impl(const uint8_t *rgb, int H, int W, int64_t pitch, cons
     int hw = W / 2, m = 0;
     for (int i = 0; i < N; ++i) {
         int y = rows[i];
-        strip_scores(rgb, H, W, pitch, y, lut_g, lut_t, lut_i, s, NULL, NULL, NULL);
+        strip_scores(rgb, H, W, pitch, y, lut_g, lut_t, lut_i, c2x0, c2y0, s, NULL, NULL, NULL);
         for (int half = 0; half < 2; ++half) {
             int x0 = half ? hw : 0, x1 = half ? W : hw;
             if (learned) {
@@ -283,14 +287,36 @@ static int candidates_impl(const uint8_t *rgb, int H, int W, int64_t pitch, cons
 
 int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
                    int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M) {
-    return candidates_impl(rgb, H, W, pitch, p, NULL, 0, cap, xs, ys, ss, M);
+    return candidates_impl(rgb, H, W, pitch, p, NULL, 0, W - 1, H - 1, cap, xs, ys, ss, M);
+}
+
+/* Doubled centre (C2x, C2y) of the angle term for a prior circle centre
+ * (cx, cy) in frame pixels: 2 cx and 2 cy (exact in binary32) rounded to the
+ * nearest integer, ties to even, then clamped into [0, 2(W-1)] x [0, 2(H-1)]
+ * (half-pixel resolution, inside the frame). */
+void orc_prior_centre2(float cx, float cy, int H, int W, int32_t out[2]) {
+    long vx = lrintf(2.0f * cx), vy = lrintf(2.0f * cy);
+    if (vx < 0) vx = 0;
+    if (vx > 2L * (W - 1)) vx = 2L * (W - 1);
+    if (vy < 0) vy = 0;
+    if (vy > 2L * (H - 1)) vy = 2L * (H - 1);
+    out[0] = (int32_t)vx;
+    out[1] = (int32_t)vy;
+}
+
+int orc_candidates_centre(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                          int32_t c2x0, int32_t c2y0, int cap, int16_t *xs, int16_t *ys,
+                          uint16_t *ss, int32_t *M) {
+    if (c2x0 < 0 || c2x0 > 2 * (W - 1) || c2y0 < 0 || c2y0 > 2 * (H - 1)) return -1;
+    return candidates_impl(rgb, H, W, pitch, p, NULL, 0, c2x0, c2y0, cap, xs, ys, ss, M);
 }
 
 int orc_learned_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
                            const uint16_t *learned, int fallback, int cap, int16_t *xs,
                            int16_t *ys, uint16_t *ss, int32_t *M) {
     if (!learned) return -1;
-    return candidates_impl(rgb, H, W, pitch, p, learned, fallback, cap, xs, ys, ss, M);
+    return candidates_impl(rgb, H, W, pitch, p, learned, fallback, W - 1, H - 1, cap, xs, ys, ss,
+                           M);
 }
 
 /* ------------------------------------------------------- Philox4x32-10 -- */

@@ -102,6 +102,18 @@ double orc_score_exact(int gx, int gy, int cx2, int cy2, int iota, const orc_par
 int orc_candidates(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
                    int cap, int16_t *xs, int16_t *ys, uint16_t *ss, int32_t *M);
 
+/* Prior-guided scoring (the use of the previous estimate that Sec. 4
+ * suggests): the angle term measures the direction of g against the vector
+ * to a prior centre instead of the image centre.  orc_prior_centre2 gives
+ * the doubled integer centre of a prior circle centre (cx, cy): round(2 cx),
+ * round(2 cy), ties to even, clamped into [0, 2(W-1)] x [0, 2(H-1)];
+ * orc_candidates_centre is orc_candidates with that doubled centre
+ * ((W-1, H-1) is the image centre: the same as orc_candidates). */
+void orc_prior_centre2(float cx, float cy, int H, int W, int32_t out[2]);
+int orc_candidates_centre(const uint8_t *rgb, int H, int W, int64_t pitch, const orc_params *p,
+                          int32_t c2x0, int32_t c2y0, int cap, int16_t *xs, int16_t *ys,
+                          uint16_t *ss, int32_t *M);
+
 /* Candidates from learned per-pixel Q15 scores (learned: N x W, strip by
  * strip), picked by the same rule; with `fallback`, a half-strip whose best
  * learned score is below 16384 (probability one half) takes the handcrafted
