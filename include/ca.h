@@ -93,6 +93,16 @@ typedef struct ca_params {
     int32_t batch_mode;      /* CA_BATCH_* (results do not depend on it) */
     int32_t wave_frames;     /* fused launch: frames per pipeline wave, 0 = chosen
                                 per call (results do not depend on it) */
+    int32_t prior_centre;    /* tracked calls (ca_estimate_tracked): 1 = for a frame
+                                whose track has an accepted previous circle, the
+                                direction term of the edge score (Eq. 2) measures
+                                the angle between g and the vector to that
+                                circle's centre instead of the image centre (the
+                                use of the previous estimate Sec. 4 suggests); the
+                                centre is taken as round(2 cx) / 2, round(2 cy) / 2
+                                (ties to even) clamped into the frame.  0 = image
+                                centre (default); other calls ignore it */
+    int32_t reserved;        /* must be 0 */
     uint64_t seed;           /* key of the RANSAC random stream */
 } ca_params;
 

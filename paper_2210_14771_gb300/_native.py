@@ -29,7 +29,8 @@ class CaParams(C.Structure):
         ("r_max", C.c_float), ("d_max", C.c_float), ("sup_px", C.c_int32),
         ("hyp_mode", C.c_int32), ("score_norm", C.c_int32), ("sobel_norm", C.c_int32),
         ("scorer_mode", C.c_int32), ("hyp_threads", C.c_int32), ("batch_mode", C.c_int32),
-        ("wave_frames", C.c_int32), ("seed", C.c_uint64),
+        ("wave_frames", C.c_int32), ("prior_centre", C.c_int32), ("reserved", C.c_int32),
+        ("seed", C.c_uint64),
     ]
 
 

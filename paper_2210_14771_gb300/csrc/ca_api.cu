@@ -279,6 +279,9 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
     if (p->t_ps < 0 || p->t_ps > 1 || p->t_cs < 0 || p->t_px < 0 || p->t_px > kMaxDim ||
         p->t_ri < 0)
         return fail(h, CA_ERR_INVALID_ARG, "threshold out of range");
+    if (p->prior_centre != 0 && p->prior_centre != 1)
+        return fail(h, CA_ERR_INVALID_ARG, "prior_centre must be 0 or 1");
+    if (p->reserved != 0) return fail(h, CA_ERR_INVALID_ARG, "reserved must be 0");
     return CA_OK;
 }
 
@@ -418,6 +421,7 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T, 
     P.io_cut = iota_cut(h->li_host, P.T_ps);
     P.NH = (int)hyps_per_frame(p);
     P.track = track ? 1 : 0;
+    P.prior_centre = (track && p.prior_centre) ? 1 : 0;
     P.hyp_threads = T;
     const long long per_tile = kHypTile / P.hyp_threads;
     P.n_tiles = (int)((P.NH + P.track + per_tile - 1) / per_tile);
@@ -706,7 +710,7 @@ ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_par
     if ((st = ensure_luts(h, *p, stream)) != CA_OK) return st;
     int max_w = 0;
     for (int i = 0; i < B; ++i) max_w = std::max(max_w, frames[i].W);
-    const DevParams P = make_params(h, *p, max_w, cfg.T, track != nullptr);
+    DevParams P = make_params(h, *p, max_w, cfg.T, track != nullptr);
     CallBlock cb;
     build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb, track);
     Staging *sg;
@@ -721,6 +725,8 @@ ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_par
     if (track) {
         ws.track = (const int32_t *)((const unsigned char *)sg->dev + cb.off_track);
         ws.state = state_dev;
+        P.trk = ws.track;   // prior-guided scoring reads the previous circles
+        P.trk_state = state_dev;
     }
     if (cfg.scorer != CA_SCORER_HAND) {
         if (cb.sc_pix > INT32_MAX) return fail(h, CA_ERR_INVALID_ARG, "batch too large for the scorer");

@@ -88,6 +88,9 @@ struct DevParams {
     int32_t hyp_threads; // threads per hypothesis in k_fit: 1, 2, 4 or 8
     int32_t io_cut;      // preceding maxima >= io_cut have s_iota < T_ps: never kept
     int32_t track;       // 1: tracked call (previous circles as extra hypotheses)
+    int32_t prior_centre;  // tracked call: the angle term points at the previous centre
+    const int32_t *trk;          // tracked call: [B] track of each frame (-1: none)
+    const ca_result *trk_state;  // tracked call: per-track previous result
 };
 
 // A candidate slot (8 bytes): x, y, Q15 score, kept flag.

@@ -150,7 +150,7 @@ __device__ __forceinline__ int qtheta(int dot, int ng, int nc) {
 }
 
 struct StripCtx {
-    int W, cy2;
+    int c2x, cy2;   // doubled centre x of the angle term; doubled vector y of the strip
     const uint16_t *lt, *lg, *li;
 };
 
@@ -160,7 +160,7 @@ struct StripCtx {
 __device__ __forceinline__ uint32_t score_from_g(const StripCtx &c, int gx, int gy, int x,
                                                  int iota, const DevParams &P) {
     const int ng = gx * gx + gy * gy;
-    const int cx2 = c.W - 1 - 2 * x;
+    const int cx2 = c.c2x - 2 * x;
     const int nc = cx2 * cx2 + c.cy2 * c.cy2;
     if (ng == 0 || nc == 0) return 0u;
     const uint32_t g = c.lg[qmag(ng, P.qg_sat)];
@@ -203,6 +203,25 @@ __device__ __forceinline__ void strip_tables_load(const DevParams &P, const uint
         const int i = threadIdx.x + k * kStripThreads;
         if (i < n16) dst[i] = v[k];
     }
+}
+
+// Doubled centre of the angle term of frame f in a tracked call with
+// prior-guided scoring: the previous accepted circle of its track, 2 cx and
+// 2 cy rounded to the nearest integer (ties to even) and clamped into
+// [0, 2(W-1)] x [0, 2(H-1)]; the image centre (W-1, H-1) otherwise.  Out of
+// line: it runs once per half-strip and keeps the scan's registers free.
+__device__ __noinline__ int2 prior_centre2(const int32_t *trk, const ca_result *state, int f,
+                                           int W, int H) {
+    int2 c2 = make_int2(W - 1, H - 1);
+    const int t = trk[f];
+    if (t >= 0) {
+        const ca_result pr = load_result(state + t);
+        if (pr.valid) {
+            c2.x = min(max(__float2int_rn(__fmul_rn(2.0f, pr.cx)), 0), 2 * (W - 1));
+            c2.y = min(max(__float2int_rn(__fmul_rn(2.0f, pr.cy)), 0), 2 * (H - 1));
+        }
+    }
+    return c2;
 }
 
 // Half `half` of strip i of frame f: the K/2 best points of the half-strip
@@ -274,7 +293,12 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
         __syncwarp();
     };
 
-    const StripCtx ctx{W, H - 1 - 2 * y, lt, lg, li};
+    // the angle term's centre, doubled: the image centre, or in a tracked
+    // call with prior-guided scoring the previous accepted circle's centre
+    // (rounded to half pixels, ties to even, clamped into the frame)
+    int2 c2 = make_int2(W - 1, H - 1);
+    if (P.prior_centre) c2 = prior_centre2(P.trk, P.trk_state, f, W, H);
+    const StripCtx ctx{c2.x, c2.y - 2 * y, lt, lg, li};
     const int dir = half ? -1 : 1;
     uint32_t best = 0u;
 

@@ -38,11 +38,11 @@ def streams():
     return synth.video_streams(5, 6, resolutions=SMALL, bank=6)
 
 
-def _oracle_chain(orc, stream, n, op):
+def _oracle_chain(orc, stream, n, op, prior_centre=False):
     out, prior = [], None
     for k in range(n):
         f, _ = stream.frame(k)
-        r = orc.estimate_tracked(f, stream.key(k), op, prior)
+        r = orc.estimate_tracked(f, stream.key(k), op, prior, prior_centre)
         out.append(r)
         prior = (r["cx"], r["cy"], r["r"]) if r["valid"] else None
     return out
@@ -71,6 +71,42 @@ def test_tracked_estimate_matches_oracle(ca, orc, streams):
         g = api.results_numpy(res)
         for i in range(B):
             assert _same(tuple(g[i]), want[i][k]), (i, k, g[i], want[i][k])
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_prior_guided_tracked_estimate_matches_oracle(ca, orc, streams, mode):
+    """prior_centre: the angle term of each frame points at its stream's
+    previous circle; bit for bit the oracle's chain, staged and fused, and
+    different from the chain without it (the option is not ignored)."""
+    from paper_2210_14771_gb300 import _native as N, api
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4, batch_mode=mode)
+    lp.prior_centre = 1
+    n = 6
+    want = [_oracle_chain(orc, s, n, op, True) for s in streams]
+    plain = [_oracle_chain(orc, s, n, op, False) for s in streams]
+    assert want != plain
+    state = torch.zeros((len(streams), 6), dtype=torch.float32, device="cuda")
+    for k in range(n):
+        ts = [torch.from_numpy(s.frame(k)[0]).cuda() for s in streams]
+        arr, B, _, res = ca._descriptors(ts, [s.key(k) for s in streams], None, None)
+        track = (C.c_int32 * B)(*range(B))
+        ca._check(N.lib().ca_estimate_tracked(ca._h, arr, B, C.byref(lp),
+                                              C.c_void_p(state.data_ptr()), track, B,
+                                              C.c_void_p(res.data_ptr()),
+                                              api._stream_ptr(None, ca.device)))
+        ca.sync()
+        g = api.results_numpy(res)
+        for i in range(B):
+            assert _same(tuple(g[i]), want[i][k]), (i, k, g[i], want[i][k])
+
+
+def test_prior_centre_argument_check(ca):
+    from paper_2210_14771_gb300 import _native as N, api
+    t = torch.zeros((1, 64, 96, 3), dtype=torch.uint8, device="cuda")
+    for kw in (dict(prior_centre=2), dict(reserved=1)):
+        with pytest.raises(N.CaError) as e:
+            ca.estimate(t, api.params(**kw))
+        assert e.value.status == 1
 
 
 def _serve(ca, streams, banks, n, sids, max_batch, budget, p):

@@ -43,7 +43,7 @@ def test_every_declared_symbol_exported(native):
 def test_struct_layouts(native):
     assert C.sizeof(native.CaResult) == 24
     assert C.sizeof(native.CaFrame) == 40
-    assert C.sizeof(native.CaParams) == 104
+    assert C.sizeof(native.CaParams) == 112
     assert C.sizeof(native.CaTuning) == 32
     assert C.sizeof(native.CaTrainParams) == 24
 
