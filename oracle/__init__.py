@@ -32,6 +32,11 @@ class OrcResult(C.Structure):
                 ("score", C.c_float), ("valid", C.c_int32), ("n_inliers", C.c_int32)]
 
 
+class OrcSmoothParams(C.Structure):
+    _fields_ = [("gamma", C.c_float), ("jump", C.c_float), ("t_hold", C.c_float),
+                ("pad", C.c_int32)]
+
+
 class OrcDebug(C.Structure):
     _fields_ = [
         ("cand_cap", C.c_int32), ("n_cands", C.POINTER(C.c_int32)),
@@ -71,6 +76,9 @@ def lib():
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_prior_centre2.argtypes = [C.c_float, C.c_float, C.c_int, C.c_int, C.c_void_p]
         L.orc_prior_centre2.restype = None
+        L.orc_smooth.argtypes = [P(OrcResult), C.c_int, P(OrcSmoothParams), C.c_void_p,
+                                 P(OrcResult)]
+        L.orc_smooth.restype = None
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
         L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
@@ -396,3 +404,20 @@ def sc_loss_grad(rgb3, y, H, labels, prm, pos_weight=1.0, mode=SC_MIXED):
     loss = lib().orc_sc_loss_grad(_ptr(s), W, int(y), int(H), _ptr(lab), float(pos_weight),
                                   _ptr(prm), mode, _ptr(g))
     return loss, g
+
+
+def smooth_chain(results, W, gamma, jump, t_hold, state=None):
+    """orc_smooth over one stream's results in order (dicts or 6-tuples
+    cx, cy, r, score, valid, n_inliers); returns (smoothed dicts, state)."""
+    sp = OrcSmoothParams(gamma, jump, t_hold, 0)
+    st = np.zeros(4, np.float32) if state is None else np.asarray(state, np.float32).copy()
+    out = []
+    for r in results:
+        if isinstance(r, dict):
+            r = (r["cx"], r["cy"], r["r"], r["score"], r["valid"], r["n_inliers"])
+        cur = OrcResult(*[float(v) for v in r[:4]], int(r[4]), int(r[5]))
+        o = OrcResult()
+        lib().orc_smooth(C.byref(cur), int(W), C.byref(sp), _ptr(st), C.byref(o))
+        out.append(dict(cx=o.cx, cy=o.cy, r=o.r, score=o.score, valid=o.valid,
+                        n_inliers=o.n_inliers))
+    return out, st

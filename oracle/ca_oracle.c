@@ -623,3 +623,41 @@ void orc_mask(const orc_result *res, int H, int W, uint8_t *out) {
             out[(int64_t)y * W + x] = m;
         }
 }
+
+/* ------------------------------------------- temporal smoothing (Sec. 4) -- */
+void orc_smooth(const orc_result *cur, int W, const orc_smooth_params *sp, float state[4],
+                orc_result *out) {
+    const float d = state[3] * sp->gamma;
+    if (cur->valid) {
+        const float J = sp->jump * (float)W;
+        const int near = d > 0.0f && fabsf(cur->cx - state[0]) <= J &&
+                         fabsf(cur->cy - state[1]) <= J && fabsf(cur->r - state[2]) <= J;
+        *out = *cur;
+        if (near) {
+            const float w = d + cur->score;
+            const float pcx = d * state[0], ccx = cur->score * cur->cx;
+            const float pcy = d * state[1], ccy = cur->score * cur->cy;
+            const float pr = d * state[2], cr = cur->score * cur->r;
+            out->cx = (pcx + ccx) / w;
+            out->cy = (pcy + ccy) / w;
+            out->r = (pr + cr) / w;
+            state[3] = w;
+        } else {
+            state[3] = cur->score;
+        }
+        state[0] = out->cx;
+        state[1] = out->cy;
+        state[2] = out->r;
+    } else if (d > 0.0f && d >= sp->t_hold) {
+        out->cx = state[0];
+        out->cy = state[1];
+        out->r = state[2];
+        out->score = 0.0f;
+        out->valid = 1;
+        out->n_inliers = 0;
+        state[3] = d;
+    } else {
+        *out = *cur;
+        state[0] = state[1] = state[2] = state[3] = 0.0f;
+    }
+}

@@ -188,6 +188,29 @@ int orc_fit_prior(const int16_t *xs, const int16_t *ys, const uint16_t *ss, int3
  * whole rectangle when the circle is not valid.  H*W bytes, 0/1. */
 void orc_mask(const orc_result *res, int H, int W, uint8_t *out);
 
+/* Temporal smoothing of one stream's results (an extension in the direction
+ * Sec. 4 points to: the estimates of earlier frames inform the current one).
+ * state = {cx, cy, r, conf} of the stream (conf 0: none), updated in place.
+ * In binary32, each operation rounded on its own, in this order:
+ *   d = conf * gamma                          (the decayed confidence)
+ *   valid frame, d > 0 and |cx - cx'|, |cy - cy'|, |r - r'| <= jump * W:
+ *     w = d + score;  c = (d * c' + score * c) / w for c in cx, cy, r;
+ *     conf = w                                  (confidence-weighted mean)
+ *   valid frame otherwise (first frame, or a jump: a new scene):
+ *     the frame's circle, conf = score
+ *   invalid frame with d > 0 and d >= t_hold:
+ *     the previous circle held (valid, score 0, n_inliers 0), conf = d
+ *   invalid frame otherwise: invalid, conf = 0 (state cleared).
+ * A valid output keeps the frame's score and n_inliers. */
+typedef struct {
+    float gamma;    /* decay of the confidence per frame, [0, 1) */
+    float jump;     /* scene-change distance, multiple of W */
+    float t_hold;   /* least decayed confidence that holds a circle */
+    int32_t pad;
+} orc_smooth_params;
+void orc_smooth(const orc_result *cur, int W, const orc_smooth_params *sp, float state[4],
+                orc_result *out);
+
 #ifdef __cplusplus
 }
 #endif
