@@ -319,6 +319,36 @@ ca_status ca_scorer_train(ca_handle *h, const uint8_t *strips_dev, const int32_t
                           const uint8_t *labels_dev, int n, int W, int H, const ca_train_params *tp,
                           int epochs, int batch, uint64_t seed, float *epoch_loss_host);
 
+/* Temporal smoothing of tracked results (an extension in the direction
+ * Sec. 4 points to: the estimates of earlier frames inform the current one).
+ * Per track a state {cx, cy, r, conf} (4 binary32 in state_dev, zero = none)
+ * is updated in binary32, each operation rounded on its own, in this order:
+ *   d = conf * gamma                            (the decayed confidence)
+ *   valid result, d > 0 and |cx - cx'|, |cy - cy'|, |r - r'| <= jump * W:
+ *     w = d + score;  c = (d * c' + score * c) / w for c in cx, cy, r;
+ *     conf = w                                  (confidence-weighted mean)
+ *   valid result otherwise (first frame, or a jump: a new scene): the
+ *     result's circle, conf = score
+ *   invalid result with d > 0 and d >= t_hold: the previous circle held
+ *     (valid, score 0, n_inliers 0), conf = d
+ *   invalid result otherwise: invalid, the state cleared.
+ * A valid output keeps the frame's score and n_inliers. */
+typedef struct ca_smooth_params {
+    float gamma;      /* confidence decay per frame, [0, 1); 0 = no memory */
+    float jump;       /* scene-change distance, multiple of W, >= 0 */
+    float t_hold;     /* least decayed confidence that holds a circle, >= 0 */
+    int32_t reserved; /* must be 0 */
+} ca_smooth_params;
+
+/* Smooths B results (res_dev, device) of frames of widths W[i] (host) on
+ * tracks track[i] (host, in [0, n_tracks), each at most once per call, or -1:
+ * passed through) into out_dev (device, may equal res_dev), updating
+ * state_dev (device, 4 x n_tracks floats).  Masks of the smoothed circles:
+ * ca_mask on out_dev.  Queued on `stream`. */
+ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const int32_t *W,
+                            const int32_t *track, int n_tracks, const ca_smooth_params *sp,
+                            float *state_dev, ca_result *out_dev, void *stream);
+
 /* ---- Serving (no counterpart in the paper, which estimates one frame at a
  * time): frames of many video streams under continuous batching.
  *
@@ -344,6 +374,10 @@ typedef struct ca_server_config {
     int32_t track;       /* 1: previous circle of each stream as an extra hypothesis */
     int32_t want_masks;  /* 1: write each frame's mask (copied to the host buffer
                             given at submit, if any) */
+    int32_t smooth;      /* 1 (with track): each stream's results are smoothed
+                            over time by ca_smooth_tracked with smooth_params
+                            before they and their masks are returned */
+    ca_smooth_params smooth_params;
 } ca_server_config;
 
 typedef struct ca_server_result {

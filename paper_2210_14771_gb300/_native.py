@@ -50,6 +50,11 @@ class CaTrainParams(C.Structure):
                 ("apply", C.c_int32), ("clip_norm", C.c_float), ("lr_schedule", C.c_int32)]
 
 
+class CaSmoothParams(C.Structure):
+    _fields_ = [("gamma", C.c_float), ("jump", C.c_float), ("t_hold", C.c_float),
+                ("reserved", C.c_int32)]
+
+
 class CaResult(C.Structure):
     _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("r", C.c_float), ("score", C.c_float),
                 ("valid", C.c_int32), ("n_inliers", C.c_int32)]
@@ -57,7 +62,8 @@ class CaResult(C.Structure):
 
 class CaServerConfig(C.Structure):
     _fields_ = [("params", CaParams), ("mem_budget", C.c_size_t), ("max_streams", C.c_int32),
-                ("max_batch", C.c_int32), ("track", C.c_int32), ("want_masks", C.c_int32)]
+                ("max_batch", C.c_int32), ("track", C.c_int32), ("want_masks", C.c_int32),
+                ("smooth", C.c_int32), ("smooth_params", CaSmoothParams)]
 
 
 class CaServerResult(C.Structure):
@@ -113,6 +119,9 @@ SIGNATURES = [
     ("ca_pool_free", C.c_int, [C.c_void_p, C.c_size_t]),
     ("ca_pool_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_size_t)]),
     ("ca_pool_destroy", C.c_int, [C.c_void_p]),
+    ("ca_smooth_tracked", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32),
+                                    _P(C.c_int32), C.c_int, _P(CaSmoothParams), C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     ("ca_mask", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32), _P(C.c_int32),
                           _P(C.c_void_p), C.c_void_p]),
     ("ca_run_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,

@@ -215,6 +215,25 @@ class ContentArea:
                                                   keys_arr, C.byref(p), C.c_void_p(res_ptr),
                                                   C.c_void_p(masks_ptr) if masks_ptr else None))
 
+    def smooth_tracked(self, res: torch.Tensor, widths, track, state: torch.Tensor, gamma: float,
+                       jump: float, t_hold: float, out: torch.Tensor | None = None, stream=None):
+        """ca_smooth_tracked: (B, 6) results (device) of frames of the given
+        widths on the given tracks -> smoothed results (device); state is the
+        (n_tracks, 4) float32 device state, updated."""
+        B = int(res.shape[0])
+        assert res.is_cuda and res.dtype == torch.float32 and res.shape == (B, 6)
+        assert state.is_cuda and state.dtype == torch.float32 and state.shape[1] == 4
+        out = res if out is None else out
+        sp = N.CaSmoothParams(gamma, jump, t_hold, 0)
+        W = (C.c_int32 * max(B, 1))(*[int(w) for w in widths])
+        T = (C.c_int32 * max(B, 1))(*[int(t) for t in track])
+        self._check(N.lib().ca_smooth_tracked(self._h, C.c_void_p(res.data_ptr()), B, W, T,
+                                              int(state.shape[0]), C.byref(sp),
+                                              C.c_void_p(state.data_ptr()),
+                                              C.c_void_p(out.data_ptr()),
+                                              _stream_ptr(stream, self.device)))
+        return out
+
     def sync(self, stream=None):
         self._check(N.lib().ca_sync(self._h, _stream_ptr(stream, self.device)))
 

@@ -1414,6 +1414,48 @@ ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const
                         track, state_dev);
 }
 
+ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const int32_t *W,
+                            const int32_t *track, int n_tracks, const ca_smooth_params *sp,
+                            float *state_dev, ca_result *out_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (B < 0 || n_tracks < 0) return fail(h, CA_ERR_INVALID_ARG, "B or n_tracks < 0");
+    if (B == 0) return CA_OK;
+    if (!res_dev || !W || !track || !sp || !state_dev || !out_dev)
+        return fail(h, CA_ERR_INVALID_ARG, "NULL argument to ca_smooth_tracked");
+    if (!std::isfinite(sp->gamma) || !std::isfinite(sp->jump) || !std::isfinite(sp->t_hold) ||
+        sp->gamma < 0.0f || sp->gamma >= 1.0f || sp->jump < 0.0f || sp->t_hold < 0.0f ||
+        sp->reserved != 0)
+        return fail(h, CA_ERR_INVALID_ARG, "bad smoothing parameters");
+    std::vector<int32_t> wt(2 * (size_t)B);
+    std::set<int32_t> seen;
+    for (int i = 0; i < B; ++i) {
+        if (W[i] < 1 || W[i] > kMaxDim) return fail(h, CA_ERR_INVALID_ARG, "frame %d: bad W", i);
+        if (track[i] < -1 || track[i] >= n_tracks)
+            return fail(h, CA_ERR_INVALID_ARG, "frame %d: track %d outside [-1, %d)", i,
+                        track[i], n_tracks);
+        if (track[i] >= 0 && !seen.insert(track[i]).second)
+            return fail(h, CA_ERR_INVALID_ARG, "track %d appears twice in one call", track[i]);
+        wt[2 * i] = W[i];
+        wt[2 * i + 1] = track[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    ca_status st = order_after_last(h, s);
+    if (st != CA_OK) return st;
+    Staging *sg;
+    const size_t bytes = sizeof(int32_t) * wt.size();
+    if ((st = take_staging(h, bytes, &sg)) != CA_OK) return st;
+    std::memcpy(sg->host, wt.data(), bytes);
+    CA_CUDA(h, cudaMemcpyAsync(sg->dev, sg->host, bytes, cudaMemcpyHostToDevice, s));
+    CA_CUDA(h, cudaEventRecord(sg->ev, s));
+    sg->used = true;
+    const cudaError_t e = launch_smooth(res_dev, B, (const int32_t *)sg->dev, sp->gamma, sp->jump,
+                                        sp->t_hold, state_dev, out_dev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_smooth launch");
+    h->launches += 1;
+    return mark_last(h, s);
+}
+
 ca_status ca_mask(ca_handle *h, const ca_result *res_dev, int B, const int32_t *H,
                   const int32_t *W, uint8_t *const *masks_dev, void *stream) {
     if (!h) return CA_ERR_INVALID_ARG;

@@ -185,6 +185,11 @@ cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_parti
                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
+// Temporal smoothing of B results (one thread per frame); w_trk: [B] pairs
+// (W, track) on the device.
+cudaError_t launch_smooth(const ca_result *res, int B, const int32_t *w_trk, float gamma,
+                          float jump, float t_hold, float *state, ca_result *out, cudaStream_t s);
+
 cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
                           const uint16_t *luts, CandSlot *slots, int grid, cudaStream_t s);
 cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const CandSlot *slots,

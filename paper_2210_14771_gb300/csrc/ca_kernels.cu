@@ -1335,4 +1335,60 @@ cudaError_t launch_batch(const DevFrame *frames, int B, const int32_t *rows, con
     }
 }
 
+// ============================================================= k_smooth ==
+// Temporal smoothing of tracked results, one thread per frame (the tracks of
+// a call are distinct, so no two threads share a state).  The order of the
+// binary32 operations is the one ca.h states.
+__global__ void k_smooth(const ca_result *res, int B, const int32_t *__restrict__ w_trk,
+                         float gamma, float jump, float t_hold, float *__restrict__ state,
+                         ca_result *out) {   // out may be res: thread i reads and writes row i
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const ca_result cur = res[i];
+    const int W = w_trk[2 * i], t = w_trk[2 * i + 1];
+    if (t < 0) {
+        out[i] = cur;
+        return;
+    }
+    float *st = state + 4 * (size_t)t;
+    const float s0 = st[0], s1 = st[1], s2 = st[2];
+    const float d = __fmul_rn(st[3], gamma);
+    ca_result o = cur;
+    if (cur.valid) {
+        const float J = __fmul_rn(jump, __int2float_rn(W));
+        const bool near = d > 0.0f && fabsf(__fsub_rn(cur.cx, s0)) <= J &&
+                          fabsf(__fsub_rn(cur.cy, s1)) <= J && fabsf(__fsub_rn(cur.r, s2)) <= J;
+        if (near) {
+            const float w = __fadd_rn(d, cur.score);
+            o.cx = __fdiv_rn(__fadd_rn(__fmul_rn(d, s0), __fmul_rn(cur.score, cur.cx)), w);
+            o.cy = __fdiv_rn(__fadd_rn(__fmul_rn(d, s1), __fmul_rn(cur.score, cur.cy)), w);
+            o.r = __fdiv_rn(__fadd_rn(__fmul_rn(d, s2), __fmul_rn(cur.score, cur.r)), w);
+            st[3] = w;
+        } else {
+            st[3] = cur.score;
+        }
+        st[0] = o.cx;
+        st[1] = o.cy;
+        st[2] = o.r;
+    } else if (d > 0.0f && d >= t_hold) {
+        o.cx = s0;
+        o.cy = s1;
+        o.r = s2;
+        o.score = 0.0f;
+        o.valid = 1;
+        o.n_inliers = 0;
+        st[3] = d;
+    } else {
+        st[0] = st[1] = st[2] = st[3] = 0.0f;
+    }
+    out[i] = o;
+}
+
+cudaError_t launch_smooth(const ca_result *res, int B, const int32_t *w_trk, float gamma,
+                          float jump, float t_hold, float *state, ca_result *out, cudaStream_t s) {
+    if (B <= 0) return cudaSuccess;
+    k_smooth<<<(B + 127) / 128, 128, 0, s>>>(res, B, w_trk, gamma, jump, t_hold, state, out);
+    return cudaGetLastError();
+}
+
 }  // namespace ca

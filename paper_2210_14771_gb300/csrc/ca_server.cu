@@ -14,6 +14,7 @@
 // estimated in submission order, so every result equals the one the frame
 // gets when its stream is served alone.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -102,6 +103,7 @@ struct Batch {
     std::vector<Request> reqs;
     cudaEvent_t done = nullptr;
     ca_result *res_dev = nullptr;    // max_batch results
+    ca_result *raw_dev = nullptr;    // max_batch results before smoothing (smooth only)
     ca_result *res_host = nullptr;   // pinned
     bool busy = false;
 };
@@ -119,6 +121,7 @@ struct ca_server {
     Pool pool;
     unsigned char *arena = nullptr;   // the device pool
     ca_result *state = nullptr;       // per stream: previous result
+    float *smooth_state = nullptr;    // per stream: smoothing state {cx, cy, r, conf}
     cudaStream_t copy = nullptr, compute = nullptr;
     cudaEvent_t copied = nullptr;     // last frame copy queued
     std::deque<Request> pending;      // admitted, not yet launched
@@ -213,9 +216,29 @@ ca_status launch(ca_server *s) {
             track[i] = s->cfg.track ? r.sid : -1;
         }
         SV_CUDA(cudaStreamWaitEvent(s->compute, s->copied, 0));
+        const bool smooth = s->smooth_state != nullptr;
+        if (smooth)   // masks follow the smoothed circles
+            for (int i = 0; i < B; ++i) fr[i].mask_dev = nullptr;
         ca_status st = ca_estimate_tracked(s->h, fr.data(), B, &s->cfg.params, s->state,
-                                           track.data(), s->cfg.max_streams, b.res_dev, s->compute);
+                                           track.data(), s->cfg.max_streams,
+                                           smooth ? b.raw_dev : b.res_dev, s->compute);
         if (st != CA_OK) return st;
+        if (smooth) {
+            std::vector<int32_t> Hs(B), Ws(B);
+            std::vector<uint8_t *> ms(B);
+            bool all_masks = true;
+            for (int i = 0; i < B; ++i) {
+                Hs[i] = b.reqs[i].H;
+                Ws[i] = b.reqs[i].W;
+                ms[i] = b.reqs[i].has_mask ? s->arena + b.reqs[i].mask_off : nullptr;
+                all_masks = all_masks && b.reqs[i].has_mask;
+            }
+            st = ca_smooth_tracked(s->h, b.raw_dev, B, Ws.data(), track.data(), s->cfg.max_streams,
+                                   &s->cfg.smooth_params, s->smooth_state, b.res_dev, s->compute);
+            if (st == CA_OK && all_masks)
+                st = ca_mask(s->h, b.res_dev, B, Hs.data(), Ws.data(), ms.data(), s->compute);
+            if (st != CA_OK) return st;
+        }
         SV_CUDA(cudaMemcpyAsync(b.res_host, b.res_dev, sizeof(ca_result) * B,
                                 cudaMemcpyDeviceToHost, s->compute));
         for (int i = 0; i < B; ++i)
@@ -238,6 +261,7 @@ void server_free(ca_server *s) {
     for (auto &b : s->batches) {
         if (b.done) cudaEventDestroy(b.done);
         cudaFree(b.res_dev);
+        cudaFree(b.raw_dev);
         if (b.res_host) cudaFreeHost(b.res_host);
     }
     if (s->copied) cudaEventDestroy(s->copied);
@@ -245,6 +269,7 @@ void server_free(ca_server *s) {
     if (s->compute) cudaStreamDestroy(s->compute);
     cudaFree(s->arena);
     cudaFree(s->state);
+    cudaFree(s->smooth_state);
     delete s;
 }
 
@@ -260,6 +285,14 @@ ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server 
     if (cfg->max_streams < 1 || cfg->max_streams > (1 << 20) || cfg->max_batch < 1 ||
         cfg->max_batch > 4096 || cfg->mem_budget < 4096)
         return CA_ERR_INVALID_ARG;
+    if (cfg->smooth != 0 && cfg->smooth != 1) return CA_ERR_INVALID_ARG;
+    if (cfg->smooth) {
+        const ca_smooth_params &sp = cfg->smooth_params;
+        if (!cfg->track || !std::isfinite(sp.gamma) || !std::isfinite(sp.jump) ||
+            !std::isfinite(sp.t_hold) || sp.gamma < 0.0f || sp.gamma >= 1.0f || sp.jump < 0.0f ||
+            sp.t_hold < 0.0f || sp.reserved != 0)
+            return CA_ERR_INVALID_ARG;
+    }
     ca_status st = ca::check_params(h, &cfg->params);
     if (st != CA_OK) return st;
     int dev = 0;
@@ -278,6 +311,12 @@ ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server 
     if ((e = cudaMalloc(&s->arena, cfg->mem_budget)) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&s->state, sizeof(ca_result) * cfg->max_streams)) != cudaSuccess) return bail(e);
     if ((e = cudaMemset(s->state, 0, sizeof(ca_result) * cfg->max_streams)) != cudaSuccess) return bail(e);
+    if (cfg->smooth) {
+        if ((e = cudaMalloc(&s->smooth_state, sizeof(float) * 4 * cfg->max_streams)) != cudaSuccess)
+            return bail(e);
+        if ((e = cudaMemset(s->smooth_state, 0, sizeof(float) * 4 * cfg->max_streams)) != cudaSuccess)
+            return bail(e);
+    }
     if ((e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
     if ((e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
     if ((e = cudaEventCreateWithFlags(&s->copied, cudaEventDisableTiming)) != cudaSuccess) return bail(e);
@@ -286,6 +325,9 @@ ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server 
     for (auto &b : s->batches) {
         if ((e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming)) != cudaSuccess) return bail(e);
         if ((e = cudaMalloc(&b.res_dev, sizeof(ca_result) * cfg->max_batch)) != cudaSuccess) return bail(e);
+        if (cfg->smooth &&
+            (e = cudaMalloc(&b.raw_dev, sizeof(ca_result) * cfg->max_batch)) != cudaSuccess)
+            return bail(e);
         if ((e = cudaMallocHost(&b.res_host, sizeof(ca_result) * cfg->max_batch)) != cudaSuccess)
             return bail(e);
     }

@@ -15,7 +15,10 @@ from .api import ContentArea, params as make_params
 
 class Server:
     def __init__(self, ca: ContentArea, p=None, mem_budget: int = 4 << 30, max_streams: int = 32,
-                 max_batch: int = 64, track: bool = True, want_masks: bool = False):
+                 max_batch: int = 64, track: bool = True, want_masks: bool = False,
+                 smooth=None):
+        """smooth: None, or (gamma, jump, t_hold) of ca_smooth_tracked applied to
+        each stream's results (and masks) before they are returned."""
         self.ca = ca
         cfg = N.CaServerConfig()
         cfg.params = p or make_params()
@@ -24,6 +27,10 @@ class Server:
         cfg.max_batch = max_batch
         cfg.track = 1 if track else 0
         cfg.want_masks = 1 if want_masks else 0
+        if smooth is not None:
+            cfg.smooth = 1
+            cfg.smooth_params = N.CaSmoothParams(float(smooth[0]), float(smooth[1]),
+                                                 float(smooth[2]), 0)
         h = C.c_void_p()
         ca._check(N.lib().ca_server_create(ca._h, C.byref(cfg), C.byref(h)))
         self._h = h

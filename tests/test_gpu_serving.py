@@ -167,3 +167,82 @@ def test_realtime_serving_latency(ca, streams):
     print("serving:", st)
     assert st["frames"] == 15 * len(streams)
     assert st["p99_ms"] < 20.0
+
+
+def _results_tensor(rows):
+    from paper_2210_14771_gb300 import api
+    a = np.zeros(len(rows), dtype=api.RESULT_DTYPE)
+    for i, r in enumerate(rows):
+        a[i] = tuple(r)
+    return torch.from_numpy(a.view(np.float32).reshape(len(rows), 6).copy()).cuda()
+
+
+def test_smooth_tracked_matches_oracle(ca, orc):
+    """ca_smooth_tracked on random result sequences of 6 tracks over 40 calls
+    (random subsets of tracks per call, random widths and validity, scene
+    jumps): every output and the final states equal the oracle's
+    orc_smooth applied to each track's sequence, bit for bit."""
+    from paper_2210_14771_gb300 import api
+    rng = np.random.default_rng(21)
+    n_tracks, gamma, jump, t_hold = 6, 0.8, 0.05, 0.06
+    widths = [int(w) for w in rng.choice([640, 720, 1280, 1920], n_tracks)]
+    state = torch.zeros((n_tracks, 4), dtype=torch.float32, device="cuda")
+    seqs = {t: [] for t in range(n_tracks)}
+    got = {t: [] for t in range(n_tracks)}
+    centre = rng.uniform(100, 500, (n_tracks, 3))
+    for _ in range(40):
+        tracks = [int(t) for t in rng.permutation(n_tracks)[:rng.integers(1, n_tracks + 1)]]
+        rows = []
+        for t in tracks:
+            if rng.random() < 0.1:                     # a new scene
+                centre[t] = rng.uniform(100, 500, 3)
+            c = centre[t] + rng.normal(0, 2.0, 3)
+            valid = int(rng.random() < 0.8)
+            rows.append((np.float32(c[0]), np.float32(c[1]), np.float32(c[2]),
+                         np.float32(rng.uniform(0.05, 1.0)) if valid else np.float32(0),
+                         valid, int(rng.integers(3, 60)) if valid else 0))
+        res = _results_tensor(rows)
+        out = ca.smooth_tracked(res, [widths[t] for t in tracks], tracks, state, gamma, jump,
+                                t_hold, out=torch.empty_like(res))
+        g = api.results_numpy(out)
+        for i, t in enumerate(tracks):
+            seqs[t].append(rows[i])
+            got[t].append(tuple(g[i]))
+    for t in range(n_tracks):
+        want, st = orc.smooth_chain(seqs[t], widths[t], gamma, jump, t_hold)
+        for a, b in zip(got[t], want):
+            assert _same(a, b), (t, a, b)
+        assert np.array_equal(state[t].cpu().numpy().view(np.uint32), st.view(np.uint32)), t
+
+
+def test_server_smoothing_matches_the_oracle_chain(ca, orc, streams):
+    """Served with smoothing: each frame's result is the oracle's tracked
+    estimate of the stream smoothed by orc_smooth, bit for bit, alone or in
+    the mix."""
+    from paper_2210_14771_gb300 import serve
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4)
+    banks = serve.pinned_banks(streams)
+    n, sm = 8, (0.75, 0.05, 0.06)
+    srv = serve.Server(ca, lp, mem_budget=1 << 30, max_streams=len(streams), max_batch=4,
+                       smooth=sm, want_masks=True)
+    recs, _ = serve.run_load(srv, streams, banks, n, realtime=False)
+    srv.close()
+    got = {(r["stream"], r["index"]): r["result"] for r in recs}
+    for s_id, s in enumerate(streams):
+        raw = _oracle_chain(orc, s, n, op)
+        want, _ = orc.smooth_chain(raw, s.W, *sm)
+        for k in range(n):
+            assert _same(got[(s_id, k)], want[k]), (s_id, k, got[(s_id, k)], want[k])
+
+
+def test_smooth_argument_errors(ca):
+    from paper_2210_14771_gb300 import _native as N
+    res = _results_tensor([(1.0, 2.0, 3.0, 0.5, 1, 4)] * 2)
+    state = torch.zeros((2, 4), dtype=torch.float32, device="cuda")
+    for kw, tr in ((dict(gamma=1.0), [0, 1]), (dict(gamma=0.5, jump=-1.0), [0, 1]),
+                   (dict(gamma=0.5), [0, 0]), (dict(gamma=0.5), [0, 2])):
+        args = dict(gamma=0.5, jump=0.05, t_hold=0.06)
+        args.update(kw)
+        with pytest.raises(N.CaError) as e:
+            ca.smooth_tracked(res, [64, 64], tr, state, **args)
+        assert e.value.status == 1, (kw, tr)
