@@ -79,6 +79,21 @@ def lib():
         L.orc_smooth.argtypes = [P(OrcResult), C.c_int, P(OrcSmoothParams), C.c_void_p,
                                  P(OrcResult)]
         L.orc_smooth.restype = None
+        L.orc_sc2_offsets.argtypes = [C.c_void_p]
+        L.orc_sc2_offsets.restype = None
+        L.orc_sc2_strip.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_int, C.c_void_p,
+                                    C.c_void_p]
+        L.orc_sc2_strip.restype = None
+        L.orc_sc2_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        L.orc_sc2_features.restype = None
+        L.orc_sc2_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                      C.c_void_p]
+        L.orc_sc2_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+        L.orc_sc2_loss_grad.restype = C.c_double
+        L.orc_sc2_targets.argtypes = [C.c_float, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int,
+                                      C.c_double, C.c_void_p]
+        L.orc_sc2_targets.restype = None
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
         L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
@@ -421,3 +436,63 @@ def smooth_chain(results, W, gamma, jump, t_hold, state=None):
         out.append(dict(cx=o.cx, cy=o.cy, r=o.r, score=o.score, valid=o.valid,
                         n_inliers=o.n_inliers))
     return out, st
+
+
+# ---- the paper's 2-D learned scorer (ca_scorer2d_oracle.c)
+SC2_NPARAM = 6209
+
+
+def sc2_offsets():
+    o = np.zeros(8, np.int32)
+    lib().orc_sc2_offsets(_ptr(o))
+    keys = ("W1", "b1", "W2", "b2", "W3", "b3", "wh", "bh")
+    return {k: int(v) for k, v in zip(keys, o)}
+
+
+def sc2_strip(frame, y):
+    """(rgb7 (7, W, 3) uint8, rows (7,) int32) of the strip centred on row y."""
+    f = _frame(frame)
+    H, W = f.shape[:2]
+    rgb7 = np.zeros((7, W, 3), np.uint8)
+    rows = np.zeros(7, np.int32)
+    lib().orc_sc2_strip(_ptr(f), H, W, W * 3, int(y), _ptr(rgb7), _ptr(rows))
+    return rgb7, rows
+
+
+def sc2_features(rgb7, rows, H):
+    rgb7 = np.ascontiguousarray(rgb7, np.uint8)
+    W = rgb7.shape[1]
+    feat = np.zeros((7, W, 5), np.float64)
+    lib().orc_sc2_features(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
+                           _ptr(feat))
+    return feat
+
+
+def sc2_forward(rgb7, rows, H, params):
+    rgb7 = np.ascontiguousarray(rgb7, np.uint8)
+    W = rgb7.shape[1]
+    prm = np.ascontiguousarray(params, np.float32)
+    assert prm.size == SC2_NPARAM
+    out = np.zeros(W, np.float64)
+    if lib().orc_sc2_forward(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
+                             _ptr(prm), _ptr(out)) != 0:
+        raise ValueError("bad scorer arguments")
+    return out
+
+
+def sc2_loss_grad(rgb7, rows, H, targets, params):
+    rgb7 = np.ascontiguousarray(rgb7, np.uint8)
+    W = rgb7.shape[1]
+    prm = np.ascontiguousarray(params, np.float32)
+    t = np.ascontiguousarray(targets, np.float64)
+    g = np.zeros(SC2_NPARAM, np.float64)
+    loss = lib().orc_sc2_loss_grad(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
+                                   _ptr(t), _ptr(prm), _ptr(g))
+    return loss, g
+
+
+def sc2_targets(cx, cy, r, valid, W, y, sigma=3.0):
+    t = np.zeros(W, np.float64)
+    lib().orc_sc2_targets(float(cx), float(cy), float(r), int(valid), int(W), int(y),
+                          float(sigma), _ptr(t))
+    return t

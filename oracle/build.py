@@ -9,6 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ca_oracle.c")
 SRC_SC = os.path.join(HERE, "ca_scorer_oracle.c")
+SRC_SC2 = os.path.join(HERE, "ca_scorer2d_oracle.c")
 HDR = os.path.join(HERE, "ca_oracle.h")
 LIB = os.path.join(HERE, "libca_oracle.so")
 
@@ -31,11 +32,11 @@ def _native_elf(path: str) -> bool:
 
 def build(force: bool = False) -> str:
     stale = force or not os.path.exists(LIB) or not _native_elf(LIB) or any(
-        os.path.getmtime(f) > os.path.getmtime(LIB) for f in (SRC, SRC_SC, HDR, __file__))
+        os.path.getmtime(f) > os.path.getmtime(LIB) for f in (SRC, SRC_SC, SRC_SC2, HDR, __file__))
     if stale:
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-Wall", "-o", tmp, SRC, SRC_SC, "-lm"]
+               "-fno-fast-math", "-Wall", "-o", tmp, SRC, SRC_SC, SRC_SC2, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB

@@ -177,6 +177,32 @@ int orc_sc_forward(const uint8_t *rgb3, int W, int y, int H, const float *prm, i
 double orc_sc_loss_grad(const uint8_t *rgb3, int W, int y, int H, const uint8_t *labels,
                         float pos_weight, const float *prm, int mode, double *grads);
 
+/* ---- The paper's own learned edge scorer (Sec. 2.2.4; see
+ * ca_scorer2d_oracle.c): 3x3 convolutions to 8, 16, 32 features with ReLU,
+ * a 1x1 head and a sigmoid, on RGBXY strips 7 rows high.  Parameters: one
+ * flat binary32 vector of ORC_SC2_NPARAM values, W1[8][5][3][3], b1[8],
+ * W2[16][8][3][3], b2[16], W3[32][16][3][3], b3[32], wh[32], bh. */
+enum { ORC_SC2_CIN = 5, ORC_SC2_NPARAM = 6209 };
+
+void orc_sc2_offsets(int32_t out[8]);
+/* The 7 rows y-3 .. y+3 of a frame (clamped into it) into rgb7 (7 x W x 3),
+ * their frame rows into rows. */
+void orc_sc2_strip(const uint8_t *rgb, int H, int W, int64_t pitch, int y, uint8_t *rgb7,
+                   int32_t rows[7]);
+/* RGBXY features of the 7 x W pixels, feat[(k W + x) 5 + c]. */
+void orc_sc2_features(const uint8_t *rgb7, const int32_t rows[7], int W, int H, double *feat);
+/* Logits of the strip's middle row (W values). */
+int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, const float *prm,
+                    double *logits);
+/* Summed soft binary cross-entropy against targets in [0, 1], gradient added
+ * into grads (ORC_SC2_NPARAM doubles). */
+double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
+                         const double *targets, const float *prm, double *grads);
+/* Soft targets of row y: exp(-d^2 / (2 sigma^2)), d the distance of the
+ * pixel to the circle; 0 without a circle. */
+void orc_sc2_targets(float cx, float cy, float r, int valid, int W, int y, double sigma,
+                     double *t);
+
 /* orc_fit with the previous frame's circle (cx, cy, r in pixel coordinates)
  * as one more hypothesis, index n_hyps (Sec. 4: using the previous
  * estimate); prior == NULL is orc_fit. */
