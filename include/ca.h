@@ -349,6 +349,21 @@ ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const
                             const int32_t *track, int n_tracks, const ca_smooth_params *sp,
                             float *state_dev, ca_result *out_dev, void *stream);
 
+/* The paper's own learned edge scorer (Sec. 2.2.4): three 3x3 convolutions
+ * to 8, 16 and 32 features with ReLU, a 1x1 head, on RGBXY strips 7 rows
+ * high (unpadded vertically: the logits are those of the strip's middle row;
+ * zero-padded horizontally).  Features: R, G, B as (v - 128) / 128, then
+ * (x - (W-1)/2) / W and (row - (H-1)/2) / H.  Parameters: CA_SCORER2D_NPARAM
+ * binary32 values in device memory, W1[8][5][3][3], b1[8], W2[16][8][3][3],
+ * b2[16], W3[32][16][3][3], b3[32], wh[32], bh.  strips7_dev: n x 7 x W x 3
+ * bytes (rows y-3 .. y+3 of each strip, packed RGB); rows_dev: n x 7 frame
+ * rows of those rows; logits_dev: n x W.  Binary32 on the CUDA cores.
+ * Queued on `stream`. */
+#define CA_SCORER2D_NPARAM 6209
+ca_status ca_scorer2d_forward(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                              int n, int W, int H, const float *params_dev, float *logits_dev,
+                              void *stream);
+
 /* ---- Serving (no counterpart in the paper, which estimates one frame at a
  * time): frames of many video streams under continuous batching.
  *

@@ -16,6 +16,7 @@ CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
 CA_DUMP_LEARNED = 4
 CA_DUMP_TRACE = 5
 CA_SCORER_NPARAM = 17601
+CA_SCORER2D_NPARAM = 6209
 CA_LR_CONSTANT, CA_LR_COSINE = 0, 1
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
 
@@ -119,6 +120,8 @@ SIGNATURES = [
     ("ca_pool_free", C.c_int, [C.c_void_p, C.c_size_t]),
     ("ca_pool_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_size_t)]),
     ("ca_pool_destroy", C.c_int, [C.c_void_p]),
+    ("ca_scorer2d_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("ca_smooth_tracked", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32),
                                     _P(C.c_int32), C.c_int, _P(CaSmoothParams), C.c_void_p,
                                     C.c_void_p, C.c_void_p]),

@@ -215,6 +215,23 @@ class ContentArea:
                                                   keys_arr, C.byref(p), C.c_void_p(res_ptr),
                                                   C.c_void_p(masks_ptr) if masks_ptr else None))
 
+    def scorer2d_forward(self, strips7: torch.Tensor, rows: torch.Tensor, H: int,
+                         params: torch.Tensor, stream=None) -> torch.Tensor:
+        """ca_scorer2d_forward: logits (n, W) of the middle rows of n strips
+        (n, 7, W, 3) uint8 with their frame rows (n, 7) int32 and the 2-D
+        network's parameters (CA_SCORER2D_NPARAM float32), all on the device."""
+        assert strips7.dtype == torch.uint8 and strips7.is_cuda and strips7.is_contiguous()
+        assert strips7.dim() == 4 and strips7.shape[1] == 7 and strips7.shape[3] == 3
+        n, W = int(strips7.shape[0]), int(strips7.shape[2])
+        assert rows.dtype == torch.int32 and rows.is_cuda and rows.shape == (n, 7)
+        assert params.dtype == torch.float32 and params.is_cuda and params.numel() == N.CA_SCORER2D_NPARAM
+        out = torch.empty((n, W), dtype=torch.float32, device=strips7.device)
+        self._check(N.lib().ca_scorer2d_forward(
+            self._h, C.c_void_p(strips7.data_ptr()), C.c_void_p(rows.contiguous().data_ptr()), n,
+            W, H, C.c_void_p(params.contiguous().data_ptr()), C.c_void_p(out.data_ptr()),
+            _stream_ptr(stream, strips7.device)))
+        return out
+
     def smooth_tracked(self, res: torch.Tensor, widths, track, state: torch.Tensor, gamma: float,
                        jump: float, t_hold: float, out: torch.Tensor | None = None, stream=None):
         """ca_smooth_tracked: (B, 6) results (device) of frames of the given

@@ -1414,6 +1414,26 @@ ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const
                         track, state_dev);
 }
 
+ca_status ca_scorer2d_forward(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                              int n, int W, int H, const float *params_dev, float *logits_dev,
+                              void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (n < 0 || W < 1 || W > kMaxDim || H < 1 || H > kMaxDim)
+        return fail(h, CA_ERR_INVALID_ARG, "bad strip set (n %d, W %d, H %d)", n, W, H);
+    if (n == 0) return CA_OK;
+    if (!strips7_dev || !rows_dev || !params_dev || !logits_dev)
+        return fail(h, CA_ERR_INVALID_ARG, "NULL argument to ca_scorer2d_forward");
+    cudaStream_t s = (cudaStream_t)stream;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    ca_status st = order_after_last(h, s);
+    if (st != CA_OK) return st;
+    const cudaError_t e = sc2_launch_forward(strips7_dev, rows_dev, n, W, H, params_dev,
+                                             logits_dev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_forward launch");
+    h->launches += 1;
+    return mark_last(h, s);
+}
+
 ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const int32_t *W,
                             const int32_t *track, int n_tracks, const ca_smooth_params *sp,
                             float *state_dev, ca_result *out_dev, void *stream) {

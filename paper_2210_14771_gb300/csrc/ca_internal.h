@@ -185,6 +185,11 @@ cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_parti
                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
+// The paper's 2-D scorer (Sec. 2.2.4): forward pass on n strips of 7 rows.
+constexpr int kScorer2dNParam = 6209;
+cudaError_t sc2_launch_forward(const uint8_t *strips7, const int32_t *rows, int n, int W, int H,
+                               const float *params, float *logits, cudaStream_t s);
+
 // Temporal smoothing of B results (one thread per frame); w_trk: [B] pairs
 // (W, track) on the device.
 cudaError_t launch_smooth(const ca_result *res, int B, const int32_t *w_trk, float gamma,
