@@ -88,6 +88,8 @@ def lib():
         L.orc_sc2_features.restype = None
         L.orc_sc2_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                       C.c_void_p]
+        L.orc_sc2_forward_mode.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_int, C.c_void_p]
         L.orc_sc2_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
         L.orc_sc2_loss_grad.restype = C.c_double
@@ -468,14 +470,14 @@ def sc2_features(rgb7, rows, H):
     return feat
 
 
-def sc2_forward(rgb7, rows, H, params):
+def sc2_forward(rgb7, rows, H, params, mixed=False):
     rgb7 = np.ascontiguousarray(rgb7, np.uint8)
     W = rgb7.shape[1]
     prm = np.ascontiguousarray(params, np.float32)
     assert prm.size == SC2_NPARAM
     out = np.zeros(W, np.float64)
-    if lib().orc_sc2_forward(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
-                             _ptr(prm), _ptr(out)) != 0:
+    if lib().orc_sc2_forward_mode(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
+                                  _ptr(prm), 1 if mixed else 0, _ptr(out)) != 0:
         raise ValueError("bad scorer arguments")
     return out
 

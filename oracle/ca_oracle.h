@@ -194,6 +194,10 @@ void orc_sc2_features(const uint8_t *rgb7, const int32_t rows[7], int W, int H, 
 /* Logits of the strip's middle row (W values). */
 int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, const float *prm,
                     double *logits);
+/* The same with a mode: ORC_SC_EXACT (= orc_sc2_forward) or ORC_SC_MIXED
+ * (the roundings of a bfloat16 tensor-core kernel, see the source). */
+int orc_sc2_forward_mode(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
+                         const float *prm, int mode, double *logits);
 /* Summed soft binary cross-entropy against targets in [0, 1], gradient added
  * into grads (ORC_SC2_NPARAM doubles). */
 double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int H,

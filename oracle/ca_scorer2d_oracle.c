@@ -12,8 +12,14 @@
  * convolution is "same" with zero padding.  Training uses the soft binary
  * cross-entropy against an edge map blurred with a Gaussian of sigma 3.
  *
- * Everything here is binary64 with no rounding (the exact network), whose
- * gradient the tests pin by finite differences.
+ * Two modes for the forward pass, as for the 1-D scorer:
+ *   ORC_SC_EXACT  binary64 with no rounding (the exact network), whose
+ *                 gradient the tests pin by finite differences;
+ *   ORC_SC_MIXED  rounded where a tensor-core kernel stores a narrower
+ *                 value: features, weights and activations in bfloat16,
+ *                 each convolution sum rounded once to binary32 and the bias
+ *                 added in binary32, the head summed in binary32 in channel
+ *                 order over bfloat16 head weights.
  *
  * Readings where the paper is silent:
  *   - colour features are (v - 128) / 128 (the paper normalises by its
@@ -80,31 +86,38 @@ void orc_sc2_features(const uint8_t *rgb7, const int32_t rows[7], int W, int H, 
         }
 }
 
+static float bf16_of(double v) { return orc_bf16((float)v); }
+
 /* One 3x3 convolution + ReLU: in rows_in x W x cin -> (rows_in - 2) x W x cout;
- * pre (optional) receives the pre-activations. */
-static void conv3x3(const double *in, int rows_in, int W, int cin, int cout, const float *w,
-                    const float *b, double *out, double *pre) {
+ * pre (optional) receives the pre-activations; mixed: ORC_SC_MIXED roundings. */
+static void conv3x3_mode(const double *in, int rows_in, int W, int cin, int cout, const float *w,
+                         const float *b, int mixed, double *out, double *pre) {
     const int ro = rows_in - 2;
     for (int r = 0; r < ro; ++r)
         for (int x = 0; x < W; ++x)
             for (int co = 0; co < cout; ++co) {
-                double z = b[co];
+                double s = 0.0;
                 for (int ci = 0; ci < cin; ++ci)
                     for (int dr = 0; dr < 3; ++dr)
                         for (int dx = 0; dx < 3; ++dx) {
                             const int xx = x + dx - 1;
                             if (xx < 0 || xx >= W) continue;
-                            z += (double)w[((co * cin + ci) * 3 + dr) * 3 + dx] *
+                            const float wv = w[((co * cin + ci) * 3 + dr) * 3 + dx];
+                            s += (mixed ? (double)orc_bf16(wv) : (double)wv) *
                                  in[((size_t)(r + dr) * W + xx) * cin + ci];
                         }
+                const double z = mixed ? (double)((float)s + b[co]) : s + (double)b[co];
                 if (pre) pre[((size_t)r * W + x) * cout + co] = z;
-                out[((size_t)r * W + x) * cout + co] = z > 0.0 ? z : 0.0;
+                const double a = z > 0.0 ? z : 0.0;
+                out[((size_t)r * W + x) * cout + co] = mixed ? (double)bf16_of(a) : a;
             }
 }
 
-int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, const float *prm,
-                    double *logits) {
-    if (W < 1 || !rgb7 || !prm || !logits) return -1;
+int orc_sc2_forward_mode(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
+                         const float *prm, int mode, double *logits) {
+    if (W < 1 || !rgb7 || !prm || !logits || (mode != ORC_SC_EXACT && mode != ORC_SC_MIXED))
+        return -1;
+    const int mixed = mode == ORC_SC_MIXED;
     int32_t off[8];
     orc_sc2_offsets(off);
     double *a[NL + 1];
@@ -112,16 +125,37 @@ int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, co
     for (int l = 0; l < NL; ++l)
         a[l + 1] = (double *)malloc(sizeof(double) * (size_t)(ROWS_IN[l] - 2) * W * COUT[l]);
     orc_sc2_features(rgb7, rows, W, H, a[0]);
+    if (mixed)   /* the kernel's features: X and Y in binary32, then bfloat16 */
+        for (int k = 0; k < 7; ++k)
+            for (int x = 0; x < W; ++x) {
+                double *f = a[0] + ((size_t)k * W + x) * CIN;
+                const float xf = ((float)x - 0.5f * (float)(W - 1)) / (float)W;
+                const float yf = ((float)rows[k] - 0.5f * (float)(H - 1)) / (float)H;
+                f[3] = orc_bf16(xf);
+                f[4] = orc_bf16(yf);
+            }
     for (int l = 0; l < NL; ++l)
-        conv3x3(a[l], ROWS_IN[l], W, CINL[l], COUT[l], prm + off[2 * l], prm + off[2 * l + 1],
-                a[l + 1], NULL);
+        conv3x3_mode(a[l], ROWS_IN[l], W, CINL[l], COUT[l], prm + off[2 * l],
+                     prm + off[2 * l + 1], mixed, a[l + 1], NULL);
     for (int x = 0; x < W; ++x) {
-        double z = prm[off[7]];
-        for (int c = 0; c < 32; ++c) z += (double)prm[off[6] + c] * a[NL][(size_t)x * 32 + c];
-        logits[x] = z;
+        if (mixed) {
+            float acc = 0.0f;
+            for (int c = 0; c < 32; ++c)
+                acc = acc + orc_bf16(prm[off[6] + c]) * (float)a[NL][(size_t)x * 32 + c];
+            logits[x] = (double)(prm[off[7]] + acc);
+        } else {
+            double z = prm[off[7]];
+            for (int c = 0; c < 32; ++c) z += (double)prm[off[6] + c] * a[NL][(size_t)x * 32 + c];
+            logits[x] = z;
+        }
     }
     for (int l = 0; l <= NL; ++l) free(a[l]);
     return 0;
+}
+
+int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, const float *prm,
+                    double *logits) {
+    return orc_sc2_forward_mode(rgb7, rows, W, H, prm, ORC_SC_EXACT, logits);
 }
 
 /* Soft binary cross-entropy of the W columns against targets t in [0, 1],
@@ -139,8 +173,8 @@ double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int 
     }
     orc_sc2_features(rgb7, rows, W, H, a[0]);
     for (int l = 0; l < NL; ++l)
-        conv3x3(a[l], ROWS_IN[l], W, CINL[l], COUT[l], prm + off[2 * l], prm + off[2 * l + 1],
-                a[l + 1], pre[l]);
+        conv3x3_mode(a[l], ROWS_IN[l], W, CINL[l], COUT[l], prm + off[2 * l],
+                     prm + off[2 * l + 1], 0, a[l + 1], pre[l]);
     /* head, loss and dL/da3 */
     double loss = 0.0;
     double *g = (double *)calloc((size_t)W * 32, sizeof(double));   /* dL/d(layer output) */

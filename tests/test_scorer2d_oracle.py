@@ -114,3 +114,32 @@ def test_soft_targets():
     assert t[28] == pytest.approx(math.exp(-0.5), rel=1e-12)   # 3 px inside: d = sigma
     assert np.all(t >= 0) and np.all(t <= 1)
     assert not np.any(orc.sc2_targets(30.0, 10.0, 5.0, 0, 64, y, 3.0))
+
+
+def test_mixed_mode_is_exact_when_nothing_rounds():
+    """The hand-set identity network moves bfloat16-exact colours (k / 128)
+    through bfloat16-exact unit weights: the mixed mode equals the exact one."""
+    f, (rgb7, rows) = _strip(13)
+    p = np.zeros(orc.SC2_NPARAM, np.float32)
+    o = orc.sc2_offsets()
+    p[o["W1"] + ((0 * 5 + 1) * 3 + 1) * 3 + 1] = 1.0     # green channel this time
+    p[o["W2"] + ((0 * 8 + 0) * 3 + 1) * 3 + 1] = 1.0
+    p[o["W3"] + ((0 * 16 + 0) * 3 + 1) * 3 + 1] = 1.0
+    p[o["wh"]] = 1.0
+    a = orc.sc2_forward(rgb7, rows, H, p)
+    b = orc.sc2_forward(rgb7, rows, H, p, mixed=True)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, np.maximum(0.0, (f[20, :, 1].astype(np.float64) - 128) / 128))
+
+
+def test_mixed_mode_within_the_bfloat16_bound():
+    """Random networks: bfloat16 weights, features and activations move a
+    logit by a few 2^-8 relative steps of the magnitudes it sums; the mode
+    stays within 0.05 (1 + |logit|) of the exact network and is not equal to it."""
+    _, (rgb7, rows) = _strip(14)
+    for seed in range(3):
+        p = _params(15 + seed, scale=0.2)
+        a = orc.sc2_forward(rgb7, rows, H, p)
+        b = orc.sc2_forward(rgb7, rows, H, p, mixed=True)
+        assert np.all(np.abs(a - b) <= 0.05 * (1.0 + np.abs(a)))
+        assert not np.array_equal(a, b)
