@@ -71,3 +71,26 @@ def test_budget_refuses_the_frame_that_does_not_fit(L):
         n += 1
     assert n == (4 << 30) // ((frame_4k + 255) // 256 * 256)
     L.lib().ca_pool_destroy(h)
+
+
+def test_latency_summary_splits_into_feed_queue_and_gpu():
+    """serve.summarise on hand-made records: percentiles of arrival-to-result
+    latency and of its three parts, which add up per frame."""
+    from paper_2210_14771_gb300 import serve
+    recs = []
+    for i in range(100):
+        a = 10.0 + i * 0.01
+        s_ = a + 0.001 * (i % 3)               # feeding delay 0-2 ms
+        l_ = s_ + 0.0005                       # 0.5 ms queued
+        d_ = l_ + 0.002 + (0.050 if i == 99 else 0.0)   # 2 ms of work, one 50 ms stall
+        recs.append(dict(t_arrival=a, t_submit=s_, t_launch=l_, t_done=d_, latency=d_ - a))
+    st = serve.summarise(recs, 2.0)
+    assert st["frames"] == 100 and st["frames_per_s"] == 50.0
+    assert st["over_10ms"] == 1 and abs(st["max_ms"] - 52.5) < 1e-6
+    assert abs(st["p50_ms"] - 3.5) < 1e-6
+    assert abs(st["p99_queue_ms"] - 0.5) < 1e-6
+    assert abs(st["p99_feed_ms"] - 2.0) < 1e-6
+    for r in recs:
+        parts = (r["t_submit"] - r["t_arrival"]) + (r["t_launch"] - r["t_submit"]) + \
+            (r["t_done"] - r["t_launch"])
+        assert abs(parts - r["latency"]) < 1e-12
