@@ -159,51 +159,105 @@ ca_status cuda_fail(ca_handle *h, cudaError_t e, const char *what) {
 namespace ca {
 
 // ------------------------------------------------------------ tables --
-// Eq. 1 strip rows, floored and clamped to [1, H-2].
+// The tables are built here from the inverse functions: every entry is the
+// number of Q15 levels whose threshold it reaches.  For a score v in [0, 1],
+// round(32768 v) (halves up) = #{k in 1..32768 : v >= (k - 1/2) / 32768}, so
+// with the threshold of level k mapped back through the inverse of the
+// soft-threshold function an entry is a count over a sorted threshold list.
+
+namespace {
+
+constexpr int kQ15Levels = 32768;
+
+// Level boundary (k - 1/2) / 32768 of Q15 level k.
+inline double level_edge(int k) { return ((double)k - 0.5) / (double)kQ15Levels; }
+
+// #{k : thr[k] <= x} for non-decreasing thr.
+inline int count_reached(const std::vector<double> &thr, double x) {
+    return (int)(std::upper_bound(thr.begin(), thr.end(), x) - thr.begin());
+}
+
+}  // namespace
+
+// Eq. 1 strip rows: row i is floor(h_i), h_i = H / (1 + exp(-s_i)) with
+// s_i = (alpha / N)(i - (N-1)/2), clamped to [1, H-2].  For 0 < v < H,
+// h_i >= v  <=>  log(v / (H - v)) <= s_i, and the left side increases with v,
+// so the row is the largest v of [1, H-2] whose log-odds do not exceed s_i
+// (a bisection; 1 when even v = 1 exceeds it).
 void strip_rows(int H, int N, float alpha, int32_t *rows) {
+    const double slope = (double)alpha / (double)N;
+    auto log_odds = [H](int v) { return std::log((double)v / (double)(H - v)); };
     for (int i = 0; i < N; ++i) {
-        const double t = (double)alpha / (double)N;
-        const double u = (double)i - (double)(N - 1) / 2.0;
-        const double e = std::exp(-(t * u));
-        const double hv = (double)H / (1.0 + e);
-        long v = (long)std::floor(hv);
-        v = std::max(1L, std::min(v, (long)H - 2));
-        rows[i] = (int32_t)v;
+        const double s = slope * ((double)i - 0.5 * (double)(N - 1));
+        int lo = 1, hi = H - 2;   // invariant: the answer lies in [lo, hi]
+        if (log_odds(lo) > s) {
+            rows[i] = 1;
+            continue;
+        }
+        while (lo < hi) {
+            const int mid = lo + (hi - lo + 1) / 2;
+            if (log_odds(mid) <= s) lo = mid;
+            else hi = mid - 1;
+        }
+        rows[i] = lo;
     }
 }
 
-uint16_t to_q15(double v) {
-    double x = std::floor(32768.0 * v + 0.5);
-    x = std::max(0.0, std::min(x, 32768.0));
-    return (uint16_t)x;
-}
-
-// Soft-threshold tables of Eq. 2: s_g at quarter steps of |g|, s_theta at the
-// centres of 8192 bins of the signed squared cosine cos|cos|, s_iota at every
-// 8-bit intensity.
+// Soft-threshold tables of Eq. 2, one Q15 entry per index:
+//   s_g      at |g| = q / 4 (divided by sobel_norm): level k is reached from
+//            q >= 4 sobel_norm t_g atanh(edge_k);
+//   s_theta  at bin q of the signed squared cosine u = cos|cos| (bin centre
+//            (q + 1/2) / 4096 - 1, capped at 1): level k needs
+//            theta <= t_theta atanh(1 - edge_k) degrees, i.e. cos theta >=
+//            cos of that angle, i.e. u >= the signed square of that cosine
+//            (every u when the angle reaches 180 degrees);
+//   s_iota   at every 8-bit iota: level k needs iota <= t_iota atanh(1 - edge_k).
+// *qg_sat: the first index from which s_g keeps its last value (the kernels
+// clamp their index there).
 void build_luts(const ca_params &p, uint16_t *out, int *qg_sat) {
     uint16_t *lg = out, *lt = out + kLutG, *li = out + kLutG + kLutT;
-    for (int q = 0; q < kLutG; ++q)
-        lg[q] = to_q15(std::tanh(((double)q * 0.25) / ((double)p.sobel_norm * (double)p.t_g)));
-    for (int q = 0; q < kLutT; ++q) {
-        double u = ((double)q + 0.5) / 4096.0 - 1.0;
-        if (u > 1.0) u = 1.0;
-        const double c = u < 0.0 ? -std::sqrt(-u) : std::sqrt(u);
-        const double deg = std::acos(c) * (180.0 / 3.14159265358979323846);
-        lt[q] = to_q15(1.0 - std::tanh(deg / (double)p.t_theta_deg));
+    const double kPi = 3.14159265358979323846;
+    std::vector<double> thr((size_t)kQ15Levels);
+    // s_g: thresholds in units of q, increasing with k
+    const double gscale = 4.0 * (double)p.sobel_norm * (double)p.t_g;
+    for (int k = 1; k <= kQ15Levels; ++k) thr[k - 1] = gscale * std::atanh(level_edge(k));
+    for (int q = 0; q < kLutG; ++q) lg[q] = (uint16_t)count_reached(thr, (double)q);
+    // s_theta: thresholds on u, increasing with k (the angle bound shrinks)
+    for (int k = 1; k <= kQ15Levels; ++k) {
+        const double deg = (double)p.t_theta_deg * std::atanh(1.0 - level_edge(k));
+        if (deg >= 180.0) {
+            thr[k - 1] = -HUGE_VAL;
+            continue;
+        }
+        const double c = std::cos(deg * (kPi / 180.0));
+        thr[k - 1] = c >= 0.0 ? c * c : -(c * c);
     }
-    for (int v = 0; v < kLutI; ++v) li[v] = to_q15(1.0 - std::tanh((double)v / (double)p.t_iota));
-    // index from which s_g stays constant (the kernels clamp there)
-    int s = kLutG - 1;
-    while (s > 0 && lg[s - 1] == lg[kLutG - 1]) --s;
-    *qg_sat = s;
+    for (int q = 0; q < kLutT; ++q) {
+        const double u = std::min(((double)q + 0.5) / 4096.0 - 1.0, 1.0);
+        lt[q] = (uint16_t)count_reached(thr, u);
+    }
+    // s_iota: a level is reached while iota stays at or below its bound; the
+    // bounds decrease with k, so count them from the top as negatives
+    for (int k = 1; k <= kQ15Levels; ++k)
+        thr[k - 1] = -((double)p.t_iota * std::atanh(1.0 - level_edge(k)));
+    for (int v = 0; v < kLutI; ++v) li[v] = (uint16_t)count_reached(thr, -(double)v);
+    *qg_sat = (int)(std::lower_bound(lg, lg + kLutG, lg[kLutG - 1]) - lg);
 }
 
+// floor(sqrt(n)) for n >= 0 by the binary digit-by-digit method (integers only).
 static int64_t isqrt_floor(int64_t n) {
-    int64_t r = (int64_t)std::sqrt((double)n);
-    while (r > 0 && r * r > n) --r;
-    while ((r + 1) * (r + 1) <= n) ++r;
-    return r;
+    uint64_t rem = (uint64_t)n, root = 0, bit = 1ull << 62;
+    while (bit > rem) bit >>= 2;
+    while (bit != 0) {
+        if (rem >= root + bit) {
+            rem -= root + bit;
+            root = (root >> 1) + bit;
+        } else {
+            root >>= 1;
+        }
+        bit >>= 2;
+    }
+    return (int64_t)root;
 }
 
 void pack_device_tables(const uint16_t *luts, int qg_sat, uint16_t *out) {

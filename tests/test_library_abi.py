@@ -118,6 +118,24 @@ def test_library_tables_equal_oracle(native, orc, kw, H):
     assert (rows == orc.strip_rows(H, p.n_strips, p.alpha)).all()
 
 
+def test_library_tables_equal_oracle_random_params(native, orc):
+    """The two table builders are different constructions (the oracle
+    evaluates tanh / acos forward at every index; the library counts the Q15
+    levels whose inverse thresholds, atanh and cos, an index reaches, and
+    bisects Eq. 1's log-odds for the rows): over seeded random parameters they
+    agree entry for entry."""
+    rng = np.random.default_rng(20221026)
+    for _ in range(12):
+        kw = dict(t_g=float(np.float32(rng.uniform(2.0, 80.0))),
+                  t_theta_deg=float(np.float32(rng.uniform(5.0, 90.0))),
+                  t_iota=float(np.float32(rng.uniform(3.0, 120.0))),
+                  sobel_norm=int(rng.choice([1, 4, 8])),
+                  n_strips=int(rng.integers(1, 65)),
+                  alpha=float(np.float32(rng.uniform(-12.0, 12.0))))
+        H = int(rng.integers(3, 4097))
+        test_library_tables_equal_oracle(native, orc, kw, H)
+
+
 def test_status_strings(native):
     L = native.lib()
     assert L.ca_status_string(0) == b"ok"

@@ -148,3 +148,69 @@ def test_fit_from_candidates_equals_estimate():
     r1, _ = orc.estimate(f, 99, p)
     r2 = orc.fit(xs, ys, ss, 240, 320, 99, p)
     assert r1 == r2
+
+
+def _by_half(xs, ys, rows, W):
+    """Candidate points grouped by (strip, half): {(i, half): [(x, y), ...]}."""
+    out = {}
+    for x, y in zip(xs.tolist(), ys.tolist()):
+        i = int(np.nonzero(rows == y)[0][0])
+        out.setdefault((i, int(x >= W // 2)), []).append((x, y))
+    return out
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_learned_fallback_rule_boundary(K):
+    """The fallback rule of the learned candidates (Sec. 2.2.4's scorer with
+    the handcrafted extractor as fallback below p = 1/2): a half-strip whose
+    best learned Q15 score is 16383 takes the handcrafted points of that half,
+    one whose best is 16384 keeps its learned point, and no other half
+    changes.  Expectations are written from the rule itself: the learned
+    point is the hand-placed peak of that half; the handcrafted points are the
+    oracle's own handcrafted candidates of that half."""
+    from paper_2210_14771_gb300 import synth
+    H, W = 480, 640
+    frame, _ = synth.frame(0, 0, H, W)
+    p = orc.params(n_strips=16, cands_per_strip=K)
+    rows = orc.strip_rows(H, 16, p.alpha)
+    hand = _by_half(*orc.candidates(frame, p)[:2], rows, W)
+    learned = np.zeros((16, W), np.uint16)
+    peaks = {}
+    rng = np.random.default_rng(5)
+    for i in range(16):
+        for half in (0, 1):
+            lo, hi = (10, W // 2 - 10) if half == 0 else (W // 2 + 10, W - 10)
+            x = int(rng.integers(lo, hi))
+            # alternate the two boundary values and a clearly confident peak
+            v = (16383, 16384, 30000)[(2 * i + half) % 3]
+            learned[i, x] = v
+            peaks[(i, half)] = (x, int(rows[i]), v)
+    for fallback in (False, True):
+        xs, ys, ss = orc.learned_candidates(frame, learned, fallback, p)
+        got = _by_half(xs, ys, rows, W)
+        for (i, half), (x, y, v) in peaks.items():
+            if fallback and v < 16384:
+                want = hand.get((i, half), [])
+            else:
+                want = [(x, y)]   # later picks (K = 4) score 0 and are dropped by t_ps
+            assert got.get((i, half), []) == want, (fallback, i, half, v)
+        # the scores carried along are the learned ones where the learned point is kept
+        kept = {(x, y): s for x, y, s in zip(xs.tolist(), ys.tolist(), ss.tolist())}
+        for (i, half), (x, y, v) in peaks.items():
+            if not (fallback and v < 16384):
+                assert kept[(x, y)] == v
+
+
+def test_learned_fallback_all_unsure_is_handcrafted():
+    """With every learned score below one half the fallback gives exactly the
+    handcrafted candidates, in order; without it nothing survives t_ps."""
+    from paper_2210_14771_gb300 import synth
+    H, W = 480, 640
+    frame, _ = synth.frame(1, 3, H, W)
+    p = orc.params(n_strips=16, cands_per_strip=2)
+    learned = np.full((16, W), 500, np.uint16)   # p ~ 0.015 everywhere: below t_ps too
+    hx, hy, hs = orc.candidates(frame, p)
+    fx, fy, fs = orc.learned_candidates(frame, learned, True, p)
+    assert np.array_equal(hx, fx) and np.array_equal(hy, fy) and np.array_equal(hs, fs)
+    nx, _, _ = orc.learned_candidates(frame, learned, False, p)
+    assert len(nx) == 0
