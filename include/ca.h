@@ -184,7 +184,12 @@ ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const
  *     requests return CA_ERR_INVALID_ARG before any work is queued.  The other
  *     limits are those of ca_estimate_uniform.  No debug capture.
  *   - The first call on each device looks up the array's device address, with
- *     that device current; make that first call before any stream capture.
+ *     that device current.
+ *   - Not for CUDA graphs: each call copies its tables and frame descriptors
+ *     from the host call stack with ordinary copies, which a graph would
+ *     replay from memory that no longer holds them.  A call made while
+ *     `stream` is being captured returns CA_ERR_UNSUPPORTED before it queues
+ *     anything.
  *   - Every call uses the same array, which keeps the last call's contents:
  *     the call clears what must start at zero, but calls whose work overlaps
  *     on the GPU (other streams, other host threads) race and corrupt each
@@ -393,12 +398,23 @@ typedef struct ca_server_config {
                             over time by ca_smooth_tracked with smooth_params
                             before they and their masks are returned */
     ca_smooth_params smooth_params;
+    int32_t zero_copy;   /* 1: frames are never copied to the device.  Every
+                            submitted frame must be page-locked host memory
+                            (cudaHostAlloc, cudaHostRegister, pinned torch
+                            tensors); the kernels read the strip rows they need
+                            straight from it over the host link, and a
+                            page-locked mask_host receives its mask directly.
+                            Admission then counts only device masks. */
+    int32_t reserved;    /* 0 */
 } ca_server_config;
 
 typedef struct ca_server_result {
     uint64_t ticket;     /* from ca_server_submit */
     int32_t stream_id;
-    int32_t pad;
+    int32_t status;      /* CA_OK, or the error of a launch whose work was
+                            already queued when a later step of it failed
+                            (result zero; the stream's previous circle and
+                            smoothing state are cleared) */
     uint64_t frame_key;
     ca_result result;
     double t_arrival;    /* as given at submit */
@@ -410,23 +426,48 @@ typedef struct ca_server_result {
 /* Monotonic clock of the server, in seconds. */
 double ca_server_now(void);
 
-/* Creates a server on the handle's device (the current device) with its own
- * streams, a device pool of cfg->mem_budget bytes and the per-stream state.
- * The handle must outlive the server. */
+/* Creates a server on the handle's device (made current by this call) with
+ * its own streams, a device pool of cfg->mem_budget bytes and the per-stream
+ * state.  The handle must outlive the server. */
 ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server **out);
 
 /* Admits frame (H x W x 3 bytes of host memory; pinned memory makes the copy
  * asynchronous) of stream `stream_id` with RANSAC key `frame_key` and arrival
  * time `t_arrival`.  The frame buffer (and mask_host, H x W bytes or NULL)
  * must stay valid and unchanged until the frame's result has been polled.
- * Returns CA_ERR_ADMISSION, with nothing queued, when the budget is full. */
+ * Returns CA_ERR_ADMISSION, with nothing queued, when the budget is full.
+ * With cfg.zero_copy the frame is not copied (it must be page-locked, else
+ * CA_ERR_INVALID_ARG). */
 ca_status ca_server_submit(ca_server *s, int stream_id, const uint8_t *frame_host, int H, int W,
                            uint64_t frame_key, double t_arrival, uint8_t *mask_host,
                            uint64_t *ticket);
 
+/* One request of ca_server_submit_batch (the arguments of ca_server_submit). */
+typedef struct ca_server_request {
+    const uint8_t *frame_host;   /* H x W x 3 bytes of host memory */
+    uint8_t *mask_host;          /* H x W bytes, or NULL */
+    uint64_t frame_key;
+    double t_arrival;
+    int32_t stream_id;
+    int32_t H, W;
+    int32_t reserved;            /* 0 */
+} ca_server_request;
+
+/* Admits reqs[0 .. n-1] in order, as n calls of ca_server_submit would, in
+ * one call.  Every request is checked before any is admitted
+ * (CA_ERR_INVALID_ARG, nothing admitted).  Admission stops at the first
+ * request the budget refuses: *n_admitted (required) receives how many were
+ * admitted, tickets (n entries, may be NULL) their tickets, and the call
+ * returns CA_ERR_ADMISSION if fewer than n were admitted. */
+ca_status ca_server_submit_batch(ca_server *s, const ca_server_request *reqs, int n,
+                                 uint64_t *tickets, int *n_admitted);
+
 /* Launches what is admitted and returns up to `max` finished results (in
  * completion order).  wait != 0: if nothing has finished, blocks until the
- * oldest launch completes. */
+ * oldest launch completes.  If a launch fails before any of its work is
+ * queued (the estimate call returns an error), its requests go back to the
+ * front of the queue in their order, the error is returned, and a later poll
+ * launches them again. */
 ca_status ca_server_poll(ca_server *s, int wait, ca_server_result *out, int max, int *n_done);
 
 /* Bytes of the pool in use, admitted frames not yet launched, launches queued. */
@@ -494,6 +535,14 @@ ca_status ca_set_debug(ca_handle *h, int level);
 /* Bound on each dependency wait of the fused launch (nanoseconds, 1 ms to
  * 60 s; default 2 s).  Waits normally last microseconds. */
 ca_status ca_set_wait_limit(ca_handle *h, uint64_t ns);
+
+/* Host-side failure injection, for testing callers' error paths without any
+ * device fault: after `after_calls` more estimates have been queued through
+ * the handle (by ca_estimate, ca_estimate_uniform, ca_estimate_tracked,
+ * ca_run_host*, the trials of ca_tune, or the launches of a server on it),
+ * the next one returns `status` (a ca_status other than CA_OK) before it
+ * queues any work, once.  status CA_OK disarms. */
+ca_status ca_inject_failure(ca_handle *h, int after_calls, int status);
 
 enum {
     /* per frame: int32 M, int32 n_slots(=N*K), then n_slots records of

@@ -64,11 +64,18 @@ class CaResult(C.Structure):
 class CaServerConfig(C.Structure):
     _fields_ = [("params", CaParams), ("mem_budget", C.c_size_t), ("max_streams", C.c_int32),
                 ("max_batch", C.c_int32), ("track", C.c_int32), ("want_masks", C.c_int32),
-                ("smooth", C.c_int32), ("smooth_params", CaSmoothParams)]
+                ("smooth", C.c_int32), ("smooth_params", CaSmoothParams),
+                ("zero_copy", C.c_int32), ("reserved", C.c_int32)]
+
+
+class CaServerRequest(C.Structure):
+    _fields_ = [("frame_host", C.c_void_p), ("mask_host", C.c_void_p), ("frame_key", C.c_uint64),
+                ("t_arrival", C.c_double), ("stream_id", C.c_int32), ("H", C.c_int32),
+                ("W", C.c_int32), ("reserved", C.c_int32)]
 
 
 class CaServerResult(C.Structure):
-    _fields_ = [("ticket", C.c_uint64), ("stream_id", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("ticket", C.c_uint64), ("stream_id", C.c_int32), ("status", C.c_int32),
                 ("frame_key", C.c_uint64), ("result", CaResult), ("t_arrival", C.c_double),
                 ("t_submit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double)]
 
@@ -111,6 +118,8 @@ SIGNATURES = [
     ("ca_server_create", C.c_int, [C.c_void_p, _P(CaServerConfig), _P(C.c_void_p)]),
     ("ca_server_submit", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_uint64,
                                    C.c_double, C.c_void_p, _P(C.c_uint64)]),
+    ("ca_server_submit_batch", C.c_int, [C.c_void_p, _P(CaServerRequest), C.c_int,
+                                         _P(C.c_uint64), _P(C.c_int)]),
     ("ca_server_poll", C.c_int, [C.c_void_p, C.c_int, _P(CaServerResult), C.c_int,
                                  _P(C.c_int)]),
     ("ca_server_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int32), _P(C.c_int32)]),
@@ -134,6 +143,7 @@ SIGNATURES = [
     ("ca_sync", C.c_int, [C.c_void_p, C.c_void_p]),
     ("ca_set_debug", C.c_int, [C.c_void_p, C.c_int]),
     ("ca_set_wait_limit", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("ca_inject_failure", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     ("ca_debug_dump", C.c_int, [C.c_void_p, C.c_int, C.c_int, _P(CaParams), C.c_void_p,
                                 C.c_size_t, _P(C.c_size_t)]),
     ("ca_launch_count", C.c_uint64, [C.c_void_p]),

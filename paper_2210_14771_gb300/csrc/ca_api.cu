@@ -113,6 +113,11 @@ struct ca_handle {
         std::vector<int32_t> last_W;
     } sc;
 
+    // host-side failure injection (ca_inject_failure): estimate calls to
+    // accept before the next one fails with inject_status (0: disarmed)
+    int inject_after = 0;
+    int inject_status = 0;
+
     // launch configurations found by ca_tune, by shape of batch
     std::map<uint64_t, LaunchCfg> tuned;
     // live plans (their fused-kernel error words are read by ca_sync)
@@ -157,6 +162,8 @@ ca_status cuda_fail(ca_handle *h, cudaError_t e, const char *what) {
 }  // namespace
 
 namespace ca {
+
+int handle_device(const ca_handle *h) { return h->device; }
 
 // ------------------------------------------------------------ tables --
 // The tables are built here from the inverse functions: every entry is the
@@ -758,6 +765,15 @@ ca_status check_call(ca_handle *h, const ca_frame *frames, int B, const ca_param
 ca_status estimate_cfg(ca_handle *h, const ca_frame *frames, int B, const ca_params *p,
                        ca_result *out_dev, cudaStream_t stream, const LaunchCfg &cfg,
                        const int32_t *track = nullptr, ca_result *state_dev = nullptr) {
+    if (h->inject_status != CA_OK) {   // armed host-side failure (tests)
+        if (h->inject_after > 0) {
+            --h->inject_after;
+        } else {
+            const ca_status inj = (ca_status)h->inject_status;
+            h->inject_status = CA_OK;
+            return fail(h, inj, "injected failure");
+        }
+    }
     CA_CUDA(h, cudaSetDevice(h->device));
     ca_status st;
     if ((st = order_after_last(h, stream)) != CA_OK) return st;
@@ -1675,6 +1691,15 @@ ca_status ca_set_wait_limit(ca_handle *h, uint64_t ns) {
         return fail(h, CA_ERR_INVALID_ARG, "wait limit %llu ns outside [1 ms, 60 s]",
                     (unsigned long long)ns);
     h->wait_ns = ns;
+    return CA_OK;
+}
+
+ca_status ca_inject_failure(ca_handle *h, int after_calls, int status) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (after_calls < 0 || status < CA_OK || status > CA_ERR_STATE)
+        return fail(h, CA_ERR_INVALID_ARG, "bad injection (%d, %d)", after_calls, status);
+    h->inject_after = after_calls;
+    h->inject_status = status;
     return CA_OK;
 }
 

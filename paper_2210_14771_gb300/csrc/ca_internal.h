@@ -217,6 +217,7 @@ size_t strips_smem_bytes(const DevParams &P);
 cudaError_t strips_occupancy(int *blocks_per_sm, size_t smem);
 
 // Host helpers (ca_api.cu).
+int handle_device(const ca_handle *h);                            // the handle's CUDA device
 void strip_rows(int H, int N, float alpha, int32_t *rows);        // Eq. 1 rows
 void build_luts(const ca_params &p, uint16_t *out, int *qg_sat);  // Eq. 2 tables
 ca_status check_params(ca_handle *h, const ca_params *p);         // h may be NULL

@@ -13,6 +13,12 @@
 // estimate, Sec. 4's use of the previous estimate).  Frames of one stream are
 // estimated in submission order, so every result equals the one the frame
 // gets when its stream is served alone.
+//
+// Zero-copy serving (cfg.zero_copy): frames stay in the caller's page-locked
+// host memory and are never copied; the strip kernels read the 3 rows of each
+// strip (9 N W bytes of a W-wide frame) over the host link, and masks go to
+// page-locked mask buffers directly.  Only device-resident masks then count
+// against the budget.
 #include <algorithm>
 #include <cmath>
 #include <chrono>
@@ -93,9 +99,11 @@ struct Request {
     int sid;
     uint64_t key;
     int H, W;
+    const uint8_t *frame_dev;   // frame as the kernels address it (pool or mapped host memory)
+    uint8_t *mask_dev;          // mask as the kernels address it, or NULL
     size_t frame_off, mask_off;
-    bool has_mask;
-    uint8_t *mask_host;
+    bool frame_in_pool, mask_in_pool;
+    uint8_t *mask_copy_to;      // host buffer the pool mask is copied to, or NULL
     double t_arrival, t_submit, t_launch;
 };
 
@@ -106,6 +114,7 @@ struct Batch {
     ca_result *raw_dev = nullptr;    // max_batch results before smoothing (smooth only)
     ca_result *res_host = nullptr;   // pinned
     bool busy = false;
+    ca_status status = CA_OK;        // a step after the estimate failed
 };
 
 }  // namespace
@@ -146,6 +155,33 @@ ca_status server_cuda(cudaError_t e) {
         if (s_ != CA_OK) return s_;                 \
     } while (0)
 
+// Completes the requests of batch b (results from its pinned copy, or zero
+// with the batch's error) and frees their pool blocks.
+void finish_batch(ca_server *s, Batch &b) {
+    const double t = now_s();
+    for (size_t i = 0; i < b.reqs.size(); ++i) {
+        const Request &r = b.reqs[i];
+        ca_server_result o;
+        std::memset(&o, 0, sizeof(o));
+        o.ticket = r.ticket;
+        o.stream_id = r.sid;
+        o.status = b.status;
+        o.frame_key = r.key;
+        if (b.status == CA_OK) o.result = b.res_host[i];
+        o.t_arrival = r.t_arrival;
+        o.t_submit = r.t_submit;
+        o.t_launch = r.t_launch;
+        o.t_done = t;
+        s->done.push_back(o);
+        if (r.frame_in_pool) s->pool.release(r.frame_off);
+        if (r.mask_in_pool) s->pool.release(r.mask_off);
+        s->stream_busy[r.sid] -= 1;
+    }
+    b.reqs.clear();
+    b.busy = false;
+    b.status = CA_OK;
+}
+
 // Moves finished launches to the done list (blocking on the oldest if `wait`).
 ca_status collect(ca_server *s, bool wait) {
     while (!s->in_flight.empty()) {
@@ -153,29 +189,41 @@ ca_status collect(ca_server *s, bool wait) {
         cudaError_t q = wait ? cudaEventSynchronize(b.done) : cudaEventQuery(b.done);
         if (q == cudaErrorNotReady) break;
         SV_CUDA(q);
-        const double t = now_s();
-        for (size_t i = 0; i < b.reqs.size(); ++i) {
-            const Request &r = b.reqs[i];
-            ca_server_result o;
-            std::memset(&o, 0, sizeof(o));
-            o.ticket = r.ticket;
-            o.stream_id = r.sid;
-            o.frame_key = r.key;
-            o.result = b.res_host[i];
-            o.t_arrival = r.t_arrival;
-            o.t_submit = r.t_submit;
-            o.t_launch = r.t_launch;
-            o.t_done = t;
-            s->done.push_back(o);
-            s->pool.release(r.frame_off);
-            if (r.has_mask) s->pool.release(r.mask_off);
-            s->stream_busy[r.sid] -= 1;
-        }
-        b.reqs.clear();
-        b.busy = false;
+        finish_batch(s, b);
         s->in_flight.pop_front();
         wait = false;   // block at most once
     }
+    return CA_OK;
+}
+
+// The steps of a launch after its estimate (smoothing, masks, copies back,
+// completion event).  A failure here leaves part of the launch queued.
+ca_status finish_launch(ca_server *s, Batch &b, const std::vector<int32_t> &track) {
+    const int B = (int)b.reqs.size();
+    if (s->smooth_state) {
+        std::vector<int32_t> Hs(B), Ws(B);
+        std::vector<uint8_t *> ms(B);
+        bool all_masks = true;
+        for (int i = 0; i < B; ++i) {
+            Hs[i] = b.reqs[i].H;
+            Ws[i] = b.reqs[i].W;
+            ms[i] = b.reqs[i].mask_dev;
+            all_masks = all_masks && ms[i] != nullptr;
+        }
+        ca_status st = ca_smooth_tracked(s->h, b.raw_dev, B, Ws.data(), track.data(),
+                                         s->cfg.max_streams, &s->cfg.smooth_params,
+                                         s->smooth_state, b.res_dev, s->compute);
+        if (st == CA_OK && all_masks)
+            st = ca_mask(s->h, b.res_dev, B, Hs.data(), Ws.data(), ms.data(), s->compute);
+        if (st != CA_OK) return st;
+    }
+    SV_CUDA(cudaMemcpyAsync(b.res_host, b.res_dev, sizeof(ca_result) * B, cudaMemcpyDeviceToHost,
+                            s->compute));
+    for (int i = 0; i < B; ++i)
+        if (b.reqs[i].mask_copy_to)
+            SV_CUDA(cudaMemcpyAsync(b.reqs[i].mask_copy_to, b.reqs[i].mask_dev,
+                                    (size_t)b.reqs[i].H * b.reqs[i].W, cudaMemcpyDeviceToHost,
+                                    s->compute));
     return CA_OK;
 }
 
@@ -207,48 +255,49 @@ ca_status launch(ca_server *s) {
         for (int i = 0; i < B; ++i) {
             Request &r = b.reqs[i];
             r.t_launch = t;
-            fr[i].rgb_dev = s->arena + r.frame_off;
-            fr[i].mask_dev = r.has_mask ? s->arena + r.mask_off : nullptr;
+            fr[i].rgb_dev = r.frame_dev;
+            fr[i].mask_dev = r.mask_dev;
             fr[i].H = r.H;
             fr[i].W = r.W;
             fr[i].pitch = (int64_t)r.W * 3;
             fr[i].frame_key = r.key;
             track[i] = s->cfg.track ? r.sid : -1;
         }
-        SV_CUDA(cudaStreamWaitEvent(s->compute, s->copied, 0));
+        if (!s->cfg.zero_copy) SV_CUDA(cudaStreamWaitEvent(s->compute, s->copied, 0));
         const bool smooth = s->smooth_state != nullptr;
         if (smooth)   // masks follow the smoothed circles
             for (int i = 0; i < B; ++i) fr[i].mask_dev = nullptr;
         ca_status st = ca_estimate_tracked(s->h, fr.data(), B, &s->cfg.params, s->state,
                                            track.data(), s->cfg.max_streams,
                                            smooth ? b.raw_dev : b.res_dev, s->compute);
-        if (st != CA_OK) return st;
-        if (smooth) {
-            std::vector<int32_t> Hs(B), Ws(B);
-            std::vector<uint8_t *> ms(B);
-            bool all_masks = true;
-            for (int i = 0; i < B; ++i) {
-                Hs[i] = b.reqs[i].H;
-                Ws[i] = b.reqs[i].W;
-                ms[i] = b.reqs[i].has_mask ? s->arena + b.reqs[i].mask_off : nullptr;
-                all_masks = all_masks && b.reqs[i].has_mask;
-            }
-            st = ca_smooth_tracked(s->h, b.raw_dev, B, Ws.data(), track.data(), s->cfg.max_streams,
-                                   &s->cfg.smooth_params, s->smooth_state, b.res_dev, s->compute);
-            if (st == CA_OK && all_masks)
-                st = ca_mask(s->h, b.res_dev, B, Hs.data(), Ws.data(), ms.data(), s->compute);
-            if (st != CA_OK) return st;
+        if (st != CA_OK) {
+            // nothing of this launch is queued: its requests go back to the
+            // front of the queue, in order, and a later poll retries them
+            for (int i = B - 1; i >= 0; --i) s->pending.push_front(b.reqs[i]);
+            b.reqs.clear();
+            return st;
         }
-        SV_CUDA(cudaMemcpyAsync(b.res_host, b.res_dev, sizeof(ca_result) * B,
-                                cudaMemcpyDeviceToHost, s->compute));
-        for (int i = 0; i < B; ++i)
-            if (b.reqs[i].has_mask && b.reqs[i].mask_host)
-                SV_CUDA(cudaMemcpyAsync(b.reqs[i].mask_host, s->arena + b.reqs[i].mask_off,
-                                        (size_t)b.reqs[i].H * b.reqs[i].W, cudaMemcpyDeviceToHost,
-                                        s->compute));
-        SV_CUDA(cudaEventRecord(b.done, s->compute));
+        st = finish_launch(s, b, track);
+        if (st != CA_OK) {
+            // the estimate is queued (and has advanced the streams' state):
+            // the frames complete with the error and their streams start afresh
+            b.status = st;
+            for (int i = 0; i < B; ++i) {
+                if (track[i] < 0) continue;
+                cudaMemsetAsync(s->state + track[i], 0, sizeof(ca_result), s->compute);
+                if (s->smooth_state)
+                    cudaMemsetAsync(s->smooth_state + 4 * (size_t)track[i], 0, 4 * sizeof(float),
+                                    s->compute);
+            }
+        }
+        if (cudaEventRecord(b.done, s->compute) != cudaSuccess) {
+            if (b.status == CA_OK) b.status = CA_ERR_CUDA;
+            finish_batch(s, b);   // nothing to wait for
+            return b.status;
+        }
         b.busy = true;
         s->in_flight.push_back(slot);
+        if (st != CA_OK) return st;
     }
     return CA_OK;
 }
@@ -293,10 +342,14 @@ ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server 
             sp.t_hold < 0.0f || sp.reserved != 0)
             return CA_ERR_INVALID_ARG;
     }
+    if (cfg->zero_copy != 0 && cfg->zero_copy != 1) return CA_ERR_INVALID_ARG;
+    if (cfg->reserved != 0) return CA_ERR_INVALID_ARG;
     ca_status st = ca::check_params(h, &cfg->params);
     if (st != CA_OK) return st;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CA_ERR_CUDA;
+    // everything the server allocates lives on the handle's device, where its
+    // estimates run
+    const int dev = ca::handle_device(h);
+    if (cudaSetDevice(dev) != cudaSuccess) return CA_ERR_CUDA;
     ca_server *s = new ca_server();
     s->h = h;
     s->device = dev;
@@ -335,44 +388,120 @@ ca_status ca_server_create(ca_handle *h, const ca_server_config *cfg, ca_server 
     return CA_OK;
 }
 
-ca_status ca_server_submit(ca_server *s, int stream_id, const uint8_t *frame_host, int H, int W,
-                           uint64_t frame_key, double t_arrival, uint8_t *mask_host,
-                           uint64_t *ticket) {
-    if (!s || !frame_host) return CA_ERR_INVALID_ARG;
-    if (stream_id < 0 || stream_id >= s->cfg.max_streams) return CA_ERR_INVALID_ARG;
-    if (W < 8 || W > 4096 || H < 3 || H > 4096) return CA_ERR_INVALID_ARG;
-    const size_t fb = (size_t)H * W * 3, mb = (size_t)H * W;
-    const bool want_mask = s->cfg.want_masks != 0;
-    size_t foff = 0, moff = 0;
-    if (!s->pool.alloc(fb, &foff)) return CA_ERR_ADMISSION;
-    if (want_mask && !s->pool.alloc(mb, &moff)) {
-        s->pool.release(foff);
-        return CA_ERR_ADMISSION;
+}  // extern "C"
+
+namespace {
+
+// Device-visible address of page-locked host memory, or NULL.
+const void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // pageable memory is not an error of the server
+        return nullptr;
     }
-    cudaSetDevice(s->device);
-    cudaError_t e = cudaMemcpyAsync(s->arena + foff, frame_host, fb, cudaMemcpyHostToDevice, s->copy);
-    if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->copy);
-    if (e != cudaSuccess) {
-        s->pool.release(foff);
-        if (want_mask) s->pool.release(moff);
-        return server_cuda(e);
-    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+ca_status check_request(const ca_server *s, const ca_server_request &q) {
+    if (!q.frame_host || q.reserved != 0) return CA_ERR_INVALID_ARG;
+    if (q.stream_id < 0 || q.stream_id >= s->cfg.max_streams) return CA_ERR_INVALID_ARG;
+    if (q.W < 8 || q.W > 4096 || q.H < 3 || q.H > 4096) return CA_ERR_INVALID_ARG;
+    return CA_OK;
+}
+
+// Admits one checked request: device buffers from the pool (the frame unless
+// zero-copy, the mask when kept on the device), the frame copy queued.
+ca_status admit(ca_server *s, const ca_server_request &q, uint64_t *ticket) {
+    const size_t fb = (size_t)q.H * q.W * 3, mb = (size_t)q.H * q.W;
     Request r;
+    std::memset(&r, 0, sizeof(r));
+    r.sid = q.stream_id;
+    r.key = q.frame_key;
+    r.H = q.H;
+    r.W = q.W;
+    const bool zc = s->cfg.zero_copy != 0;
+    if (zc) {
+        r.frame_dev = static_cast<const uint8_t *>(mapped_host(q.frame_host));
+        if (!r.frame_dev) return CA_ERR_INVALID_ARG;   // not page-locked
+    }
+    const void *mask_mapped =
+        zc && q.mask_host && s->cfg.want_masks ? mapped_host(q.mask_host) : nullptr;
+    if (!zc) {
+        if (!s->pool.alloc(fb, &r.frame_off)) return CA_ERR_ADMISSION;
+        r.frame_in_pool = true;
+    }
+    if (s->cfg.want_masks) {
+        if (mask_mapped) {   // written straight into the caller's page-locked buffer
+            r.mask_dev = static_cast<uint8_t *>(const_cast<void *>(mask_mapped));
+        } else {
+            if (!s->pool.alloc(mb, &r.mask_off)) {
+                if (r.frame_in_pool) s->pool.release(r.frame_off);
+                return CA_ERR_ADMISSION;
+            }
+            r.mask_in_pool = true;
+            r.mask_dev = s->arena + r.mask_off;
+            r.mask_copy_to = q.mask_host;
+        }
+    }
+    if (!zc) {
+        r.frame_dev = s->arena + r.frame_off;
+        cudaError_t e = cudaMemcpyAsync(s->arena + r.frame_off, q.frame_host, fb,
+                                        cudaMemcpyHostToDevice, s->copy);
+        if (e == cudaSuccess) e = cudaEventRecord(s->copied, s->copy);
+        if (e != cudaSuccess) {
+            s->pool.release(r.frame_off);
+            if (r.mask_in_pool) s->pool.release(r.mask_off);
+            return server_cuda(e);
+        }
+    }
     r.ticket = s->next_ticket++;
-    r.sid = stream_id;
-    r.key = frame_key;
-    r.H = H;
-    r.W = W;
-    r.frame_off = foff;
-    r.mask_off = moff;
-    r.has_mask = want_mask;
-    r.mask_host = mask_host;
-    r.t_arrival = t_arrival;
+    r.t_arrival = q.t_arrival;
     r.t_submit = now_s();
     r.t_launch = 0.0;
     s->pending.push_back(r);
-    s->stream_busy[stream_id] += 1;
+    s->stream_busy[q.stream_id] += 1;
     if (ticket) *ticket = r.ticket;
+    return CA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ca_status ca_server_submit(ca_server *s, int stream_id, const uint8_t *frame_host, int H, int W,
+                           uint64_t frame_key, double t_arrival, uint8_t *mask_host,
+                           uint64_t *ticket) {
+    if (!s) return CA_ERR_INVALID_ARG;
+    ca_server_request q;
+    std::memset(&q, 0, sizeof(q));
+    q.frame_host = frame_host;
+    q.mask_host = mask_host;
+    q.frame_key = frame_key;
+    q.t_arrival = t_arrival;
+    q.stream_id = stream_id;
+    q.H = H;
+    q.W = W;
+    ca_status st = check_request(s, q);
+    if (st != CA_OK) return st;
+    if (cudaSetDevice(s->device) != cudaSuccess) return CA_ERR_CUDA;
+    return admit(s, q, ticket);
+}
+
+ca_status ca_server_submit_batch(ca_server *s, const ca_server_request *reqs, int n,
+                                 uint64_t *tickets, int *n_admitted) {
+    if (!s || !n_admitted || n < 0 || (n > 0 && !reqs)) return CA_ERR_INVALID_ARG;
+    *n_admitted = 0;
+    for (int i = 0; i < n; ++i) {
+        ca_status st = check_request(s, reqs[i]);
+        if (st != CA_OK) return st;
+        if (s->cfg.zero_copy && !mapped_host(reqs[i].frame_host)) return CA_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(s->device) != cudaSuccess) return CA_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        ca_status st = admit(s, reqs[i], tickets ? tickets + i : nullptr);
+        if (st != CA_OK) return st;
+        *n_admitted = i + 1;
+    }
     return CA_OK;
 }
 

@@ -87,6 +87,10 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     }
     if (nh > CA_STATIC_MAX_HYPS) return CA_ERR_INVALID_ARG;
 
+    // the host-stack copies below cannot be recorded into a graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) return CA_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return CA_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CA_ERR_CUDA;
     unsigned char *scratch = nullptr;

@@ -16,9 +16,11 @@ from .api import ContentArea, params as make_params
 class Server:
     def __init__(self, ca: ContentArea, p=None, mem_budget: int = 4 << 30, max_streams: int = 32,
                  max_batch: int = 64, track: bool = True, want_masks: bool = False,
-                 smooth=None):
+                 smooth=None, zero_copy: bool = False):
         """smooth: None, or (gamma, jump, t_hold) of ca_smooth_tracked applied to
-        each stream's results (and masks) before they are returned."""
+        each stream's results (and masks) before they are returned.
+        zero_copy: frames (page-locked) are read in place by the kernels,
+        never copied to the device."""
         self.ca = ca
         cfg = N.CaServerConfig()
         cfg.params = p or make_params()
@@ -27,6 +29,7 @@ class Server:
         cfg.max_batch = max_batch
         cfg.track = 1 if track else 0
         cfg.want_masks = 1 if want_masks else 0
+        cfg.zero_copy = 1 if zero_copy else 0
         if smooth is not None:
             cfg.smooth = 1
             cfg.smooth_params = N.CaSmoothParams(float(smooth[0]), float(smooth[1]),
@@ -58,6 +61,31 @@ class Server:
         self.ca._check(st)
         return int(t.value)
 
+    def submit_batch(self, items):
+        """items: list of (sid, frame, key, t_arrival) in admission order.
+        One library call; returns the tickets of the admitted prefix (the
+        budget refused the rest)."""
+        n = len(items)
+        if n == 0:
+            return []
+        reqs = (N.CaServerRequest * n)()
+        for i, (sid, frame, key, t_arr) in enumerate(items):
+            q = reqs[i]
+            if isinstance(frame, torch.Tensor):
+                q.frame_host = frame.data_ptr()
+            else:
+                q.frame_host = frame.ctypes.data
+            q.frame_key = key
+            q.t_arrival = t_arr
+            q.stream_id = sid
+            q.H, q.W = int(frame.shape[0]), int(frame.shape[1])
+        tickets = (C.c_uint64 * n)()
+        got = C.c_int(0)
+        st = N.lib().ca_server_submit_batch(self._h, reqs, n, tickets, C.byref(got))
+        if st != N.CA_ERR_ADMISSION:
+            self.ca._check(st)
+        return [int(tickets[i]) for i in range(got.value)]
+
     def poll(self, wait: bool = False):
         n = C.c_int(0)
         self.ca._check(N.lib().ca_server_poll(self._h, 1 if wait else 0, self._out, 1024,
@@ -65,7 +93,7 @@ class Server:
         out = []
         for i in range(n.value):
             r = self._out[i]
-            out.append(dict(ticket=r.ticket, sid=r.stream_id, key=r.frame_key,
+            out.append(dict(ticket=r.ticket, sid=r.stream_id, key=r.frame_key, status=r.status,
                             result=(r.result.cx, r.result.cy, r.result.r, r.result.score,
                                     r.result.valid, r.result.n_inliers),
                             t_arrival=r.t_arrival, t_submit=r.t_submit, t_launch=r.t_launch,
@@ -98,11 +126,13 @@ def pinned_banks(streams):
 
 
 def run_load(server: Server, streams, banks, n_frames: int, realtime: bool = True,
-             sids=None):
+             sids=None, batched: bool = True):
     """Feeds n_frames of each stream (all, or the ids in `sids`) to the server.
     realtime: frames are submitted at their Poisson arrival times; else all
-    arrive at once (saturation).  Returns per-frame records (stream, index,
-    result, latency) and the wall time."""
+    arrive at once (saturation).  batched: every frame that has arrived is
+    submitted by one ca_server_submit_batch call per loop (in arrival order),
+    else one ca_server_submit call per frame.  Returns per-frame records
+    (stream, index, result, latency) and the wall time."""
     sids = list(range(len(streams))) if sids is None else list(sids)
     arr = {s: (streams[s].arrivals(n_frames) if realtime else np.zeros(n_frames)) for s in sids}
     nxt = {s: 0 for s in sids}
@@ -113,16 +143,31 @@ def run_load(server: Server, streams, banks, n_frames: int, realtime: bool = Tru
     while len(records) < total:
         now = server.now() - t0
         progressed = False
-        for s in sids:
-            while nxt[s] < n_frames and arr[s][nxt[s]] <= now:
+        if batched:
+            due = []
+            for s in sids:
                 k = nxt[s]
-                fr = banks[s][k % len(banks[s])]
-                t = server.submit(s, fr, streams[s].key(k), t0 + float(arr[s][k]))
-                if t is None:   # budget full: retry after the next poll
-                    break
+                while k < n_frames and arr[s][k] <= now:
+                    due.append((float(arr[s][k]), s, k))
+                    k += 1
+            due.sort(key=lambda d: d[0])   # stable: each stream's frames stay in order
+            items = [(s, banks[s][k % len(banks[s])], streams[s].key(k), t0 + a)
+                     for a, s, k in due]
+            for (a, s, k), t in zip(due, server.submit_batch(items)):
                 ticket_of[t] = (s, k)
-                nxt[s] += 1
+                nxt[s] = k + 1
                 progressed = True
+        else:
+            for s in sids:
+                while nxt[s] < n_frames and arr[s][nxt[s]] <= now:
+                    k = nxt[s]
+                    fr = banks[s][k % len(banks[s])]
+                    t = server.submit(s, fr, streams[s].key(k), t0 + float(arr[s][k]))
+                    if t is None:   # budget full: retry after the next poll
+                        break
+                    ticket_of[t] = (s, k)
+                    nxt[s] += 1
+                    progressed = True
         done = server.poll(wait=False)
         for d in done:
             s, k = ticket_of.pop(d["ticket"])

@@ -134,6 +134,94 @@ def test_server_result_same_alone_and_in_the_mix(ca, orc, streams):
     del api
 
 
+def test_zero_copy_server_reads_frames_in_place(ca, orc, streams):
+    """With zero_copy the frames stay in page-locked host memory (the kernels
+    read their strip rows over the host link) and masks go straight into
+    page-locked host buffers: every result equals the copying server's and
+    the oracle's tracked chain bit for bit, every mask equals the oracle's
+    mask of that result, and the pool holds nothing but device masks."""
+    from paper_2210_14771_gb300 import serve
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4)
+    banks = serve.pinned_banks(streams)
+    n = 8
+    copied = _serve(ca, streams, banks, n, None, 4, 1 << 30, lp)
+    srv = serve.Server(ca, lp, mem_budget=4096, max_streams=len(streams), max_batch=4,
+                       zero_copy=True)
+    recs, _ = serve.run_load(srv, streams, banks, n, realtime=False)
+    assert srv.stats()["bytes_in_use"] == 0
+    srv.close()
+    zc = {(r["stream"], r["index"]): r["result"] for r in recs}
+    assert zc == copied
+    want = _oracle_chain(orc, streams[1], n, op)
+    assert all(_same(zc[(1, k)], want[k]) for k in range(n))
+    # masks into page-locked host buffers, one stream, frame by frame
+    s = streams[3]
+    srv = serve.Server(ca, lp, mem_budget=4096, max_streams=len(streams), want_masks=True,
+                       zero_copy=True)
+    masks = [torch.zeros((s.H, s.W), dtype=torch.uint8).pin_memory() for _ in range(n)]
+    got = {}
+    for k in range(n):
+        t = srv.submit(3, banks[3][k % len(banks[3])], s.key(k), srv.now(),
+                       mask_host=masks[k].data_ptr())
+        assert t is not None
+        for d in srv.poll(wait=True):
+            got[d["ticket"]] = (k, d)
+    srv.close()
+    want = _oracle_chain(orc, s, n, op)
+    for k, d in got.values():
+        assert d["status"] == 0 and _same(d["result"], want[k])
+        assert np.array_equal(masks[k].numpy(), orc.mask(want[k], s.H, s.W)), k
+
+
+def test_zero_copy_server_refuses_pageable_frames(ca, streams):
+    from paper_2210_14771_gb300 import _native as N, serve
+    srv = serve.Server(ca, None, mem_budget=4096, max_streams=2, zero_copy=True)
+    f = np.ascontiguousarray(streams[0].frames[0])      # pageable numpy memory
+    with pytest.raises(N.CaError) as e:
+        srv.submit(0, f, 1, srv.now())
+    assert e.value.status == 1
+    with pytest.raises(N.CaError) as e:
+        srv.submit_batch([(0, f, 1, srv.now())])
+    assert e.value.status == 1 and srv.stats()["pending"] == 0
+    srv.close()
+
+
+def test_failed_launch_is_requeued_and_served_in_order(ca, orc, streams):
+    """A launch whose estimate fails on the host (an injected CA_ERR_OOM)
+    queues nothing: poll reports the error, the frames go back to the front
+    of the queue, and later polls serve every stream in order with the
+    results of an undisturbed run."""
+    from paper_2210_14771_gb300 import _native as N, serve
+    lp, op = both_params(orc, n_strips=16, cands_per_strip=2, n_hyps=64, seed=4)
+    banks = serve.pinned_banks(streams)
+    n = 4
+    clean = _serve(ca, streams, banks, n, None, 3, 1 << 30, lp)
+    srv = serve.Server(ca, lp, mem_budget=1 << 30, max_streams=len(streams), max_batch=3)
+    tickets = {}
+    items = [(s, banks[s][k % len(banks[s])], streams[s].key(k), srv.now())
+             for k in range(n) for s in range(len(streams))]
+    for (s, _, _, _), t in zip(items, srv.submit_batch(items)):
+        tickets[t] = s
+    assert len(tickets) == n * len(streams)
+    ca._check(N.lib().ca_inject_failure(ca._h, 1, N.CA_ERR_OOM))   # the second launch fails
+    with pytest.raises(N.CaError) as e:
+        srv.poll(wait=False)
+    assert e.value.status == N.CA_ERR_OOM
+    assert srv.stats()["pending"] == n * len(streams) - 3       # only the first launch left
+    done = []
+    while len(done) < n * len(streams):
+        done += srv.poll(wait=True)
+    srv.close()
+    order = {}
+    for d in sorted(done, key=lambda d: d["ticket"]):
+        assert d["status"] == 0
+        order.setdefault(d["sid"], []).append(d)
+    for sid, ds in order.items():
+        for k, d in enumerate(ds):
+            assert d["key"] == streams[sid].key(k)
+            assert d["result"] == clean[(sid, k)], (sid, k)
+
+
 def test_admission_refuses_beyond_the_budget(ca, streams):
     from paper_2210_14771_gb300 import serve
     s = streams[0]

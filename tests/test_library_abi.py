@@ -51,7 +51,7 @@ def test_struct_layouts(native):
 STRUCTS = (("ca_params", "CaParams"), ("ca_frame", "CaFrame"), ("ca_result", "CaResult"),
            ("ca_tuning", "CaTuning"), ("ca_train_params", "CaTrainParams"),
            ("ca_server_config", "CaServerConfig"), ("ca_server_result", "CaServerResult"),
-           ("ca_smooth_params", "CaSmoothParams"))
+           ("ca_smooth_params", "CaSmoothParams"), ("ca_server_request", "CaServerRequest"))
 
 
 def test_binding_structs_match_the_header(native, tmp_path):

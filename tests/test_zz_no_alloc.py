@@ -56,12 +56,25 @@ def test_static_entry_matches_handle_entry_on_two_calls(lib):
         res = torch.full_like(ref_res, -1.0)
         masks = torch.full_like(ref_masks, 7)
         prepared.append((d, keys, p, ref_res, ref_masks, res, masks))
+    # one warm-up call per case: the first use of the library's kernels and of
+    # its scratch array loads their code and data, which is not an allocation
+    # of the call
+    for d, keys, p, _, _, res, masks in prepared:
+        assert _static_call(lib, d, keys, p, res, masks) == 0
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
+    free_before, _ = torch.cuda.mem_get_info()
+    for d, keys, p, _, _, res, masks in prepared:
+        res.fill_(-1.0)
+        masks.fill_(7)
+    torch.cuda.synchronize()
     for d, keys, p, _, _, res, masks in prepared:       # two calls in a row
         assert _static_call(lib, d, keys, p, res, masks) == 0
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated() == before      # nothing taken from torch's pool
+    # nor from the device by any other route (cudaMalloc takes whole 2 MiB pages)
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_before - free_after < (2 << 20), (free_before, free_after)
     for d, keys, p, ref_res, ref_masks, res, masks in prepared:
         assert res.cpu().numpy().tobytes() == ref_res.cpu().numpy().tobytes()
         assert torch.equal(masks, ref_masks)
@@ -87,3 +100,24 @@ def test_static_entry_rejects_requests_beyond_its_scratch(lib):
                         api.params(n_strips=16, cands_per_strip=4, hyp_mode=1), res[:4], None) == 1
     torch.cuda.synchronize()
     assert (res == 0).all()                              # rejected before any work was queued
+
+
+def test_static_entry_refuses_stream_capture(lib):
+    """A call made while its stream is being captured into a CUDA graph is
+    refused (CA_ERR_UNSUPPORTED) before it queues anything: its host-stack
+    copies could not be replayed."""
+    from paper_2210_14771_gb300 import api
+    frames = torch.zeros((2, 64, 96, 3), dtype=torch.uint8, device="cuda")
+    res = torch.zeros((2, 6), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        rc = lib.lib().ca_estimate_static(
+            C.c_void_p(frames.data_ptr()), 2, 64, 96, None, C.byref(api.params()),
+            C.c_void_p(res.data_ptr()), None, C.c_void_p(side.cuda_stream))
+        g.capture_end()
+    torch.cuda.synchronize()
+    assert rc == 5
+    assert (res == 0).all()
