@@ -57,9 +57,12 @@ enum { CA_HYP_RANDOM = 0, CA_HYP_EXHAUSTIVE = 1 };
 /* divisor of the circle score compared with t_cs (Sec. 2.2.5): the paper's
  * candidate count 2N, the slot count N*K, or none */
 enum { CA_NORM_2N = 0, CA_NORM_NK = 1, CA_NORM_RAW = 2 };
-/* edge scorer: handcrafted (Sec. 2.2.3), learned 1-D CNN, or learned with the
- * handcrafted score taking over half-strips the network is unsure about */
-enum { CA_SCORER_HAND = 0, CA_SCORER_LEARNED = 1, CA_SCORER_LEARNED_FALLBACK = 2 };
+/* edge scorer: handcrafted (Sec. 2.2.3); a learned 1-D CNN over 3-row strip
+ * profiles, alone or with the handcrafted score taking over half-strips the
+ * network is unsure about; the paper's own 2-D CNN over 7-row strips
+ * (Sec. 2.2.4), alone or with the same fallback */
+enum { CA_SCORER_HAND = 0, CA_SCORER_LEARNED = 1, CA_SCORER_LEARNED_FALLBACK = 2,
+       CA_SCORER_2D = 3, CA_SCORER_2D_FALLBACK = 4 };
 /* how a call is launched (results never depend on it): AUTO = the fastest
  * configuration ca_tune found for this shape of batch, else a size-based
  * choice; STAGED = three kernels (strips, fit, mask); FUSED = one persistent
@@ -355,19 +358,66 @@ ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const
                             float *state_dev, ca_result *out_dev, void *stream);
 
 /* The paper's own learned edge scorer (Sec. 2.2.4): three 3x3 convolutions
- * to 8, 16 and 32 features with ReLU, a 1x1 head, on RGBXY strips 7 rows
- * high (unpadded vertically: the logits are those of the strip's middle row;
- * zero-padded horizontally).  Features: R, G, B as (v - 128) / 128, then
- * (x - (W-1)/2) / W and (row - (H-1)/2) / H.  Parameters: CA_SCORER2D_NPARAM
- * binary32 values in device memory, W1[8][5][3][3], b1[8], W2[16][8][3][3],
- * b2[16], W3[32][16][3][3], b3[32], wh[32], bh.  strips7_dev: n x 7 x W x 3
- * bytes (rows y-3 .. y+3 of each strip, packed RGB); rows_dev: n x 7 frame
- * rows of those rows; logits_dev: n x W.  Binary32 on the CUDA cores.
- * Queued on `stream`. */
+ * to 8, 16 and 32 features with ReLU, a 1x1 head and a sigmoid, on RGBXY
+ * strips 7 rows high (unpadded vertically: the logits are those of the
+ * strip's middle row; zero-padded horizontally), run on the tensor cores
+ * (bf16 weights and activations, f32 accumulation).  Features: R, G, B as
+ * (v - 128) / 128, then (x - (W-1)/2) / W and (row - (H-1)/2) / H.  The 7
+ * rows of a strip at row y are y-3 .. y+3 clamped into the frame.
+ * Parameters: CA_SCORER2D_NPARAM binary32 values, W1[8][5][3][3], b1[8],
+ * W2[16][8][3][3], b2[16], W3[32][16][3][3], b3[32], wh[32], bh, with
+ * conv[r][x][co] = b[co] + sum_{ci,dr,dx} W[co][ci][dr][dx] in[r+dr][x+dx-1][ci].
+ *
+ * With scorer_mode CA_SCORER_2D the candidates of every half-strip come from
+ * the network's scores round(32768 p) of the strip's middle row (same pick
+ * rule, K <= 16); with CA_SCORER_2D_FALLBACK a half-strip whose best score is
+ * below 16384 (p < 1/2) keeps its handcrafted candidates.  Either mode needs
+ * 2-D parameters (init, set or load) first. */
 #define CA_SCORER2D_NPARAM 6209
+
+/* Seeded initial parameters (He-normal convolutions, head weights N(0, 1/32),
+ * head bias -3); resets the momentum. */
+ca_status ca_scorer2d_init(ca_handle *h, uint64_t seed);
+/* Copies n = CA_SCORER2D_NPARAM parameters in / out (host memory); set resets
+ * the momentum. */
+ca_status ca_scorer2d_set_params(ca_handle *h, const float *params, size_t n);
+ca_status ca_scorer2d_get_params(ca_handle *h, float *params, size_t n);
+/* Parameters and momentum to / from a file (little-endian: magic "CAS2",
+ * version, count, then binary32 values). */
+ca_status ca_scorer2d_save(ca_handle *h, const char *path);
+ca_status ca_scorer2d_load(ca_handle *h, const char *path);
+
+/* Forward pass on n strips: strips7_dev = n x 7 x W x 3 bytes (the 7 rows of
+ * each strip, packed RGB), rows_dev = n x 7 frame rows of those rows (device),
+ * frames of height H.  params_dev: CA_SCORER2D_NPARAM binary32 values in
+ * device memory, or NULL for the handle's parameters.  Writes the n x W
+ * logits (f32) and/or the Q15 scores round(32768 p) (either may be NULL).
+ * Queued on `stream`. */
 ca_status ca_scorer2d_forward(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
                               int n, int W, int H, const float *params_dev, float *logits_dev,
-                              void *stream);
+                              uint16_t *scores_dev, void *stream);
+
+/* One training step on the strips idx_dev[0 .. n-1] (device indices, or NULL
+ * for strips 0 .. n-1) of a strip set as in ca_scorer2d_forward, with
+ * targets_dev = per strip W soft targets in [0, 1] (the paper blurs its edge
+ * map with a Gaussian of sigma 3).  Loss: the soft binary cross-entropy of the
+ * columns, each weighted by 1 + (pos_weight - 1) t (pos_weight = 1: the
+ * paper's unweighted loss), mean over the columns of the step; update as
+ * ca_scorer_step.  Synchronous.  loss_host (may be NULL): the summed loss;
+ * grads_host (may be NULL): the summed gradient (CA_SCORER2D_NPARAM values,
+ * before the 1/columns scaling of the update). */
+ca_status ca_scorer2d_step(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                           const float *targets_dev, const int32_t *idx_dev, int n, int W, int H,
+                           const ca_train_params *tp, float *loss_host, float *grads_host);
+
+/* `epochs` passes of steps of `batch` strips over the n strips, shuffled per
+ * epoch by `seed`, with tp->lr_schedule as ca_scorer_train.  epoch_loss_host
+ * (may be NULL) receives the mean loss per column of each epoch.
+ * Synchronous. */
+ca_status ca_scorer2d_train(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                            const float *targets_dev, int n, int W, int H,
+                            const ca_train_params *tp, int epochs, int batch, uint64_t seed,
+                            float *epoch_loss_host);
 
 /* ---- Serving (no counterpart in the paper, which estimates one frame at a
  * time): frames of many video streams under continuous batching.

@@ -91,7 +91,7 @@ def lib():
         L.orc_sc2_forward_mode.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                            C.c_int, C.c_void_p]
         L.orc_sc2_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
-                                        C.c_void_p, C.c_void_p]
+                                        C.c_double, C.c_void_p, C.c_void_p]
         L.orc_sc2_loss_grad.restype = C.c_double
         L.orc_sc2_targets.argtypes = [C.c_float, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int,
                                       C.c_double, C.c_void_p]
@@ -482,14 +482,14 @@ def sc2_forward(rgb7, rows, H, params, mixed=False):
     return out
 
 
-def sc2_loss_grad(rgb7, rows, H, targets, params):
+def sc2_loss_grad(rgb7, rows, H, targets, params, pos_weight=1.0):
     rgb7 = np.ascontiguousarray(rgb7, np.uint8)
     W = rgb7.shape[1]
     prm = np.ascontiguousarray(params, np.float32)
     t = np.ascontiguousarray(targets, np.float64)
     g = np.zeros(SC2_NPARAM, np.float64)
     loss = lib().orc_sc2_loss_grad(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
-                                   _ptr(t), _ptr(prm), _ptr(g))
+                                   _ptr(t), float(pos_weight), _ptr(prm), _ptr(g))
     return loss, g
 
 

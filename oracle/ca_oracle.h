@@ -195,13 +195,16 @@ void orc_sc2_features(const uint8_t *rgb7, const int32_t rows[7], int W, int H, 
 int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, const float *prm,
                     double *logits);
 /* The same with a mode: ORC_SC_EXACT (= orc_sc2_forward) or ORC_SC_MIXED
- * (the roundings of a bfloat16 tensor-core kernel, see the source). */
+ * (the stored-value roundings of a bfloat16 tensor-core kernel, sums in
+ * binary64: a tolerance reference, see the source). */
 int orc_sc2_forward_mode(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
                          const float *prm, int mode, double *logits);
-/* Summed soft binary cross-entropy against targets in [0, 1], gradient added
- * into grads (ORC_SC2_NPARAM doubles). */
+/* Summed soft binary cross-entropy against targets in [0, 1], column x
+ * weighted by 1 + (pos_weight - 1) t_x; gradient added into grads
+ * (ORC_SC2_NPARAM doubles). */
 double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
-                         const double *targets, const float *prm, double *grads);
+                         const double *targets, double pos_weight, const float *prm,
+                         double *grads);
 /* Soft targets of row y: exp(-d^2 / (2 sigma^2)), d the distance of the
  * pixel to the circle; 0 without a circle. */
 void orc_sc2_targets(float cx, float cy, float r, int valid, int W, int y, double sigma,

@@ -10,16 +10,21 @@
  * convolutions, unpadded in the vertical direction, leave exactly the
  * strip's middle row (7 -> 5 -> 3 -> 1 rows).  Horizontally each
  * convolution is "same" with zero padding.  Training uses the soft binary
- * cross-entropy against an edge map blurred with a Gaussian of sigma 3.
+ * cross-entropy against an edge map blurred with a Gaussian of sigma 3
+ * (here optionally weighted: column x counts 1 + (pos_weight - 1) t_x times,
+ * pos_weight = 1 being the paper's unweighted loss).
  *
  * Two modes for the forward pass, as for the 1-D scorer:
  *   ORC_SC_EXACT  binary64 with no rounding (the exact network), whose
  *                 gradient the tests pin by finite differences;
  *   ORC_SC_MIXED  rounded where a tensor-core kernel stores a narrower
- *                 value: features, weights and activations in bfloat16,
- *                 each convolution sum rounded once to binary32 and the bias
- *                 added in binary32, the head summed in binary32 in channel
- *                 order over bfloat16 head weights.
+ *                 value: features, weights and activations in bfloat16, the
+ *                 bias added in binary32, the head summed in binary32 in
+ *                 channel order over bfloat16 head weights.  Each convolution
+ *                 sum itself is taken in binary64 and rounded once to
+ *                 binary32: a tensor core accumulates its products in its
+ *                 own order and width, so this mode is the reference a
+ *                 kernel meets within a tolerance, not its bit pattern.
  *
  * Readings where the paper is silent:
  *   - colour features are (v - 128) / 128 (the paper normalises by its
@@ -159,9 +164,11 @@ int orc_sc2_forward(const uint8_t *rgb7, const int32_t rows[7], int W, int H, co
 }
 
 /* Soft binary cross-entropy of the W columns against targets t in [0, 1],
- * summed, and its gradient added into grads (ORC_SC2_NPARAM doubles). */
+ * column x weighted by w_x = 1 + (pos_weight - 1) t_x, summed, and its
+ * gradient added into grads (ORC_SC2_NPARAM doubles). */
 double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int H,
-                         const double *targets, const float *prm, double *grads) {
+                         const double *targets, double pos_weight, const float *prm,
+                         double *grads) {
     int32_t off[8];
     orc_sc2_offsets(off);
     double *a[NL + 1], *pre[NL];
@@ -182,11 +189,12 @@ double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int 
         double z = prm[off[7]];
         for (int c = 0; c < 32; ++c) z += (double)prm[off[6] + c] * a[NL][(size_t)x * 32 + c];
         const double t = targets[x];
+        const double w = 1.0 + (pos_weight - 1.0) * t;
         /* -t log p - (1 - t) log(1 - p) = softplus(z) - t z, stably */
         const double sp = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
-        loss += sp - t * z;
+        loss += w * (sp - t * z);
         const double p = 1.0 / (1.0 + exp(-z));
-        const double dz = p - t;
+        const double dz = w * (p - t);
         grads[off[7]] += dz;
         for (int c = 0; c < 32; ++c) {
             grads[off[6] + c] += dz * a[NL][(size_t)x * 32 + c];

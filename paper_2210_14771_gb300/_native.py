@@ -11,6 +11,7 @@ CA_ERR_TIMEOUT, CA_ERR_UNSUPPORTED, CA_ERR_ADMISSION, CA_ERR_STATE = 4, 5, 6, 7
 CA_HYP_RANDOM, CA_HYP_EXHAUSTIVE = 0, 1
 CA_NORM_2N, CA_NORM_NK, CA_NORM_RAW = 0, 1, 2
 CA_SCORER_HAND, CA_SCORER_LEARNED, CA_SCORER_LEARNED_FALLBACK = 0, 1, 2
+CA_SCORER_2D, CA_SCORER_2D_FALLBACK = 3, 4
 CA_DUMP_CANDIDATES, CA_DUMP_HYPOTHESES, CA_DUMP_TABLES = 1, 2, 3
 CA_BATCH_AUTO, CA_BATCH_STAGED, CA_BATCH_FUSED = 0, 1, 2
 CA_DUMP_LEARNED = 4
@@ -129,8 +130,19 @@ SIGNATURES = [
     ("ca_pool_free", C.c_int, [C.c_void_p, C.c_size_t]),
     ("ca_pool_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_size_t)]),
     ("ca_pool_destroy", C.c_int, [C.c_void_p]),
+    ("ca_scorer2d_init", C.c_int, [C.c_void_p, C.c_uint64]),
+    ("ca_scorer2d_set_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("ca_scorer2d_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    ("ca_scorer2d_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ca_scorer2d_load", C.c_int, [C.c_void_p, C.c_char_p]),
     ("ca_scorer2d_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
-                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ca_scorer2d_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_int, C.c_int, C.c_int, _P(CaTrainParams), _P(C.c_float),
+                                   C.c_void_p]),
+    ("ca_scorer2d_train", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_int, C.c_int, _P(CaTrainParams), C.c_int, C.c_int,
+                                    C.c_uint64, C.c_void_p]),
     ("ca_smooth_tracked", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, _P(C.c_int32),
                                     _P(C.c_int32), C.c_int, _P(CaSmoothParams), C.c_void_p,
                                     C.c_void_p, C.c_void_p]),

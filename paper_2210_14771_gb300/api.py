@@ -215,22 +215,87 @@ class ContentArea:
                                                   keys_arr, C.byref(p), C.c_void_p(res_ptr),
                                                   C.c_void_p(masks_ptr) if masks_ptr else None))
 
-    def scorer2d_forward(self, strips7: torch.Tensor, rows: torch.Tensor, H: int,
-                         params: torch.Tensor, stream=None) -> torch.Tensor:
-        """ca_scorer2d_forward: logits (n, W) of the middle rows of n strips
-        (n, 7, W, 3) uint8 with their frame rows (n, 7) int32 and the 2-D
-        network's parameters (CA_SCORER2D_NPARAM float32), all on the device."""
+    # ---------------------------------------- the paper's 2-D scorer --
+    @staticmethod
+    def _strip7_args(strips7, rows):
         assert strips7.dtype == torch.uint8 and strips7.is_cuda and strips7.is_contiguous()
         assert strips7.dim() == 4 and strips7.shape[1] == 7 and strips7.shape[3] == 3
         n, W = int(strips7.shape[0]), int(strips7.shape[2])
-        assert rows.dtype == torch.int32 and rows.is_cuda and rows.shape == (n, 7)
-        assert params.dtype == torch.float32 and params.is_cuda and params.numel() == N.CA_SCORER2D_NPARAM
+        assert rows.dtype == torch.int32 and rows.is_cuda and rows.is_contiguous()
+        assert rows.shape == (n, 7)
+        return n, W
+
+    def scorer2d_forward(self, strips7: torch.Tensor, rows: torch.Tensor, H: int,
+                         params: torch.Tensor | None = None, stream=None, scores=False):
+        """ca_scorer2d_forward: logits (n, W) of the middle rows of n strips
+        (n, 7, W, 3) uint8 with their frame rows (n, 7) int32, all on the
+        device; params: CA_SCORER2D_NPARAM float32 on the device, or None for
+        the handle's parameters.  scores=True also returns the Q15 scores."""
+        n, W = self._strip7_args(strips7, rows)
+        if params is not None:
+            assert params.dtype == torch.float32 and params.is_cuda
+            assert params.numel() == N.CA_SCORER2D_NPARAM
+            params = params.contiguous()
         out = torch.empty((n, W), dtype=torch.float32, device=strips7.device)
+        sc = torch.empty((n, W), dtype=torch.int16, device=strips7.device) if scores else None
         self._check(N.lib().ca_scorer2d_forward(
-            self._h, C.c_void_p(strips7.data_ptr()), C.c_void_p(rows.contiguous().data_ptr()), n,
-            W, H, C.c_void_p(params.contiguous().data_ptr()), C.c_void_p(out.data_ptr()),
+            self._h, C.c_void_p(strips7.data_ptr()), C.c_void_p(rows.data_ptr()), n, W, H,
+            C.c_void_p(params.data_ptr()) if params is not None else None,
+            C.c_void_p(out.data_ptr()), C.c_void_p(sc.data_ptr()) if sc is not None else None,
             _stream_ptr(stream, strips7.device)))
-        return out
+        return (out, sc) if scores else out
+
+    def scorer2d_init(self, seed: int = 0):
+        self._check(N.lib().ca_scorer2d_init(self._h, seed))
+
+    def scorer2d_set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(N.lib().ca_scorer2d_set_params(self._h, p.ctypes.data_as(C.c_void_p), p.size))
+
+    def scorer2d_get_params(self) -> np.ndarray:
+        p = np.zeros(N.CA_SCORER2D_NPARAM, np.float32)
+        self._check(N.lib().ca_scorer2d_get_params(self._h, p.ctypes.data_as(C.c_void_p), p.size))
+        return p
+
+    def scorer2d_save(self, path: str):
+        self._check(N.lib().ca_scorer2d_save(self._h, path.encode()))
+
+    def scorer2d_load(self, path: str):
+        self._check(N.lib().ca_scorer2d_load(self._h, path.encode()))
+
+    def scorer2d_step(self, strips7, rows, targets, H: int, idx=None, lr=0.0, momentum=0.9,
+                      pos_weight=1.0, apply=False, want_grads=True, clip_norm=0.0):
+        """One training step of the 2-D network on soft targets (n, W) float32;
+        returns (summed loss, summed gradient or None)."""
+        n, W = self._strip7_args(strips7, rows)
+        assert targets.dtype == torch.float32 and targets.is_cuda and targets.shape == (n, W)
+        if idx is not None:
+            assert idx.dtype == torch.int32 and idx.is_cuda
+            n = int(idx.numel())
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1 if apply else 0, clip_norm,
+                             N.CA_LR_CONSTANT)
+        loss = C.c_float(0.0)
+        g = np.zeros(N.CA_SCORER2D_NPARAM, np.float32) if want_grads else None
+        self._check(N.lib().ca_scorer2d_step(
+            self._h, C.c_void_p(strips7.data_ptr()), C.c_void_p(rows.data_ptr()),
+            C.c_void_p(targets.data_ptr()), C.c_void_p(idx.data_ptr()) if idx is not None else None,
+            n, W, H, C.byref(tp), C.byref(loss),
+            g.ctypes.data_as(C.c_void_p) if g is not None else None))
+        return float(loss.value), g
+
+    def scorer2d_train(self, strips7, rows, targets, H: int, epochs=1, batch=64, seed=0, lr=0.05,
+                       momentum=0.9, pos_weight=1.0, clip_norm=1.0, schedule="cosine"):
+        """ca_scorer2d_train; returns the mean loss per column of each epoch."""
+        n, W = self._strip7_args(strips7, rows)
+        assert targets.dtype == torch.float32 and targets.shape == (n, W)
+        sched = {"constant": N.CA_LR_CONSTANT, "cosine": N.CA_LR_COSINE}[schedule]
+        tp = N.CaTrainParams(lr, momentum, pos_weight, 1, clip_norm, sched)
+        out = np.zeros(max(epochs, 1), np.float32)
+        self._check(N.lib().ca_scorer2d_train(
+            self._h, C.c_void_p(strips7.data_ptr()), C.c_void_p(rows.data_ptr()),
+            C.c_void_p(targets.data_ptr()), n, W, H, C.byref(tp), epochs, batch, seed,
+            out.ctypes.data_as(C.c_void_p)))
+        return out[:epochs]
 
     def smooth_tracked(self, res: torch.Tensor, widths, track, state: torch.Tensor, gamma: float,
                        jump: float, t_hold: float, out: torch.Tensor | None = None, stream=None):

@@ -64,6 +64,7 @@ struct ca_handle {
     LutKey lut_key;
     int qg_sat = kLutG - 1;
     uint16_t li_host[kLutI] = {};   // host copy of the s_iota table
+    uint16_t lt_host[kLutT] = {};   // host copy of the s_theta table
     bool luts_ready = false;
 
     Staging ring[kRing];
@@ -112,6 +113,19 @@ struct ca_handle {
         std::vector<int64_t> last_pix_off;
         std::vector<int32_t> last_W;
     } sc;
+
+    // the paper's 2-D scorer: f32 parameters and momentum, packed bf16 weight
+    // block (and one for parameters passed by the caller), gradient partials
+    struct {
+        bool ready = false;
+        float *params = nullptr, *mom = nullptr, *partial = nullptr, *grads = nullptr,
+              *losses = nullptr, *norm = nullptr;
+        unsigned char *block = nullptr, *block_tmp = nullptr;
+        uint32_t *err = nullptr;
+        int32_t *idx = nullptr;
+        size_t idx_cap = 0, losses_cap = 0;
+        int partial_n = 0;
+    } sc2;
 
     // host-side failure injection (ca_inject_failure): estimate calls to
     // accept before the next one fails with inject_status (0: disarmed)
@@ -290,6 +304,20 @@ int iota_cut(const uint16_t *li, uint32_t T_ps) {
     return kLutI;
 }
 
+// Angle cut of the strip kernels.  s_theta is non-decreasing in its bin, so
+// the bins q <= q_cut with s_theta[q] < T_ps form a prefix; a pixel there has
+// score <= s_theta < T_ps and is never kept.  Its bin is below q_cut + 1 iff
+// u = dot |dot| / (ng nc) < (q_cut + 1) / 4096 - 1; the kernels test that in
+// binary32 against the bound lowered by 2^-10, far more than the test's
+// rounding error (a few parts in 10^7 of |u| <= 1), so they drop only pixels
+// of those bins.
+void angle_cut(const uint16_t *lt, uint32_t T_ps, DevParams &P) {
+    int q = -1;
+    while (q + 1 < kLutT && lt[q + 1] < T_ps) ++q;
+    P.theta_cut_on = q >= 0 ? 1 : 0;
+    P.theta_u_cut = q >= 0 ? (float)((double)(q + 1) / 4096.0 - 1.0 - 1.0 / 1024.0) : -2.0f;
+}
+
 // ------------------------------------------------------ validation --
 ca_status check_params(ca_handle *h, const ca_params *p) {
     if (!p) return fail(h, CA_ERR_INVALID_ARG, "params is NULL");
@@ -321,9 +349,16 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
     if (p->hyp_threads != 0 && p->hyp_threads != 1 && p->hyp_threads != 2 &&
         p->hyp_threads != 4 && p->hyp_threads != 8)
         return fail(h, CA_ERR_INVALID_ARG, "hyp_threads %d not in {0, 1, 2, 4, 8}", p->hyp_threads);
-    if (p->scorer_mode < CA_SCORER_HAND || p->scorer_mode > CA_SCORER_LEARNED_FALLBACK)
+    if (p->scorer_mode < CA_SCORER_HAND || p->scorer_mode > CA_SCORER_2D_FALLBACK)
         return fail(h, CA_ERR_INVALID_ARG, "bad scorer_mode %d", p->scorer_mode);
-    if (p->scorer_mode != CA_SCORER_HAND) {
+    if (p->scorer_mode == CA_SCORER_2D || p->scorer_mode == CA_SCORER_2D_FALLBACK) {
+        if (!h || !h->sc2.ready)
+            return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs 2-D scorer parameters "
+                        "(ca_scorer2d_init / set_params / load)", p->scorer_mode);
+        if (p->cands_per_strip / 2 > kScMaxPicks)
+            return fail(h, CA_ERR_INVALID_ARG, "learned scorer: cands_per_strip <= %d",
+                        2 * kScMaxPicks);
+    } else if (p->scorer_mode != CA_SCORER_HAND) {
         if (!h || !h->sc.ready)
             return fail(h, CA_ERR_UNSUPPORTED, "scorer_mode %d needs scorer parameters "
                         "(ca_scorer_init / set_params / load)", p->scorer_mode);
@@ -441,6 +476,7 @@ ca_status ensure_luts(ca_handle *h, const ca_params &p, cudaStream_t stream) {
     std::vector<uint16_t> host((size_t)kLutG + kLutT + kLutI);
     build_luts(p, host.data(), &h->qg_sat);
     std::memcpy(h->li_host, host.data() + kLutG + kLutT, sizeof(h->li_host));
+    std::memcpy(h->lt_host, host.data() + kLutG, sizeof(h->lt_host));
     pack_device_tables(host.data(), h->qg_sat, (uint16_t *)s->host);
     if (!h->d_luts) CA_CUDA(h, cudaMalloc(&h->d_luts, bytes));
     CA_CUDA(h, cudaMemcpyAsync(h->d_luts, s->host, bytes, cudaMemcpyHostToDevice, stream));
@@ -480,6 +516,7 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T, 
     P.score_den = 32768.0 * norm;
     P.qg_sat = h->qg_sat;
     P.io_cut = iota_cut(h->li_host, P.T_ps);
+    angle_cut(h->lt_host, P.T_ps, P);
     P.NH = (int)hyps_per_frame(p);
     P.track = track ? 1 : 0;
     P.prior_centre = (track && p.prior_centre) ? 1 : 0;
@@ -545,6 +582,11 @@ LaunchCfg choose_cfg(const ca_handle *h, const ca_frame *frames, int B, const ca
     return c;
 }
 
+// True for the scorer modes of the paper's 2-D network.
+inline bool sc2_mode(int scorer) {
+    return scorer == CA_SCORER_2D || scorer == CA_SCORER_2D_FALLBACK;
+}
+
 // Host image of a call's descriptor block: frames | strip rows | segments.
 struct CallBlock {
     std::vector<unsigned char> host;
@@ -585,7 +627,8 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
                       : ((uintptr_t)f.mask_dev % 16 == 0 && f.W % 16 == 0) ? 1 : 0;
         d.sc_seg_off = sc_segs;
         d.sc_pix_off = (int32_t)sc_pix;
-        sc_segs += N * ((f.W + kScSegOutInfer - 1) / kScSegOutInfer);
+        const int seg_out = sc2_mode(cfg.scorer) ? kSc2SegOut : kScSegOutInfer;
+        sc_segs += N * ((f.W + seg_out - 1) / seg_out);
         sc_pix += (int64_t)N * f.W;
         if (f.mask_dev) {
             units += (f.H + kMaskRowsPerUnit - 1) / kMaskRowsPerUnit;
@@ -706,14 +749,34 @@ ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32
     // uneven half-strips
     const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
     cudaEvent_t t0 = nullptr;
-    if (cfg.scorer != CA_SCORER_LEARNED) {
+    const bool no_hand = cfg.scorer == CA_SCORER_LEARNED || cfg.scorer == CA_SCORER_2D;
+    if (!no_hand) {
         t0 = timed ? time_begin(h, stream) : nullptr;
         e = launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "k_strips launch");
         time_end(h, 0, t0, stream);
         *kernels += 1;
     }
-    if (cfg.scorer != CA_SCORER_HAND) {
+    if (sc2_mode(cfg.scorer)) {
+        // the paper's 2-D network on the 7 rows around every strip row, then
+        // the picks per half-strip
+        Sc2Source src{};
+        src.frames = d_frames;
+        src.B = B;
+        src.rows = d_rows;
+        src.N = P.N;
+        const int grid = std::max(1, std::min(cb.sc_segs, h->sm_count * sc2_infer_blocks_per_sm()));
+        t0 = timed ? time_begin(h, stream) : nullptr;
+        e = sc2_launch_infer(src, h->sc2.block, h->sc.scores, nullptr, cb.sc_segs, h->sc2.err, grid,
+                             stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_infer launch");
+        time_end(h, 4, t0, stream);
+        const int pgrid = std::max(1, std::min((2 * B * P.N + 7) / 8, h->sm_count * 8));
+        e = sc_launch_pick(d_frames, B, d_rows, P, h->sc.scores,
+                           cfg.scorer == CA_SCORER_2D_FALLBACK, ws.slots, pgrid, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_pick launch");
+        *kernels += 2;
+    } else if (cfg.scorer != CA_SCORER_HAND) {
         // learned scores of every strip column, then the picks per half-strip
         ScSource src{};
         src.frames = d_frames;
@@ -944,6 +1007,16 @@ ca_status ca_destroy(ca_handle *h) {
     cudaFree(h->sc.err);
     cudaFree(h->sc.idx);
     cudaFree(h->sc.scores);
+    cudaFree(h->sc2.params);
+    cudaFree(h->sc2.mom);
+    cudaFree(h->sc2.partial);
+    cudaFree(h->sc2.grads);
+    cudaFree(h->sc2.norm);
+    cudaFree(h->sc2.losses);
+    cudaFree(h->sc2.block);
+    cudaFree(h->sc2.block_tmp);
+    cudaFree(h->sc2.err);
+    cudaFree(h->sc2.idx);
     cudaFree(h->e2e_frames);
     cudaFree(h->e2e_masks);
     cudaFree(h->e2e_res);
@@ -1385,15 +1458,17 @@ ca_status ca_plan_create(ca_handle *h, const ca_frame *frames, int B, const ca_p
     pack_device_tables(luts.data(), qg_sat, dev_tab.data());
     // make_params reads the handle's table state: point it at these tables
     const int saved_qg = h->qg_sat;
-    uint16_t saved_li[kLutI];
-    std::memcpy(saved_li, h->li_host, sizeof(saved_li));
+    std::vector<uint16_t> saved_li(h->li_host, h->li_host + kLutI);
+    std::vector<uint16_t> saved_lt(h->lt_host, h->lt_host + kLutT);
     h->qg_sat = qg_sat;
     std::memcpy(h->li_host, luts.data() + kLutG + kLutT, sizeof(h->li_host));
+    std::memcpy(h->lt_host, luts.data() + kLutG, sizeof(h->lt_host));
     int max_w = 0;
     for (int i = 0; i < B; ++i) max_w = std::max(max_w, frames[i].W);
     const DevParams P = make_params(h, *p, max_w, cfg.T);
     h->qg_sat = saved_qg;
-    std::memcpy(h->li_host, saved_li, sizeof(saved_li));
+    std::memcpy(h->li_host, saved_li.data(), sizeof(h->li_host));
+    std::memcpy(h->lt_host, saved_lt.data(), sizeof(h->lt_host));
     CallBlock cb;
     build_block(frames, B, p->n_strips, p->alpha, &P, cfg, cb);
 
@@ -1484,24 +1559,278 @@ ca_status ca_estimate_tracked(ca_handle *h, const ca_frame *frames, int B, const
                         track, state_dev);
 }
 
-ca_status ca_scorer2d_forward(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
-                              int n, int W, int H, const float *params_dev, float *logits_dev,
-                              void *stream) {
-    if (!h) return CA_ERR_INVALID_ARG;
+// --------------------------------------------- the paper's 2-D scorer --
+namespace {
+
+ca_status sc2_alloc(ca_handle *h) {
+    auto &S = h->sc2;
+    if (S.params) return CA_OK;
+    CA_CUDA(h, cudaSetDevice(h->device));
+    S.partial_n = h->sm_count;   // one partial slice per training CTA (one CTA per SM)
+    CA_CUDA(h, cudaMalloc(&S.params, sizeof(float) * kScorer2dNParam));
+    CA_CUDA(h, cudaMalloc(&S.mom, sizeof(float) * kScorer2dNParam));
+    CA_CUDA(h, cudaMalloc(&S.grads, sizeof(float) * kScorer2dNParam));
+    CA_CUDA(h, cudaMalloc(&S.norm, sizeof(float) * kSc2SgdBlocks));
+    CA_CUDA(h, cudaMalloc(&S.partial, sizeof(float) * kSc2PartialStride * (size_t)S.partial_n));
+    CA_CUDA(h, cudaMalloc(&S.block, kSc2BlockBytes));
+    CA_CUDA(h, cudaMalloc(&S.block_tmp, kSc2BlockBytes));
+    CA_CUDA(h, cudaMalloc(&S.err, sizeof(uint32_t)));
+    CA_CUDA(h, cudaMemset(S.partial, 0, sizeof(float) * kSc2PartialStride * (size_t)S.partial_n));
+    CA_CUDA(h, cudaMemset(S.block, 0, kSc2BlockBytes));
+    CA_CUDA(h, cudaMemset(S.err, 0, sizeof(uint32_t)));
+    return CA_OK;
+}
+
+// Uploads parameters (and zero momentum) and packs the weight block.
+ca_status sc2_upload(ca_handle *h, const float *params, const float *mom) {
+    ca_status st = sc2_alloc(h);
+    if (st != CA_OK) return st;
+    auto &S = h->sc2;
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    CA_CUDA(h, cudaMemcpy(S.params, params, sizeof(float) * kScorer2dNParam, cudaMemcpyHostToDevice));
+    if (mom) CA_CUDA(h, cudaMemcpy(S.mom, mom, sizeof(float) * kScorer2dNParam, cudaMemcpyHostToDevice));
+    else CA_CUDA(h, cudaMemset(S.mom, 0, sizeof(float) * kScorer2dNParam));
+    CA_CUDA(h, sc2_launch_pack(S.params, S.block, nullptr));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    S.ready = true;
+    return CA_OK;
+}
+
+ca_status sc2_check_err(ca_handle *h) {
+    uint32_t e = 0;
+    CA_CUDA(h, cudaMemcpy(&e, h->sc2.err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) {
+        CA_CUDA(h, cudaMemset(h->sc2.err, 0, sizeof(uint32_t)));
+        return fail(h, CA_ERR_TIMEOUT, "a tensor-core wait of the 2-D scorer gave up (flags 0x%x)", e);
+    }
+    return CA_OK;
+}
+
+ca_status check_strips7(ca_handle *h, const uint8_t *strips, const int32_t *rows, int n, int W,
+                        int H) {
+    if (!strips || !rows) return fail(h, CA_ERR_INVALID_ARG, "strips7 or rows is NULL");
     if (n < 0 || W < 1 || W > kMaxDim || H < 1 || H > kMaxDim)
         return fail(h, CA_ERR_INVALID_ARG, "bad strip set (n %d, W %d, H %d)", n, W, H);
+    return CA_OK;
+}
+
+// Forward + loss + gradient partials of n strips, then the reduction (and the
+// update when tp->apply).  Queued on `s`.
+ca_status sc2_step_async(ca_handle *h, const uint8_t *strips7, const int32_t *rows7,
+                         const float *targets, const int32_t *idx, int n, int W, int H,
+                         const ca_train_params &tp, float *loss_dev, float *grads_dev,
+                         cudaStream_t s) {
+    auto &S = h->sc2;
+    Sc2Source src{};
+    src.strips7 = strips7;
+    src.rows7 = rows7;
+    src.idx = idx;
+    src.n = n;
+    src.W = W;
+    src.H = H;
+    const int segs = sc_segs_of(n, W, kSc2SegOut);
+    const int grid = std::max(1, std::min(segs, S.partial_n));
+    cudaError_t e = sc2_launch_train(src, targets, tp.pos_weight, S.block, S.partial, segs, S.err,
+                                     grid, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_train launch");
+    const float scale = 1.0f / (float)((double)n * W);
+    e = sc2_launch_sgd(S.params, S.mom, S.partial, grid, scale, tp.lr, tp.momentum, tp.apply,
+                       tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_sgd launch");
+    h->launches += (tp.apply && tp.clip_norm > 0.0f) ? 3 : 2;
+    if (tp.apply) {
+        e = sc2_launch_pack(S.params, S.block, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_pack launch");
+        h->launches += 1;
+    }
+    return CA_OK;
+}
+
+}  // namespace
+
+ca_status ca_scorer2d_init(ca_handle *h, uint64_t seed) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    std::vector<float> p(kScorer2dNParam, 0.0f);
+    uint64_t st = seed ^ 0x2D5CA1AB1E5EEDull;
+    auto fill = [&](int off, int count, double stdv) {
+        for (int i = 0; i < count; ++i) p[off + i] = (float)(stdv * gauss(st));
+    };
+    fill(kSc2PW1, kSc2PB1 - kSc2PW1, std::sqrt(2.0 / 45.0));
+    fill(kSc2PW2, kSc2PB2 - kSc2PW2, std::sqrt(2.0 / 72.0));
+    fill(kSc2PW3, kSc2PB3 - kSc2PW3, std::sqrt(2.0 / 144.0));
+    fill(kSc2PWh, 32, std::sqrt(1.0 / 32.0));
+    p[kSc2PBh] = -3.0f;
+    return sc2_upload(h, p.data(), nullptr);
+}
+
+ca_status ca_scorer2d_set_params(ca_handle *h, const float *params, size_t n) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (!params || n != (size_t)kScorer2dNParam)
+        return fail(h, CA_ERR_INVALID_ARG, "2-D scorer parameters: need %d values", kScorer2dNParam);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(params[i])) return fail(h, CA_ERR_INVALID_ARG, "non-finite parameter %zu", i);
+    return sc2_upload(h, params, nullptr);
+}
+
+ca_status ca_scorer2d_get_params(ca_handle *h, float *params, size_t n) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    if (!params || n != (size_t)kScorer2dNParam)
+        return fail(h, CA_ERR_INVALID_ARG, "2-D scorer parameters: need %d values", kScorer2dNParam);
+    if (!h->sc2.ready) return fail(h, CA_ERR_STATE, "2-D scorer has no parameters");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    CA_CUDA(h, cudaMemcpy(params, h->sc2.params, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return CA_OK;
+}
+
+ca_status ca_scorer2d_save(ca_handle *h, const char *path) {
+    if (!h || !path) return CA_ERR_INVALID_ARG;
+    if (!h->sc2.ready) return fail(h, CA_ERR_STATE, "2-D scorer has no parameters");
+    std::vector<float> p(kScorer2dNParam), m(kScorer2dNParam);
+    CA_CUDA(h, cudaSetDevice(h->device));
+    CA_CUDA(h, cudaDeviceSynchronize());
+    CA_CUDA(h, cudaMemcpy(p.data(), h->sc2.params, sizeof(float) * p.size(), cudaMemcpyDeviceToHost));
+    CA_CUDA(h, cudaMemcpy(m.data(), h->sc2.mom, sizeof(float) * m.size(), cudaMemcpyDeviceToHost));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(h, CA_ERR_INVALID_ARG, "cannot write %s", path);
+    const uint32_t hdr[4] = {0x32534143u /* "CAS2" */, 1u, (uint32_t)kScorer2dNParam, 2u};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size() &&
+              std::fwrite(m.data(), sizeof(float), m.size(), f) == m.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? CA_OK : fail(h, CA_ERR_INVALID_ARG, "short write to %s", path);
+}
+
+ca_status ca_scorer2d_load(ca_handle *h, const char *path) {
+    if (!h || !path) return CA_ERR_INVALID_ARG;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(h, CA_ERR_INVALID_ARG, "cannot read %s", path);
+    uint32_t hdr[4] = {0, 0, 0, 0};
+    std::vector<float> p(kScorer2dNParam), m(kScorer2dNParam);
+    bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 0x32534143u && hdr[1] == 1u &&
+              hdr[2] == (uint32_t)kScorer2dNParam && hdr[3] == 2u &&
+              std::fread(p.data(), sizeof(float), p.size(), f) == p.size() &&
+              std::fread(m.data(), sizeof(float), m.size(), f) == m.size();
+    std::fclose(f);
+    if (!ok) return fail(h, CA_ERR_INVALID_ARG, "%s is not a 2-D scorer checkpoint", path);
+    return sc2_upload(h, p.data(), m.data());
+}
+
+ca_status ca_scorer2d_forward(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                              int n, int W, int H, const float *params_dev, float *logits_dev,
+                              uint16_t *scores_dev, void *stream) {
+    if (!h) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips7(h, strips7_dev, rows_dev, n, W, H);
+    if (st != CA_OK) return st;
     if (n == 0) return CA_OK;
-    if (!strips7_dev || !rows_dev || !params_dev || !logits_dev)
-        return fail(h, CA_ERR_INVALID_ARG, "NULL argument to ca_scorer2d_forward");
+    if (!logits_dev && !scores_dev)
+        return fail(h, CA_ERR_INVALID_ARG, "ca_scorer2d_forward: no output");
+    if (!params_dev && !h->sc2.ready) return fail(h, CA_ERR_STATE, "2-D scorer has no parameters");
+    if ((st = sc2_alloc(h)) != CA_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     CA_CUDA(h, cudaSetDevice(h->device));
-    ca_status st = order_after_last(h, s);
-    if (st != CA_OK) return st;
-    const cudaError_t e = sc2_launch_forward(strips7_dev, rows_dev, n, W, H, params_dev,
-                                             logits_dev, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_forward launch");
+    if ((st = order_after_last(h, s)) != CA_OK) return st;
+    const unsigned char *block = h->sc2.block;
+    if (params_dev) {   // the caller's parameters, packed into the handle's spare block
+        const cudaError_t e = sc2_launch_pack(params_dev, h->sc2.block_tmp, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_pack launch");
+        block = h->sc2.block_tmp;
+        h->launches += 1;
+    }
+    Sc2Source src{};
+    src.strips7 = strips7_dev;
+    src.rows7 = rows_dev;
+    src.n = n;
+    src.W = W;
+    src.H = H;
+    const int segs = sc_segs_of(n, W, kSc2SegOut);
+    const int grid = std::max(1, std::min(segs, h->sm_count * sc2_infer_blocks_per_sm()));
+    cudaEvent_t t0 = time_begin(h, s);
+    const cudaError_t e = sc2_launch_infer(src, block, scores_dev, logits_dev, segs, h->sc2.err,
+                                           grid, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_infer launch");
+    time_end(h, 4, t0, s);
     h->launches += 1;
     return mark_last(h, s);
+}
+
+ca_status ca_scorer2d_step(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                           const float *targets_dev, const int32_t *idx_dev, int n, int W, int H,
+                           const ca_train_params *tp, float *loss_host, float *grads_host) {
+    if (!h || !tp) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips7(h, strips7_dev, rows_dev, n, W, H);
+    if (st != CA_OK) return st;
+    if ((st = check_train_params(h, *tp)) != CA_OK) return st;
+    if (!targets_dev || n == 0) return fail(h, CA_ERR_INVALID_ARG, "no targets or no strips");
+    if (!h->sc2.ready) return fail(h, CA_ERR_STATE, "2-D scorer has no parameters");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    if (!h->sc2.losses) {
+        CA_CUDA(h, cudaMalloc(&h->sc2.losses, sizeof(float) * 1024));
+        h->sc2.losses_cap = 1024;
+    }
+    if ((st = sc2_step_async(h, strips7_dev, rows_dev, targets_dev, idx_dev, n, W, H, *tp,
+                             h->sc2.losses, grads_host ? h->sc2.grads : nullptr, nullptr)) != CA_OK)
+        return st;
+    CA_CUDA(h, cudaDeviceSynchronize());
+    if ((st = sc2_check_err(h)) != CA_OK) return st;
+    if (loss_host)
+        CA_CUDA(h, cudaMemcpy(loss_host, h->sc2.losses, sizeof(float), cudaMemcpyDeviceToHost));
+    if (grads_host)
+        CA_CUDA(h, cudaMemcpy(grads_host, h->sc2.grads, sizeof(float) * kScorer2dNParam,
+                              cudaMemcpyDeviceToHost));
+    return CA_OK;
+}
+
+ca_status ca_scorer2d_train(ca_handle *h, const uint8_t *strips7_dev, const int32_t *rows_dev,
+                            const float *targets_dev, int n, int W, int H,
+                            const ca_train_params *tp, int epochs, int batch, uint64_t seed,
+                            float *epoch_loss_host) {
+    if (!h || !tp) return CA_ERR_INVALID_ARG;
+    ca_status st = check_strips7(h, strips7_dev, rows_dev, n, W, H);
+    if (st != CA_OK) return st;
+    if ((st = check_train_params(h, *tp)) != CA_OK) return st;
+    if (!targets_dev || n == 0 || epochs < 0 || batch < 1)
+        return fail(h, CA_ERR_INVALID_ARG, "bad training arguments");
+    if (!h->sc2.ready) return fail(h, CA_ERR_STATE, "2-D scorer has no parameters");
+    CA_CUDA(h, cudaSetDevice(h->device));
+    if (h->has_last) CA_CUDA(h, cudaEventSynchronize(h->last_ev));
+    auto &S = h->sc2;
+    const int steps = (n + batch - 1) / batch;
+    if ((size_t)n > S.idx_cap) {
+        if ((st = grow(h, &S.idx, 0, (size_t)n, false)) != CA_OK) return st;
+        S.idx_cap = (size_t)n;
+    }
+    if ((size_t)steps > S.losses_cap) {
+        if ((st = grow(h, &S.losses, 0, (size_t)steps, false)) != CA_OK) return st;
+        S.losses_cap = (size_t)steps;
+    }
+    std::vector<int32_t> order((size_t)n);
+    std::vector<float> losses((size_t)steps);
+    uint64_t rs = seed ^ 0x2DEA1C0DEull;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = 0; i < n; ++i) order[i] = i;
+        for (int i = n - 1; i > 0; --i) std::swap(order[i], order[splitmix64(rs) % (uint64_t)(i + 1)]);
+        CA_CUDA(h, cudaMemcpy(S.idx, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+        for (int k = 0; k < steps; ++k) {
+            const int cnt = std::min(batch, n - k * batch);
+            ca_train_params tk = *tp;
+            tk.lr = scheduled_lr(*tp, (long long)ep * steps + k, (long long)epochs * steps);
+            if ((st = sc2_step_async(h, strips7_dev, rows_dev, targets_dev,
+                                     S.idx + (size_t)k * batch, cnt, W, H, tk, S.losses + k,
+                                     nullptr, nullptr)) != CA_OK)
+                return st;
+        }
+        CA_CUDA(h, cudaMemcpy(losses.data(), S.losses, sizeof(float) * steps, cudaMemcpyDeviceToHost));
+        if ((st = sc2_check_err(h)) != CA_OK) return st;
+        if (epoch_loss_host) {
+            double t = 0.0;
+            for (float v : losses) t += v;
+            epoch_loss_host[ep] = (float)(t / ((double)n * W));
+        }
+    }
+    CA_CUDA(h, cudaDeviceSynchronize());
+    return CA_OK;
 }
 
 ca_status ca_smooth_tracked(ca_handle *h, const ca_result *res_dev, int B, const int32_t *W,
@@ -1675,6 +2004,7 @@ ca_status ca_sync(ca_handle *h, void *stream) {
     for (ca_plan *pl : h->plans)
         if (st == CA_OK) st = check_sync_word(h, pl->ws);
     if (st == CA_OK && h->sc.err) st = sc_check_err(h);
+    if (st == CA_OK && h->sc2.err) st = sc2_check_err(h);
     return st;
 }
 

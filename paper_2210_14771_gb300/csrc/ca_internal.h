@@ -89,6 +89,8 @@ struct DevParams {
     int32_t io_cut;      // preceding maxima >= io_cut have s_iota < T_ps: never kept
     int32_t track;       // 1: tracked call (previous circles as extra hypotheses)
     int32_t prior_centre;  // tracked call: the angle term points at the previous centre
+    int32_t theta_cut_on;  // 1: pixels whose angle bin has s_theta < T_ps are skipped
+    float theta_u_cut;     // their signed squared cosines are below this (margin included)
     const int32_t *trk;          // tracked call: [B] track of each frame (-1: none)
     const ca_result *trk_state;  // tracked call: per-track previous result
 };
@@ -184,11 +186,54 @@ cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_parti
                           float lr, float momentum, int apply, float clip, float *gbuf,
                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
 
-// Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
-// The paper's 2-D scorer (Sec. 2.2.4): forward pass on n strips of 7 rows.
+// ---- The paper's 2-D scorer (ca_scorer2d.cu, Sec. 2.2.4): 3x3 convolutions
+// to 8, 16, 32 features over 7-row RGBXY strips, on tcgen05.
 constexpr int kScorer2dNParam = 6209;
-cudaError_t sc2_launch_forward(const uint8_t *strips7, const int32_t *rows, int n, int W, int H,
-                               const float *params, float *logits, cudaStream_t s);
+constexpr int kSc2Tiles = 3;                               // 128-column tiles per segment
+constexpr int kSc2Halo = 3;                                // one column of context per layer
+constexpr int kSc2SegOut = 128 * kSc2Tiles - 2 * kSc2Halo; // output columns per segment
+// parameter offsets: W1[8][5][3][3], b1, W2[16][8][3][3], b2, W3[32][16][3][3], b3, wh, bh
+constexpr int kSc2PW1 = 0, kSc2PB1 = 360, kSc2PW2 = 368, kSc2PB2 = 1520, kSc2PW3 = 1536,
+              kSc2PB3 = 6144, kSc2PWh = 6176, kSc2PBh = 6208;
+// packed device weight block (bytes): bf16 B operands of the forward
+// convolutions (L1, L2: per row tap and column-tap pair [2 chunks][16 out][8 in];
+// L3: per tap [2 chunks][32 out][8 in]), of the input-gradient convolutions
+// (W3 transposed: per tap [4 chunks of 8 out][16 in][8]; W2 transposed: per
+// tap [2 chunks][16 (8 real) in][8]), then floats
+constexpr int kSc2OffW1 = 0, kSc2OffW2 = 3072, kSc2OffW3 = 6144, kSc2OffW3b = 15360,
+              kSc2OffW2b = 24576, kSc2OffVec = 29184;
+constexpr int kSc2FwdBytes = 15360, kSc2VecBytes = 384, kSc2BlockBytes = 29568;
+constexpr int kSc2PartialStride = 6272;   // per-CTA gradient partials (+ loss at kScorer2dNParam)
+constexpr int kSc2SgdBlocks = (kScorer2dNParam + 1 + 63) / 64;
+
+// Strips the 2-D scorer reads: frames (the 7 rows around each strip row of the
+// strip-row table, clamped into the frame) or stand-alone 7-row strips.
+struct Sc2Source {
+    const DevFrame *frames;   // frames mode (segments numbered by DevFrame::sc_seg_off)
+    int B;
+    const int32_t *rows;
+    int N;
+    const uint8_t *strips7;   // strips mode (frames == nullptr): n x 7 x W x 3 bytes
+    const int32_t *rows7;     // n x 7 frame rows of the strips' rows
+    const int32_t *idx;       // optional index list of the strips to use
+    int n, W, H;
+};
+
+cudaError_t sc2_launch_pack(const float *params, unsigned char *block, cudaStream_t s);
+size_t sc2_infer_smem();
+int sc2_infer_blocks_per_sm();
+cudaError_t sc2_launch_infer(const Sc2Source &src, const unsigned char *block, uint16_t *scores,
+                             float *logits, int total_segs, uint32_t *err, int grid,
+                             cudaStream_t s);
+size_t sc2_train_smem();
+cudaError_t sc2_launch_train(const Sc2Source &src, const float *targets, float pos_weight,
+                             const unsigned char *block, float *partial, int total_segs,
+                             uint32_t *err, int grid, cudaStream_t s);
+cudaError_t sc2_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
+                           float lr, float momentum, int apply, float clip, float *gbuf,
+                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
+
+// Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
 
 // Temporal smoothing of B results (one thread per frame); w_trk: [B] pairs
 // (W, track) on the device.
@@ -222,6 +267,7 @@ void strip_rows(int H, int N, float alpha, int32_t *rows);        // Eq. 1 rows
 void build_luts(const ca_params &p, uint16_t *out, int *qg_sat);  // Eq. 2 tables
 ca_status check_params(ca_handle *h, const ca_params *p);         // h may be NULL
 int iota_cut(const uint16_t *li, uint32_t T_ps);                  // see ca_api.cu
+void angle_cut(const uint16_t *lt, uint32_t T_ps, DevParams &P);  // see ca_api.cu
 // Device table block (kDevTableU16 entries) from build_luts' [s_g][s_theta][s_iota].
 void pack_device_tables(const uint16_t *luts, int qg_sat, uint16_t *out);
 

@@ -111,9 +111,14 @@ __host__ __device__ __forceinline__ size_t strip_tables_bytes(const DevParams &P
     return 2 * (size_t)(kDevOffG - kDevOffI + strip_lg_len(P));
 }
 
+// K = 2: each warp's queue of pixels awaiting their exact score (one round of
+// 32 pushes on top of at most 31 waiting entries).
+constexpr int kQueueCap = 64;
+
 size_t strips_smem_bytes(const DevParams &P) {
     size_t b = strip_tables_bytes(P) + (size_t)kStripWarps * strip_cols(P) * 4;
     if (P.K > 2) b += (size_t)kStripWarps * (strip_cols(P) * 2 + 4 * (kMaxSlots / 2));
+    else b += (size_t)kStripWarps * kQueueCap * sizeof(uint2);
     return b;
 }
 
@@ -171,6 +176,21 @@ __device__ __forceinline__ uint32_t score_from_g(const StripCtx &c, int gx, int 
     return (gt * ii + 16384u) >> 15;
 }
 
+// Angle cut: false when the pixel's angle bin certainly has s_theta < T_ps, so
+// that its score (at most s_theta) can never be kept.  The bins below the cut
+// are those with u = dot |dot| / (ng nc) < u_cut; the host passes u_cut lowered
+// by a margin far above the rounding error of this binary32 test, so the cut
+// never drops a pixel whose bin reaches the threshold.
+__device__ __forceinline__ bool angle_ok(const StripCtx &c, int gx, int gy, int x, int ng,
+                                         const DevParams &P) {
+    if (!P.theta_cut_on) return true;
+    const int cx2 = c.c2x - 2 * x;
+    const int dot = gx * cx2 + gy * c.cy2;
+    const float fd = __int2float_rn(dot);
+    const float fnc = __int2float_rn(cx2 * cx2 + c.cy2 * c.cy2);
+    return __fmul_rn(fd, fabsf(fd)) >= __fmul_rn(P.theta_u_cut, __fmul_rn(__int2float_rn(ng), fnc));
+}
+
 }  // namespace
 
 namespace {
@@ -179,7 +199,7 @@ namespace {
 // the per-warp buffers.
 struct StripShared {
     const uint16_t *li, *lgb, *lg;   // s_iota, s_g bin bounds, s_g
-    unsigned char *wmem;             // per-warp column words (+ scores, picks)
+    unsigned char *wmem;             // per-warp column words (+ scores, picks or queues)
     int *s_qmax;                     // [kStripWarps] per-warp maxima (quads)
     uint32_t *s_qbest;               // [kStripWarps] per-warp best keys (quads)
 };
@@ -240,6 +260,7 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
     uint32_t *yy = reinterpret_cast<uint32_t *>(ss.wmem) + warp * cols;
     uint16_t *sc = reinterpret_cast<uint16_t *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
     int *s_pick = reinterpret_cast<int *>(ss.wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
+    uint2 *queue = reinterpret_cast<uint2 *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * kQueueCap;
     const int kk = P.K >> 1;   // picks per half-strip
     const bool quads = kk == 1;
     const int quad = warp >> 2, qw = warp & 3;
@@ -263,8 +284,10 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
     int base = col_lo;
     __syncwarp();   // the previous item is done with yy / sc
 
-    // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned)
-    auto load_words = [&]() {
+    // ---- rows y-1, y, y+1 -> column words (16-byte loads when aligned);
+    // returns this lane's maximum of the middle row over columns [xa, xb]
+    auto load_words = [&](int xa, int xb) -> int {
+        int qm = 0;
         if (fr.vec_ok) {
             const int g0 = col_lo >> 4, g1 = (col_hi + 15) >> 4;
             base = g0 << 4;
@@ -280,17 +303,36 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
                 dst[1] = interleave4(L0.y, L1.y, L2.y);
                 dst[2] = interleave4(L0.z, L1.z, L2.z);
                 dst[3] = interleave4(L0.w, L1.w, L2.w);
+                // middle-row maximum over the group's pixels inside [xa, xb]
+                const int x0 = 16 * g;
+                uint32_t m;
+                if (x0 >= xa && x0 + 15 <= xb) {
+                    m = __vmaxu4(__vmaxu4(L1.x, L1.y), __vmaxu4(L1.z, L1.w));
+                } else {
+                    const uint32_t wv[4] = {L1.x, L1.y, L1.z, L1.w};
+                    m = 0u;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int x = x0 + k;
+                        if (x >= xa && x <= xb) m = max(m, (wv[k >> 2] >> (8 * (k & 3))) & 0xffu);
+                    }
+                }
+                m = __vmaxu4(m, m >> 16);
+                m = __vmaxu4(m, m >> 8);
+                qm = max(qm, (int)(m & 0xffu));
             }
         } else {
             base = col_lo;
             for (int cc = col_lo + lane; cc < col_hi; cc += 32) {
                 const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * cc;
                 const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
-                yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
-                                (luma(p2[0], p2[1], p2[2]) << 16);
+                const uint32_t m1 = luma(p1[0], p1[1], p1[2]);
+                yy[cc - base] = luma(p0[0], p0[1], p0[2]) | (m1 << 8) | (luma(p2[0], p2[1], p2[2]) << 16);
+                if (cc >= xa && cc <= xb) qm = max(qm, (int)m1);
             }
         }
         __syncwarp();
+        return qm;
     };
 
     // the angle term's centre, doubled: the image centre, or in a tracked
@@ -303,44 +345,58 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
     uint32_t best = 0u;
 
     if (kk == 1) {
-        // preceding maximum before this warp's quarter: maxima of the
-        // earlier quarters of the quad, each from its middle row alone -- a
-        // quarter whose preceding maximum already reaches io_cut keeps no
-        // pixel, and loads nothing more
+        // rows of this warp's quarter, loaded at once; the maxima of the
+        // earlier quarters' middle rows give the preceding maximum before it
         int qm = 0;
         if (q0 < q1) {
             const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
-            const uint8_t *r1 = fr.rgb + (int64_t)y * fr.pitch;
-            if (fr.vec_ok) {
-                for (int g = (xa >> 4) + lane; g <= (xb >> 4); g += 32) {
-                    const uint8_t *p1 = r1 + g * 48;
-                    const uint4 L = luma16(ld_nc_v4(p1), ld_nc_v4(p1 + 16), ld_nc_v4(p1 + 32));
-                    const uint32_t wv[4] = {L.x, L.y, L.z, L.w};
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int x = 16 * g + k;
-                        if (x >= xa && x <= xb)
-                            qm = max(qm, (int)((wv[k >> 2] >> (8 * (k & 3))) & 0xffu));
-                    }
-                }
-            } else {
-                for (int x = xa + lane; x <= xb; x += 32)
-                    qm = max(qm, (int)luma(r1[3 * x], r1[3 * x + 1], r1[3 * x + 2]));
-            }
+            qm = load_words(xa, xb);
         }
         qm = __reduce_max_sync(kFull, qm);
         if (lane == 0) s_qmax[warp] = qm;
         quad_barrier(quad);
         int carry = 0;
         for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
-        if (carry < P.io_cut && q0 < q1) load_words();
+        // every scanned pixel has at least the key of score 0, (0 << 16) | rank,
+        // and the largest of those is the quarter's first pixel (ranks fall
+        // along the scan); pixels whose score can only be 0 need no other key
+        if (q0 < q1 && carry < P.io_cut) {
+            const int x = half ? (W - 1 - q0) : q0;
+            best = (uint32_t)(half ? x : (0xFFFF - x));
+        }
+        // Pixels that pass the angle cut and whose bound beats the best so far
+        // wait in the warp's queue; 32 at a time they get their exact score
+        // with every lane busy.  qn: entries (warp-uniform); qtop: largest
+        // bound key waiting.
+        int qn = 0;
+        uint32_t qtop = 0u;
+        auto flush = [&]() {
+            __syncwarp();   // the pushes are visible
+            for (int b0 = 0; b0 < qn; b0 += 32) {
+                uint32_t key = 0u;
+                if (b0 + lane < qn) {
+                    const uint2 e = queue[b0 + lane];
+                    const int x = (int)(e.x >> 16), iota = (int)(e.x & 0xffu);
+                    const int gx = (int)(int16_t)(e.y & 0xffffu), gy = (int)(int16_t)(e.y >> 16);
+                    const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
+                    key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
+                }
+                best = max(best, __reduce_max_sync(kFull, key));
+            }
+            qn = 0;
+            qtop = 0u;
+            __syncwarp();   // the entries are read before new pushes
+        };
         // ---- rounds of 32 consecutive pixels in scan order (outer edge
         // inwards), one per lane; `carry` is the preceding maximum before
-        // the round, `best` this warp's best key so far
+        // the round
         for (int r0 = q0; r0 < q1; r0 += 32) {
             // no remaining pixel of the quarter can be kept (iota cut) or
-            // beat `best`: their s_iota <= s_iota(carry) bounds their scores
-            if (carry >= P.io_cut || (best != 0u && (best >> 16) >= (uint32_t)li[carry])) break;
+            // beat the best: their s_iota <= s_iota(carry) bounds their scores
+            if (carry >= P.io_cut) break;
+            const uint32_t lic = li[carry];
+            if (qn > 0 && (qtop >> 16) >= lic) flush();   // the waiting ones may decide it
+            if (best != 0u && (best >> 16) >= lic) break;
             const int p = r0 + lane;
             const bool act = p < q1;
             const int x = half ? (W - 1 - p) : p;
@@ -357,11 +413,10 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
             if (lane == 0) excl = 0;
             const int iota = max(carry, excl);
             const int carry_next = max(carry, __shfl_sync(kFull, inc, 31));
-            uint32_t key = 0u;
-            const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
-            if (act && iota < P.io_cut && (x == 0 || x == W - 1)) {
-                key = rank;   // no gradient on the first and last column: score 0
-            } else if (act && iota < P.io_cut) {
+            bool cand = false;
+            uint32_t bkey = 0u;
+            uint2 ent = make_uint2(0u, 0u);
+            if (act && iota < P.io_cut && x != 0 && x != W - 1) {
                 const uint32_t w0 = yy[x - 1 - base], w2 = yy[x + 1 - base];
                 const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
                 const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
@@ -369,21 +424,31 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
                 const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
                 const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
                 const int ng = gx * gx + gy * gy;
-                const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
-                const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
-                if (((bound << 16) | rank) > best)   // could beat the best so far
-                    key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
+                if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P)) {
+                    const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
+                    const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
+                    const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
+                    bkey = (bound << 16) | rank;
+                    cand = bkey > best;   // could beat the best so far
+                    ent = make_uint2(((uint32_t)x << 16) | (uint32_t)iota,
+                                     ((uint32_t)gx & 0xffffu) | ((uint32_t)gy << 16));
+                }
             }
-            best = max(best, __reduce_max_sync(kFull, key));
+            const unsigned bal = __ballot_sync(kFull, cand);
+            if (cand) queue[qn + __popc(bal & ((1u << lane) - 1u))] = ent;
+            qn += __popc(bal);
+            qtop = max(qtop, __reduce_max_sync(kFull, cand ? bkey : 0u));
+            if (qn >= 32) flush();
             carry = carry_next;
         }
+        if (qn > 0) flush();
         // best of the quad
         if (lane == 0) s_qbest[warp] = best;
         quad_barrier(quad);
         best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
                    max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
     } else {
-        load_words();
+        load_words(0, -1);
         // ---- K > 2: exact score per pixel over this lane's chunk, with a
         // sliding window of the vertical Sobel sums
         const int cpl = (len + 31) >> 5;
@@ -417,8 +482,12 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
             if (run < P.io_cut) {
                 int S2, T2, M2;
                 col(x + dir, S2, T2, M2);
-                if (x != 0 && x != W - 1)
-                    sv = score_from_g(ctx, dir * (S2 - S0), T0 + 2 * T1 + T2, x, run, P);
+                if (x != 0 && x != W - 1) {
+                    const int gx = dir * (S2 - S0), gy = T0 + 2 * T1 + T2;
+                    const int ng = gx * gx + gy * gy;
+                    if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P))
+                        sv = score_from_g(ctx, gx, gy, x, run, P);
+                }
                 run = max(run, M1);
                 S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
             }

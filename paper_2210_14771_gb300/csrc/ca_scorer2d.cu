@@ -1,117 +1,885 @@
-// ca_scorer2d.cu -- the paper's own learned edge scorer (Sec. 2.2.4): three
-// 3x3 convolutions to 8, 16 and 32 features with ReLU, a 1x1 head, on RGBXY
-// strips 7 rows high (unpadded vertically, so 7 -> 5 -> 3 -> 1 rows: the
-// strip's middle row; zero-padded horizontally).  Forward pass in binary32
-// on the CUDA cores: one CTA per 128 output columns of a strip, every layer
-// of the tile kept in shared memory with the halo columns it needs.
+// ca_scorer2d.cu -- the paper's own learned edge scorer (Sec. 2.2.4) on the
+// 5th-generation tensor cores: three 3x3 convolutions to 8, 16 and 32
+// features with ReLU, a 1x1 head and a sigmoid, on RGBXY strips 7 rows high
+// (unpadded vertically, so 7 -> 5 -> 3 -> 1 rows: the strip's middle row;
+// zero-padded horizontally).  bf16 operands, f32 accumulators in TMEM.
+//
+// Convention: out[r][x] = b + sum_{dr, dx, ci} W[co][ci][dr][dx] in[r + dr][x + dx - 1][ci].
+//
+// Layout.  A strip is processed in segments of 384 consecutive columns (3
+// tiles of 128); three layers of 3x3 need one column of context each, so the
+// middle 378 columns are outputs.  Every image row of a layer lives in shared
+// memory as "planes" of 8 channels: one 16-byte row per column, 8 zero guard
+// rows at both ends.  A tile of 128 columns of one plane is a K-major operand
+// core-matrix column (SBO = 128 bytes between 8-column groups).  With the
+// leading byte offset (the step between the two K halves of a K = 16 MMA) set
+// to 16 bytes, the second half is the same plane one column further on: one
+// MMA then covers two column taps of 8 channels, so the 5- and 8-channel
+// inputs of layers 1 and 2 need 2 MMAs per row tap (taps -1/0, then +1 with a
+// zero-weight fourth tap) and no zero padding of channels.  Layer 3 reads its
+// 16-channel input as two planes (LBO = one plane), one MMA per tap.  Column
+// taps are 16-byte offsets of the operand start: no im2col copy.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
 #include "ca_internal.h"
 
 namespace ca {
+
 namespace {
 
-constexpr int kT = 128;                        // output columns per CTA (one per thread)
-constexpr int kInC = kT + 6, kA1C = kT + 4, kA2C = kT + 2;
-constexpr int kWOff1 = 0, kBOff1 = 360, kWOff2 = 368, kBOff2 = 1520, kWOff3 = 1536,
-              kBOff3 = 6144, kWhOff = 6176, kBhOff = 6208;
-constexpr int kWFloats = 6212;                 // 6209 parameters, padded
-constexpr int kInFloats = 7 * kInC * 5, kA1Floats = 5 * kA1C * 8, kA2Floats = 3 * kA2C * 16;
-constexpr size_t kSmem = sizeof(float) * (kWFloats + kInFloats + kA1Floats + kA2Floats);
-static_assert(kBhOff + 1 == kScorer2dNParam, "parameter layout");
+#include "ca_tc.cuh"
 
-__global__ void __launch_bounds__(kT)
-    k_sc2_forward(const uint8_t *__restrict__ strips7, const int32_t *__restrict__ rows, int W,
-                  int H, const float *__restrict__ prm, float *__restrict__ logits) {
-    extern __shared__ float sm2[];
-    float *w = sm2;
-    float *in = w + kWFloats;       // 7 rows x columns x0-3 .. x0+130 x 5 features
-    float *a1 = in + kInFloats;     // 5 rows x columns x0-2 .. x0+129 x 8
-    float *a2 = a1 + kA1Floats;     // 3 rows x columns x0-1 .. x0+128 x 16
-    const int tid = threadIdx.x;
-    const int tiles = (W + kT - 1) / kT;
-    const int s = blockIdx.x / tiles, x0 = (blockIdx.x % tiles) * kT;
-    for (int i = tid; i < kScorer2dNParam; i += kT) w[i] = prm[i];
-    const uint8_t *src = strips7 + (size_t)s * 7 * W * 3;
-    const float xc = 0.5f * (float)(W - 1), yc = 0.5f * (float)(H - 1);
-    for (int i = tid; i < 7 * kInC; i += kT) {
-        const int k = i / kInC, c = i - k * kInC, x = x0 - 3 + c;
-        float *f = in + i * 5;
-        if (x >= 0 && x < W) {
-            const uint8_t *p = src + ((size_t)k * W + x) * 3;
-            f[0] = (float)((int)p[0] - 128) * (1.0f / 128.0f);
-            f[1] = (float)((int)p[1] - 128) * (1.0f / 128.0f);
-            f[2] = (float)((int)p[2] - 128) * (1.0f / 128.0f);
-            f[3] = __fdiv_rn(__fsub_rn((float)x, xc), (float)W);
-            f[4] = __fdiv_rn(__fsub_rn((float)rows[(size_t)s * 7 + k], yc), (float)H);
-        } else {
-            f[0] = f[1] = f[2] = f[3] = f[4] = 0.0f;
+constexpr int kTile = 128;
+constexpr int kCols = kTile * kSc2Tiles;     // columns of a segment
+constexpr int kG = 8;                         // guard rows at each end of a plane
+constexpr int kPlane = (kCols + 2 * kG) * 16; // bytes of one plane
+static_assert(kCols - 2 * kSc2Halo == kSc2SegOut, "segment geometry");
+
+struct Sc2Vec {   // float part of the weight block
+    float b1[8], b2[16], b3[32];
+    float whq[32];   // head weights rounded to bf16
+    float bh;
+    float pad[7];
+};
+static_assert(sizeof(Sc2Vec) == kSc2VecBytes, "vector block size");
+
+// Where segment g of a launch reads and writes.
+struct Seg2 {
+    const uint8_t *base;   // frame (frames mode) or the strip's 7 rows (strips mode)
+    int64_t pitch;         // bytes between rows of `base`
+    int W, H, y;           // y: the strip's middle row
+    int s0, s1;            // output columns [s0, s1)
+    int64_t out;           // index of column 0 of the strip in the per-column outputs
+    int strip;             // strips mode: index of the strip in the source
+    const int32_t *rows7;  // strips mode: frame rows of the 7 rows
+};
+
+__device__ __forceinline__ Seg2 seg2_info(const Sc2Source &src, int g) {
+    Seg2 si;
+    if (src.frames) {
+        int lo = 0, hi = src.B - 1;   // frame of segment g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (src.frames[mid].sc_seg_off <= g) lo = mid;
+            else hi = mid - 1;
         }
+        const DevFrame &fr = src.frames[lo];
+        const int nseg = (fr.W + kSc2SegOut - 1) / kSc2SegOut;
+        const int local = g - fr.sc_seg_off;
+        const int i = local / nseg, s = local - i * nseg;
+        si.base = fr.rgb;
+        si.pitch = fr.pitch;
+        si.W = fr.W;
+        si.H = fr.H;
+        si.y = src.rows[fr.rows_off + i];
+        si.s0 = s * kSc2SegOut;
+        si.out = (int64_t)fr.sc_pix_off + (int64_t)i * fr.W;
+        si.strip = -1;
+        si.rows7 = nullptr;
+    } else {
+        const int nseg = (src.W + kSc2SegOut - 1) / kSc2SegOut;
+        const int j = g / nseg, s = g - j * nseg;
+        const int id = src.idx ? src.idx[j] : j;
+        si.W = src.W;
+        si.H = src.H;
+        si.pitch = (int64_t)src.W * 3;
+        si.base = src.strips7 + (int64_t)id * 7 * si.pitch;
+        si.rows7 = src.rows7 + (int64_t)id * 7;
+        si.y = si.rows7[3];
+        si.s0 = s * kSc2SegOut;
+        si.out = (int64_t)j * src.W;
+        si.strip = id;
     }
-    __syncthreads();
-    // layer 1: 5 output rows, columns x0-2 .. x0+129; zero outside the strip
-    for (int i = tid; i < 5 * kA1C; i += kT) {
-        const int r = i / kA1C, c = i - r * kA1C, x = x0 - 2 + c;
-        float *o = a1 + i * 8;
-        if (x < 0 || x >= W) {
-            for (int co = 0; co < 8; ++co) o[co] = 0.0f;
-            continue;
-        }
-        for (int co = 0; co < 8; ++co) {
-            float z = w[kBOff1 + co];
-            for (int ci = 0; ci < 5; ++ci)
-                for (int dr = 0; dr < 3; ++dr)
-                    for (int dx = 0; dx < 3; ++dx)
-                        z = fmaf(w[kWOff1 + ((co * 5 + ci) * 3 + dr) * 3 + dx],
-                                 in[((r + dr) * kInC + c + dx) * 5 + ci], z);
-            o[co] = fmaxf(z, 0.0f);
-        }
+    si.s1 = min(si.W, si.s0 + kSc2SegOut);
+    return si;
+}
+
+// Image row k (0..6) of the strip: its bytes and its frame row.
+__device__ __forceinline__ const uint8_t *seg2_row(const Seg2 &si, int k, int *frame_row) {
+    if (si.rows7) {
+        *frame_row = si.rows7[k];
+        return si.base + k * si.pitch;
     }
-    __syncthreads();
-    // layer 2: 3 output rows, columns x0-1 .. x0+128
-    for (int i = tid; i < 3 * kA2C; i += kT) {
-        const int r = i / kA2C, c = i - r * kA2C, x = x0 - 1 + c;
-        float *o = a2 + i * 16;
-        if (x < 0 || x >= W) {
-            for (int co = 0; co < 16; ++co) o[co] = 0.0f;
-            continue;
+    const int r = min(max(si.y - 3 + k, 0), si.H - 1);
+    *frame_row = r;
+    return si.base + (int64_t)r * si.pitch;
+}
+
+// RGBXY features of the 7 x 384 pixels of a segment (columns b0 ...) into 7
+// planes: channels R, G, B as (v - 128) / 128, X = (x - (W-1)/2) / W and
+// Y = (row - (H-1)/2) / H in binary32, all rounded to bf16; zero outside the
+// frame's columns.
+__device__ __forceinline__ void build_x(unsigned char *X, const Seg2 &si, int b0) {
+    const float xc = __fmul_rn(0.5f, (float)(si.W - 1)), Wf = (float)si.W;
+    const float yc = __fmul_rn(0.5f, (float)(si.H - 1)), Hf = (float)si.H;
+    for (int i = threadIdx.x; i < 7 * kCols; i += blockDim.x) {
+        const int k = i / kCols, c = i - k * kCols, x = b0 + c;
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (x >= 0 && x < si.W) {
+            int fr_row;
+            const uint8_t *p = seg2_row(si, k, &fr_row) + 3 * x;
+            const float R = (float)((int)p[0] - 128) * (1.0f / 128.0f);
+            const float G = (float)((int)p[1] - 128) * (1.0f / 128.0f);
+            const float B = (float)((int)p[2] - 128) * (1.0f / 128.0f);
+            const float Xf = __fdiv_rn(__fsub_rn((float)x, xc), Wf);
+            const float Yf = __fdiv_rn(__fsub_rn((float)fr_row, yc), Hf);
+            q = make_uint4(pack_bf16(R, G), pack_bf16(B, Xf), pack_bf16(Yf, 0.0f), 0u);
         }
-        for (int co = 0; co < 16; ++co) {
-            float z = w[kBOff2 + co];
-            for (int ci = 0; ci < 8; ++ci)
-                for (int dr = 0; dr < 3; ++dr)
-                    for (int dx = 0; dx < 3; ++dx)
-                        z = fmaf(w[kWOff2 + ((co * 8 + ci) * 3 + dr) * 3 + dx],
-                                 a1[((r + dr) * kA1C + c + dx) * 8 + ci], z);
-            o[co] = fmaxf(z, 0.0f);
-        }
+        *reinterpret_cast<uint4 *>(X + k * kPlane + (kG + c) * 16) = q;
     }
-    __syncthreads();
-    // layer 3 and the head: this thread's column x0 + tid
-    const int x = x0 + tid;
-    if (x >= W) return;
-    float lg = w[kBhOff];
-    for (int co = 0; co < 32; ++co) {
-        float z = w[kBOff3 + co];
-        for (int ci = 0; ci < 16; ++ci)
+}
+
+// Zero guard rows of n planes from `p`.
+__device__ __forceinline__ void zero_guards(unsigned char *p, int n) {
+    for (int i = threadIdx.x; i < n * kG * 2; i += blockDim.x) {
+        const int plane = i / (2 * kG), g = i % (2 * kG);
+        const int row = g < kG ? g : kCols + g;
+        *reinterpret_cast<uint4 *>(p + plane * kPlane + row * 16) = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// ---- forward MMAs (one thread issues them)
+
+// Layers 1 and 2: 8-channel input planes `in` (rows r + dr), N = 16 outputs
+// per row into TMEM columns tile * stride + 16 r.  Per row tap two MMAs:
+// column taps (-1, 0), then (+1, +2) with the +2 weights zero.
+__device__ __forceinline__ void issue_conv8(uint32_t tmem, const unsigned char *in,
+                                            const unsigned char *w, int out_rows, int stride) {
+    constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
+    const uint64_t db = sdesc(smem_u32(w), 256, 128);
+    for (int j = 0; j < kSc2Tiles; ++j)
+        for (int r = 0; r < out_rows; ++r)
+#pragma unroll
             for (int dr = 0; dr < 3; ++dr)
-                for (int dx = 0; dx < 3; ++dx)
-                    z = fmaf(w[kWOff3 + ((co * 16 + ci) * 3 + dr) * 3 + dx],
-                             a2[(dr * kA2C + tid + dx) * 16 + ci], z);
-        lg = fmaf(w[kWhOff + co], fmaxf(z, 0.0f), lg);
-    }
-    logits[(size_t)s * W + x] = lg;
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const uint64_t da = sdesc(smem_u32(in + (r + dr) * kPlane) +
+                                                  (kG + kTile * j + 2 * o - 1) * 16,
+                                              16, 128);
+                    mma_bf16(tmem + stride * j + 16 * r, da, db + (uint32_t)(((dr * 2 + o) * 512) >> 4),
+                             idesc, (dr | o) != 0);
+                }
+}
+
+// Layer 3: 16-channel input rows (two planes each, rows dr = 0..2), N = 32
+// outputs into TMEM columns 32 tile; one MMA per tap.
+__device__ __forceinline__ void issue_conv16(uint32_t tmem, const unsigned char *in,
+                                             const unsigned char *w) {
+    constexpr uint32_t idesc = idesc_bf16(128, 32, false, false);
+    const uint64_t db = sdesc(smem_u32(w), 512, 128);
+    for (int j = 0; j < kSc2Tiles; ++j)
+#pragma unroll
+        for (int dr = 0; dr < 3; ++dr)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint64_t da = sdesc(smem_u32(in + 2 * dr * kPlane) +
+                                              (kG + kTile * j + dx - 1) * 16,
+                                          kPlane, 128);
+                mma_bf16(tmem + 32 * j, da, db + (uint32_t)(((dr * 3 + dx) * 1024) >> 4), idesc,
+                         (dr | dx) != 0);
+            }
+}
+
+// TMEM address of the calling warp's lane quarter at column `col`.
+__device__ __forceinline__ uint32_t tq(uint32_t tmem, int col) {
+    const int q = (threadIdx.x >> 5) & 3;
+    return tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col;
+}
+
+// relu(v + b) of 8 values rounded to bf16 into one 16-byte plane row (zero
+// when `inside` is false).
+__device__ __forceinline__ uint4 relu_row8(const float *v, const float *b, bool inside) {
+    if (!inside) return make_uint4(0u, 0u, 0u, 0u);
+    return make_uint4(pack_relu_bf16(__fadd_rn(v[0], b[0]), __fadd_rn(v[1], b[1])),
+                      pack_relu_bf16(__fadd_rn(v[2], b[2]), __fadd_rn(v[3], b[3])),
+                      pack_relu_bf16(__fadd_rn(v[4], b[4]), __fadd_rn(v[5], b[5])),
+                      pack_relu_bf16(__fadd_rn(v[6], b[6]), __fadd_rn(v[7], b[7])));
 }
 
 }  // namespace
 
-cudaError_t sc2_launch_forward(const uint8_t *strips7, const int32_t *rows, int n, int W, int H,
-                               const float *params, float *logits, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_sc2_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+// =============================================================== pack ==
+// f32 parameters -> the device weight block (bf16 B operands, floats).
+__global__ void k_sc2_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kScorer2dNParam) return;
+    const float w = prm[p];
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    Sc2Vec *vec = reinterpret_cast<Sc2Vec *>(blk + kSc2OffVec);
+    auto put = [&](int off) { *reinterpret_cast<__nv_bfloat16 *>(blk + off) = wb; };
+    if (p < kSc2PB1) {                        // W1[co][ci][dr][dx]
+        const int co = p / 45, ci = (p / 9) % 5, dr = (p / 3) % 3, dx = p % 3;
+        const int o = dx >> 1, c = dx & 1;    // pair o: taps 2o, 2o + 1
+        put(kSc2OffW1 + (dr * 2 + o) * 512 + (c * 16 + co) * 16 + ci * 2);
+    } else if (p < kSc2PW2) {
+        vec->b1[p - kSc2PB1] = w;
+    } else if (p < kSc2PB2) {                 // W2[co][ci][dr][dx]
+        const int q = p - kSc2PW2;
+        const int co = q / 72, ci = (q / 9) % 8, dr = (q / 3) % 3, dx = q % 3;
+        const int o = dx >> 1, c = dx & 1;
+        put(kSc2OffW2 + (dr * 2 + o) * 512 + (c * 16 + co) * 16 + ci * 2);
+        // input gradient of layer 2: B[n = ci][k = co] per tap, 2 chunks of 8 co
+        put(kSc2OffW2b + (dr * 3 + dx) * 512 + ((co >> 3) * 16 + ci) * 16 + (co & 7) * 2);
+    } else if (p < kSc2PW3) {
+        vec->b2[p - kSc2PB2] = w;
+    } else if (p < kSc2PB3) {                 // W3[co][ci][dr][dx]
+        const int q = p - kSc2PW3;
+        const int co = q / 144, ci = (q / 9) % 16, dr = (q / 3) % 3, dx = q % 3;
+        put(kSc2OffW3 + (dr * 3 + dx) * 1024 + ((ci >> 3) * 32 + co) * 16 + (ci & 7) * 2);
+        // input gradient of layer 3: B[n = ci][k = co] per tap, 4 chunks of 8 co
+        put(kSc2OffW3b + (dr * 3 + dx) * 1024 + ((co >> 3) * 16 + ci) * 16 + (co & 7) * 2);
+    } else if (p < kSc2PWh) {
+        vec->b3[p - kSc2PB3] = w;
+    } else if (p < kSc2PBh) {
+        vec->whq[p - kSc2PWh] = __bfloat162float(wb);
+    } else {
+        vec->bh = w;
+    }
+}
+
+cudaError_t sc2_launch_pack(const float *params, unsigned char *block, cudaStream_t s) {
+    // padding (the zero weights of the fourth column tap and of the padded
+    // channels) must be zero
+    cudaError_t e = cudaMemsetAsync(block, 0, kSc2BlockBytes, s);
     if (e != cudaSuccess) return e;
-    const long long blocks = (long long)n * ((W + kT - 1) / kT);
-    if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
-    k_sc2_forward<<<(unsigned)blocks, kT, kSmem, s>>>(strips7, rows, W, H, params, logits);
+    k_sc2_pack<<<(kScorer2dNParam + 255) / 256, 256, 0, s>>>(params, block);
+    return cudaGetLastError();
+}
+
+// ========================================================== inference ==
+// One CTA (8 warps, two per TMEM lane quarter) per segment at a time, 2 CTAs
+// per SM.  Output per output column: the Q15 score round(32768 p) and/or the
+// logit.
+constexpr int kInf2Threads = 256;
+constexpr int kInf2Cols = 256;                        // TMEM columns (layer 1: 3 x 80)
+constexpr size_t kInf2Smem = 12 * (size_t)kPlane + kSc2FwdBytes + kSc2VecBytes + 64;
+
+__global__ void __launch_bounds__(kInf2Threads, 2)
+    k_sc2_infer(Sc2Source src, const unsigned char *__restrict__ wblock,
+                uint16_t *__restrict__ scores, float *__restrict__ logits, int total_segs,
+                uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *X = sm;                     // 7 planes: features; then a2 (3 rows x 2 planes)
+    unsigned char *A1 = sm + 7 * kPlane;       // 5 planes: a1
+    unsigned char *Wf = A1 + 5 * kPlane;
+    Sc2Vec *vec = reinterpret_cast<Sc2Vec *>(Wf + kSc2FwdBytes);
+    uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kSc2VecBytes);
+    uint64_t *bar_m = bar_w + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
+    unsigned char *A2 = X;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    zero_guards(sm, 12);
+    if (tid == 0) {
+        bar_init(bar_w, 1);
+        bar_init(bar_m, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, kInf2Cols);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        bar_expect_tx(bar_w, kSc2FwdBytes + kSc2VecBytes);
+        bulk_g2s(Wf, wblock, kSc2FwdBytes, bar_w);
+        bulk_g2s(vec, wblock + kSc2OffVec, kSc2VecBytes, bar_w);
+    }
+    bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
+    uint32_t phase = 0;
+    const int q = warp & 3, half = warp >> 2;   // lane quarter; two warps per quarter
+
+    auto sync_point = [&]() {   // st.shared visible to the MMAs, TMEM reads done
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+    };
+    auto run = [&](int layer) {   // issue one layer, wait for it
+        if (tid == 0) {
+            if (layer == 0) issue_conv8(tmem, X, Wf + kSc2OffW1, 5, 80);
+            else if (layer == 1) issue_conv8(tmem, A1, Wf + kSc2OffW2, 3, 48);
+            else issue_conv16(tmem, A2, Wf + kSc2OffW3);
+            mma_commit(bar_m);
+        }
+        const bool ok = bar_wait(bar_m, phase, err);
+        phase ^= 1u;
+        tc_after_sync();
+        if (__syncthreads_or(!ok)) abort = true;
+        return !abort;
+    };
+
+    for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
+        const Seg2 si = seg2_info(src, g);
+        const int b0 = si.s0 - kSc2Halo;
+        __syncthreads();   // the previous segment is done with X / A1 / A2
+        build_x(X, si, b0);
+        sync_point();
+        // ---- layer 1: 5 rows of 8 channels
+        if (!run(0)) break;
+        for (int it = half; it < kSc2Tiles * 5; it += 2) {
+            const int j = it / 5, r = it - 5 * j;
+            float v[8];
+            tmem_ld8(tq(tmem, 80 * j + 16 * r), v);
+            const int row = kTile * j + 32 * q + lane, x = b0 + row;
+            *reinterpret_cast<uint4 *>(A1 + r * kPlane + (kG + row) * 16) =
+                relu_row8(v, vec->b1, x >= 0 && x < si.W);
+        }
+        sync_point();
+        // ---- layer 2: 3 rows of 16 channels (two planes each), over the features
+        if (!run(1)) break;
+        for (int it = half; it < kSc2Tiles * 3; it += 2) {
+            const int j = it / 3, r = it - 3 * j;
+            float v[16];
+            tmem_ld16(tq(tmem, 48 * j + 16 * r), v);
+            const int row = kTile * j + 32 * q + lane, x = b0 + row;
+            const bool inside = x >= 0 && x < si.W;
+            *reinterpret_cast<uint4 *>(A2 + 2 * r * kPlane + (kG + row) * 16) =
+                relu_row8(v, vec->b2, inside);
+            *reinterpret_cast<uint4 *>(A2 + (2 * r + 1) * kPlane + (kG + row) * 16) =
+                relu_row8(v + 8, vec->b2 + 8, inside);
+        }
+        sync_point();
+        // ---- layer 3 and the head
+        if (!run(2)) break;
+        for (int j = half; j < kSc2Tiles; j += 2) {
+            float v[32];
+            tmem_ld32(tq(tmem, 32 * j), v);
+            const int row = kTile * j + 32 * q + lane, x = b0 + row;
+            if (x >= si.s0 && x < si.s1) {
+                // relu(z + b3) rounded to bf16; logit = bh + sum_c whq[c] a3[c]
+                // in channel order, each product and sum rounded
+                float acc = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    const uint32_t a = pack_relu_bf16(__fadd_rn(v[c], vec->b3[c]),
+                                                      __fadd_rn(v[c + 1], vec->b3[c + 1]));
+                    acc = __fadd_rn(acc, __fmul_rn(vec->whq[c], bf16_lo(a)));
+                    acc = __fadd_rn(acc, __fmul_rn(vec->whq[c + 1], bf16_hi(a)));
+                }
+                const float lg = __fadd_rn(vec->bh, acc);
+                if (logits) logits[si.out + x] = lg;
+                if (scores) {
+                    const float p = 1.0f / (1.0f + expf(-lg));
+                    scores[si.out + x] = (uint16_t)min(32768, max(0, __float2int_rn(p * 32768.0f)));
+                }
+            }
+        }
+        sync_point();
+    }
+    __syncthreads();
+    if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
+        mma_commit(bar_m);
+        bar_wait(bar_m, phase, nullptr);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, kInf2Cols);
+}
+
+size_t sc2_infer_smem() { return kInf2Smem; }
+
+int sc2_infer_blocks_per_sm() {
+    // shared memory per SM (each CTA also reserves 1 KB), at most 2 CTAs for
+    // the 512 TMEM columns (256 each)
+    static int nb = [] {
+        int dev = 0, smem_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess)
+            return 1;
+        const int v = smem_sm / (int)(kInf2Smem + 1024);
+        return v < 1 ? 1 : (v > 2 ? 2 : v);
+    }();
+    return nb;
+}
+
+cudaError_t sc2_launch_infer(const Sc2Source &src, const unsigned char *block, uint16_t *scores,
+                             float *logits, int total_segs, uint32_t *err, int grid,
+                             cudaStream_t s) {
+    if (total_segs <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_sc2_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kInf2Smem);
+    if (e != cudaSuccess) return e;
+    k_sc2_infer<<<grid, kInf2Threads, kInf2Smem, s>>>(src, block, scores, logits, total_segs, err);
+    return cudaGetLastError();
+}
+
+// ============================================================= training ==
+// One CTA (8 warps, one CTA per SM) per segment, segments assigned statically
+// (g = blockIdx.x + k gridDim.x) so that every run sums the same gradient
+// terms in the same order.  Per segment: forward (features -> a1 -> a2 ->
+// a3 -> head), soft cross-entropy and its gradient at the logits, then for
+// layers 3, 2, 1 the weight gradient (tcgen05 with MN-major operands: M = 64
+// rows of output channels of which 8 / 16 / 32 are real, N = input channels,
+// K = 16 columns per MMA, one accumulator per tap) and, for layers 3 and 2,
+// the input gradient (a forward convolution of the gradient planes with the
+// transposed weights).  Gradient sums stay in shared memory across the CTA's
+// segments; the CTA writes them to its own slice of `partial` at the end.
+constexpr int kTrain2Threads = 256;
+constexpr int kTrain2Planes = 24;   // D (6: dz3, then dz2, then dz1) | X (7) | A1 (5) | A2 (6)
+constexpr int kTrain2Sum = 6272;    // floats of the CTA's gradient sums (+ loss)
+constexpr size_t kTrain2Smem = (size_t)kTrain2Planes * kPlane + (kSc2BlockBytes - kSc2VecBytes) +
+                               kSc2VecBytes + 64 + 4 * kTrain2Sum + 4 * 8 * 64;
+constexpr int kDw = 256;            // TMEM column of the weight-gradient accumulators
+static_assert(kTrain2Sum >= kScorer2dNParam + 1 && kTrain2Sum % 4 == 0, "sum slots");
+static_assert(kTrain2Sum == kSc2PartialStride, "partial stride");
+
+namespace {
+
+// Weight-gradient MMAs of one layer, for every tap (dr, dx) one accumulator
+// of N = 8 n_in_planes columns at kDw + N (3 dr + dx):
+//   dW[co][ci][dr][dx] += sum_r sum_x dz[r][x][co] in[r + dr][x + dx - 1][ci].
+// dz rows: planes dz + r dz_rs (M = 64: 8 planes from there, the padding rows
+// are ignored); in rows: planes in + (r + dr) in_rs, n_in_planes planes each.
+__device__ __forceinline__ void issue_dw2(uint32_t tmem, const unsigned char *dz, int dz_rs,
+                                          const unsigned char *in, int in_rs, int n_in_planes,
+                                          int rows) {
+    const int N = 8 * n_in_planes;
+    const uint32_t idesc = idesc_bf16(64, N, true, true);
+    for (int dr = 0; dr < 3; ++dr)
+        for (int dx = 0; dx < 3; ++dx) {
+            const uint32_t d = tmem + kDw + N * (3 * dr + dx);
+            for (int r = 0; r < rows; ++r) {
+                const uint64_t da = sdesc(smem_u32(dz + r * dz_rs) + kG * 16, 128, kPlane);
+                const uint64_t db =
+                    sdesc(smem_u32(in + (r + dr) * in_rs) + (kG + dx - 1) * 16, 128, kPlane);
+#pragma unroll 4
+                for (int k = 0; k < kCols / 16; ++k)
+                    mma_bf16(d, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc,
+                             (r | k) != 0);
+            }
+        }
+}
+
+// Adds the weight-gradient accumulators of a layer (n_out real output
+// channels, n_in real input channels of N = 8 n_in_planes) into the sums,
+// layout [co][ci][dr][dx] at `off`.  Row co of an M = 64 accumulator is in
+// lane co % 16 of TMEM lane quarter co / 16: warp w (< n_out / 16, or warp 0
+// for 8 outputs) reads its quarter.
+__device__ __forceinline__ void flush_dw2(uint32_t tmem, float *sum, int off, int n_out, int n_in,
+                                          int n_in_planes) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = 8 * n_in_planes;
+    if (warp < (n_out + 15) / 16) {
+        const int co = 16 * warp + lane;
+        for (int t = 0; t < 9; ++t) {
+            float v[16];
+            if (N == 16) {
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kDw + N * t, v);
+            } else {
+                float v8[8];
+                tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + kDw + N * t, v8);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] = v8[c];
+            }
+            if (lane < 16 && co < n_out) {
+                for (int ci = 0; ci < n_in; ++ci) {
+                    float &dst = sum[off + (co * n_in + ci) * 9 + t];
+                    dst = __fadd_rn(dst, v[ci]);
+                }
+            }
+        }
+    }
+}
+
+// Sums a per-thread vector of n values over the CTA (fixed order) into
+// sum[off + c]; red: 8 x 64 floats of scratch.
+template <int NV>
+__device__ __forceinline__ void flush_vec(const float (&v)[NV], float *red, float *sum, int off) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        float w = v[c];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) w = __fadd_rn(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (lane == 0) red[warp * 64 + c] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float t = 0.0f;
+        for (int k = 0; k < kTrain2Threads / 32; ++k) t = __fadd_rn(t, red[k * 64 + threadIdx.x]);
+        sum[off + threadIdx.x] = __fadd_rn(sum[off + threadIdx.x], t);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kTrain2Threads, 1)
+    k_sc2_train(Sc2Source src, const float *__restrict__ targets, float pos_weight,
+                const unsigned char *__restrict__ wblock, float *__restrict__ partial,
+                int total_segs, uint32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *D = sm;                     // gradient planes (the 6 after them pad M = 64)
+    unsigned char *X = sm + 6 * kPlane;
+    unsigned char *A1 = X + 7 * kPlane;
+    unsigned char *A2 = A1 + 5 * kPlane;
+    unsigned char *Wall = sm + kTrain2Planes * kPlane;
+    Sc2Vec *vec = reinterpret_cast<Sc2Vec *>(Wall + (kSc2BlockBytes - kSc2VecBytes));
+    uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kSc2VecBytes);
+    uint64_t *bar_m = bar_w + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
+    float *sum = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(bar_w) + 64);
+    float *red = sum + kTrain2Sum;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, half = warp >> 2;
+    zero_guards(sm, kTrain2Planes);
+    for (int i = tid; i < kTrain2Sum; i += kTrain2Threads) sum[i] = 0.0f;
+    if (tid == 0) {
+        bar_init(bar_w, 1);
+        bar_init(bar_m, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, 512);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        bar_expect_tx(bar_w, kSc2BlockBytes);
+        bulk_g2s(Wall, wblock, kSc2BlockBytes - kSc2VecBytes, bar_w);
+        bulk_g2s(vec, wblock + kSc2OffVec, kSc2VecBytes, bar_w);
+    }
+    bool abort = __syncthreads_or(!bar_wait(bar_w, 0, err)) != 0;
+    uint32_t phase = 0;
+    const unsigned char *W3b = Wall + kSc2OffW3b, *W2b = Wall + kSc2OffW2b;
+
+    auto sync_point = [&]() {
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+    };
+    auto wait_mma = [&]() {
+        const bool ok = bar_wait(bar_m, phase, err);
+        phase ^= 1u;
+        tc_after_sync();
+        if (__syncthreads_or(!ok)) abort = true;
+        return !abort;
+    };
+
+    for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
+        const Seg2 si = seg2_info(src, g);
+        const int b0 = si.s0 - kSc2Halo;
+        const float *tgt = targets + (int64_t)si.strip * si.W;
+        __syncthreads();
+        build_x(X, si, b0);
+        sync_point();
+        // ---- forward: layer 1
+        if (tid == 0) {
+            issue_conv8(tmem, X, Wall + kSc2OffW1, 5, 80);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        for (int it = half; it < kSc2Tiles * 5; it += 2) {
+            const int j = it / 5, r = it - 5 * j;
+            float v[8];
+            tmem_ld8(tq(tmem, 80 * j + 16 * r), v);
+            const int row = kTile * j + 32 * q + lane, x = b0 + row;
+            *reinterpret_cast<uint4 *>(A1 + r * kPlane + (kG + row) * 16) =
+                relu_row8(v, vec->b1, x >= 0 && x < si.W);
+        }
+        sync_point();
+        // ---- layer 2
+        if (tid == 0) {
+            issue_conv8(tmem, A1, Wall + kSc2OffW2, 3, 48);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        for (int it = half; it < kSc2Tiles * 3; it += 2) {
+            const int j = it / 3, r = it - 3 * j;
+            float v[16];
+            tmem_ld16(tq(tmem, 48 * j + 16 * r), v);
+            const int row = kTile * j + 32 * q + lane, x = b0 + row;
+            const bool inside = x >= 0 && x < si.W;
+            *reinterpret_cast<uint4 *>(A2 + 2 * r * kPlane + (kG + row) * 16) =
+                relu_row8(v, vec->b2, inside);
+            *reinterpret_cast<uint4 *>(A2 + (2 * r + 1) * kPlane + (kG + row) * 16) =
+                relu_row8(v + 8, vec->b2 + 8, inside);
+        }
+        sync_point();
+        // ---- layer 3, head, loss; gradient at the logits and at z3 (plane D, 4 planes)
+        if (tid == 0) {
+            issue_conv16(tmem, A2, Wall + kSc2OffW3);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        {
+            float gwh[32], gb3[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) gwh[c] = gb3[c] = 0.0f;
+            float gbh = 0.0f, loss = 0.0f;
+            for (int j = half; j < kSc2Tiles; j += 2) {
+                float v[32];
+                tmem_ld32(tq(tmem, 32 * j), v);
+                const int row = kTile * j + 32 * q + lane, x = b0 + row;
+                const bool out = x >= si.s0 && x < si.s1;
+                float acc = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 32; c += 2) {
+                    const uint32_t a = pack_relu_bf16(__fadd_rn(v[c], vec->b3[c]),
+                                                      __fadd_rn(v[c + 1], vec->b3[c + 1]));
+                    v[c] = out ? bf16_lo(a) : 0.0f;
+                    v[c + 1] = out ? bf16_hi(a) : 0.0f;
+                    acc = __fadd_rn(acc, __fmul_rn(vec->whq[c], v[c]));
+                    acc = __fadd_rn(acc, __fmul_rn(vec->whq[c + 1], v[c + 1]));
+                }
+                float dl = 0.0f;
+                if (out) {
+                    const float lg = __fadd_rn(vec->bh, acc);
+                    const float t = tgt[x];
+                    const float w = __fadd_rn(1.0f, __fmul_rn(__fsub_rn(pos_weight, 1.0f), t));
+                    const float p = 1.0f / (1.0f + expf(-lg));
+                    dl = __fmul_rn(w, __fsub_rn(p, t));
+                    const float sp = lg > 0.0f ? lg + log1pf(expf(-lg)) : log1pf(expf(lg));
+                    loss = __fadd_rn(loss, __fmul_rn(w, __fsub_rn(sp, __fmul_rn(t, lg))));
+                }
+                gbh = __fadd_rn(gbh, dl);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    gwh[c] = __fadd_rn(gwh[c], __fmul_rn(dl, v[c]));
+                    const float dz = v[c] > 0.0f
+                                         ? __bfloat162float(__float2bfloat16_rn(__fmul_rn(dl, vec->whq[c])))
+                                         : 0.0f;
+                    gb3[c] = __fadd_rn(gb3[c], dz);
+                    v[c] = dz;
+                }
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4)
+                    *reinterpret_cast<uint4 *>(D + c4 * kPlane + (kG + row) * 16) = make_uint4(
+                        pack_bf16(v[8 * c4], v[8 * c4 + 1]), pack_bf16(v[8 * c4 + 2], v[8 * c4 + 3]),
+                        pack_bf16(v[8 * c4 + 4], v[8 * c4 + 5]), pack_bf16(v[8 * c4 + 6], v[8 * c4 + 7]));
+            }
+            // rows no warp wrote this segment are the tiles of the other half
+            // of the warps: every row of D is written (half 0: tiles 0, 2;
+            // half 1: tile 1)
+            flush_vec<32>(gwh, red, sum, kSc2PWh);
+            flush_vec<32>(gb3, red, sum, kSc2PB3);
+            float tail[2] = {gbh, loss};
+            flush_vec<2>(tail, red, sum, kSc2PBh);   // bh, then the loss slot after it
+        }
+        sync_point();
+        // ---- layer 3: weight gradient (N = 16 over the two a2 planes of a row)
+        // and the input gradient da2 (3 rows x 16 channels per tile)
+        if (tid == 0) {
+            issue_dw2(tmem, D, 0, A2, 2 * kPlane, 2, 1);
+            constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
+            for (int j = 0; j < kSc2Tiles; ++j)
+                for (int dr = 0; dr < 3; ++dr)
+                    for (int dx = 0; dx < 3; ++dx)
+                        for (int h2 = 0; h2 < 2; ++h2) {   // input channels 16 h2 .. 16 h2 + 15
+                            const uint64_t da = sdesc(smem_u32(D + 2 * h2 * kPlane) +
+                                                          (kG + kTile * j + 1 - dx) * 16,
+                                                      kPlane, 128);
+                            const uint64_t db = sdesc(smem_u32(W3b + (dr * 3 + dx) * 1024 + h2 * 512),
+                                                      256, 128);
+                            mma_bf16(tmem + 48 * j + 16 * dr, da, db, idesc, (dx | h2) != 0);
+                        }
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        flush_dw2(tmem, sum, kSc2PW3, 32, 16, 2);
+        {
+            float gb[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) gb[c] = 0.0f;
+            for (int it = half; it < kSc2Tiles * 3; it += 2) {
+                const int j = it / 3, r = it - 3 * j;
+                float v[16];
+                tmem_ld16(tq(tmem, 48 * j + 16 * r), v);
+                const int row = kTile * j + 32 * q + lane;
+                const uint4 a0 = *reinterpret_cast<const uint4 *>(A2 + 2 * r * kPlane + (kG + row) * 16);
+                const uint4 a1 = *reinterpret_cast<const uint4 *>(A2 + (2 * r + 1) * kPlane + (kG + row) * 16);
+                const uint32_t aw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float a = (c & 1) ? bf16_hi(aw[c >> 1]) : bf16_lo(aw[c >> 1]);
+                    v[c] = a > 0.0f ? __bfloat162float(__float2bfloat16_rn(v[c])) : 0.0f;
+                    gb[c] = __fadd_rn(gb[c], v[c]);
+                }
+                // dz2 of row r: planes 2r, 2r + 1 of D (every MMA reading D is done)
+                *reinterpret_cast<uint4 *>(D + 2 * r * kPlane + (kG + row) * 16) =
+                    make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                               pack_bf16(v[6], v[7]));
+                *reinterpret_cast<uint4 *>(D + (2 * r + 1) * kPlane + (kG + row) * 16) =
+                    make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]),
+                               pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
+            }
+            flush_vec<16>(gb, red, sum, kSc2PB2);
+        }
+        sync_point();
+        // ---- layer 2: weight gradient (N = 8) and the input gradient da1
+        // (5 rows x 16 columns of which 8 real per tile)
+        if (tid == 0) {
+            issue_dw2(tmem, D, 2 * kPlane, A1, kPlane, 1, 3);
+            constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
+            for (int j = 0; j < kSc2Tiles; ++j)
+                for (int r1 = 0; r1 < 5; ++r1) {
+                    bool first = true;
+                    for (int r = 0; r < 3; ++r) {
+                        const int dr = r1 - r;
+                        if (dr < 0 || dr > 2) continue;
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t da = sdesc(smem_u32(D + 2 * r * kPlane) +
+                                                          (kG + kTile * j + 1 - dx) * 16,
+                                                      kPlane, 128);
+                            const uint64_t db = sdesc(smem_u32(W2b + (dr * 3 + dx) * 512), 256, 128);
+                            mma_bf16(tmem + 80 * j + 16 * r1, da, db, idesc, first ? 0u : 1u);
+                            first = false;
+                        }
+                    }
+                }
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        flush_dw2(tmem, sum, kSc2PW2, 16, 8, 1);
+        {
+            float gb[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gb[c] = 0.0f;
+            for (int it = half; it < kSc2Tiles * 5; it += 2) {
+                const int j = it / 5, r = it - 5 * j;
+                float v[8];
+                tmem_ld8(tq(tmem, 80 * j + 16 * r), v);
+                const int row = kTile * j + 32 * q + lane;
+                const uint4 a0 = *reinterpret_cast<const uint4 *>(A1 + r * kPlane + (kG + row) * 16);
+                const uint32_t aw[4] = {a0.x, a0.y, a0.z, a0.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float a = (c & 1) ? bf16_hi(aw[c >> 1]) : bf16_lo(aw[c >> 1]);
+                    v[c] = a > 0.0f ? __bfloat162float(__float2bfloat16_rn(v[c])) : 0.0f;
+                    gb[c] = __fadd_rn(gb[c], v[c]);
+                }
+                // dz1 of row r: plane r of D (every MMA reading D is done)
+                *reinterpret_cast<uint4 *>(D + r * kPlane + (kG + row) * 16) =
+                    make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                               pack_bf16(v[6], v[7]));
+            }
+            flush_vec<8>(gb, red, sum, kSc2PB1);
+        }
+        sync_point();
+        // ---- layer 1: weight gradient only (N = 8, of which 5 real)
+        if (tid == 0) {
+            issue_dw2(tmem, D, kPlane, X, kPlane, 1, 5);
+            mma_commit(bar_m);
+        }
+        if (!wait_mma()) break;
+        flush_dw2(tmem, sum, kSc2PW1, 8, 5, 1);
+        tc_before_sync();
+    }
+    __syncthreads();
+    // the CTA's sums to its slice of the partials (every CTA has a segment)
+    float *part = partial + (size_t)blockIdx.x * kSc2PartialStride;
+    for (int i = tid; i < kTrain2Sum; i += kTrain2Threads) part[i] = sum[i];
+    if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
+        mma_commit(bar_m);
+        bar_wait(bar_m, phase, nullptr);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 512);
+}
+
+size_t sc2_train_smem() { return kTrain2Smem; }
+
+cudaError_t sc2_launch_train(const Sc2Source &src, const float *targets, float pos_weight,
+                             const unsigned char *block, float *partial, int total_segs,
+                             uint32_t *err, int grid, cudaStream_t s) {
+    if (total_segs <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_sc2_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTrain2Smem);
+    if (e != cudaSuccess) return e;
+    k_sc2_train<<<grid, kTrain2Threads, kTrain2Smem, s>>>(src, targets, pos_weight, block, partial,
+                                                          total_segs, err);
+    return cudaGetLastError();
+}
+
+// ================================================================ SGD ==
+// Sums the per-CTA partials in a fixed order, then optionally a momentum SGD
+// step (clipped by the global gradient norm when clip > 0), as the 1-D
+// scorer's step: v = momentum v + f scale g, w = w - lr v.
+constexpr int kSgd2Params = 64;
+
+__global__ void __launch_bounds__(256)
+    k_sc2_sgd(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ part,
+              int n_part, float scale, float lr, float momentum, int apply,
+              float *__restrict__ grads_out, float *__restrict__ loss_out,
+              float *__restrict__ gbuf, float *__restrict__ norm_part) {
+    __shared__ float red2[4][kSgd2Params];
+    const int pl = threadIdx.x % kSgd2Params, qq = threadIdx.x / kSgd2Params;
+    const int p = blockIdx.x * kSgd2Params + pl;
+    float g = 0.0f;
+    if (p <= kScorer2dNParam)
+        for (int c = qq; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(part + (size_t)c * kSc2PartialStride + p));
+    red2[qq][pl] = g;
+    __syncthreads();
+    g = __fadd_rn(__fadd_rn(__fadd_rn(red2[0][pl], red2[1][pl]), red2[2][pl]), red2[3][pl]);
+    if (norm_part) {
+        __syncthreads();
+        if (qq == 0) {
+            const float m = __fmul_rn(scale, g);
+            red2[1][pl] = p < kScorer2dNParam ? __fmul_rn(m, m) : 0.0f;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.0f;
+            for (int i = 0; i < kSgd2Params; ++i) t = __fadd_rn(t, red2[1][i]);
+            norm_part[blockIdx.x] = t;
+        }
+    }
+    if (qq != 0 || p > kScorer2dNParam) return;
+    if (p == kScorer2dNParam) {   // loss slot
+        if (loss_out) *loss_out = g;
+        return;
+    }
+    if (grads_out) grads_out[p] = g;
+    if (norm_part) {
+        gbuf[p] = g;
+    } else if (apply) {
+        const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), __fmul_rn(scale, g));
+        mom[p] = v;
+        prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+    }
+}
+
+__global__ void __launch_bounds__(kSgd2Params)
+    k_sc2_clip_step(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ gbuf,
+                    const float *__restrict__ norm_part, float scale, float lr, float momentum,
+                    float clip) {
+    __shared__ float red2[kSgd2Params];
+    __shared__ float f_s;
+    float t = 0.0f;
+    for (int i = threadIdx.x; i < kSc2SgdBlocks; i += kSgd2Params) t = __fadd_rn(t, __ldcg(norm_part + i));
+    red2[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = kSgd2Params / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red2[threadIdx.x] = __fadd_rn(red2[threadIdx.x], red2[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float n = sqrtf(red2[0]);
+        f_s = n > clip ? __fdiv_rn(clip, n) : 1.0f;
+    }
+    __syncthreads();
+    const int p = blockIdx.x * kSgd2Params + threadIdx.x;
+    if (p >= kScorer2dNParam) return;
+    const float m = __fmul_rn(f_s, __fmul_rn(scale, gbuf[p]));
+    const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), m);
+    mom[p] = v;
+    prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+}
+
+cudaError_t sc2_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
+                           float lr, float momentum, int apply, float clip, float *gbuf,
+                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s) {
+    const bool clipped = apply && clip > 0.0f;
+    k_sc2_sgd<<<kSc2SgdBlocks, 256, 0, s>>>(params, mom, partial, n_partials, scale, lr, momentum,
+                                            apply, grads_out, loss_out, clipped ? gbuf : nullptr,
+                                            clipped ? norm_part : nullptr);
+    if (clipped)
+        k_sc2_clip_step<<<kSc2SgdBlocks, kSgd2Params, 0, s>>>(params, mom, gbuf, norm_part, scale,
+                                                              lr, momentum, clip);
     return cudaGetLastError();
 }
 

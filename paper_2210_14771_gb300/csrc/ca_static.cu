@@ -123,6 +123,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     P.score_den = 32768.0 * norm;
     P.qg_sat = qg_sat;
     P.io_cut = iota_cut(ht.luts + kLutG + kLutT, P.T_ps);
+    angle_cut(ht.luts + kLutG, P.T_ps, P);
     P.NH = (int)nh;
     P.hyp_threads = choose_hyp_threads(p->hyp_threads, B, nh, sms);
     P.n_tiles = (int)((nh + kHypTile / P.hyp_threads - 1) / (kHypTile / P.hyp_threads));

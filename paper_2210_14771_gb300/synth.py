@@ -212,40 +212,43 @@ def _grams(H, W):
     return _GRAMS[(H, W)]
 
 
-def training_strip(seed: int, idx: int, H: int, W: int, geometry: str = "mixed"):
-    """One labelled training strip: rows y-1, y, y+1 (3, W, 3) of a scene drawn
-    like `frame` (same geometry classes and appearance), its middle row y and
-    per-column labels: 1 within 2 px of a crossing of the true circle with
-    row y, else 0.  Only the three rows are rendered."""
+def _render_strip(seed: int, idx: int, H: int, W: int, geometry: str, half_rows: int):
+    """Rows y - half_rows .. y + half_rows (clamped into the frame) of a scene
+    drawn like `frame` (same geometry classes and appearance); only those rows
+    are rendered.  Returns (pixels (2 half_rows + 1, W, 3) uint8, y, the
+    frame rows, the circle (cx, cy, r) or None, its ground-truth validity)."""
     rng = np.random.default_rng([0x57A1, seed & 0xFFFFFFFF, idx & 0xFFFFFFFF, H, W])
     kind = geometry_of(geometry, idx) if geometry == "mixed" else geometry
     base = kind
     if kind == "hard":
         base = "clipped" if rng.uniform() < 0.5 else "full"
     y = int(rng.integers(1, H - 1))
-    ys = np.array([y - 1, y, y + 1], np.float32)
+    rows = np.clip(np.arange(y - half_rows, y + half_rows + 1), 0, H - 1)
+    n = len(rows)
+    ys = rows.astype(np.float32)
     mean = rng.uniform(80, 200)
     tint = rng.uniform(-15, 15, size=3)
     gains = rng.uniform(0.8, 1.2, size=3)
     g = rng.standard_normal((8, 8)).astype(np.float32)
     wy, wx, gy, gx, sy, sx = _grams(H, W)
-    tex = wy[y - 1:y + 2] @ g @ wx.T
+    tex = wy[rows] @ g @ wx.T
     # standard deviation of the whole frame's texture, from 8x8 Gram matrices
     g64 = g.astype(np.float64)
     m1 = float(sy @ g64 @ sx) / (H * W)
     m2 = float(np.trace(g64.T @ gy @ g64 @ gx)) / (H * W)
     sd = math.sqrt(max(m2 - m1 * m1, 0.0)) or 1.0
     tex = tex * np.float32(25.0 / sd)
-    noise_in = rng.standard_normal((3, W, 3), dtype=np.float32) * 2.0
+    noise_in = rng.standard_normal((n, W, 3), dtype=np.float32) * 2.0
     interior = (mean + tint[None, None, :]).astype(np.float32) + \
         tex[:, :, None] * gains[None, None, :].astype(np.float32) + noise_in
     level = rng.uniform(0, 15)
-    border = level + rng.standard_normal((3, W, 3), dtype=np.float32) * 3.0
-    labels = np.zeros(W, np.uint8)
+    border = level + rng.standard_normal((n, W, 3), dtype=np.float32) * 3.0
+    circle, valid = None, False
     if base == "none":
         img = interior
     else:
         cx, cy, r = _draw_circle(rng, base, H, W)
+        circle, valid = (cx, cy, r), gt_valid(cx, cy, r, H, W)
         xs = np.arange(W, dtype=np.float32)[None, :]
         d = np.sqrt((xs - np.float32(cx)) ** 2 + (ys[:, None] - np.float32(cy)) ** 2)
         if kind == "hard":
@@ -268,6 +271,19 @@ def training_strip(seed: int, idx: int, H: int, W: int, geometry: str = "mixed")
                 interior = interior * (1 - beta) + 255.0 * beta
         a = np.clip((np.float32(r) + 1.0 - d) / 2.0, 0.0, 1.0)[:, :, None]
         img = interior * a + border * (1.0 - a)
+    out = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    return out, y, rows.astype(np.int32), circle, valid
+
+
+def training_strip(seed: int, idx: int, H: int, W: int, geometry: str = "mixed"):
+    """One labelled training strip: rows y-1, y, y+1 (3, W, 3) of a scene drawn
+    like `frame` (same geometry classes and appearance), its middle row y and
+    per-column labels: 1 within 2 px of a crossing of the true circle with
+    row y, else 0.  Only the three rows are rendered."""
+    out, y, _, circle, _ = _render_strip(seed, idx, H, W, geometry, 1)
+    labels = np.zeros(W, np.uint8)
+    if circle is not None:
+        cx, cy, r = circle
         dy = y - cy
         if abs(dy) <= r:
             h = math.sqrt(r * r - dy * dy)
@@ -276,8 +292,58 @@ def training_strip(seed: int, idx: int, H: int, W: int, geometry: str = "mixed")
                 lo, hi = max(lo, 0), min(hi, W - 1)
                 if lo <= hi:
                     labels[lo:hi + 1] = 1
-    out = np.clip(np.rint(img), 0, 255).astype(np.uint8)
     return out, y, labels
+
+
+def soft_targets(circle, valid: bool, W: int, y: int, sigma: float = 3.0) -> np.ndarray:
+    """Soft edge targets of row y (the paper blurs its edge map with a Gaussian
+    of sigma 3): exp(-d^2 / (2 sigma^2)), d the distance of pixel (x, y) to
+    the true circle; zero when the circle does not bound the content area."""
+    if circle is None or not valid:
+        return np.zeros(W, np.float32)
+    cx, cy, r = circle
+    d = np.abs(np.hypot(np.arange(W, dtype=np.float64) - cx, float(y) - cy) - r)
+    return np.exp(-d * d / (2.0 * sigma * sigma)).astype(np.float32)
+
+
+def training_strip7(seed: int, idx: int, H: int, W: int, geometry: str = "mixed",
+                    sigma: float = 3.0):
+    """One training strip of the paper's 2-D scorer: rows y-3 .. y+3 (clamped
+    into the frame) (7, W, 3), their frame rows (7,) and the soft targets of
+    the middle row (W,) float32."""
+    out, y, rows, circle, valid = _render_strip(seed, idx, H, W, geometry, 3)
+    return out, rows, soft_targets(circle, valid, W, y, sigma)
+
+
+def _strip7_job(args):
+    seed, i0, i1, H, W, geometry = args
+    n = i1 - i0
+    s = np.empty((n, 7, W, 3), np.uint8)
+    rows = np.empty((n, 7), np.int32)
+    tg = np.empty((n, W), np.float32)
+    for k in range(n):
+        s[k], rows[k], tg[k] = training_strip7(seed, i0 + k, H, W, geometry)
+    return s, rows, tg
+
+
+def training_strips7(seed: int, n: int, H: int = 1080, W: int = 1920, geometry: str = "mixed",
+                     workers: int = 0):
+    """n training strips of the 2-D scorer: (strips (n, 7, W, 3) uint8, frame
+    rows (n, 7) int32, soft targets (n, W) float32)."""
+    chunk = 256
+    jobs = [(seed, i, min(n, i + chunk), H, W, geometry) for i in range(0, n, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_strip7_job, jobs))
+    else:
+        parts = [_strip7_job(j) for j in jobs]
+    if not parts:
+        return (np.empty((0, 7, W, 3), np.uint8), np.empty((0, 7), np.int32),
+                np.empty((0, W), np.float32))
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+            np.concatenate([p[2] for p in parts]))
 
 
 def _strip_job(args):

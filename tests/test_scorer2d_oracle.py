@@ -35,11 +35,12 @@ def test_layout_and_strip_rows():
     assert rows.tolist() == [H - 5, H - 4, H - 3, H - 2, H - 1, H - 1, H - 1]
 
 
-def test_gradient_matches_finite_differences():
+@pytest.mark.parametrize("pw", [1.0, 6.0])
+def test_gradient_matches_finite_differences(pw):
     _, (rgb7, rows) = _strip(2)
     p = _params(3)
     t = np.random.default_rng(4).random(W)
-    _, g = orc.sc2_loss_grad(rgb7, rows, H, t, p)
+    _, g = orc.sc2_loss_grad(rgb7, rows, H, t, p, pw)
     o = orc.sc2_offsets()
     rng = np.random.default_rng(5)
     blocks = [(o["W1"], o["b1"]), (o["b1"], o["W2"]), (o["W2"], o["b2"]), (o["b2"], o["W3"]),
@@ -50,8 +51,8 @@ def test_gradient_matches_finite_differences():
             pp, pm = p.copy(), p.copy()
             pp[i] = np.float32(p[i] + h)
             pm[i] = np.float32(p[i] - h)
-            lp, _ = orc.sc2_loss_grad(rgb7, rows, H, t, pp)
-            lm, _ = orc.sc2_loss_grad(rgb7, rows, H, t, pm)
+            lp, _ = orc.sc2_loss_grad(rgb7, rows, H, t, pp, pw)
+            lm, _ = orc.sc2_loss_grad(rgb7, rows, H, t, pm, pw)
             fd = (lp - lm) / (float(pp[i]) - float(pm[i]))
             assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (a, i, fd, g[i])
 
@@ -105,6 +106,19 @@ def test_constant_network_loss_and_bias_gradient():
     assert loss == pytest.approx(W * math.log(2.0), rel=1e-15)
     assert g[orc.sc2_offsets()["bh"]] == pytest.approx(float((0.5 - t).sum()), abs=1e-12)
     assert not np.any(g[:orc.sc2_offsets()["bh"]])      # dead ReLUs: nothing else moves
+
+
+def test_weighted_constant_network_closed_form():
+    """Column x counts 1 + (pw - 1) t_x times: for the zero network (p = 1/2
+    everywhere) the loss is log 2 sum_x w_x and the head-bias gradient
+    sum_x w_x (1/2 - t_x)."""
+    _, (rgb7, rows) = _strip(13)
+    t = np.random.default_rng(14).random(W)
+    pw = 9.0
+    w = 1.0 + (pw - 1.0) * t
+    loss, g = orc.sc2_loss_grad(rgb7, rows, H, t, np.zeros(orc.SC2_NPARAM, np.float32), pw)
+    assert loss == pytest.approx(math.log(2.0) * float(w.sum()), rel=1e-14)
+    assert g[orc.sc2_offsets()["bh"]] == pytest.approx(float((w * (0.5 - t)).sum()), abs=1e-11)
 
 
 def test_soft_targets():
