@@ -616,6 +616,20 @@ def run_ours(args):
     nh = [metrics.normalised_hausdorff(m_host[b].astype(bool), metrics.gt_mask(gts[b], H, W))
           for b in range(B)]
     acc = metrics.summarise(nh)
+    # per geometry class, under the default circle normaliser of t_cs and the
+    # 2N reading (same frames, same RANSAC draws)
+    by_class = {}
+    for norm_name, norm in (("circle", 3), ("2N", 0)):
+        qn = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],
+                        n_hyps=WORKLOAD["n_hyps"], score_norm=norm)
+        _, mq = ca.estimate(d_frames_all[0], qn, keys=keys, masks=True)
+        mq = mq.cpu().numpy()
+        per = {}
+        for b in range(B):
+            per.setdefault(gts[b]["kind"], []).append(
+                metrics.normalised_hausdorff(mq[b].astype(bool), metrics.gt_mask(gts[b], H, W)))
+        by_class[norm_name] = {k: metrics.summarise(v) for k, v in sorted(per.items())}
+    acc["by_class"] = by_class
 
     # ---- per-phase kernels of the staged launch (CUDA events per kernel)
     q = api.params(n_strips=WORKLOAD["n_strips"], cands_per_strip=WORKLOAD["cands_per_strip"],

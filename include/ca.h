@@ -55,8 +55,10 @@ typedef enum {
 
 enum { CA_HYP_RANDOM = 0, CA_HYP_EXHAUSTIVE = 1 };
 /* divisor of the circle score compared with t_cs (Sec. 2.2.5): the paper's
- * candidate count 2N, the slot count N*K, or none */
-enum { CA_NORM_2N = 0, CA_NORM_NK = 1, CA_NORM_RAW = 2 };
+ * candidate count 2N, the slot count N*K, none, or (the default) the most
+ * inliers the best circle can have, K per strip whose row lies within
+ * r + t_ri of the circle's centre row (|h_i - cy| <= r + t_ri in binary32) */
+enum { CA_NORM_2N = 0, CA_NORM_NK = 1, CA_NORM_RAW = 2, CA_NORM_CIRCLE = 3 };
 /* edge scorer: handcrafted (Sec. 2.2.3); a learned 1-D CNN over 3-row strip
  * profiles, alone or with the handcrafted score taking over half-strips the
  * network is unsure about; the paper's own 2-D CNN over 7-row strips

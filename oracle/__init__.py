@@ -52,7 +52,7 @@ class OrcDebug(C.Structure):
 
 LUT_G, LUT_T, LUT_I = 5772, 8193, 256
 HYP_RANDOM, HYP_EXHAUSTIVE = 0, 1
-NORM_2N, NORM_NK, NORM_RAW = 0, 1, 2
+NORM_2N, NORM_NK, NORM_RAW, NORM_CIRCLE = 0, 1, 2, 3
 
 
 def lib():
@@ -96,6 +96,8 @@ def lib():
         L.orc_sc2_targets.argtypes = [C.c_float, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int,
                                       C.c_double, C.c_void_p]
         L.orc_sc2_targets.restype = None
+        L.orc_circle_strips.argtypes = [C.c_void_p, C.c_int, C.c_float, C.c_float, C.c_float]
+        L.orc_circle_strips.restype = C.c_int
         L.orc_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
         L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
@@ -491,6 +493,12 @@ def sc2_loss_grad(rgb7, rows, H, targets, params, pos_weight=1.0):
     loss = lib().orc_sc2_loss_grad(_ptr(rgb7), _ptr(np.ascontiguousarray(rows, np.int32)), W, H,
                                    _ptr(t), float(pos_weight), _ptr(prm), _ptr(g))
     return loss, g
+
+
+def circle_strips(rows, cy, r, t_ri):
+    """Strips whose row is within r + t_ri of the circle's centre row (binary32)."""
+    rw = np.ascontiguousarray(rows, np.int32)
+    return int(lib().orc_circle_strips(_ptr(rw), len(rw), float(cy), float(r), float(t_ri)))
 
 
 def sc2_targets(cx, cy, r, valid, W, y, sigma=3.0):

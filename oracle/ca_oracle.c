@@ -48,7 +48,7 @@ void orc_params_default(orc_params *p) {
     p->d_max = 0.2f;
     p->sup_px = 8;
     p->hyp_mode = ORC_HYP_RANDOM;
-    p->score_norm = ORC_NORM_2N;
+    p->score_norm = ORC_NORM_CIRCLE;
     p->sobel_norm = 1;
     p->seed = 0;
 }
@@ -597,18 +597,37 @@ int orc_fit_prior(const int16_t *cx16, const int16_t *cy16, const uint16_t *cs, 
     if (dbg && dbg->best_h) *dbg->best_h = (int32_t)best;
 
     if (best >= 0) {
-        double norm = p->score_norm == ORC_NORM_2N ? 2.0 * N
-                    : p->score_norm == ORC_NORM_NK ? (double)N * K : 1.0;
-        uint32_t T_cs = (uint32_t)ceil((double)p->t_cs * 32768.0 * norm);
         res->cx = (float)ox + bestc[0];
         res->cy = (float)oy + bestc[1];
         res->r = bestc[2];
-        res->score = (float)((double)bestS / (32768.0 * norm));
+        /* divisor of the score compared with t_cs (Sec. 2.2.5): the paper's
+         * candidate count 2N, the slot count N K, none, or the most inliers
+         * the best circle can have, K per strip it crosses */
+        double norm = p->score_norm == ORC_NORM_2N ? 2.0 * N
+                    : p->score_norm == ORC_NORM_NK ? (double)N * K : 1.0;
+        if (p->score_norm == ORC_NORM_CIRCLE) {
+            int32_t *rows = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+            orc_strip_rows(H, N, p->alpha, rows);
+            norm = (double)K * orc_circle_strips(rows, N, res->cy, res->r, p->t_ri);
+            free(rows);
+        }
+        uint32_t T_cs = (uint32_t)ceil((double)p->t_cs * 32768.0 * norm);
+        res->score = norm > 0.0 ? (float)((double)bestS / (32768.0 * norm)) : 0.0f;
         res->n_inliers = bestn;
-        res->valid = bestS >= T_cs;
+        res->valid = norm > 0.0 && bestS >= T_cs;
     }
     free(X); free(Y); free(flag); free(IX); free(IY);
     return 0;
+}
+
+int orc_circle_strips(const int32_t *rows, int N, float cy, float r, float t_ri) {
+    const float reach = r + t_ri;
+    int n = 0;
+    for (int i = 0; i < N; ++i) {
+        const float dy = (float)rows[i] - cy;
+        if (fabsf(dy) <= reach) ++n;
+    }
+    return n;
 }
 
 /* ----------------------------------------------------- Sec. 1.1, Fig. 1 -- */

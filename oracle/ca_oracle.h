@@ -26,7 +26,7 @@ extern "C" {
 #endif
 
 enum { ORC_HYP_RANDOM = 0, ORC_HYP_EXHAUSTIVE = 1 };
-enum { ORC_NORM_2N = 0, ORC_NORM_NK = 1, ORC_NORM_RAW = 2 };
+enum { ORC_NORM_2N = 0, ORC_NORM_NK = 1, ORC_NORM_RAW = 2, ORC_NORM_CIRCLE = 3 };
 
 /* Sizes of the quantised score tables (index ranges are 0..N-1). */
 enum { ORC_LUT_G = 5772, ORC_LUT_T = 8193, ORC_LUT_I = 256 };
@@ -209,6 +209,12 @@ double orc_sc2_loss_grad(const uint8_t *rgb7, const int32_t rows[7], int W, int 
  * pixel to the circle; 0 without a circle. */
 void orc_sc2_targets(float cx, float cy, float r, int valid, int W, int y, double sigma,
                      double *t);
+
+/* Strips whose row is within r + t_ri of the circle's centre row,
+ * |rows[i] - cy| <= r + t_ri in binary32: the strips the circle (widened by
+ * the inlier distance) crosses, each of which can give it at most K inliers
+ * (the normaliser K n of ORC_NORM_CIRCLE). */
+int orc_circle_strips(const int32_t *rows, int N, float cy, float r, float t_ri);
 
 /* orc_fit with the previous frame's circle (cx, cy, r in pixel coordinates)
  * as one more hypothesis, index n_hyps (Sec. 4: using the previous

@@ -344,7 +344,7 @@ ca_status check_params(ca_handle *h, const ca_params *p) {
         return fail(h, CA_ERR_INVALID_ARG, "sup_px %d invalid", p->sup_px);
     if (p->sobel_norm != 1 && p->sobel_norm != 8)
         return fail(h, CA_ERR_INVALID_ARG, "sobel_norm must be 1 or 8");
-    if (p->score_norm < CA_NORM_2N || p->score_norm > CA_NORM_RAW)
+    if (p->score_norm < CA_NORM_2N || p->score_norm > CA_NORM_CIRCLE)
         return fail(h, CA_ERR_INVALID_ARG, "bad score_norm %d", p->score_norm);
     if (p->hyp_threads != 0 && p->hyp_threads != 1 && p->hyp_threads != 2 &&
         p->hyp_threads != 4 && p->hyp_threads != 8)
@@ -514,6 +514,8 @@ DevParams make_params(const ca_handle *h, const ca_params &p, int max_w, int T, 
                       : p.score_norm == CA_NORM_NK ? (double)p.n_strips * p.cands_per_strip : 1.0;
     P.T_cs = (uint32_t)std::ceil((double)p.t_cs * 32768.0 * norm);
     P.score_den = 32768.0 * norm;
+    P.tcs_unit = (double)p.t_cs * 32768.0;
+    P.norm_circle = p.score_norm == CA_NORM_CIRCLE ? 1 : 0;
     P.qg_sat = h->qg_sat;
     P.io_cut = iota_cut(h->li_host, P.T_ps);
     angle_cut(h->lt_host, P.T_ps, P);
@@ -728,12 +730,14 @@ ca_status prepare_kernels(ca_handle *h, const DevParams &P, const LaunchCfg &cfg
 
 // Queues the kernels of one call.  `timed`: record kernel events.
 ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32_t *d_rows,
-                      const BatchSeg *d_segs, const CallBlock &cb, const DevParams &P,
+                      const BatchSeg *d_segs, const CallBlock &cb, const DevParams &P0,
                       const LaunchCfg &cfg, int fused_grid, const uint16_t *d_luts,
                       const Workspace &ws, ca_result *out, cudaStream_t stream, bool timed,
                       int *kernels) {
     cudaError_t e;
     *kernels = 0;
+    DevParams P = P0;
+    P.rows_tab = d_rows;   // the circle normaliser counts the strips of each frame
     if (cfg.mode == CA_BATCH_FUSED) {
         const int grid = std::max(1, std::min(fused_grid, cb.total_items));
         cudaEvent_t t0 = timed ? time_begin(h, stream) : nullptr;
@@ -944,7 +948,7 @@ void ca_params_default(ca_params *p) {
     p->d_max = 0.2f;
     p->sup_px = 8;
     p->hyp_mode = CA_HYP_RANDOM;
-    p->score_norm = CA_NORM_2N;
+    p->score_norm = CA_NORM_CIRCLE;
     p->sobel_norm = 1;
     p->scorer_mode = CA_SCORER_HAND;
     p->hyp_threads = 0;

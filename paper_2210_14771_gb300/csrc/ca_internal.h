@@ -78,11 +78,14 @@ __host__ __device__ inline size_t sync_words(int nf) { return kSyncGlobal + 3 * 
 struct DevParams {
     int32_t N, K, NH, refine;
     int32_t T_px, sup_px, hyp_mode, debug;
-    uint32_t T_ps, T_cs;
+    uint32_t T_ps, T_cs;   // T_cs: with norm_circle, computed per frame instead
     int32_t qg_sat;      // first index from which the s_g table stays at 32768
     int32_t n_tiles;     // fit CTAs per frame (each 256 / hyp_threads hypotheses)
     float t_ri, r_min, r_max, d_max;
-    double score_den;    // 32768 * normaliser
+    double score_den;    // 32768 * normaliser (fixed normalisers)
+    double tcs_unit;     // t_cs * 32768 (circle normaliser: threshold = ceil(tcs_unit * K n))
+    int32_t norm_circle; // 1: normaliser K n, n = strips the best circle crosses
+    const int32_t *rows_tab;   // the call's strip-row table (DevFrame::rows_off)
     uint64_t seed;
     int32_t max_w;       // widest frame of the call (shared-memory sizing)
     int32_t hyp_threads; // threads per hypothesis in k_fit: 1, 2, 4 or 8

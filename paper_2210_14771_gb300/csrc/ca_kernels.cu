@@ -998,8 +998,21 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
             res.cy = __fadd_rn(__int2float_rn(oy), tr->cy);
             res.r = tr->r;
             res.n_inliers = tr->n_inl;
-            res.score = __double2float_rn(__ddiv_rn((double)S, P.score_den));
-            res.valid = S >= P.T_cs ? 1 : 0;
+            double den = P.score_den;
+            uint32_t T = P.T_cs;
+            if (P.norm_circle) {
+                // the most inliers this circle can have: K per strip whose
+                // row is within r + t_ri of the centre row
+                const float reach = __fadd_rn(res.r, P.t_ri);
+                int n = 0;
+                for (int i = 0; i < P.N; ++i)
+                    n += fabsf(__fsub_rn(__int2float_rn(P.rows_tab[fr.rows_off + i]), res.cy)) <= reach;
+                const double norm = __dmul_rn((double)P.K, (double)n);
+                den = __dmul_rn(32768.0, norm);
+                T = n > 0 ? (uint32_t)ceil(__dmul_rn(P.tcs_unit, norm)) : 0xFFFFFFFFu;
+            }
+            res.score = den > 0.0 ? __double2float_rn(__ddiv_rn((double)S, den)) : 0.0f;
+            res.valid = den > 0.0 && S >= T ? 1 : 0;
         }
         out[f] = res;
         if (trk >= 0) ws.state[trk] = res;   // every tile of the frame has read the prior

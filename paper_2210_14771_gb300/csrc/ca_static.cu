@@ -121,6 +121,8 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
                                                     : 1.0;
     P.T_cs = (uint32_t)std::ceil((double)p->t_cs * 32768.0 * norm);
     P.score_den = 32768.0 * norm;
+    P.tcs_unit = (double)p->t_cs * 32768.0;
+    P.norm_circle = p->score_norm == CA_NORM_CIRCLE ? 1 : 0;
     P.qg_sat = qg_sat;
     P.io_cut = iota_cut(ht.luts + kLutG + kLutT, P.T_ps);
     angle_cut(ht.luts + kLutG, P.T_ps, P);
@@ -168,6 +170,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
     ws.tiles = reinterpret_cast<TileRec *>(scratch + kOffTiles);
     ws.best = reinterpret_cast<unsigned long long *>(scratch + kOffBest);
     ws.done = reinterpret_cast<uint32_t *>(scratch + kOffDone);
+    P.rows_tab = d_rows;
 
     if (cudaMemcpyAsync(d_luts, ht.dev, kLutBytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d_rows, ht.rows, sizeof(int32_t) * P.N, cudaMemcpyHostToDevice, s) !=

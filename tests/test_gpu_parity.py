@@ -260,6 +260,21 @@ def test_hypothesis_split_invariance(ca, orc, T):
         _compare_frame(orc, ca, b, frames[b], keys[b], lp, op, gres, gmask[b], True)
 
 
+@pytest.mark.parametrize("norm", [0, 1, 2, 3])
+def test_parity_score_normalisers(ca, orc, hd_batch, norm):
+    """Every reading of the t_cs divisor (2N, N K, none, and the default
+    circle normaliser, which counts each frame's strips within r + t_ri of
+    the best circle's centre row): results and masks equal the oracle's on
+    16 frames of the 1080p mix, in both launch modes."""
+    frames, _, keys = hd_batch
+    for mode in (1, 2):
+        lp, op = both_params(orc, n_strips=32, cands_per_strip=2, n_hyps=256, score_norm=norm,
+                             batch_mode=mode)
+        gres, gmask = _gpu_batch(ca, frames[:16], keys[:16], lp)
+        for b in range(16):
+            _compare_frame(orc, ca, b, frames[b], keys[b], lp, op, gres, gmask[b], False)
+
+
 @pytest.mark.parametrize("K", [2, 4])
 def test_parity_zero_thresholds(ca, orc, K):
     """t_ps = 0 and t_px = 0 keep zero-score picks (flat runs, image edges):

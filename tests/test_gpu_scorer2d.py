@@ -9,7 +9,7 @@ a relative difference of about 144 * 2^-24 of the sum of |terms|.  Such a
 difference flips the bf16 rounding of an activation (one step = 2^-8
 relative) only when the exact value lies that close to a rounding boundary;
 a logit depends on 32 activations of layer 3, each on 144 of layer 2, each
-on 72 of layer 1.  LOGIT_TOL below is ten times the largest difference
+on 72 of layer 1.  LOGIT_TOL below is three times the largest difference
 measured on these inputs (printed by the test).  The gradient passes
 through three more bf16 roundings (the gradient planes), so each parameter
 block is compared with the binary64 oracle to GRAD_REL of its largest
@@ -211,3 +211,52 @@ def test_2d_mode_needs_parameters():
         h.estimate(t, api.params(scorer_mode=3))
     assert e.value.status == N.CA_ERR_UNSUPPORTED
     h.close()
+
+
+def _hit_rate(xs, ys, gt, tol=3.0):
+    """Fraction of candidates within tol pixels of the true circle."""
+    if gt["kind"] == "none" or len(xs) == 0:
+        return None
+    d = np.abs(np.hypot(xs - gt["cx"], ys - gt["cy"]) - gt["r"])
+    return float((d <= tol).mean())
+
+
+def test_trained_2d_network_gains_over_handcrafted(ca):
+    """What the paper's learned variant buys here: the 2-D network trained on
+    the GPU (its own kernels) on 8192 synthetic 1080p strips with sigma-3
+    soft targets, then run before RANSAC on 48 held-out 1080p frames of the
+    geometry mix.  Its candidates land on the true boundary more often than
+    the handcrafted ones, and with the handcrafted fallback no more frames are
+    missed (normalised Hausdorff > 15 px, Sec. 2.3)."""
+    from paper_2210_14771_gb300 import api, metrics
+    s, rows, tg = synth.training_strips7(100, 8192, 1080, 1920, "mixed", workers=4)
+    ds, dr, dt = (torch.from_numpy(s).cuda(), torch.from_numpy(rows).cuda(),
+                  torch.from_numpy(tg).cuda())
+    ca.scorer2d_init(1)
+    losses = ca.scorer2d_train(ds, dr, dt, 1080, epochs=6, batch=64, seed=3, lr=0.05,
+                               momentum=0.9, pos_weight=10.0, clip_norm=1.0)
+    print("2-D training losses per column:", losses)
+    assert losses[-1] < 0.6 * losses[0]
+    frames, gts, keys = synth.mixed_batch(200, 48, workers=4, resolutions=((1080, 1920),))
+    fr = [torch.from_numpy(f).cuda() for f in frames]
+    out = {}
+    for mode in (0, 3, 4):
+        p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=mode)
+        ca.set_debug(1)
+        _, m = ca.estimate(fr, p, keys=keys, masks=True)
+        ca.sync()
+        hits, nh = [], []
+        for b in range(len(fr)):
+            c = ca.dump_candidates(b)
+            h = _hit_rate(c["x"].astype(float), c["y"].astype(float), gts[b])
+            if h is not None:
+                hits.append(h)
+            nh.append(metrics.normalised_hausdorff(m[b].cpu().numpy().astype(bool),
+                                                   metrics.gt_mask(gts[b], 1080, 1920)))
+        nh = np.asarray(nh)
+        out[mode] = dict(hit=float(np.mean(hits)), mean_nh=float(nh.mean()),
+                         miss=float((nh > 15).mean()), within5=float((nh <= 5).mean()))
+    ca.set_debug(0)
+    print("hand %s | 2-D %s | 2-D + fallback %s" % (out[0], out[3], out[4]))
+    assert out[3]["hit"] >= out[0]["hit"] + 0.15
+    assert out[4]["miss"] <= out[0]["miss"]
