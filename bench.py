@@ -34,6 +34,7 @@ PAPER_CONTEXT = {"ms_per_frame": 0.129, "hardware": "NVIDIA GeForce GTX 980 Ti",
                  "source": "Table 1 (handcrafted variant)"}
 MIXED = dict(B=512, seed=2, unique=128)   # 4 resolutions, 25 % each
 LEARNED = dict(seed=3, train_strips=200000, epochs=3, frames=256, unique=64, eval_frames=64)
+LEARNED2 = dict(train_strips=16384, epochs=6)   # the paper's 2-D network
 SERVING = dict(seed=4, streams=32, budget=4 << 30, n_strips=32, n_hyps=1024, realtime_frames=90,
                saturation_frames=60)
 ROTATE_INPUTS = 4   # resident copies of the batch, used in turn (1.6 GB > L2)
@@ -416,6 +417,11 @@ def batching_leg(ca, mixed, p_ref, stream, steps, warmup, small_plain=None):
 # (forward, input gradients of layers 3 and 2, weight gradients of all three)
 SC_FWD_MACS = 14 * 7 * 32 + 2 * 32 * 7 * 32 + 32
 SC_TRAIN_MACS = SC_FWD_MACS + 2 * 32 * 7 * 32 + (14 * 7 * 32 + 2 * 32 * 7 * 32)
+# the paper's 2-D network per strip column: layers 5x8x5x9, 3x16x8x9, 32x16x9, head 32;
+# training adds the weight gradients and the input gradients of layers 3 and 2
+SC2_FWD_MACS = 5 * 8 * 5 * 9 + 3 * 16 * 8 * 9 + 32 * 16 * 9 + 32
+SC2_TRAIN_MACS = SC2_FWD_MACS + (5 * 8 * 5 * 9 + 3 * 16 * 8 * 9 + 32 * 16 * 9) + \
+    (32 * 16 * 9 + 3 * 16 * 8 * 9) + 32
 
 
 def learned_leg(ca, data, stream, steps):
@@ -489,6 +495,77 @@ def learned_leg(ca, data, stream, steps):
         ca.set_debug(0)
         acc[name] = {"candidate_hit_rate_3px": float(np.mean(hits)), **metrics.summarise(nh)}
     out["accuracy"] = acc
+    out["scorer2d"] = scorer2d_leg(ca, data, stream, steps, fr, keys, gts, sample)
+    return out
+
+
+def scorer2d_leg(ca, data, stream, steps, fr, keys, gts, sample):
+    """The paper's own 2-D network (Sec. 2.2.4) on the same footing: trained
+    on the GPU on LEARNED2["train_strips"] 7-row 1080p strips with sigma-3
+    soft targets, run before RANSAC on the 256 frames; accuracy on the same
+    sample as the 1-D network's, with and without the handcrafted fallback."""
+    import numpy as np
+    import torch
+    from paper_2210_14771_gb300 import api, metrics, synth
+    dev = fr.device
+    W, H = 1920, 1080
+    w = min(16, os.cpu_count() or 1)
+    s, rows, tg = synth.training_strips7(LEARNED["seed"] + 7, LEARNED2["train_strips"], H, W,
+                                         "mixed", workers=w)
+    ds, dr, dt = (torch.from_numpy(s).to(dev), torch.from_numpy(rows).to(dev),
+                  torch.from_numpy(tg).to(dev))
+    n, ep = len(s), LEARNED2["epochs"]
+    ca.scorer2d_init(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ca.scorer2d_train(ds, dr, dt, H, epochs=ep, batch=64, seed=1, lr=0.05, momentum=0.9,
+                               pos_weight=10.0, clip_norm=1.0, schedule="cosine")
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    tc_peak, tc_kind = tensor_peak()
+    out = {"train": {"strips": n, "epochs": ep, "batch": 64, "seconds": el, "pos_weight": 10.0,
+                     "strips_per_s": n * ep / el,
+                     "tflops": n * ep * W * 2 * SC2_TRAIN_MACS / el / 1e12,
+                     "loss_per_epoch": [float(v) for v in losses]}}
+    B = fr.shape[0]
+    masks = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+    p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=4)
+    for _ in range(3):
+        ca.estimate(fr, p, keys=keys, masks=masks)
+    torch.cuda.synchronize()
+    ca.kernel_times()
+    ca.set_timing(True)
+    total, _ = timed_loop(stream, steps, lambda k: ca.estimate(fr, p, keys=keys, masks=masks))
+    ca.set_timing(False)
+    ca.sync()
+    kt = ca.kernel_times()
+    sc_ms = kt["scorer"][0] / max(1, kt["scorer"][1])
+    flops = B * 32 * W * 2 * SC2_FWD_MACS
+    out["infer"] = {"frames": B, "frames_per_s": B * steps / (total / 1e3),
+                    "ms_per_call": total / steps, "scorer_ms": sc_ms,
+                    "roofline": {"bound": "tensor", "kernel": "k_sc2_infer",
+                                 "achieved": flops / (sc_ms / 1e3) / 1e12, "peak": tc_peak,
+                                 "unit": "TFLOP/s", "peak_kind": tc_kind,
+                                 "frac": flops / (sc_ms / 1e3) / 1e12 / tc_peak}}
+    sub = [fr[i] for i in sample]
+    acc = {}
+    for mode, name in ((3, "scorer2d"), (4, "scorer2d_fallback")):
+        q = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, scorer_mode=mode)
+        ca.set_debug(1)
+        _, m = ca.estimate(sub, q, keys=[keys[i] for i in sample], masks=True)
+        ca.sync()
+        hits, nh = [], []
+        for j, i in enumerate(sample):
+            g = gts[i]
+            c = ca.dump_candidates(j)
+            if g["kind"] != "none" and len(c["x"]):
+                d = np.abs(np.hypot(c["x"] - g["cx"], c["y"] - g["cy"]) - g["r"])
+                hits.append(float((d <= 3.0).mean()))
+            nh.append(metrics.normalised_hausdorff(m[j].cpu().numpy().astype(bool),
+                                                   metrics.gt_mask(g, H, W)))
+        ca.set_debug(0)
+        acc[name] = {"candidate_hit_rate_3px": float(np.mean(hits)), **metrics.summarise(nh)}
+    out["accuracy"] = acc
     return out
 
 
@@ -516,10 +593,33 @@ def serving_leg(ca, streams):
         recs, wall = serve.run_load(srv, streams, banks, n_rt, realtime=True)
         srv.close()
         out[name] = serve.summarise(recs, wall)
+    # saturation (every frame arrives at once): frames copied to the device
+    # and submitted one call per frame, as before; then zero-copy frames (the
+    # kernels read their strip rows from page-locked host memory) submitted
+    # in batches, one library call per feeding-loop pass
     srv = serve.Server(ca, p, mem_budget=SERVING["budget"], max_streams=len(streams), max_batch=64)
-    recs, wall = serve.run_load(srv, streams, banks, SERVING["saturation_frames"], realtime=False)
+    recs, wall = serve.run_load(srv, streams, banks, SERVING["saturation_frames"], realtime=False,
+                                batched=False)
     srv.close()
     out["saturation"] = serve.summarise(recs, wall)
+    srv = serve.Server(ca, p, mem_budget=SERVING["budget"], max_streams=len(streams), max_batch=64,
+                       zero_copy=True)
+    serve.run_load(srv, streams, banks, 4, realtime=False)   # warm-up
+    recs, wall = serve.run_load(srv, streams, banks, SERVING["saturation_frames"], realtime=False)
+    srv.close()
+    zc = serve.summarise(recs, wall)
+    # bytes that cross the host link per frame: the strip rows the kernels read
+    # (9 N W) and the 24-byte result, against the whole frame (3 H W) copied
+    n = SERVING["n_strips"]
+    per = [(9 * n * s.W + 24, 3 * s.H * s.W + 24) for s in streams]
+    zc["link_bytes_per_frame"] = float(sum(a for a, _ in per) / len(per))
+    zc["copy_bytes_per_frame"] = float(sum(b for _, b in per) / len(per))
+    out["saturation_zero_copy"] = zc
+    srv = serve.Server(ca, p, mem_budget=SERVING["budget"], max_streams=len(streams), max_batch=64,
+                       zero_copy=True)
+    recs, wall = serve.run_load(srv, streams, banks, n_rt, realtime=True)
+    srv.close()
+    out["zero_copy_realtime"] = serve.summarise(recs, wall)
     return out
 
 

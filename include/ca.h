@@ -223,6 +223,10 @@ typedef struct ca_tuning {
     float ms_staged;      /* fastest staged configuration */
     float ms_fused;       /* fastest fused configuration */
     float ms_untuned;     /* the configuration CA_BATCH_AUTO used before tuning */
+    int32_t fit_lag;      /* chosen (fused): the fit of a wave follows the strips of
+                             the wave fit_lag waves later */
+    int32_t mask_lag;     /* chosen (fused): its masks follow the strips of the wave
+                             mask_lag waves later */
 } ca_tuning;
 
 /* Autotuner.  Runs the batch (arguments as in ca_estimate) under every launch

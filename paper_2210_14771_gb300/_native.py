@@ -44,7 +44,8 @@ class CaFrame(C.Structure):
 class CaTuning(C.Structure):
     _fields_ = [("batch_mode", C.c_int32), ("hyp_threads", C.c_int32),
                 ("wave_frames", C.c_int32), ("n_tried", C.c_int32), ("ms", C.c_float),
-                ("ms_staged", C.c_float), ("ms_fused", C.c_float), ("ms_untuned", C.c_float)]
+                ("ms_staged", C.c_float), ("ms_fused", C.c_float), ("ms_untuned", C.c_float),
+                ("fit_lag", C.c_int32), ("mask_lag", C.c_int32)]
 
 
 class CaTrainParams(C.Structure):

@@ -31,6 +31,8 @@ struct LaunchCfg {
     int mode = CA_BATCH_STAGED;   // CA_BATCH_STAGED or CA_BATCH_FUSED
     int T = 1;                    // threads per hypothesis
     int wave = 1;                 // fused: frames per wave
+    int fit_lag = 1;              // fused: the fit of wave t - fit_lag follows the strips of wave t
+    int mask_lag = 2;             // fused: then the masks of wave t - mask_lag (> fit_lag)
     int scorer = CA_SCORER_HAND;  // learned modes always run staged
 };
 
@@ -638,10 +640,14 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
         }
     }
     // fused launch: software pipeline over waves of frames -- step t holds the
-    // strips of wave t, the fit of wave t-1 and the masks of wave t-2
+    // strips of wave t, the fit of wave t - fit_lag and the masks of wave
+    // t - mask_lag (mask_lag > fit_lag >= 1: each frame's strips, fit and
+    // masks stay in that order).  Lags longer than a fit tile's run keep mask
+    // items from holding a CTA while their circle is computed.
     std::vector<BatchSeg> segs;
     int items = 0;
     if (P && cfg.mode == CA_BATCH_FUSED) {
+        const int FL = std::max(1, cfg.fit_lag), ML = std::max(FL + 1, cfg.mask_lag);
         const int wave = std::max(1, cfg.wave);
         const int nw = (B + wave - 1) / wave;
         const int spf = strip_items_of(P->N, P->K);
@@ -655,10 +661,10 @@ void build_block(const ca_frame *frames, int B, int N, float alpha, const DevPar
             segs.push_back(BatchSeg{items, phase, f0, f1});
             items += cnt;
         };
-        for (int t = 0; t < nw + 2; ++t) {
+        for (int t = 0; t < nw + ML; ++t) {
             if (t < nw) add(kPhaseStrips, t);
-            if (t >= 1 && t - 1 < nw) add(kPhaseFit, t - 1);
-            if (t >= 2 && t - 2 < nw) add(kPhaseMask, t - 2);
+            if (t >= FL && t - FL < nw) add(kPhaseFit, t - FL);
+            if (t >= ML && t - ML < nw) add(kPhaseMask, t - ML);
         }
     }
     cb.off_rows = align_up(sizeof(DevFrame) * B, 256);
@@ -1373,7 +1379,20 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
             waves.push_back(w);
             if (w == 1) break;
         }
-        for (int w : waves) cands.push_back(LaunchCfg{CA_BATCH_FUSED, T, w});
+        for (int w : waves) {
+            const int nw = (B + w - 1) / w;
+            // lags beyond the last wave all mean "after everything": try each once
+            for (int fl : {1, 2, 4}) {
+                if (fl > 1 && fl >= nw) continue;
+                for (int ml : {2, 4, 8, 16}) {
+                    if (ml <= fl || (ml > 2 && ml - 1 > nw)) continue;
+                    LaunchCfg c{CA_BATCH_FUSED, T, w};
+                    c.fit_lag = fl;
+                    c.mask_lag = ml;
+                    cands.push_back(c);
+                }
+            }
+        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CA_CUDA(h, cudaEventCreate(&e0));
@@ -1399,9 +1418,23 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
     res.ms_staged = res.ms_fused = 1e30f;
     LaunchCfg best;
     float best_ms = 1e30f;
+    // every configuration must give the first one's results, byte for byte
+    std::vector<ca_result> first((size_t)B), cur((size_t)B);
     for (const LaunchCfg &c : cands) {
         float ms = 0.0f;
         if ((st = time_cfg(c, &ms)) != CA_OK) break;
+        std::vector<ca_result> &dst = res.n_tried == 0 ? first : cur;
+        if (cudaMemcpy(dst.data(), out_dev, sizeof(ca_result) * B, cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            st = cuda_fail(h, cudaGetLastError(), "tune results");
+            break;
+        }
+        if (res.n_tried > 0 && std::memcmp(first.data(), cur.data(), sizeof(ca_result) * B) != 0) {
+            st = fail(h, CA_ERR_STATE,
+                      "launch configuration (mode %d, T %d, wave %d, lags %d/%d) changed the results",
+                      c.mode, c.T, c.wave, c.fit_lag, c.mask_lag);
+            break;
+        }
         res.n_tried += 1;
         if (c.mode == CA_BATCH_STAGED) res.ms_staged = std::min(res.ms_staged, ms);
         else res.ms_fused = std::min(res.ms_fused, ms);
@@ -1417,6 +1450,8 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
     res.batch_mode = best.mode;
     res.hyp_threads = best.T;
     res.wave_frames = best.wave;
+    res.fit_lag = best.fit_lag;
+    res.mask_lag = best.mask_lag;
     res.ms = best_ms;
     res.ms_untuned = ms_u;
     if (out) *out = res;

@@ -999,7 +999,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
             res.r = tr->r;
             res.n_inliers = tr->n_inl;
             double den = P.score_den;
-            uint32_t T = P.T_cs;
+            uint32_t Tcs = P.T_cs;
             if (P.norm_circle) {
                 // the most inliers this circle can have: K per strip whose
                 // row is within r + t_ri of the centre row
@@ -1009,10 +1009,10 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
                     n += fabsf(__fsub_rn(__int2float_rn(P.rows_tab[fr.rows_off + i]), res.cy)) <= reach;
                 const double norm = __dmul_rn((double)P.K, (double)n);
                 den = __dmul_rn(32768.0, norm);
-                T = n > 0 ? (uint32_t)ceil(__dmul_rn(P.tcs_unit, norm)) : 0xFFFFFFFFu;
+                Tcs = n > 0 ? (uint32_t)ceil(__dmul_rn(P.tcs_unit, norm)) : 0xFFFFFFFFu;
             }
             res.score = den > 0.0 ? __double2float_rn(__ddiv_rn((double)S, den)) : 0.0f;
-            res.valid = den > 0.0 && S >= T ? 1 : 0;
+            res.valid = den > 0.0 && S >= Tcs ? 1 : 0;
         }
         out[f] = res;
         if (trk >= 0) ws.state[trk] = res;   // every tile of the frame has read the prior

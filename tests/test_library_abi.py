@@ -44,7 +44,7 @@ def test_struct_layouts(native):
     assert C.sizeof(native.CaResult) == 24
     assert C.sizeof(native.CaFrame) == 40
     assert C.sizeof(native.CaParams) == 112
-    assert C.sizeof(native.CaTuning) == 32
+    assert C.sizeof(native.CaTuning) == 40
     assert C.sizeof(native.CaTrainParams) == 24
 
 
