@@ -401,12 +401,17 @@ def batching_leg(ca, mixed, p_ref, stream, steps, warmup, small_plain=None):
     out["speedup_vs_plain"] = out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]
     if small_plain:
         out["speedup_vs_640x480_plain"] = out["batched"]["frames_per_s"] / small_plain
-    # accuracy-constrained sweep of N, K, NH on a calibration subset
-    cal = list(range(0, B, max(1, B // 32)))[:32]
+    # accuracy-constrained sweep of N, K, NH on a calibration subset: the
+    # distinct scenes, geometry classes in turn
+    distinct = list(range(min(B, MIXED["unique"])))
+    cal = [distinct[i] for i in tune.calibration_subset([mg[i] for i in distinct], 128)]
     trials, ref_t, best = tune.sweep(ca, [ts[i] for i in cal], [mg[i] for i in cal],
                                      [mk[i] for i in cal])
-    out["sweep"] = {"calibration_frames": len(cal), "reference": tune.as_dict(ref_t),
-                    "chosen": tune.as_dict(best), "trials": [tune.as_dict(t) for t in trials]}
+    out["sweep"] = {"calibration_frames": len(cal),
+                    "rule": "fastest trial whose paired per-frame NH excess over the reference is "
+                            "at most 2 standard errors and which misses no more frames",
+                    "reference": tune.as_dict(ref_t), "chosen": tune.as_dict(best, ref_t),
+                    "trials": [tune.as_dict(t, ref_t) for t in trials]}
     if (best.N, best.K, best.NH) != (ref_t.N, ref_t.K, ref_t.NH):
         q = api.params(n_strips=best.N, cands_per_strip=best.K, n_hyps=best.NH)
         out["batched_autotuned"], _ = run_plan(q, "autotuned")

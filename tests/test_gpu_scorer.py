@@ -7,10 +7,11 @@ products in binary32 in their own order, a relative difference of about
 224 * 2^-24 of the sum of |terms|.  That difference flips the bf16 rounding
 of an activation (one step = 2^-8 relative) about once in 300 activations;
 a logit depends on ~900 activations of the three layers, so a few flips of
-~1e-3 each reach it: 0.03 absolute is ten times that.  The gradient passes
-through three more bf16 roundings (one per layer), so each parameter block
-is compared to 5 % of its largest entry, with a cosine similarity of the
-whole gradient of at least 0.999.  The picks and the circle fit, given the
+~1e-3 each could reach it.  Measured: at most 6.1e-4 over the strips below;
+LOGIT_TOL is ten times that.  The gradient passes through three more bf16
+roundings (one per layer); each parameter block is compared to GRAD_REL of
+its largest entry (about ten times the worst block measured, printed by the
+test), with a cosine similarity of the whole gradient of at least 0.999.  The picks and the circle fit, given the
 same learned scores, are exact (integer and binary32 decisions taken the
 same way on both sides) and compared bit for bit.
 """
@@ -28,7 +29,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-LOGIT_TOL = 0.03
+LOGIT_TOL = 6e-3
+GRAD_REL = 0.05
 
 
 @pytest.fixture(scope="module")
@@ -101,10 +103,13 @@ def test_gradient_matches_oracle(ca, orc):
     assert loss == pytest.approx(ref_loss, rel=1e-3)
     off = orc.sc_offsets()
     bounds = list(off.items()) + [("end", orc.SC_NPARAM)]
+    worst = {}
     for (name, a), (_, b) in zip(bounds[:-1], bounds[1:]):
         gb, rb = g[a:b].astype(np.float64), ref[a:b]
-        assert np.abs(gb - rb).max() <= 0.05 * np.abs(rb).max() + 1e-6, name
+        worst[name] = float(np.abs(gb - rb).max() / (np.abs(rb).max() + 1e-12))
+        assert np.abs(gb - rb).max() <= GRAD_REL * np.abs(rb).max() + 1e-6, (name, worst[name])
     cos = float(g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)))
+    print("1-D gradient: cosine %.6f, worst block error / block max %s" % (cos, worst))
     assert cos >= 0.999, cos
 
 
@@ -199,8 +204,8 @@ def test_learned_pipeline_parity(ca, orc, mode):
         for i, y in enumerate(rows):
             ref = orc.sc_forward(frames[b][y - 1:y + 2], y, 480, p, mode=orc.SC_MIXED)
             dq = np.abs(learned[i].astype(np.int64) - orc.sc_q15(ref).astype(np.int64))
-            # Q15 step of the sigmoid at the logit tolerance: 32768 * 0.25 * 0.03
-            assert dq.max() <= 250, (b, i, int(dq.max()))
+            # Q15 step of the sigmoid at the logit tolerance: 32768 * 0.25 * LOGIT_TOL
+            assert dq.max() <= 32768 * 0.25 * LOGIT_TOL + 1, (b, i, int(dq.max()))
         xs, ys_, ss = orc.learned_candidates(frames[b], learned, fallback=(mode == 2), p=op)
         gc = ca.dump_candidates(b)
         assert np.array_equal(gc["x"], xs) and np.array_equal(gc["y"], ys_)
