@@ -754,10 +754,10 @@ ca_status launch_call(ca_handle *h, const DevFrame *d_frames, int B, const int32
         *kernels = 1;
         return CA_OK;
     }
-    // strips: one half-strip per quad of warps (K = 2) or per warp (K > 2);
+    // strips: one strip per CTA (K = 2) or one half-strip per warp (K > 2);
     // CTAs beyond the resident ones wait for a free slot, which balances
-    // uneven half-strips
-    const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
+    // uneven strips
+    const int sgrid = P.K == 2 ? B * P.N : (2 * B * P.N + 7) / 8;
     cudaEvent_t t0 = nullptr;
     const bool no_hand = cfg.scorer == CA_SCORER_LEARNED || cfg.scorer == CA_SCORER_2D;
     if (!no_hand) {

@@ -114,11 +114,23 @@ __host__ __device__ __forceinline__ size_t strip_tables_bytes(const DevParams &P
 // K = 2: each warp's queue of pixels awaiting their exact score (one round of
 // 32 pushes on top of at most 31 waiting entries).
 constexpr int kQueueCap = 64;
+constexpr int kMaxBlocks = (kMaxDim / 2 + 31) / 32;   // 32-pixel blocks of a half-strip
+
+// K = 2 (a CTA per strip): column words of the whole strip, then per half the
+// block maxima and carries of the preceding maximum, the warps' queues and
+// the two halves' best keys.
+__host__ __device__ __forceinline__ int pair_words(const DevParams &P) {
+    return ((P.max_w + 15) & ~15) + 16;
+}
 
 size_t strips_smem_bytes(const DevParams &P) {
-    size_t b = strip_tables_bytes(P) + (size_t)kStripWarps * strip_cols(P) * 4;
-    if (P.K > 2) b += (size_t)kStripWarps * (strip_cols(P) * 2 + 4 * (kMaxSlots / 2));
-    else b += (size_t)kStripWarps * kQueueCap * sizeof(uint2);
+    size_t b = strip_tables_bytes(P);
+    if (P.K > 2)
+        b += (size_t)kStripWarps * strip_cols(P) * 4 +
+             (size_t)kStripWarps * (strip_cols(P) * 2 + 4 * (kMaxSlots / 2));
+    else
+        b += (size_t)pair_words(P) * 4 + 4 * 4 * kMaxBlocks +
+             (size_t)kStripWarps * kQueueCap * sizeof(uint2) + 16;
     return b;
 }
 
@@ -199,9 +211,8 @@ namespace {
 // the per-warp buffers.
 struct StripShared {
     const uint16_t *li, *lgb, *lg;   // s_iota, s_g bin bounds, s_g
-    unsigned char *wmem;             // per-warp column words (+ scores, picks or queues)
-    int *s_qmax;                     // [kStripWarps] per-warp maxima (quads)
-    uint32_t *s_qbest;               // [kStripWarps] per-warp best keys (quads)
+    unsigned char *wmem;             // per-warp column words (+ scores, picks), or the
+                                     // strip's words, block carries and queues (K = 2)
 };
 
 // Copies the table block from s_iota on into shared memory: every 16-byte
@@ -244,10 +255,9 @@ __device__ __noinline__ int2 prior_centre2(const int32_t *trk, const ca_result *
     return c2;
 }
 
-// Half `half` of strip i of frame f: the K/2 best points of the half-strip
-// into their candidate slots.  K = 2: the 4 warps of quad `quad` share the
-// half (warp qw of the quad scans the qw-th quarter, quad barriers combine
-// them); K > 2: the calling warp alone takes the half.
+// K > 2: half `half` of strip i of frame f by the calling warp alone: the
+// exact score of every pixel, then K/2 picks, each excluding +-sup_px around
+// the earlier ones.
 __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
                                            const int32_t *__restrict__ rows, const DevParams &P,
                                            const uint16_t *__restrict__ lt, const StripShared &ss,
@@ -255,26 +265,19 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cols = strip_cols(P);
     const uint16_t *li = ss.li, *lgb = ss.lgb, *lg = ss.lg;
-    int *s_qmax = ss.s_qmax;
-    uint32_t *s_qbest = ss.s_qbest;
     uint32_t *yy = reinterpret_cast<uint32_t *>(ss.wmem) + warp * cols;
     uint16_t *sc = reinterpret_cast<uint16_t *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
     int *s_pick = reinterpret_cast<int *>(ss.wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
-    uint2 *queue = reinterpret_cast<uint2 *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * kQueueCap;
     const int kk = P.K >> 1;   // picks per half-strip
-    const bool quads = kk == 1;
-    const int quad = warp >> 2, qw = warp & 3;
-    const int nseg = quads ? 4 : 1, seg_id = quads ? qw : 0;
     const DevFrame fr = frames[f];
     const int W = fr.W, H = fr.H;
     const int y = rows[fr.rows_off + i];
     const int hw = W >> 1;
     const int c_lo = half ? hw - 1 : 0, c_hi = half ? W : hw + 1;   // columns of the half
     const int len = half ? (W - hw) : hw;
-    // this warp's scan positions [q0, q1) (whole rounds of 32) and the
-    // columns they need (one neighbour on each side)
-    const int seg = nseg == 1 ? len : ((len + 32 * nseg - 1) / (32 * nseg)) * 32;
-    const int q0 = min(seg_id * seg, len), q1 = min(q0 + seg, len);
+    // the half's scan positions [q0, q1) and the columns they need (one
+    // neighbour on each side)
+    const int q0 = 0, q1 = len;
     int col_lo = c_lo, col_hi = c_lo;
     if (q0 < q1) {
         const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
@@ -344,160 +347,55 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
     const int dir = half ? -1 : 1;
     uint32_t best = 0u;
 
-    if (kk == 1) {
-        // rows of this warp's quarter, loaded at once; the maxima of the
-        // earlier quarters' middle rows give the preceding maximum before it
-        int qm = 0;
-        if (q0 < q1) {
-            const int xa = half ? W - q1 : q0, xb = half ? W - 1 - q0 : q1 - 1;
-            qm = load_words(xa, xb);
-        }
-        qm = __reduce_max_sync(kFull, qm);
-        if (lane == 0) s_qmax[warp] = qm;
-        quad_barrier(quad);
-        int carry = 0;
-        for (int k = 0; k < qw; ++k) carry = max(carry, s_qmax[quad * 4 + k]);
-        // every scanned pixel has at least the key of score 0, (0 << 16) | rank,
-        // and the largest of those is the quarter's first pixel (ranks fall
-        // along the scan); pixels whose score can only be 0 need no other key
-        if (q0 < q1 && carry < P.io_cut) {
-            const int x = half ? (W - 1 - q0) : q0;
-            best = (uint32_t)(half ? x : (0xFFFF - x));
-        }
-        // Pixels that pass the angle cut and whose bound beats the best so far
-        // wait in the warp's queue; 32 at a time they get their exact score
-        // with every lane busy.  qn: entries (warp-uniform); qtop: largest
-        // bound key waiting.
-        int qn = 0;
-        uint32_t qtop = 0u;
-        auto flush = [&]() {
-            __syncwarp();   // the pushes are visible
-            for (int b0 = 0; b0 < qn; b0 += 32) {
-                uint32_t key = 0u;
-                if (b0 + lane < qn) {
-                    const uint2 e = queue[b0 + lane];
-                    const int x = (int)(e.x >> 16), iota = (int)(e.x & 0xffu);
-                    const int gx = (int)(int16_t)(e.y & 0xffffu), gy = (int)(int16_t)(e.y >> 16);
-                    const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
-                    key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) | rank;
-                }
-                best = max(best, __reduce_max_sync(kFull, key));
-            }
-            qn = 0;
-            qtop = 0u;
-            __syncwarp();   // the entries are read before new pushes
-        };
-        // ---- rounds of 32 consecutive pixels in scan order (outer edge
-        // inwards), one per lane; `carry` is the preceding maximum before
-        // the round
-        for (int r0 = q0; r0 < q1; r0 += 32) {
-            // no remaining pixel of the quarter can be kept (iota cut) or
-            // beat the best: their s_iota <= s_iota(carry) bounds their scores
-            if (carry >= P.io_cut) break;
-            const uint32_t lic = li[carry];
-            if (qn > 0 && (qtop >> 16) >= lic) flush();   // the waiting ones may decide it
-            if (best != 0u && (best >> 16) >= lic) break;
-            const int p = r0 + lane;
-            const bool act = p < q1;
-            const int x = half ? (W - 1 - p) : p;
-            const int xc = act ? x : (half ? W - q1 : q1 - 1);
-            const uint32_t w1 = yy[xc - base];
-            const int m1 = (w1 >> 8) & 0xff;
-            int inc = act ? m1 : 0;
+    load_words(0, -1);
+    // ---- K > 2: exact score per pixel over this lane's chunk, with a
+    // sliding window of the vertical Sobel sums
+    const int cpl = (len + 31) >> 5;
+    const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
+    const int xs = half ? (W - 1 - p0) : p0;
+    int lm = 0;
+    for (int p = p0, x = xs; p < p1; ++p, x += dir) lm = max(lm, (int)((yy[x - base] >> 8) & 0xff));
+    int inc = lm;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o) inc = max(inc, t);
-            }
-            int excl = __shfl_up_sync(kFull, inc, 1);
-            if (lane == 0) excl = 0;
-            const int iota = max(carry, excl);
-            const int carry_next = max(carry, __shfl_sync(kFull, inc, 31));
-            bool cand = false;
-            uint32_t bkey = 0u;
-            uint2 ent = make_uint2(0u, 0u);
-            if (act && iota < P.io_cut && x != 0 && x != W - 1) {
-                const uint32_t w0 = yy[x - 1 - base], w2 = yy[x + 1 - base];
-                const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
-                const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
-                const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
-                const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
-                const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc = max(inc, t);
+    }
+    int run = __shfl_up_sync(kFull, inc, 1);
+    if (lane == 0) run = 0;
+    auto col = [&](int cc, int &S, int &T, int &M) {
+        cc = min(max(cc, c_lo), c_hi - 1);
+        const uint32_t w = yy[cc - base];
+        const int u = w & 0xff, m = (w >> 8) & 0xff, d = (w >> 16) & 0xff;
+        S = u + 2 * m + d;
+        T = d - u;
+        M = m;
+    };
+    int S0, T0, M0, S1, T1, M1;
+    col(xs - dir, S0, T0, M0);
+    col(xs, S1, T1, M1);
+    // the preceding maximum never decreases along the scan: once it
+    // reaches io_cut no later pixel of the half can be kept
+    for (int p = p0, x = xs; p < p1; ++p, x += dir) {
+        uint32_t sv = 0u;
+        if (run < P.io_cut) {
+            int S2, T2, M2;
+            col(x + dir, S2, T2, M2);
+            if (x != 0 && x != W - 1) {
+                const int gx = dir * (S2 - S0), gy = T0 + 2 * T1 + T2;
                 const int ng = gx * gx + gy * gy;
-                if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P)) {
-                    const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
-                    const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
-                    const uint32_t rank = (uint32_t)(half ? x : (0xFFFF - x));
-                    bkey = (bound << 16) | rank;
-                    cand = bkey > best;   // could beat the best so far
-                    ent = make_uint2(((uint32_t)x << 16) | (uint32_t)iota,
-                                     ((uint32_t)gx & 0xffffu) | ((uint32_t)gy << 16));
-                }
+                if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P))
+                    sv = score_from_g(ctx, gx, gy, x, run, P);
             }
-            const unsigned bal = __ballot_sync(kFull, cand);
-            if (cand) queue[qn + __popc(bal & ((1u << lane) - 1u))] = ent;
-            qn += __popc(bal);
-            qtop = max(qtop, __reduce_max_sync(kFull, cand ? bkey : 0u));
-            if (qn >= 32) flush();
-            carry = carry_next;
+            run = max(run, M1);
+            S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
         }
-        if (qn > 0) flush();
-        // best of the quad
-        if (lane == 0) s_qbest[warp] = best;
-        quad_barrier(quad);
-        best = max(max(s_qbest[quad * 4], s_qbest[quad * 4 + 1]),
-                   max(s_qbest[quad * 4 + 2], s_qbest[quad * 4 + 3]));
-    } else {
-        load_words(0, -1);
-        // ---- K > 2: exact score per pixel over this lane's chunk, with a
-        // sliding window of the vertical Sobel sums
-        const int cpl = (len + 31) >> 5;
-        const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
-        const int xs = half ? (W - 1 - p0) : p0;
-        int lm = 0;
-        for (int p = p0, x = xs; p < p1; ++p, x += dir) lm = max(lm, (int)((yy[x - base] >> 8) & 0xff));
-        int inc = lm;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc = max(inc, t);
-        }
-        int run = __shfl_up_sync(kFull, inc, 1);
-        if (lane == 0) run = 0;
-        auto col = [&](int cc, int &S, int &T, int &M) {
-            cc = min(max(cc, c_lo), c_hi - 1);
-            const uint32_t w = yy[cc - base];
-            const int u = w & 0xff, m = (w >> 8) & 0xff, d = (w >> 16) & 0xff;
-            S = u + 2 * m + d;
-            T = d - u;
-            M = m;
-        };
-        int S0, T0, M0, S1, T1, M1;
-        col(xs - dir, S0, T0, M0);
-        col(xs, S1, T1, M1);
-        // the preceding maximum never decreases along the scan: once it
-        // reaches io_cut no later pixel of the half can be kept
-        for (int p = p0, x = xs; p < p1; ++p, x += dir) {
-            uint32_t sv = 0u;
-            if (run < P.io_cut) {
-                int S2, T2, M2;
-                col(x + dir, S2, T2, M2);
-                if (x != 0 && x != W - 1) {
-                    const int gx = dir * (S2 - S0), gy = T0 + 2 * T1 + T2;
-                    const int ng = gx * gx + gy * gy;
-                    if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P))
-                        sv = score_from_g(ctx, gx, gy, x, run, P);
-                }
-                run = max(run, M1);
-                S0 = S1; T0 = T1; S1 = S2; T1 = T2; M1 = M2;
-            }
-            sc[x - base] = (uint16_t)sv;
-        }
+        sc[x - base] = (uint16_t)sv;
     }
 
     // ---- K/2 picks per half, each excluding +-sup_px around earlier picks
     for (int r = 0; r < kk; ++r) {
-        if (kk > 1) {
+        {
             const int cpl = (len + 31) >> 5;
             const int p0 = min(lane * cpl, len), p1 = min(p0 + cpl, len);
             const int xs = half ? (W - 1 - p0) : p0;
@@ -525,11 +423,202 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
             out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
                                   y >= P.T_px && y <= H - 1 - P.T_px);
         }
-        if (lane == 0 && (!quads || qw == 0)) {
-            if (kk > 1) s_pick[r] = px;
+        if (lane == 0) {
+            s_pick[r] = px;
             slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
         }
         __syncwarp();   // this round's pick visible to the whole warp
+    }
+}
+
+// K = 2: both halves of strip i of frame f by the whole CTA, the best point of
+// each half into its candidate slot.  The preceding maximum iota of a pixel
+// depends only on the middle row before it, so it is known for every block
+// of 32 scan positions up front (the maximum of the earlier blocks, then a
+// warp scan inside the block); the blocks whose carry has not reached io_cut
+// -- the border region from each outer edge to the content -- are then
+// independent and are shared out among the 8 warps.  A pixel's key is
+// (Q15 score << 16) | outer rank exactly as the paper's argmax needs; the
+// exact score is formed only for pixels that pass the angle cut and whose
+// bound beats the best key so far, 32 at a time from each warp's queue.
+__device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
+                                           const int32_t *__restrict__ rows, const DevParams &P,
+                                           const uint16_t *__restrict__ lt, const StripShared &ss,
+                                           CandSlot *__restrict__ slots, int f, int i) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint16_t *li = ss.li, *lgb = ss.lgb, *lg = ss.lg;
+    uint32_t *yy = reinterpret_cast<uint32_t *>(ss.wmem);           // column words, x = 0 .. W-1
+    int *bmax = reinterpret_cast<int *>(yy + pair_words(P));        // [2][kMaxBlocks]
+    int *carry = bmax + 2 * kMaxBlocks;                              // [2][kMaxBlocks]
+    uint2 *queue = reinterpret_cast<uint2 *>(carry + 2 * kMaxBlocks) + warp * kQueueCap;
+    uint32_t *s_best = reinterpret_cast<uint32_t *>(queue - warp * kQueueCap + kStripWarps * kQueueCap);
+    int *s_live = reinterpret_cast<int *>(s_best + 2);
+    const DevFrame fr = frames[f];
+    const int W = fr.W, H = fr.H;
+    const int y = rows[fr.rows_off + i];
+    const int hw = W >> 1;
+    const int len[2] = {hw, W - hw};                  // scan positions of each half
+    const int nb0 = (len[0] + 31) >> 5, nb1 = (len[1] + 31) >> 5;
+    __syncthreads();   // the previous item is done with the words and queues
+
+    // ---- rows y-1, y, y+1 of the whole strip -> column words
+    if (fr.vec_ok) {
+        const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
+        for (int g = tid; g < (W >> 4); g += blockDim.x) {
+            const uint8_t *p0 = r0 + g * 48, *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+            const uint4 a0 = ld_nc_v4(p0), b0 = ld_nc_v4(p0 + 16), c0 = ld_nc_v4(p0 + 32);
+            const uint4 a1 = ld_nc_v4(p1), b1 = ld_nc_v4(p1 + 16), c1 = ld_nc_v4(p1 + 32);
+            const uint4 a2 = ld_nc_v4(p2), b2 = ld_nc_v4(p2 + 16), c2 = ld_nc_v4(p2 + 32);
+            const uint4 L0 = luma16(a0, b0, c0), L1 = luma16(a1, b1, c1), L2 = luma16(a2, b2, c2);
+            uint4 *dst = reinterpret_cast<uint4 *>(yy + g * 16);
+            dst[0] = interleave4(L0.x, L1.x, L2.x);
+            dst[1] = interleave4(L0.y, L1.y, L2.y);
+            dst[2] = interleave4(L0.z, L1.z, L2.z);
+            dst[3] = interleave4(L0.w, L1.w, L2.w);
+        }
+    } else {
+        for (int x = tid; x < W; x += blockDim.x) {
+            const uint8_t *p0 = fr.rgb + (int64_t)(y - 1) * fr.pitch + 3 * x;
+            const uint8_t *p1 = p0 + fr.pitch, *p2 = p1 + fr.pitch;
+            yy[x] = luma(p0[0], p0[1], p0[2]) | (luma(p1[0], p1[1], p1[2]) << 8) |
+                    (luma(p2[0], p2[1], p2[2]) << 16);
+        }
+    }
+    __syncthreads();
+    // ---- middle-row maximum of every block of 32 scan positions
+    for (int k = warp; k < nb0 + nb1; k += kStripWarps) {
+        const int h = k < nb0 ? 0 : 1, b = h ? k - nb0 : k;
+        const int p = 32 * b + lane;
+        int m = 0;
+        if (p < len[h]) m = (int)((yy[h ? W - 1 - p : p] >> 8) & 0xffu);
+        m = __reduce_max_sync(kFull, m);
+        if (lane == 0) bmax[h * kMaxBlocks + b] = m;
+    }
+    __syncthreads();
+    // ---- carry of each block (maximum of the earlier blocks of its half) and
+    // the live blocks (carry below io_cut; the carry never decreases)
+    if (warp < 2) {
+        const int h = warp, nb = h ? nb1 : nb0;
+        int run = 0, live = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            int inc = b < nb ? bmax[h * kMaxBlocks + b] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc = max(inc, t);
+            }
+            int excl = __shfl_up_sync(kFull, inc, 1);
+            if (lane == 0) excl = 0;
+            const int c = max(run, excl);
+            if (b < nb) carry[h * kMaxBlocks + b] = c;
+            live += __popc(__ballot_sync(kFull, b < nb && c < P.io_cut));
+            run = max(run, __shfl_sync(kFull, inc, 31));
+        }
+        if (lane == 0) {
+            s_live[h] = live;
+            // every scanned pixel has at least the key of score 0, (0 << 16) |
+            // rank; the largest is the half's first pixel (ranks fall along
+            // the scan)
+            const int x = h ? W - 1 : 0;
+            s_best[h] = live > 0 ? (uint32_t)(h ? x : (0xFFFF - x)) : 0u;
+        }
+    }
+    __syncthreads();
+
+    // ---- the live blocks of both halves, shared out among the warps
+    const int2 c2 = P.prior_centre ? prior_centre2(P.trk, P.trk_state, f, W, H)
+                                   : make_int2(W - 1, H - 1);
+    const StripCtx ctx{c2.x, c2.y - 2 * y, lt, lg, li};
+    const int L0 = s_live[0], L1 = s_live[1];
+    uint32_t best0 = s_best[0], best1 = s_best[1];   // this warp's best keys
+    int qn = 0;
+    auto flush = [&]() {
+        __syncwarp();   // the pushes are visible
+        for (int e0 = 0; e0 < qn; e0 += 32) {
+            uint32_t k0 = 0u, k1 = 0u;
+            if (e0 + lane < qn) {
+                const uint2 e = queue[e0 + lane];
+                const int x = (int)(e.x >> 16), iota = (int)(e.x & 0xffu), h = (int)((e.x >> 8) & 1u);
+                const int gx = (int)(int16_t)(e.y & 0xffffu), gy = (int)(int16_t)(e.y >> 16);
+                const uint32_t key = (score_from_g(ctx, gx, gy, x, iota, P) << 16) |
+                                     (uint32_t)(h ? x : (0xFFFF - x));
+                if (h) k1 = key; else k0 = key;
+            }
+            best0 = max(best0, __reduce_max_sync(kFull, k0));
+            best1 = max(best1, __reduce_max_sync(kFull, k1));
+        }
+        qn = 0;
+        __syncwarp();   // the entries are read before new pushes
+    };
+    for (int k = warp; k < L0 + L1; k += kStripWarps) {
+        const int h = k < L0 ? 0 : 1, b = h ? k - L0 : k;
+        const int cin = carry[h * kMaxBlocks + b];
+        const uint32_t bh = h ? best1 : best0;
+        // no pixel of this block (its s_iota <= s_iota(cin)) can beat the best
+        if (bh != 0u && (bh >> 16) >= (uint32_t)li[cin]) continue;
+        const int p = 32 * b + lane;
+        const bool act = p < len[h];
+        const int x = h ? (W - 1 - p) : p;
+        const uint32_t w1 = yy[act ? x : (h ? W - len[h] : len[h] - 1)];
+        int inc = act ? (int)((w1 >> 8) & 0xffu) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc = max(inc, t);
+        }
+        int excl = __shfl_up_sync(kFull, inc, 1);
+        if (lane == 0) excl = 0;
+        const int iota = max(cin, excl);
+        bool cand = false;
+        uint2 ent = make_uint2(0u, 0u);
+        if (act && iota < P.io_cut && x != 0 && x != W - 1) {
+            const uint32_t w0 = yy[x - 1], w2 = yy[x + 1];
+            const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
+            const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
+            const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
+            const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
+            const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
+            const int ng = gx * gx + gy * gy;
+            if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P)) {
+                const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
+                const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
+                const uint32_t rank = (uint32_t)(h ? x : (0xFFFF - x));
+                cand = ((bound << 16) | rank) > bh;   // could beat the best so far
+                ent = make_uint2(((uint32_t)x << 16) | ((uint32_t)h << 8) | (uint32_t)iota,
+                                 ((uint32_t)gx & 0xffffu) | ((uint32_t)gy << 16));
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, cand);
+        if (cand) queue[qn + __popc(bal & ((1u << lane) - 1u))] = ent;
+        qn += __popc(bal);
+        if (qn >= 32) flush();
+    }
+    if (qn > 0) flush();
+    if (lane == 0) {
+        atomicMax(s_best, best0);
+        atomicMax(s_best + 1, best1);
+    }
+    __syncthreads();
+    // ---- the best point of each half into its slot
+    if (tid < 2) {
+        const int h = tid;
+        const uint32_t best = s_best[h];
+        CandSlot out;
+        out.kept = 0;
+        out.x = -1;
+        out.y = (int16_t)y;
+        out.s = 0;
+        if (best != 0u) {
+            const int rank = (int)(best & 0xFFFFu);
+            const int px = h ? rank : (0xFFFF - rank);
+            const uint32_t scv = best >> 16;
+            out.x = (int16_t)px;
+            out.s = (uint16_t)scv;
+            out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
+                                  y >= P.T_px && y <= H - 1 - P.T_px);
+        }
+        slots[(int64_t)f * kMaxSlots + i * P.K + h] = out;
     }
 }
 
@@ -539,25 +628,26 @@ __global__ void __launch_bounds__(kStripThreads)
     k_strips(const DevFrame *__restrict__ frames, int B, const int32_t *__restrict__ rows,
              DevParams P, const uint16_t *__restrict__ luts, CandSlot *__restrict__ slots) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_qmax[kStripWarps];
-    __shared__ uint32_t s_qbest[kStripWarps];
     const int warp = threadIdx.x >> 5;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);   // table block from s_iota on
     strip_tables_load(P, luts, tab);
     __syncthreads();
     const StripShared ss{tab, tab + (kDevOffB - kDevOffI), tab + (kDevOffG - kDevOffI),
-                         smem_raw + strip_tables_bytes(P), s_qmax, s_qbest};
+                         smem_raw + strip_tables_bytes(P)};
     const uint16_t *lt = luts + kDevOffT;   // global, through L1
 
-    // K = 2: a quad of 4 warps takes a half-strip; K > 2: one warp takes a
-    // half-strip.  Items are interleaved across frames (consecutive items
-    // belong to consecutive frames), so every CTA and SM gets a mix of cheap
-    // and expensive half-strips.
-    const bool quads = P.K == 2;
-    const int per_cta = quads ? kStripWarps / 4 : kStripWarps;
-    const int gid = quads ? (warp >> 2) : warp;
+    // K = 2: the CTA takes a strip; K > 2: a warp takes a half-strip.  Items
+    // are interleaved across frames (consecutive items belong to consecutive
+    // frames), so every CTA and SM gets a mix of cheap and expensive strips.
+    if (P.K == 2) {
+        for (int it = blockIdx.x; it < B * P.N; it += gridDim.x) {
+            const int i = it / B;
+            strip_pair(frames, rows, P, lt, ss, slots, it - i * B, i);
+        }
+        return;
+    }
     const int items = B * P.N * 2;
-    for (int it = blockIdx.x * per_cta + gid; it < items; it += gridDim.x * per_cta) {
+    for (int it = blockIdx.x * kStripWarps + warp; it < items; it += gridDim.x * kStripWarps) {
         const int j = it / B;
         const int f = it - j * B;
         strip_half(frames, rows, P, lt, ss, slots, f, j >> 1, j & 1);
@@ -1255,6 +1345,13 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
+// Adds 1 to *p at GPU scope with release semantics: everything this thread
+// wrote or observed before it -- the writes of its CTA, ordered by the
+// preceding barrier -- is visible to whoever acquires the new value.
+__device__ __forceinline__ void red_release_add1(uint32_t *p) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
+}
+
 // Thread-level wait until *p >= target; false after `limit_ns` (error flag set).
 __device__ __noinline__ bool wait_at_least(const uint32_t *p, uint32_t target, uint32_t *err,
                                            uint64_t limit_ns) {
@@ -1281,14 +1378,11 @@ __global__ void __launch_bounds__(kStripThreads, 4)
             const uint16_t *__restrict__ luts, Workspace ws, ca_result *out,
             const BatchSeg *__restrict__ segs, int n_segs, int total_items, uint64_t wait_ns) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_qmax[kStripWarps];
-    __shared__ uint32_t s_qbest[kStripWarps];
     __shared__ int s_item;
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem_raw);
     strip_tables_load(P, luts, tab);   // once per CTA; visible after the first barrier
     unsigned char *un = smem_raw + strip_tables_bytes(P);   // strip buffers or FitSmem
-    const StripShared ss{tab, tab + (kDevOffB - kDevOffI), tab + (kDevOffG - kDevOffI), un,
-                         s_qmax, s_qbest};
+    const StripShared ss{tab, tab + (kDevOffB - kDevOffI), tab + (kDevOffG - kDevOffI), un};
     FitSmem &fs = *reinterpret_cast<FitSmem *>(un);
     const uint16_t *lt = luts + kDevOffT;
     uint32_t *sync = ws.sync;
@@ -1314,16 +1408,13 @@ __global__ void __launch_bounds__(kStripThreads, 4)
         if (sg.phase == kPhaseStrips) {
             const int f = sg.f0 + local / spf, si = local % spf;
             if (P.K == 2) {
-                strip_half(frames, rows, P, lt, ss, ws.slots, f, si, warp >> 2);
+                strip_pair(frames, rows, P, lt, ss, ws.slots, f, si);
             } else {
                 const int i = 4 * si + (warp >> 1);
                 if (i < P.N) strip_half(frames, rows, P, lt, ss, ws.slots, f, i, warp & 1);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(sync_strips(sync, nf) + f, 1u);
-            }
+            if (threadIdx.x == 0) red_release_add1(sync_strips(sync, nf) + f);
         } else if (sg.phase == kPhaseFit) {
             const int f = sg.f0 + local / P.n_tiles, tile = local % P.n_tiles;
             if (threadIdx.x == 0) {

@@ -185,7 +185,7 @@ extern "C" ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H,
 
     int nb = 0;
     if (strips_occupancy(&nb, strips_smem_bytes(P)) != cudaSuccess) return CA_ERR_CUDA;
-    const int sgrid = P.K == 2 ? (2 * B * P.N + 1) / 2 : (2 * B * P.N + 7) / 8;
+    const int sgrid = P.K == 2 ? B * P.N : (2 * B * P.N + 7) / 8;
     (void)nb;
     if (launch_strips(d_frames, B, d_rows, P, d_luts, ws.slots, sgrid, s) != cudaSuccess ||
         launch_fit(d_frames, B, P, ws.slots, ws, out_dev, s) != cudaSuccess)
