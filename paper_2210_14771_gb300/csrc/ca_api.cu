@@ -924,8 +924,10 @@ ca_status check_sync_word(ca_handle *h, const Workspace &ws) {
     uint32_t err = 0;
     CA_CUDA(h, cudaMemcpy(&err, ws.sync + 2, sizeof(err), cudaMemcpyDeviceToHost));
     if (err == 0) return CA_OK;
-    // a wait gave up: the counters of that call are inconsistent; re-arm all
+    // a wait gave up: the counters and slot flags of that call are
+    // inconsistent; re-arm all
     CA_CUDA(h, cudaMemset(ws.sync, 0, sizeof(uint32_t) * sync_words(ws.sync_frames)));
+    CA_CUDA(h, cudaMemset(ws.slots, 0, sizeof(CandSlot) * kMaxSlots * (size_t)ws.sync_frames));
     return fail(h, CA_ERR_TIMEOUT, "a wait of the fused kernel gave up (flags 0x%x)", err);
 }
 
@@ -1539,7 +1541,8 @@ ca_status ca_plan_create(ca_handle *h, const ca_frame *frames, int B, const ca_p
                  "plan block")) != CA_OK ||
         (st = cu(cudaMemset(pl->ws.best, 0, sizeof(unsigned long long) * nb), "plan")) != CA_OK ||
         (st = cu(cudaMemset(pl->ws.done, 0, sizeof(uint32_t) * nb), "plan")) != CA_OK ||
-        (st = cu(cudaMemset(pl->ws.sync, 0, sizeof(uint32_t) * sync_words(B)), "plan")) != CA_OK)
+        (st = cu(cudaMemset(pl->ws.sync, 0, sizeof(uint32_t) * sync_words(B)), "plan")) != CA_OK ||
+        (st = cu(cudaMemset(pl->ws.slots, 0, sizeof(CandSlot) * nb * kMaxSlots), "plan")) != CA_OK)
         return bail(st);
     int fgrid = 0;
     if ((st = prepare_kernels(h, P, cfg, &fgrid)) != CA_OK) return bail(st);

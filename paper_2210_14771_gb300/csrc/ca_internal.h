@@ -62,17 +62,17 @@ __host__ __device__ inline int mask_items_of(int H) {
 __host__ __device__ inline int strip_items_of(int N, int K) { return K == 2 ? N : (N + 3) / 4; }
 
 // Synchronisation words of the fused kernel: [0] next item, [1] CTAs that
-// have finished, [2] error flags, [3] unused, then per frame: strip items
-// done, result ready, mask items done.  Every word returns to 0 by the end of
-// a call that completes without error.
+// have finished, [2] error flags, [3] unused, then per frame: result ready,
+// mask items done.  Every word returns to 0 by the end of a call that
+// completes without error.  (A fit item learns that the strips of its frame
+// are done from their candidate slots themselves: kSlotFresh below.)
 constexpr int kSyncGlobal = 4;
 constexpr uint32_t kSyncErrTimeout = 1u;
-__host__ __device__ inline uint32_t *sync_strips(uint32_t *s, int nf) { return s + kSyncGlobal; }
-__host__ __device__ inline uint32_t *sync_ready(uint32_t *s, int nf) { return s + kSyncGlobal + nf; }
+__host__ __device__ inline uint32_t *sync_ready(uint32_t *s, int nf) { return s + kSyncGlobal; }
 __host__ __device__ inline uint32_t *sync_maskdone(uint32_t *s, int nf) {
-    return s + kSyncGlobal + 2 * nf;
+    return s + kSyncGlobal + nf;
 }
-__host__ __device__ inline size_t sync_words(int nf) { return kSyncGlobal + 3 * (size_t)nf; }
+__host__ __device__ inline size_t sync_words(int nf) { return kSyncGlobal + 2 * (size_t)nf; }
 
 // Per-call constants, passed by value (kernel parameter space).
 struct DevParams {
@@ -98,11 +98,39 @@ struct DevParams {
     const ca_result *trk_state;  // tracked call: per-track previous result
 };
 
-// A candidate slot (8 bytes): x, y, Q15 score, kept flag.
+// A candidate slot (8 bytes): x, y, Q15 score, flags.  Flag kSlotKept: the
+// point is a candidate.  Flag kSlotFresh: written by the current call and not
+// yet consumed; the fit tile that completes the frame clears it.  A slot is
+// stored and loaded as one 64-bit word, so a reader that sees kSlotFresh sees
+// the rest of that write too.
 struct CandSlot {
     int16_t x, y;
     uint16_t s, kept;
 };
+constexpr uint16_t kSlotKept = 1u, kSlotFresh = 2u;
+
+__device__ __forceinline__ unsigned long long slot_bits(CandSlot v) {
+    return (unsigned long long)(uint16_t)v.x | ((unsigned long long)(uint16_t)v.y << 16) |
+           ((unsigned long long)v.s << 32) | ((unsigned long long)v.kept << 48);
+}
+__device__ __forceinline__ CandSlot slot_of(unsigned long long b) {
+    CandSlot v;
+    v.x = (int16_t)(b & 0xFFFFu);
+    v.y = (int16_t)((b >> 16) & 0xFFFFu);
+    v.s = (uint16_t)((b >> 32) & 0xFFFFu);
+    v.kept = (uint16_t)(b >> 48);
+    return v;
+}
+// Writes slot *p of the current call (kSlotFresh set) in one store.
+__device__ __forceinline__ void store_slot(CandSlot *p, CandSlot v) {
+    v.kept = (uint16_t)(v.kept | kSlotFresh);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(slot_bits(v)) : "memory");
+}
+__device__ __forceinline__ unsigned long long load_slot_bits(const CandSlot *p) {
+    unsigned long long b;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+    return b;
+}
 
 // Best circle of one fit CTA.
 struct TileRec {
@@ -245,7 +273,7 @@ cudaError_t launch_smooth(const ca_result *res, int B, const int32_t *w_trk, flo
 
 cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, const DevParams &P,
                           const uint16_t *luts, CandSlot *slots, int grid, cudaStream_t s);
-cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const CandSlot *slots,
+cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, CandSlot *slots,
                        const Workspace &ws, ca_result *out, cudaStream_t s);
 cudaError_t launch_mask(const DevFrame *frames, int B, const ca_result *res, int total_units,
                         int grid, cudaStream_t s);

@@ -425,7 +425,7 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
         }
         if (lane == 0) {
             s_pick[r] = px;
-            slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
+            store_slot(slots + (int64_t)f * kMaxSlots + i * P.K + half * kk + r, out);
         }
         __syncwarp();   // this round's pick visible to the whole warp
     }
@@ -618,7 +618,7 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
             out.kept = (uint16_t)(scv >= P.T_ps && px >= P.T_px && px <= W - 1 - P.T_px &&
                                   y >= P.T_px && y <= H - 1 - P.T_px);
         }
-        slots[(int64_t)f * kMaxSlots + i * P.K + h] = out;
+        store_slot(slots + (int64_t)f * kMaxSlots + i * P.K + h, out);
     }
 }
 
@@ -899,18 +899,43 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
 }
 
+__device__ __forceinline__ uint64_t clock_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until slot *p carries kSlotFresh and returns it; after limit_ns sets
+// kSyncErrTimeout in *err and returns an empty slot.
+__device__ __noinline__ unsigned long long wait_slot(const CandSlot *p, uint32_t *err,
+                                                     uint64_t limit_ns) {
+    const uint64_t t0 = clock_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        const unsigned long long b = load_slot_bits(p);
+        if ((b >> 48) & kSlotFresh) return b;
+        __nanosleep(128);
+        if ((it & 15u) == 15u && clock_ns() - t0 > limit_ns) break;
+    }
+    atomicOr(err, kSyncErrTimeout);
+    return 0ull;
+}
+
 }  // namespace
 
 // Tile `tile` of the hypotheses of frame f.  T threads share one hypothesis
 // (points split among them, moments combined by shuffles); a CTA holds
-// 256 / T hypotheses.  The last tile of the frame to finish writes the
-// frame's result; with `sync` (fused kernel) it also re-arms the frame's
-// strip counter and publishes the result to the frame's mask items.
+// 256 / T hypotheses.  With `sync` (fused kernel) the strips of the frame may
+// still be running: each thread waits for its slot to be written (kSlotFresh),
+// bounded by limit_ns (error flag set, slot taken as empty).  The last tile of
+// the frame to finish clears the slots' kSlotFresh and writes the frame's
+// result; with `sync` it also publishes the result to the frame's mask items.
+// t_ready (fused kernel traces, thread 0): when every slot had been read.
 template <int T>
 __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict__ frames,
-                                         const DevParams &P, const CandSlot *slots,
+                                         const DevParams &P, CandSlot *slots,
                                          const Workspace &ws, ca_result *out, int f, int tile,
-                                         uint32_t *sync) {
+                                         uint32_t *sync, uint64_t limit_ns = 0,
+                                         uint64_t *t_ready = nullptr) {
     constexpr int HPT = kHypTile / T;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = tid & (T - 1);
@@ -922,14 +947,17 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
     CandSlot c;
     c.x = c.y = 0;
     c.s = c.kept = 0;
-    if (tid < NK) {   // L2 load: in the fused kernel other CTAs wrote the slots
-        const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(slots + (int64_t)f * kMaxSlots + tid));
-        c = *reinterpret_cast<const CandSlot *>(&v);
+    if (tid < NK) {   // L2 load: in the fused kernel other CTAs write the slots
+        const CandSlot *sp = slots + (int64_t)f * kMaxSlots + tid;
+        unsigned long long b = load_slot_bits(sp);
+        if (sync && !((b >> 48) & kSlotFresh)) b = wait_slot(sp, sync + 2, limit_ns);
+        c = slot_of(b);
     }
-    const bool kept = tid < NK && c.kept;
+    const bool kept = tid < NK && (c.kept & kSlotKept);
     const unsigned bal = __ballot_sync(kFull, kept);
     if (lane == 0) sm.wcount[warp] = __popc(bal);
     __syncthreads();
+    if (t_ready && tid == 0) *t_ready = clock_ns();
     int off = 0, M = 0;
     for (int w = 0; w < kHypTile / 32; ++w) {
         off += (w < warp) ? sm.wcount[w] : 0;
@@ -1073,6 +1101,11 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
         sm.last = prev == (unsigned)(P.n_tiles - 1);
     }
     __syncthreads();
+    if (sm.last && tid < NK) {   // every tile of this frame has read the slots
+        CandSlot *sp = slots + (int64_t)f * kMaxSlots + tid;
+        const unsigned long long b = load_slot_bits(sp);
+        *reinterpret_cast<unsigned long long *>(sp) = b & ~((unsigned long long)kSlotFresh << 48);
+    }
     if (sm.last && tid == 0) {   // last CTA of this frame writes the result
         __threadfence();
         const unsigned long long k = atomicAdd(&ws.best[f], 0ull);
@@ -1109,9 +1142,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
         ws.best[f] = 0ull;   // ready for the next call
         ws.done[f] = 0u;
         if (sync) {
-            // every tile of this frame has passed its wait on the strip
-            // counter: re-arm it, then publish the result to the mask items
-            sync_strips(sync, ws.sync_frames)[f] = 0u;
+            // publish the result to the mask items
             if (fr.mask && P.debug < 3) {   // debug level 3 withholds it (tests the bounded waits)
                 __threadfence();
                 atomicExch(sync_ready(sync, ws.sync_frames) + f, 1u);
@@ -1124,7 +1155,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
 template <int T>
 __global__ void __launch_bounds__(kHypTile, 4)
     k_fit(const DevFrame *__restrict__ frames, int B, DevParams P,
-          const CandSlot *__restrict__ slots, Workspace ws, ca_result *__restrict__ out) {
+          CandSlot *__restrict__ slots, Workspace ws, ca_result *__restrict__ out) {
     __shared__ FitSmem sm;
     fit_tile<T>(sm, frames, P, slots, ws, out, blockIdx.x, blockIdx.y, nullptr);
 }
@@ -1153,7 +1184,7 @@ int choose_hyp_threads(int requested, long long B, long long NH, int sms) {
     return T;
 }
 
-cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, const CandSlot *slots,
+cudaError_t launch_fit(const DevFrame *frames, int B, const DevParams &P, CandSlot *slots,
                        const Workspace &ws, ca_result *out, cudaStream_t s) {
     dim3 grid((unsigned)B, (unsigned)P.n_tiles);
     switch (P.hyp_threads) {
@@ -1230,40 +1261,59 @@ __device__ __forceinline__ uint32_t exact_word(int x0, float cx, float dy2, floa
     return w;
 }
 
-// Unit u (rows 8u .. 8u+7) of the mask of one frame, by one warp: lane r
-// computes the span of row r, then the warp stores each row with consecutive
-// 16-byte vectors per lane.
+// Unit u (rows 8u .. 8u+7) of the mask of one frame, by one warp: lanes r
+// and 8 + r compute the span of row r and the 16-byte vectors holding its
+// left and right ends; then the warp stores each row with consecutive 16-byte
+// vectors per lane, whole vectors from two comparisons, end vectors from the
+// lanes that built them.
 __device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &res, int u) {
     const int lane = threadIdx.x & 31;
     const int W = fr.W, H = fr.H;
     const int y0 = u * kMaskRowsPerUnit;
     const int nrows = min(kMaskRowsPerUnit, H - y0);
-    const RowSpan sp = row_span(res, W, y0 + min(lane, nrows - 1));
+    const RowSpan sp = row_span(res, W, y0 + min(lane & 7, nrows - 1));
     const float rr = __fmul_rn(res.r, res.r);
+    uint4 ev = make_uint4(0u, 0u, 0u, 0u);   // end vector: left (lanes 0-7) or right (8-15)
+    if (fr.mask_vec_ok && sp.exact && sp.a <= sp.b) {
+        const int x0 = ((lane & 8) ? sp.b : sp.a) & ~15;
+        ev = make_uint4(span_word(x0, sp.a, sp.b), span_word(x0 + 4, sp.a, sp.b),
+                        span_word(x0 + 8, sp.a, sp.b), span_word(x0 + 12, sp.a, sp.b));
+    }
     for (int r = 0; r < nrows; ++r) {
         const int a = __shfl_sync(kFull, sp.a, r);
         const int b = __shfl_sync(kFull, sp.b, r);
         const int ex = __shfl_sync(kFull, sp.exact, r);
         const int y = y0 + r;
         uint8_t *row = fr.mask + (int64_t)y * W;
-        const float dy = __fsub_rn(__int2float_rn(y), res.cy);
-        const float dy2 = __fmul_rn(dy, dy);
         if (fr.mask_vec_ok && ex) {
+            uint4 la, ra;   // the row's end vectors
+            la.x = __shfl_sync(kFull, ev.x, r);
+            la.y = __shfl_sync(kFull, ev.y, r);
+            la.z = __shfl_sync(kFull, ev.z, r);
+            la.w = __shfl_sync(kFull, ev.w, r);
+            ra.x = __shfl_sync(kFull, ev.x, r + 8);
+            ra.y = __shfl_sync(kFull, ev.y, r + 8);
+            ra.z = __shfl_sync(kFull, ev.z, r + 8);
+            ra.w = __shfl_sync(kFull, ev.w, r + 8);
             // vectors wholly inside [a, b] are ones, wholly outside zeros; the
-            // (at most two) that hold an end are built byte by byte
+            // (at most two) that hold an end come from the end vectors (both
+            // built from the whole span, so equal when the ends share one)
             const int VW = W >> 4;
             const int fa = (a + 15) >> 4, fb = ((b + 1) >> 4) - 1;   // whole vectors inside
             const int ea = a >> 4, eb = b >> 4;                      // vectors holding an end
             for (int v = lane; v < VW; v += 32) {
-                const int x0 = v << 4;
-                const uint32_t w = (v >= fa && v <= fb) ? 0x01010101u : 0u;
+                const bool whole = v >= fa && v <= fb;
+                const uint32_t w = whole ? 0x01010101u : 0u;
                 uint4 val = make_uint4(w, w, w, w);
-                if ((v == ea || v == eb) && a <= b && !(v >= fa && v <= fb))
-                    val = make_uint4(span_word(x0, a, b), span_word(x0 + 4, a, b),
-                                     span_word(x0 + 8, a, b), span_word(x0 + 12, a, b));
-                st_cs_v4(row + x0, val);
+                if (!whole && a <= b) {
+                    if (v == ea) val = la;
+                    else if (v == eb) val = ra;
+                }
+                st_cs_v4(row + (v << 4), val);
             }
         } else if (fr.mask_vec_ok) {
+            const float dy = __fsub_rn(__int2float_rn(y), res.cy);
+            const float dy2 = __fmul_rn(dy, dy);
             const int VW = W >> 4;
             for (int v = lane; v < VW; v += 32) {
                 const int x0 = v << 4;
@@ -1273,6 +1323,8 @@ __device__ __forceinline__ void mask_unit(const DevFrame &fr, const ca_result &r
                                               exact_word(x0 + 12, res.cx, dy2, rr)));
             }
         } else {
+            const float dy = __fsub_rn(__int2float_rn(y), res.cy);
+            const float dy2 = __fmul_rn(dy, dy);
             for (int x = lane; x < W; x += 32) {
                 uint8_t v;
                 if (!res.valid) v = 1;
@@ -1345,13 +1397,6 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-// Adds 1 to *p at GPU scope with release semantics: everything this thread
-// wrote or observed before it -- the writes of its CTA, ordered by the
-// preceding barrier -- is visible to whoever acquires the new value.
-__device__ __forceinline__ void red_release_add1(uint32_t *p) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
-}
-
 // Thread-level wait until *p >= target; false after `limit_ns` (error flag set).
 __device__ __noinline__ bool wait_at_least(const uint32_t *p, uint32_t target, uint32_t *err,
                                            uint64_t limit_ns) {
@@ -1413,17 +1458,11 @@ __global__ void __launch_bounds__(kStripThreads, 4)
                 const int i = 4 * si + (warp >> 1);
                 if (i < P.N) strip_half(frames, rows, P, lt, ss, ws.slots, f, i, warp & 1);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) red_release_add1(sync_strips(sync, nf) + f);
+            // the slots it wrote tell the fit items of f that it is done
         } else if (sg.phase == kPhaseFit) {
             const int f = sg.f0 + local / P.n_tiles, tile = local % P.n_tiles;
-            if (threadIdx.x == 0) {
-                wait_at_least(sync_strips(sync, nf) + f, (uint32_t)spf, sync + 2, wait_ns);
-                __threadfence();
-                if (ws.trace) t_ready = globaltimer_ns();
-            }
-            __syncthreads();
-            fit_tile<T>(fs, frames, P, ws.slots, ws, out, f, tile, sync);
+            fit_tile<T>(fs, frames, P, ws.slots, ws, out, f, tile, sync, wait_ns,
+                        ws.trace ? &t_ready : nullptr);
         } else {
             const int g = frames[sg.f0].mitem_off + local;
             int a = sg.f0, b = sg.f1 - 1;   // frame of mask item g

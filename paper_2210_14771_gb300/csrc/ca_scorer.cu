@@ -802,7 +802,7 @@ __global__ void __launch_bounds__(256)
                 out.s = (uint16_t)scv;
                 out.kept = (uint16_t)(b != 0u && scv >= P.T_ps && px >= P.T_px &&
                                       px <= W - 1 - P.T_px && y >= P.T_px && y <= H - 1 - P.T_px);
-                slots[(int64_t)f * kMaxSlots + i * P.K + half * kk + r] = out;
+                store_slot(slots + (int64_t)f * kMaxSlots + i * P.K + half * kk + r, out);
             }
         }
     }
