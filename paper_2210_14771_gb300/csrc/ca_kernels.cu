@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "ca_internal.h"
+#include "ca_fconv.h"
 
 namespace ca {
 
@@ -150,6 +151,15 @@ __device__ __forceinline__ uint4 interleave4(uint32_t a, uint32_t b, uint32_t c)
                       __byte_perm(t23, c, 0x0610), __byte_perm(t23, c, 0x0732));
 }
 
+// Float near a 64-bit integer of magnitude below 2^63 (relative error below
+// 2^-22), from two 32-bit conversions.
+__device__ __forceinline__ float approx_f32(long long v) {
+    const uint64_t u = (uint64_t)(v < 0 ? -v : v);
+    const float f = __fadd_rn(__fmul_rn(__uint2float_rn((uint32_t)(u >> 32)), 4294967296.0f),
+                              __uint2float_rn((uint32_t)u));
+    return v < 0 ? -f : f;
+}
+
 // Angle bin floor(4096 (u + 1)), u = dot |dot| / (ng nc) the signed squared
 // cosine between g and c, as an exact integer quotient: a float estimate is
 // corrected by one exact comparison (the estimate is within one bin).
@@ -157,7 +167,7 @@ __device__ __forceinline__ int qtheta(int dot, int ng, int nc) {
     const long long P = (long long)ng * nc;
     const long long d2 = (long long)dot * (dot < 0 ? -dot : dot);
     const long long num = (d2 + P) << 12;
-    const float uf = __fdividef(__ll2float_rn(d2), __ll2float_rn(P));
+    const float uf = __fdividef(approx_f32(d2), approx_f32(P));
     int q = __float2int_rz(__fmul_rn(__fadd_rn(uf, 1.0f), 4096.0f));
     q = min(max(q, 0), kLutT - 1);
     const long long t = (long long)q * P;
@@ -687,23 +697,12 @@ cudaError_t launch_strips(const DevFrame *frames, int B, const int32_t *rows, co
 // ================================================================= k_fit ==
 namespace {
 
-// Correctly rounded binary32 value of a 128-bit integer.
+// Correctly rounded binary32 value of a 128-bit integer (integer arithmetic:
+// ca_fconv.h).
 __device__ __forceinline__ float i128_to_f32(__int128 v) {
     const bool neg = v < 0;
     const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
-    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
-    float f;
-    if (hi == 0) {
-        f = __ull2float_rn(lo);
-    } else {
-        const int lz = __clzll((long long)hi);
-        const int sh = 64 - lz;   // bits dropped to fit 64
-        uint64_t top, rest;
-        if (lz == 0) { top = hi; rest = lo; }
-        else { top = (hi << lz) | (lo >> sh); rest = lo << lz; }
-        top |= (rest != 0) ? 1ull : 0ull;   // sticky bit, far below the rounding point
-        f = __fmul_rn(__ull2float_rn(top), __int_as_float((127 + sh) << 23));
-    }
+    const float f = u128_to_f32((uint64_t)(u >> 64), (uint64_t)u);
     return neg ? -f : f;
 }
 
@@ -727,9 +726,9 @@ __device__ __forceinline__ bool circumcircle(int ax, int ay, int bx, int by, int
         o.cx = __double2float_rn(__ddiv_rn(__ll2double_rn(Ux), __ll2double_rn(D)));
         o.cy = __double2float_rn(__ddiv_rn(__ll2double_rn(Uy), __ll2double_rn(D)));
     } else {
-        const float fD = __ll2float_rn(D);
-        o.cx = __fdiv_rn(__ll2float_rn(Ux), fD);
-        o.cy = __fdiv_rn(__ll2float_rn(Uy), fD);
+        const float fD = i64_to_f32(D);
+        o.cx = __fdiv_rn(i64_to_f32(Ux), fD);
+        o.cy = __fdiv_rn(i64_to_f32(Uy), fD);
     }
     const float dx = __fsub_rn(__int2float_rn(ax), o.cx);
     const float dy = __fsub_rn(__int2float_rn(ay), o.cy);
@@ -794,7 +793,7 @@ __device__ __forceinline__ bool ls_fit(const Moments &m, Circle &o) {
     o.cy = __fdiv_rn(i128_to_f32(cyn), fden);
     const float af = __fdiv_rn(i128_to_f32(an), fden);
     const float bf = __fdiv_rn(i128_to_f32(bn), fden);
-    const float t1 = __fdiv_rn(__ll2float_rn(A + C), __ll2float_rn(n * n));
+    const float t1 = __fdiv_rn(i64_to_f32(A + C), i64_to_f32(n * n));
     const float r2 = __fadd_rn(__fadd_rn(t1, __fmul_rn(af, af)), __fmul_rn(bf, bf));
     o.r = __fsqrt_rn(r2);
     return true;
@@ -810,6 +809,9 @@ struct __align__(16) Pt {
 
 struct FitSmem {
     Pt pt[kMaxSlots];
+    Moments lsq[kHypTile];   // a refinement round's fit queue: moments in,
+    Circle lsc[kHypTile];    // circles out (r < 0: no fit)
+    int nls[2];              // queue lengths of alternate rounds
     int wcount[kHypTile / 32];
     unsigned long long wbest[kHypTile / 32];
     int last;
@@ -956,6 +958,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
     const bool kept = tid < NK && (c.kept & kSlotKept);
     const unsigned bal = __ballot_sync(kFull, kept);
     if (lane == 0) sm.wcount[warp] = __popc(bal);
+    if (tid == 0) sm.nls[0] = 0;
     __syncthreads();
     if (t_ready && tid == 0) *t_ready = clock_ns();
     int off = 0, M = 0;
@@ -999,6 +1002,7 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
     int n_fin = 0;
     uint32_t S_fin = 0u;
     int t0 = 0, t1 = 0, t2 = 0, pass = 0;
+    bool active = false;   // the group refines a circle
     if (h < NH_all) {   // uniform across the T threads of a group
         bool have_circle;
         if (h == NH) {
@@ -1030,48 +1034,74 @@ __device__ __forceinline__ void fit_tile(FitSmem &sm, const DevFrame *__restrict
         have_circle = circumcircle(sm.pt[s0].X, sm.pt[s0].Y, sm.pt[s1].X, sm.pt[s1].Y,
                                    sm.pt[s2].X, sm.pt[s2].Y, c0);
         }
-        if (have_circle) {
-            uint32_t bits[8 / T];
+        active = have_circle;
+        if (!have_circle) c0 = Circle{0.f, 0.f, 0.f};
+    }
+
+    // ---- refinement, in step across the CTA: each group's inlier pass, then
+    // the least-squares fits the groups need, each computed once (by one of
+    // the CTA's first threads, from the group's moments in shared memory)
+    // rather than by all T threads of its group
+    uint32_t bits[8 / T];
 #pragma unroll
-            for (int w = 0; w < 8 / T; ++w) bits[w] = 0u;
-            Moments m;
-            bool final_known = false;
-            const unsigned gm = group_mask<T>();
-            for (int it = 0; it < P.refine; ++it) {
-                int changed = inlier_pass<T>(sm, M, sub, c0, P.t_ri, true, bits, m) ? 1 : 0;
-                group_sum<T>(m, gm);
+    for (int w = 0; w < 8 / T; ++w) bits[w] = 0u;
+    Moments m = Moments{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0u};
+    bool final_known = !active;   // the group's inlier set is final
+    const unsigned gm = group_mask<T>();
+    for (int it = 0; it < P.refine; ++it) {
+        int q = -1;   // the group's entry in this round's fit queue
+        if (!final_known) {   // uniform across the T threads of a group
+            int changed = inlier_pass<T>(sm, M, sub, c0, P.t_ri, true, bits, m) ? 1 : 0;
+            group_sum<T>(m, gm);
 #pragma unroll
-                for (int o = 1; o < T; o <<= 1) changed |= __shfl_xor_sync(gm, changed, o);
-                if (it > 0 && !changed) { final_known = true; break; }   // fit would repeat
-                Circle nc;
-                if (!ls_fit(m, nc)) { final_known = true; break; }       // circle unchanged
-                c0 = nc;
+            for (int o = 1; o < T; o <<= 1) changed |= __shfl_xor_sync(gm, changed, o);
+            if (it > 0 && !changed) {
+                final_known = true;   // the fit would repeat
+            } else {
+                if (sub == 0) {
+                    q = atomicAdd(&sm.nls[it & 1], 1);
+                    sm.lsq[q] = m;
+                }
+                q = __shfl_sync(gm, q, lane & ~(T - 1));
             }
-            if (!final_known) {
-                inlier_pass<T>(sm, M, sub, c0, P.t_ri, false, bits, m);
-                group_sum<T>(m, gm);
-            }
-            n_fin = m.n;
-            S_fin = m.S;
-            const float Wf = __int2float_rn(fr.W);
-            const float rlo = __fmul_rn(P.r_min, Wf), rhi = __fmul_rn(P.r_max, Wf);
-            const float dm = __fmul_rn(P.d_max, Wf);
-            const float ex = (fr.W & 1) ? 0.0f : -0.5f, ey = (fr.H & 1) ? 0.0f : -0.5f;
-            const float dx = __fsub_rn(c0.cx, ex), dy = __fsub_rn(c0.cy, ey);
-            pass = c0.r >= rlo && c0.r <= rhi &&
-                   __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= __fmul_rn(dm, dm);
-            if (pass && sub == 0)
-                key = ((unsigned long long)(S_fin + 1u) << 32) | (0xFFFFFFFFu - (uint32_t)h);
-        } else {
-            c0 = Circle{0.f, 0.f, 0.f};
         }
-        if (P.debug >= 2 && sub == 0) {
-            HypRec rec;
-            rec.i0 = t0; rec.i1 = t1; rec.i2 = t2;
-            rec.n_inl = n_fin; rec.S = S_fin; rec.pass = pass;
-            rec.cx = c0.cx; rec.cy = c0.cy; rec.r = c0.r;
-            ws.hyps[(int64_t)f * (P.NH + P.track) + h] = rec;
+        if (!__syncthreads_or(q >= 0)) break;   // every set is final
+        if (tid == 0) sm.nls[(it + 1) & 1] = 0;   // the next round's queue
+        if (tid < sm.nls[it & 1]) {
+            Circle nc;
+            if (!ls_fit(sm.lsq[tid], nc)) nc.r = -1.0f;   // no fit: circle unchanged
+            sm.lsc[tid] = nc;
         }
+        __syncthreads();
+        if (q >= 0) {
+            const Circle nc = sm.lsc[q];
+            if (nc.r < 0.0f) final_known = true;
+            else c0 = nc;
+        }
+    }
+    if (active) {
+        if (!final_known) {
+            inlier_pass<T>(sm, M, sub, c0, P.t_ri, false, bits, m);
+            group_sum<T>(m, gm);
+        }
+        n_fin = m.n;
+        S_fin = m.S;
+        const float Wf = __int2float_rn(fr.W);
+        const float rlo = __fmul_rn(P.r_min, Wf), rhi = __fmul_rn(P.r_max, Wf);
+        const float dm = __fmul_rn(P.d_max, Wf);
+        const float ex = (fr.W & 1) ? 0.0f : -0.5f, ey = (fr.H & 1) ? 0.0f : -0.5f;
+        const float dx = __fsub_rn(c0.cx, ex), dy = __fsub_rn(c0.cy, ey);
+        pass = c0.r >= rlo && c0.r <= rhi &&
+               __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= __fmul_rn(dm, dm);
+        if (pass && sub == 0)
+            key = ((unsigned long long)(S_fin + 1u) << 32) | (0xFFFFFFFFu - (uint32_t)h);
+    }
+    if (h < NH_all && P.debug >= 2 && sub == 0) {
+        HypRec rec;
+        rec.i0 = t0; rec.i1 = t1; rec.i2 = t2;
+        rec.n_inl = n_fin; rec.S = S_fin; rec.pass = pass;
+        rec.cx = c0.cx; rec.cy = c0.cy; rec.r = c0.r;
+        ws.hyps[(int64_t)f * (P.NH + P.track) + h] = rec;
     }
 
     // ---- best of the CTA: highest score, lowest hypothesis index
