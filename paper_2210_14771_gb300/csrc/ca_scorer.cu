@@ -35,7 +35,7 @@ namespace ca {
 
 namespace {
 
-constexpr int kCin = kScCin, kCh = kScCh, kTaps = kScTaps;
+constexpr int kCh = kScCh, kTaps = kScTaps;
 constexpr int kTile = 128;
 constexpr int kGuard = 8;
 
@@ -120,10 +120,10 @@ __device__ __forceinline__ void build_features(unsigned char *x0, const uint8_t 
             const uint8_t *p[3] = {row0 + o, row1 + o, row2 + o};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const uint32_t R = p[k][0], G = p[k][1], B = p[k][2];
-                f[4 * k + 0] = luma_f(R, G, B);
+                const uint32_t R = p[k][0], Gr = p[k][1], B = p[k][2];
+                f[4 * k + 0] = luma_f(R, Gr, B);
                 f[4 * k + 1] = (float)((int)R - 128) * (1.0f / 128.0f);
-                f[4 * k + 2] = (float)((int)G - 128) * (1.0f / 128.0f);
+                f[4 * k + 2] = (float)((int)Gr - 128) * (1.0f / 128.0f);
                 f[4 * k + 3] = (float)((int)B - 128) * (1.0f / 128.0f);
             }
             f[12] = __fdiv_rn(__fsub_rn((float)x, xc), Wf);

@@ -45,7 +45,9 @@ __device__ __forceinline__ void tc_after_sync() {
 }
 
 // Bounded wait for the completion of phase `parity` of an mbarrier; false
-// (error flag set) if it does not complete within ~2 s.
+// (error flag set) if it does not complete within ~2 s.  Each try suspends
+// the thread until the phase completes or 0.1 ms pass, so waiting warps do
+// not take issue slots from the warps that have work.
 __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, uint32_t *err) {
     const uint32_t a = smem_u32(bar);
     uint64_t t0;
@@ -53,17 +55,15 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, uint32_
     for (uint32_t it = 0; it < (1u << 26); ++it) {
         uint32_t done;
         asm volatile(
-            "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             "selp.u32 %0, 1, 0, p;}"
             : "=r"(done)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(100000u)
             : "memory");
         if (done) return true;
-        if ((it & 255u) == 255u) {
-            uint64_t t;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-            if (t - t0 > 2000000000ull) break;
-        }
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) break;
     }
     if (err) atomicOr(err, kScErrTimeout);
     return false;

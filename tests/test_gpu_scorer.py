@@ -10,8 +10,9 @@ a logit depends on ~900 activations of the three layers, so a few flips of
 ~1e-3 each could reach it.  Measured: at most 6.1e-4 over the strips below;
 LOGIT_TOL is ten times that.  The gradient passes through three more bf16
 roundings (one per layer); each parameter block is compared to GRAD_REL of
-its largest entry (about ten times the worst block measured, printed by the
-test), with a cosine similarity of the whole gradient of at least 0.999.  The picks and the circle fit, given the
+its largest entry: measured at most 3.8e-5 of the block maximum (W1; the
+others below 2.4e-5, printed by the test), GRAD_REL about ten times that,
+with a cosine similarity of the whole gradient of at least 0.999.  The picks and the circle fit, given the
 same learned scores, are exact (integer and binary32 decisions taken the
 same way on both sides) and compared bit for bit.
 """
@@ -30,7 +31,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 LOGIT_TOL = 6e-3
-GRAD_REL = 0.05
+GRAD_REL = 4e-4
 
 
 @pytest.fixture(scope="module")
