@@ -2,10 +2,14 @@
 fused call was taken, released by its dependencies and finished.
 
     python -m paper_2210_14771_gb300.timeline [--T 1 2 4 8] [--waves 16 32 64]
+    python -m paper_2210_14771_gb300.timeline --staged [--T 2]
 
 runs the 64-frame 1080p batch (N=32, K=2, 1024 hypotheses) once per launch
 shape and prints, per phase, when its items ran and how long they waited
 and worked; the CUDA-event time of the same call is printed beside it.
+With --staged it times the staged launch (k_strips, k_fit, k_mask) per
+hypothesis split instead, with no trace: three warm-up calls, then ten
+timed ones (a fixed launch sequence for profilers).
 """
 from __future__ import annotations
 
@@ -60,6 +64,7 @@ def main():
     ap.add_argument("--T", type=int, nargs="+", default=[1, 2, 4, 8])
     ap.add_argument("--waves", type=int, nargs="+", default=[16, 32, 64])
     ap.add_argument("--bins", action="store_true", help="print items in progress per 5 us")
+    ap.add_argument("--staged", action="store_true", help="time the staged launch instead")
     a = ap.parse_args()
     from . import synth
     frames, _, keys = synth.batch(1, 64, 1080, 1920, "mixed")
@@ -73,6 +78,21 @@ def main():
     masks = torch.empty((64, 1080, 1920), dtype=torch.uint8, device=dev)
     res = api.new_results(64, dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.staged:
+        for T in a.T:
+            p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, batch_mode=1,
+                           hyp_threads=T)
+            for _ in range(3):
+                ca.estimate(fr, p, keys=keys, masks=masks, results=res)
+            e0.record()
+            for _ in range(10):
+                ca.estimate(fr, p, keys=keys, masks=masks, results=res)
+            e1.record()
+            torch.cuda.synchronize()
+            print("staged T=%d  %.1f us per call (events)" % (T, e0.elapsed_time(e1) / 10 * 1e3),
+                  flush=True)
+        ca.close()
+        return
     for T in a.T:
         for wave in a.waves:
             p = api.params(n_strips=32, cands_per_strip=2, n_hyps=1024, batch_mode=2,
