@@ -342,11 +342,14 @@ __global__ void __launch_bounds__(kInfThreads, 3)
     unsigned char *stage = A + kGuard * 16;
     bool staged = false;   // this segment's bytes are in `stage`
 
+    // where the current and the next segment of this CTA read and write: the
+    // next one's (a search over the frames) is looked up while the current
+    // segment's first convolution runs
+    SegInfo si, sn;
+    if ((int)blockIdx.x < total_segs) si = seg_info<SegI>(src, blockIdx.x);
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
-        const SegInfo si = seg_info<SegI>(src, g);
         const int b0 = si.s0 - kScHalo;
-        if (tid == 0 && g + (int)gridDim.x < total_segs)   // this CTA's next segment
-            prefetch_rows<SegI>(seg_info<SegI>(src, g + gridDim.x));
+        const bool has_next = g + (int)gridDim.x < total_segs;
         __syncthreads();   // the previous segment is done with A and X0
         if (staged) {
             stage_wait();
@@ -369,12 +372,15 @@ __global__ void __launch_bounds__(kInfThreads, 3)
                 else issue_conv<SegI, 4>(tmem, A, Wf + woff);
                 mma_commit(bar_m);
             }
+            if (l == 0 && has_next) {   // this CTA's next segment
+                sn = seg_info<SegI>(src, g + gridDim.x);
+                if (tid == 0) prefetch_rows<SegI>(sn);
+            }
             const bool ok = bar_wait(bar_m, phase, err);
             phase ^= 1u;
             tc_after_sync();
             if (__syncthreads_or(!ok)) { abort = true; break; }
-            if (l == 2 && g + (int)gridDim.x < total_segs) {   // the MMAs are done with A
-                const SegInfo sn = seg_info<SegI>(src, g + gridDim.x);
+            if (l == 2 && has_next) {   // the MMAs are done with A
                 if (stageable(sn)) {
                     stage_rows<SegI>(stage, sn);
                     staged = true;
@@ -424,6 +430,7 @@ __global__ void __launch_bounds__(kInfThreads, 3)
             __syncthreads();
             tc_after_sync();
         }
+        si = sn;
     }
     stage_wait();   // no copy outlives the CTA
     __syncthreads();

@@ -108,6 +108,24 @@ __device__ __forceinline__ const uint8_t *seg2_row(const Seg2 &si, int k, int *f
     return si.base + (int64_t)r * si.pitch;
 }
 
+// L2 prefetch (TMA) of the bytes a segment reads from its 7 rows, shrunk
+// to whole 16-byte blocks inside each row (a hint: the loads read the same
+// bytes).
+__device__ __forceinline__ void prefetch7(const Seg2 &si) {
+    const int b0 = si.s0 - kSc2Halo;
+    const int c0 = max(b0, 0), c1 = min(b0 + kCols, si.W);
+    if (c1 <= c0) return;
+    for (int k = 0; k < 7; ++k) {
+        int fr_row;
+        const uint8_t *row = seg2_row(si, k, &fr_row);
+        const uintptr_t a = ((uintptr_t)(row + 3 * c0) + 15) & ~(uintptr_t)15;
+        const uintptr_t b = (uintptr_t)(row + 3 * c1) & ~(uintptr_t)15;
+        if (b > a)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                         : "memory");
+    }
+}
+
 // RGBXY features of the 7 x 384 pixels of a segment (columns b0 ...) into 7
 // planes: channels R, G, B as (v - 128) / 128, X = (x - (W-1)/2) / W and
 // Y = (row - (H-1)/2) / H in binary32, all rounded to bf16; zero outside the
@@ -297,12 +315,21 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         __syncthreads();
         tc_after_sync();
     };
-    auto run = [&](int layer) {   // issue one layer, wait for it
+    // where the current and the next segment of this CTA read and write: the
+    // next one's (a search over the frames) is looked up, and its rows are
+    // prefetched into L2, while the current segment's first layer runs
+    Seg2 si, sn;
+    bool has_next = false;
+    auto run = [&](int layer, int g) {   // issue one layer, wait for it
         if (tid == 0) {
             if (layer == 0) issue_conv8(tmem, X, Wf + kSc2OffW1, 5, 80);
             else if (layer == 1) issue_conv8(tmem, A1, Wf + kSc2OffW2, 3, 48);
             else issue_conv16(tmem, A2, Wf + kSc2OffW3);
             mma_commit(bar_m);
+        }
+        if (layer == 0 && has_next) {
+            sn = seg2_info(src, g + gridDim.x);
+            if (tid == 0) prefetch7(sn);
         }
         const bool ok = bar_wait(bar_m, phase, err);
         phase ^= 1u;
@@ -311,14 +338,15 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         return !abort;
     };
 
+    if ((int)blockIdx.x < total_segs) si = seg2_info(src, blockIdx.x);
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
-        const Seg2 si = seg2_info(src, g);
         const int b0 = si.s0 - kSc2Halo;
+        has_next = g + (int)gridDim.x < total_segs;
         __syncthreads();   // the previous segment is done with X / A1 / A2
         build_x(X, si, b0);
         sync_point();
         // ---- layer 1: 5 rows of 8 channels
-        if (!run(0)) break;
+        if (!run(0, g)) break;
         for (int it = half; it < kSc2Tiles * 5; it += 2) {
             const int j = it / 5, r = it - 5 * j;
             float v[8];
@@ -329,7 +357,7 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         }
         sync_point();
         // ---- layer 2: 3 rows of 16 channels (two planes each), over the features
-        if (!run(1)) break;
+        if (!run(1, g)) break;
         for (int it = half; it < kSc2Tiles * 3; it += 2) {
             const int j = it / 3, r = it - 3 * j;
             float v[16];
@@ -343,7 +371,7 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         }
         sync_point();
         // ---- layer 3 and the head
-        if (!run(2)) break;
+        if (!run(2, g)) break;
         for (int j = half; j < kSc2Tiles; j += 2) {
             float v[32];
             tmem_ld32(tq(tmem, 32 * j), v);
@@ -368,6 +396,7 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
             }
         }
         sync_point();
+        si = sn;
     }
     __syncthreads();
     if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
