@@ -133,20 +133,31 @@ __device__ __forceinline__ void prefetch7(const Seg2 &si) {
 __device__ __forceinline__ void build_x(unsigned char *X, const Seg2 &si, int b0) {
     const float xc = __fmul_rn(0.5f, (float)(si.W - 1)), Wf = (float)si.W;
     const float yc = __fmul_rn(0.5f, (float)(si.H - 1)), Hf = (float)si.H;
-    for (int i = threadIdx.x; i < 7 * kCols; i += blockDim.x) {
-        const int k = i / kCols, c = i - k * kCols, x = b0 + c;
-        uint4 q = make_uint4(0u, 0u, 0u, 0u);
-        if (x >= 0 && x < si.W) {
-            int fr_row;
-            const uint8_t *p = seg2_row(si, k, &fr_row) + 3 * x;
-            const float R = (float)((int)p[0] - 128) * (1.0f / 128.0f);
-            const float G = (float)((int)p[1] - 128) * (1.0f / 128.0f);
-            const float B = (float)((int)p[2] - 128) * (1.0f / 128.0f);
-            const float Xf = __fdiv_rn(__fsub_rn((float)x, xc), Wf);
-            const float Yf = __fdiv_rn(__fsub_rn((float)fr_row, yc), Hf);
-            q = make_uint4(pack_bf16(R, G), pack_bf16(B, Xf), pack_bf16(Yf, 0.0f), 0u);
+    // a thread per column: X once per column, Y once per row
+    const uint8_t *rowp[7];
+    float Yf[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        int fr_row;
+        rowp[k] = seg2_row(si, k, &fr_row);
+        Yf[k] = __fdiv_rn(__fsub_rn((float)fr_row, yc), Hf);
+    }
+    for (int c = threadIdx.x; c < kCols; c += blockDim.x) {
+        const int x = b0 + c;
+        const bool inside = x >= 0 && x < si.W;
+        const float Xf = inside ? __fdiv_rn(__fsub_rn((float)x, xc), Wf) : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (inside) {
+                const uint8_t *p = rowp[k] + 3 * x;
+                const float R = (float)((int)p[0] - 128) * (1.0f / 128.0f);
+                const float G = (float)((int)p[1] - 128) * (1.0f / 128.0f);
+                const float B = (float)((int)p[2] - 128) * (1.0f / 128.0f);
+                q = make_uint4(pack_bf16(R, G), pack_bf16(B, Xf), pack_bf16(Yf[k], 0.0f), 0u);
+            }
+            *reinterpret_cast<uint4 *>(X + k * kPlane + (kG + c) * 16) = q;
         }
-        *reinterpret_cast<uint4 *>(X + k * kPlane + (kG + c) * 16) = q;
     }
 }
 
