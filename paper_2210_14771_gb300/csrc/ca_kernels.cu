@@ -471,7 +471,11 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
     const int nb0 = (len[0] + 31) >> 5, nb1 = (len[1] + 31) >> 5;
     __syncthreads();   // the previous item is done with the words and queues
 
-    // ---- rows y-1, y, y+1 of the whole strip -> column words
+    // ---- rows y-1, y, y+1 of the whole strip -> column words.  With
+    // 64-column alignment (W a multiple of 64) every block of 32 scan
+    // positions of either half is one aligned group of 32 columns, so its
+    // middle-row maximum comes from the two 16-column groups of a lane pair.
+    const bool blocks_aligned = fr.vec_ok && (W & 63) == 0;
     if (fr.vec_ok) {
         const uint8_t *r0 = fr.rgb + (int64_t)(y - 1) * fr.pitch;
         for (int g = tid; g < (W >> 4); g += blockDim.x) {
@@ -485,6 +489,18 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
             dst[1] = interleave4(L0.y, L1.y, L2.y);
             dst[2] = interleave4(L0.z, L1.z, L2.z);
             dst[3] = interleave4(L0.w, L1.w, L2.w);
+            if (blocks_aligned) {   // W / 16 is even: lanes g and g ^ 1 are both here
+                uint32_t m = __vmaxu4(__vmaxu4(L1.x, L1.y), __vmaxu4(L1.z, L1.w));
+                m = __vmaxu4(m, m >> 16);
+                m = __vmaxu4(m, m >> 8);
+                m &= 0xffu;
+                m = max(m, __shfl_xor_sync(__activemask(), m, 1));
+                const int G = g >> 1;   // columns [32 G, 32 G + 32)
+                if ((g & 1) == 0) {
+                    if (32 * G < hw) bmax[G] = (int)m;
+                    else bmax[kMaxBlocks + (W >> 5) - 1 - G] = (int)m;
+                }
+            }
         }
     } else {
         for (int x = tid; x < W; x += blockDim.x) {
@@ -496,7 +512,7 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
     }
     __syncthreads();
     // ---- middle-row maximum of every block of 32 scan positions
-    for (int k = warp; k < nb0 + nb1; k += kStripWarps) {
+    for (int k = warp; k < nb0 + nb1 && !blocks_aligned; k += kStripWarps) {
         const int h = k < nb0 ? 0 : 1, b = h ? k - nb0 : k;
         const int p = 32 * b + lane;
         int m = 0;
