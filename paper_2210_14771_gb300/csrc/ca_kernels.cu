@@ -137,13 +137,6 @@ size_t strips_smem_bytes(const DevParams &P) {
 
 namespace {
 
-// Barrier over the 128 threads of quad `quad` (0 or 1) of a 256-thread CTA;
-// the ids are immediates so that only barriers 1 and 2 are reserved.
-__device__ __forceinline__ void quad_barrier(int quad) {
-    if (quad == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
-    else asm volatile("bar.sync 2, 128;" ::: "memory");
-}
-
 // Luma of rows h-1, h, h+1 for 4 pixels (bytes of a, b, c) -> 4 column words.
 __device__ __forceinline__ uint4 interleave4(uint32_t a, uint32_t b, uint32_t c) {
     const uint32_t t01 = __byte_perm(a, b, 0x5140), t23 = __byte_perm(a, b, 0x7362);
@@ -274,7 +267,7 @@ __device__ __forceinline__ void strip_half(const DevFrame *__restrict__ frames,
                                            CandSlot *__restrict__ slots, int f, int i, int half) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cols = strip_cols(P);
-    const uint16_t *li = ss.li, *lgb = ss.lgb, *lg = ss.lg;
+    const uint16_t *li = ss.li, *lg = ss.lg;
     uint32_t *yy = reinterpret_cast<uint32_t *>(ss.wmem) + warp * cols;
     uint16_t *sc = reinterpret_cast<uint16_t *>(ss.wmem + (size_t)kStripWarps * cols * 4) + warp * cols;
     int *s_pick = reinterpret_cast<int *>(ss.wmem + (size_t)kStripWarps * cols * 6) + warp * (kMaxSlots / 2);
@@ -577,17 +570,33 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
         qn = 0;
         __syncwarp();   // the entries are read before new pushes
     };
-    for (int k = warp; k < L0 + L1; k += kStripWarps) {
-        const int h = k < L0 ? 0 : 1, b = h ? k - L0 : k;
-        const int cin = carry[h * kMaxBlocks + b];
+    // chunks of kPpl live blocks (32 kPpl scan positions), kPpl consecutive
+    // positions per lane: a serial prefix maximum inside the lane, one warp
+    // scan per chunk, and the Sobel terms from the lane's kPpl + 2 column words
+    constexpr int kPpl = 2;
+    const int C0 = (L0 + kPpl - 1) / kPpl, C1 = (L1 + kPpl - 1) / kPpl;
+    for (int k = warp; k < C0 + C1; k += kStripWarps) {
+        const int h = k < C0 ? 0 : 1, c = h ? k - C0 : k;
+        const int cin = carry[h * kMaxBlocks + kPpl * c];
         const uint32_t bh = h ? best1 : best0;
-        // no pixel of this block (its s_iota <= s_iota(cin)) can beat the best
+        // no pixel of this chunk (its s_iota <= s_iota(cin)) can beat the best
         if (bh != 0u && (bh >> 16) >= (uint32_t)li[cin]) continue;
-        const int p = 32 * b + lane;
-        const bool act = p < len[h];
-        const int x = h ? (W - 1 - p) : p;
-        const uint32_t w1 = yy[act ? x : (h ? W - len[h] : len[h] - 1)];
-        int inc = act ? (int)((w1 >> 8) & 0xffu) : 0;
+        const int p0 = 32 * kPpl * c + kPpl * lane, lh = len[h];
+        // sw[i]: the column word of scan position p0 - 1 + i (clamped into the row)
+        uint32_t sw[kPpl + 2];
+#pragma unroll
+        for (int i = 0; i < kPpl + 2; ++i) {
+            const int xc = h ? W - p0 - i : p0 - 1 + i;
+            sw[i] = yy[min(max(xc, 0), W - 1)];
+        }
+        int lp[kPpl];   // inclusive prefix maxima of the middle row along the lane
+        int run = 0;
+#pragma unroll
+        for (int j = 0; j < kPpl; ++j) {
+            if (p0 + j < lh) run = max(run, (int)((sw[j + 1] >> 8) & 0xffu));
+            lp[j] = run;
+        }
+        int inc = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(kFull, inc, o);
@@ -595,30 +604,40 @@ __device__ __forceinline__ void strip_pair(const DevFrame *__restrict__ frames,
         }
         int excl = __shfl_up_sync(kFull, inc, 1);
         if (lane == 0) excl = 0;
-        const int iota = max(cin, excl);
-        bool cand = false;
-        uint2 ent = make_uint2(0u, 0u);
-        if (act && iota < P.io_cut && x != 0 && x != W - 1) {
-            const uint32_t w0 = yy[x - 1], w2 = yy[x + 1];
-            const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
-            const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
-            const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
-            const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
-            const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
-            const int ng = gx * gx + gy * gy;
-            if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P)) {
-                const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
-                const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
-                const uint32_t rank = (uint32_t)(h ? x : (0xFFFF - x));
-                cand = ((bound << 16) | rank) > bh;   // could beat the best so far
-                ent = make_uint2(((uint32_t)x << 16) | ((uint32_t)h << 8) | (uint32_t)iota,
-                                 ((uint32_t)gx & 0xffffu) | ((uint32_t)gy << 16));
+        const int base = max(cin, excl);   // preceding maximum of the lane's first position
+        // no pixel of this lane (s_iota <= s_iota(base)) can beat the best
+        const bool lane_live = !(bh != 0u && (bh >> 16) >= (uint32_t)li[base]);
+#pragma unroll
+        for (int j = 0; j < kPpl; ++j) {
+            const int p = p0 + j;
+            const int x = h ? (W - 1 - p) : p;
+            const int iota = j ? max(base, lp[j - 1]) : base;
+            bool cand = false;
+            uint2 ent = make_uint2(0u, 0u);
+            if (lane_live && p < lh && iota < P.io_cut && x != 0 && x != W - 1) {
+                // columns x - 1, x, x + 1 (the scan runs right to left in the right half)
+                const uint32_t w0 = h ? sw[j + 2] : sw[j], w1 = sw[j + 1];
+                const uint32_t w2 = h ? sw[j] : sw[j + 2];
+                const int u0 = w0 & 0xff, m0 = (w0 >> 8) & 0xff, d0 = (w0 >> 16) & 0xff;
+                const int u1 = w1 & 0xff, d1 = (w1 >> 16) & 0xff;
+                const int u2 = w2 & 0xff, m2 = (w2 >> 8) & 0xff, d2 = (w2 >> 16) & 0xff;
+                const int gx = (u2 + 2 * m2 + d2) - (u0 + 2 * m0 + d0);
+                const int gy = (d0 + 2 * d1 + d2) - (u0 + 2 * u1 + u2);
+                const int ng = gx * gx + gy * gy;
+                if (ng != 0 && angle_ok(ctx, gx, gy, x, ng, P)) {
+                    const uint32_t gub = (ng >> 4) < kBoundBins ? (uint32_t)lgb[ng >> 4] : 32768u;
+                    const uint32_t bound = (gub * (uint32_t)li[iota] + 16384u) >> 15;
+                    const uint32_t rank = (uint32_t)(h ? x : (0xFFFF - x));
+                    cand = ((bound << 16) | rank) > bh;   // could beat the best so far
+                    ent = make_uint2(((uint32_t)x << 16) | ((uint32_t)h << 8) | (uint32_t)iota,
+                                     ((uint32_t)gx & 0xffffu) | ((uint32_t)gy << 16));
+                }
             }
+            const unsigned bal = __ballot_sync(kFull, cand);
+            if (cand) queue[qn + __popc(bal & ((1u << lane) - 1u))] = ent;
+            qn += __popc(bal);
+            if (qn >= 32) flush();
         }
-        const unsigned bal = __ballot_sync(kFull, cand);
-        if (cand) queue[qn + __popc(bal & ((1u << lane) - 1u))] = ent;
-        qn += __popc(bal);
-        if (qn >= 32) flush();
     }
     if (qn > 0) flush();
     if (lane == 0) {
