@@ -213,15 +213,17 @@ ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H, int W, con
  * which runs one frame per launch, Sec. 2.2.6). */
 
 /* Outcome of ca_tune.  Times are mean milliseconds per call on the tuning
- * batch, measured with CUDA events on the call's stream. */
+ * batch, measured with CUDA events on the call's stream: 3 calls per
+ * configuration in the sweep, then 24 for each of the 6 fastest, of which
+ * the lowest mean is chosen. */
 typedef struct ca_tuning {
     int32_t batch_mode;   /* chosen CA_BATCH_STAGED or CA_BATCH_FUSED */
     int32_t hyp_threads;  /* chosen threads per hypothesis */
     int32_t wave_frames;  /* chosen frames per wave (fused) */
     int32_t n_tried;      /* configurations timed */
-    float ms;             /* chosen configuration */
-    float ms_staged;      /* fastest staged configuration */
-    float ms_fused;       /* fastest fused configuration */
+    float ms;             /* chosen configuration (24 calls) */
+    float ms_staged;      /* fastest staged configuration in the sweep */
+    float ms_fused;       /* fastest fused configuration in the sweep */
     float ms_untuned;     /* the configuration CA_BATCH_AUTO used before tuning */
     int32_t fit_lag;      /* chosen (fused): the fit of a wave follows the strips of
                              the wave fit_lag waves later */

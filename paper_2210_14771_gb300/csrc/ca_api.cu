@@ -581,6 +581,10 @@ LaunchCfg choose_cfg(const ca_handle *h, const ca_frame *frames, int B, const ca
         : choose_hyp_threads(0, B, hyps_per_frame(p), h->sm_count);
     c.wave = p.wave_frames > 0 ? std::min(p.wave_frames, B)
            : (t && t->mode == c.mode) ? t->wave : default_wave(h, B, p, c.T);
+    if (t && t->mode == c.mode && t->T == c.T && t->wave == c.wave) {   // the tuned schedule
+        c.fit_lag = t->fit_lag;
+        c.mask_lag = t->mask_lag;
+    }
     c.scorer = p.scorer_mode;
     if (c.scorer != CA_SCORER_HAND) c.mode = CA_BATCH_STAGED;   // the scorer runs between phases
     return c;
@@ -1401,10 +1405,9 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
     CA_CUDA(h, cudaEventCreate(&e1));
     const bool timing = h->timing;
     h->timing = false;
-    auto time_cfg = [&](const LaunchCfg &c, float *ms) -> ca_status {
+    auto time_cfg = [&](const LaunchCfg &c, float *ms, int reps = 3) -> ca_status {
         ca_status r = estimate_cfg(h, frames, B, &q, out_dev, s, c);   // warm-up
         if (r != CA_OK) return r;
-        const int reps = 3;
         CA_CUDA(h, cudaEventRecord(e0, s));
         for (int i = 0; i < reps && r == CA_OK; ++i) r = estimate_cfg(h, frames, B, &q, out_dev, s, c);
         if (r != CA_OK) return r;
@@ -1422,6 +1425,11 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
     float best_ms = 1e30f;
     // every configuration must give the first one's results, byte for byte
     std::vector<ca_result> first((size_t)B), cur((size_t)B);
+    struct Timed {
+        float ms;
+        LaunchCfg cfg;
+    };
+    std::vector<Timed> timed;
     for (const LaunchCfg &c : cands) {
         float ms = 0.0f;
         if ((st = time_cfg(c, &ms)) != CA_OK) break;
@@ -1440,7 +1448,23 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
         res.n_tried += 1;
         if (c.mode == CA_BATCH_STAGED) res.ms_staged = std::min(res.ms_staged, ms);
         else res.ms_fused = std::min(res.ms_fused, ms);
-        if (ms < best_ms) { best_ms = ms; best = c; }
+        timed.push_back({ms, c});
+    }
+    // the configurations within a few percent of each other differ by less
+    // than the noise of 3 calls: time the fastest few again, longer, in two
+    // interleaved rounds, and keep the lowest mean
+    if (st == CA_OK && !timed.empty()) {
+        std::stable_sort(timed.begin(), timed.end(),
+                         [](const Timed &a, const Timed &b) { return a.ms < b.ms; });
+        const size_t nf = std::min<size_t>(timed.size(), 6);
+        std::vector<float> sum(nf, 0.0f);
+        for (int round = 0; round < 2 && st == CA_OK; ++round)
+            for (size_t i = 0; i < nf && st == CA_OK; ++i) {
+                float ms = 0.0f;
+                if ((st = time_cfg(timed[i].cfg, &ms, 12)) == CA_OK) sum[i] += ms;
+            }
+        for (size_t i = 0; i < nf && st == CA_OK; ++i)
+            if (sum[i] / 2 < best_ms) { best_ms = sum[i] / 2; best = timed[i].cfg; }
     }
     float ms_u = 0.0f;
     if (st == CA_OK) st = time_cfg(untuned, &ms_u);

@@ -156,7 +156,9 @@ def test_tune_keeps_results(ca):
     r_before, m_before = _run(ca, ts, keys, lp)
     t = ca.tune(ts, lp, keys=keys, masks=True)
     assert t["batch_mode"] in (1, 2) and t["hyp_threads"] in (1, 2, 4, 8)
-    assert t["n_tried"] >= 8 and 0 < t["ms"] <= min(t["ms_staged"], t["ms_fused"]) + 1e-6
+    # the chosen configuration is re-timed over more calls than the sweep's
+    # 3, so its time is the sweep's best give or take the noise of 3 calls
+    assert t["n_tried"] >= 8 and 0 < t["ms"] <= 1.25 * min(t["ms_staged"], t["ms_fused"])
     r_after, m_after = _run(ca, ts, keys, lp)
     assert r_after.tobytes() == r_before.tobytes()
     assert all(np.array_equal(a, b) for a, b in zip(m_after, m_before))
