@@ -126,20 +126,65 @@ __device__ __forceinline__ void prefetch7(const Seg2 &si) {
     }
 }
 
+// Staging of a segment's 7 rows in shared memory by cp.async (16-byte
+// asynchronous copies), issued one segment ahead into the interior rows of
+// the a1 planes (free from the end of the third layer until the next
+// segment's first epilogue; the planes' zero guard rows are not touched).
+// Possible when the copies stay inside each row: rows start on 16-byte
+// boundaries and 3 W is a multiple of 16.  Row k lands at stage2_row(k).
+constexpr int kStage2Row = 1200;   // >= 3 x 384 columns + 30 bytes of alignment, 16 x 75
+static_assert(3 * kCols + 30 <= kStage2Row && 5 * kStage2Row <= kCols * 16, "staged rows fit");
+
+__device__ __forceinline__ unsigned char *stage2_row(unsigned char *a1, int k) {
+    return a1 + (k / 5) * kPlane + kG * 16 + (k % 5) * kStage2Row;
+}
+
+__device__ __forceinline__ bool stageable2(const Seg2 &si) {
+    return (((uintptr_t)si.base | (uintptr_t)si.pitch | (uintptr_t)(3 * si.W)) & 15) == 0;
+}
+
+// First byte (a multiple of 16, relative to a row) of the staged block.
+__device__ __forceinline__ int stage2_bias(const Seg2 &si) {
+    return (3 * max(si.s0 - kSc2Halo, 0)) & ~15;
+}
+
+__device__ __forceinline__ void stage2_rows(unsigned char *a1, const Seg2 &si) {
+    const int b0 = si.s0 - kSc2Halo;
+    const int c0 = max(b0, 0), c1 = min(b0 + kCols, si.W);
+    const int a = stage2_bias(si), b = (3 * c1 + 15) & ~15;
+    const int nb = c1 > c0 ? (b - a) >> 4 : 0;   // 16-byte blocks per row
+    for (int i = threadIdx.x; i < 7 * nb; i += blockDim.x) {
+        const int k = i / nb, j = i - k * nb;
+        int fr_row;
+        const uint8_t *src = seg2_row(si, k, &fr_row) + a + 16 * j;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         smem_u32(stage2_row(a1, k) + 16 * j)),
+                     "l"(src)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage2_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // RGBXY features of the 7 x 384 pixels of a segment (columns b0 ...) into 7
 // planes: channels R, G, B as (v - 128) / 128, X = (x - (W-1)/2) / W and
 // Y = (row - (H-1)/2) / H in binary32, all rounded to bf16; zero outside the
 // frame's columns.
-__device__ __forceinline__ void build_x(unsigned char *X, const Seg2 &si, int b0) {
+__device__ __forceinline__ void build_x(unsigned char *X, const Seg2 &si, int b0,
+                                        unsigned char *staged_a1 = nullptr) {
     const float xc = __fmul_rn(0.5f, (float)(si.W - 1)), Wf = (float)si.W;
     const float yc = __fmul_rn(0.5f, (float)(si.H - 1)), Hf = (float)si.H;
-    // a thread per column: X once per column, Y once per row
+    // a thread per column: X once per column, Y once per row; pixel x of row
+    // k at rowp[k] + 3 x (the staged copy is offset by its first byte)
     const uint8_t *rowp[7];
     float Yf[7];
+    const int bias = staged_a1 ? stage2_bias(si) : 0;
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         int fr_row;
         rowp[k] = seg2_row(si, k, &fr_row);
+        if (staged_a1) rowp[k] = stage2_row(staged_a1, k) - bias;
         Yf[k] = __fdiv_rn(__fsub_rn((float)fr_row, yc), Hf);
     }
     for (int c = threadIdx.x; c < kCols; c += blockDim.x) {
@@ -350,11 +395,19 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
     };
 
     if ((int)blockIdx.x < total_segs) si = seg2_info(src, blockIdx.x);
+    bool staged = false;   // this segment's rows are in A1's interior
     for (int g = blockIdx.x; g < total_segs && !abort; g += gridDim.x) {
         const int b0 = si.s0 - kSc2Halo;
         has_next = g + (int)gridDim.x < total_segs;
         __syncthreads();   // the previous segment is done with X / A1 / A2
-        build_x(X, si, b0);
+        if (staged) {
+            stage2_wait();
+            __syncthreads();
+            build_x(X, si, b0, A1);
+        } else {
+            build_x(X, si, b0);
+        }
+        staged = false;
         sync_point();
         // ---- layer 1: 5 rows of 8 channels
         if (!run(0, g)) break;
@@ -383,6 +436,10 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         sync_point();
         // ---- layer 3 and the head
         if (!run(2, g)) break;
+        if (has_next && stageable2(sn)) {   // the MMAs are done with A1
+            stage2_rows(A1, sn);
+            staged = true;
+        }
         for (int j = half; j < kSc2Tiles; j += 2) {
             float v[32];
             tmem_ld32(tq(tmem, 32 * j), v);
@@ -409,6 +466,7 @@ __global__ void __launch_bounds__(kInf2Threads, 2)
         sync_point();
         si = sn;
     }
+    stage2_wait();   // no copy outlives the CTA
     __syncthreads();
     if (abort && tid == 0) {   // let MMAs still in flight finish (bounded) before freeing TMEM
         mma_commit(bar_m);
