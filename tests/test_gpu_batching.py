@@ -145,6 +145,33 @@ def test_plan_graph_replay(ca, orc):
         plan.close()
 
 
+def test_plans_on_two_streams_overlap_safely(ca, orc):
+    """Two plans over the same frames, with their own results and masks,
+    launched alternately on two streams (the benchmark's headline loop):
+    consecutive launches overlap on the GPU, and every result and mask still
+    equals the oracle's, bit for bit."""
+    from paper_2210_14771_gb300 import api
+    frames, _, keys = synth.mixed_batch(4, 12, unique=4, workers=1,
+                                        resolutions=((480, 640), (1080, 1920)))
+    ts = [torch.from_numpy(f).cuda() for f in frames]
+    lp, op = both_params(orc, n_strips=32, cands_per_strip=2, n_hyps=512, batch_mode=2)
+    outs = []
+    for _ in range(2):
+        res = api.new_results(len(frames), "cuda")
+        masks = [torch.zeros(f.shape[:2], dtype=torch.uint8, device="cuda") for f in frames]
+        outs.append((ca.plan(ts, lp, keys=keys, masks=masks, results=res), res, masks))
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for k in range(10):
+        outs[k % 2][0].launch(streams[k % 2])
+    ca.sync()
+    torch.cuda.synchronize()
+    for plan, res, masks in outs:
+        _check_oracle(orc, frames, keys, op, api.results_numpy(res),
+                      [m.cpu().numpy() for m in masks], range(len(frames)))
+        plan.close()
+
+
 def test_tune_keeps_results(ca):
     """ca_tune times every result-preserving configuration and the tuned AUTO
     call returns the same bytes as the untuned one."""
