@@ -214,14 +214,16 @@ ca_status ca_estimate_static(const uint8_t *frames_dev, int B, int H, int W, con
 
 /* Outcome of ca_tune.  Times are mean milliseconds per call on the tuning
  * batch, measured with CUDA events on the call's stream: 3 calls per
- * configuration in the sweep, then 24 for each of the 6 fastest, of which
- * the lowest mean is chosen. */
+ * configuration in the sweep (host side included), then, for each of the 6
+ * fastest (among them the fastest staged and the fastest fused one), 24
+ * replays of a plan captured with it (as ca_plan_launch runs it); the lowest
+ * mean of those is chosen. */
 typedef struct ca_tuning {
     int32_t batch_mode;   /* chosen CA_BATCH_STAGED or CA_BATCH_FUSED */
     int32_t hyp_threads;  /* chosen threads per hypothesis */
     int32_t wave_frames;  /* chosen frames per wave (fused) */
     int32_t n_tried;      /* configurations timed */
-    float ms;             /* chosen configuration (24 calls) */
+    float ms;             /* chosen configuration (24 plan replays) */
     float ms_staged;      /* fastest staged configuration in the sweep */
     float ms_fused;       /* fastest fused configuration in the sweep */
     float ms_untuned;     /* the configuration CA_BATCH_AUTO used before tuning */

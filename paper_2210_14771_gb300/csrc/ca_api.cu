@@ -1450,18 +1450,55 @@ ca_status ca_tune(ca_handle *h, const ca_frame *frames, int B, const ca_params *
         else res.ms_fused = std::min(res.ms_fused, ms);
         timed.push_back({ms, c});
     }
-    // the configurations within a few percent of each other differ by less
-    // than the noise of 3 calls: time the fastest few again, longer, in two
-    // interleaved rounds, and keep the lowest mean
+    // The sweep's calls include the host side of each call, which for small
+    // batches outweighs the GPU time, and configurations within a few
+    // percent differ by less than the noise of 3 calls.  So the fastest few
+    // are timed again as captured plans (graph replays, as plans run them),
+    // 12 launches in each of two interleaved rounds; the lowest mean wins.
+    auto time_plan = [&](const LaunchCfg &c, float *ms) -> ca_status {
+        h->tuned[key] = c;
+        ca_params qp = q;
+        qp.hyp_threads = 0;   // the tuned entry decides the shape
+        qp.wave_frames = 0;
+        ca_plan *pl = nullptr;
+        ca_status r = ca_plan_create(h, frames, B, &qp, out_dev, &pl);
+        h->tuned.erase(key);
+        if (r != CA_OK) return time_cfg(c, ms, 12);   // e.g. debug capture is on
+        const int reps = 12;
+        for (int i = 0; i < 2 && r == CA_OK; ++i) r = ca_plan_launch(pl, s);
+        if (r == CA_OK && cudaEventRecord(e0, s) != cudaSuccess) r = cuda_fail(h, cudaGetLastError(), "tune");
+        for (int i = 0; i < reps && r == CA_OK; ++i) r = ca_plan_launch(pl, s);
+        if (r == CA_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            r = cuda_fail(h, cudaGetLastError(), "tune");
+        float t = 0.0f;
+        if (r == CA_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            r = cuda_fail(h, cudaGetLastError(), "tune");
+        *ms = t / reps;
+        const ca_status rd = ca_plan_destroy(pl);
+        return r != CA_OK ? r : rd;
+    };
     if (st == CA_OK && !timed.empty()) {
         std::stable_sort(timed.begin(), timed.end(),
                          [](const Timed &a, const Timed &b) { return a.ms < b.ms; });
+        // the 6 fastest, and the fastest of each launch mode (a staged call
+        // carries three launches of host work, so the sweep ranks it low even
+        // when its replays are the fastest)
+        for (int mode : {CA_BATCH_STAGED, CA_BATCH_FUSED}) {
+            for (size_t i = 6; i < timed.size(); ++i)
+                if (timed[i].cfg.mode == mode) {
+                    bool have = false;
+                    for (size_t j = 0; j < 6 && j < timed.size(); ++j)
+                        have = have || timed[j].cfg.mode == mode;
+                    if (!have) std::swap(timed[mode == CA_BATCH_STAGED ? 5 : 4], timed[i]);
+                    break;
+                }
+        }
         const size_t nf = std::min<size_t>(timed.size(), 6);
         std::vector<float> sum(nf, 0.0f);
         for (int round = 0; round < 2 && st == CA_OK; ++round)
             for (size_t i = 0; i < nf && st == CA_OK; ++i) {
                 float ms = 0.0f;
-                if ((st = time_cfg(timed[i].cfg, &ms, 12)) == CA_OK) sum[i] += ms;
+                if ((st = time_plan(timed[i].cfg, &ms)) == CA_OK) sum[i] += ms;
             }
         for (size_t i = 0; i < nf && st == CA_OK; ++i)
             if (sum[i] / 2 < best_ms) { best_ms = sum[i] / 2; best = timed[i].cfg; }
