@@ -102,6 +102,8 @@ def lib():
         L.orc_triple.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p]
         L.orc_triple_exhaustive.argtypes = [C.c_int64, C.c_int, C.c_void_p]
         L.orc_circumcircle.argtypes = [C.c_int] * 6 + [C.c_void_p]
+        L.orc_rn_ratio.argtypes = [C.c_int64, C.c_int64]
+        L.orc_rn_ratio.restype = C.c_float
         L.orc_ls_fit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.orc_i128_to_f32.argtypes = [C.c_int64, C.c_uint64]
         L.orc_i128_to_f32.restype = C.c_float
@@ -264,6 +266,11 @@ def triple_exhaustive(h, M):
     out = np.zeros(3, np.int32)
     lib().orc_triple_exhaustive(h, M, _ptr(out))
     return out
+
+
+def rn_ratio(num, den):
+    """The binary32 value nearest to num / den (ties to even)."""
+    return np.float32(lib().orc_rn_ratio(int(num), int(den)))
 
 
 def circumcircle(a, b, c):

@@ -375,10 +375,44 @@ float orc_i128_to_f32(int64_t hi, uint64_t lo) {
     return (float)v; /* correctly rounded (IEEE round-to-nearest-even) */
 }
 
+/* The binary32 value nearest to num / den (den != 0; ties to even; +0 for
+ * num = 0), by integer steps: the quotient scaled by a power of two to 25 or
+ * 26 significant bits, then rounded on the bits below 24 and the remainder.
+ * Needs |num|, |den| < 2^38 (so that the scaled operand fits in 64 bits). */
+float orc_rn_ratio(int64_t num, int64_t den) {
+    if (num == 0) return 0.0f;
+    const int neg = (num < 0) != (den < 0);
+    const uint64_t a = num < 0 ? (uint64_t)0 - (uint64_t)num : (uint64_t)num;
+    const uint64_t b = den < 0 ? (uint64_t)0 - (uint64_t)den : (uint64_t)den;
+    int la = 63, lb = 63;
+    while (!((a >> la) & 1u)) --la;
+    while (!((b >> lb) & 1u)) --lb;
+    const int s = 25 - (la - lb);   /* a 2^s / b lies in [2^24, 2^26) */
+    uint64_t q, r;
+    if (s >= 0) {
+        q = (a << s) / b;
+        r = (a << s) % b;
+    } else {
+        q = a / (b << -s);
+        r = a % (b << -s);
+    }
+    int e = -s;                     /* num / den = (q + remainder) 2^e */
+    int sticky = r != 0;
+    if (q >= (1ull << 25)) {        /* keep 25 bits: 24 of mantissa and a round bit */
+        sticky |= (int)(q & 1u);
+        q >>= 1;
+        e += 1;
+    }
+    uint64_t m = q >> 1;
+    const int round_bit = (int)(q & 1u);
+    if (round_bit && (sticky || (m & 1u))) m += 1;   /* may reach 2^24: still exact */
+    const float v = ldexpf((float)m, e + 1);
+    return neg ? -v : v;
+}
+
 /* Circle through a, b, c (Sec. 2.2.5, "analytically"): the circumcentre is
- * (Ux/D, Uy/D) with exact integer D, Ux, Uy.  The quotient is taken in
- * binary64 when |D| < 2^16 (nearly collinear triples) and in binary32
- * otherwise; the radius is the binary32 distance to a. */
+ * (Ux/D, Uy/D) with exact integer D, Ux, Uy, each coordinate the binary32
+ * value nearest to that ratio; the radius is the binary32 distance to a. */
 int orc_circumcircle(int ax, int ay, int bx, int by, int cx, int cy, float out[3]) {
     int64_t D = 2 * ((int64_t)ax * (by - cy) + (int64_t)bx * (cy - ay) + (int64_t)cx * (ay - by));
     if (D == 0) return 0;
@@ -387,15 +421,7 @@ int orc_circumcircle(int ax, int ay, int bx, int by, int cx, int cy, float out[3
     int64_t c2 = (int64_t)cx * cx + (int64_t)cy * cy;
     int64_t Ux = a2 * (by - cy) + b2 * (cy - ay) + c2 * (ay - by);
     int64_t Uy = a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax);
-    float ox, oy;
-    int64_t aD = D < 0 ? -D : D;
-    if (aD < 65536) {
-        ox = (float)((double)Ux / (double)D);
-        oy = (float)((double)Uy / (double)D);
-    } else {
-        ox = (float)Ux / (float)D;
-        oy = (float)Uy / (float)D;
-    }
+    const float ox = orc_rn_ratio(Ux, D), oy = orc_rn_ratio(Uy, D);
     float dx = (float)ax - ox, dy = (float)ay - oy;
     out[0] = ox; out[1] = oy; out[2] = sqrtf(dx * dx + dy * dy);
     return 1;

@@ -132,6 +132,7 @@ void orc_triple(uint64_t seed, uint64_t frame_key, uint32_t h, int M, int32_t ou
 void orc_triple_exhaustive(int64_t h, int M, int32_t out[3]);
 
 /* Circle through three integer points; 0 if collinear. out = cx, cy, r. */
+float orc_rn_ratio(int64_t num, int64_t den);
 int orc_circumcircle(int ax, int ay, int bx, int by, int cx, int cy, float out[3]);
 
 /* Algebraic least-squares circle (Coope 1993) of n integer points; 0 if the

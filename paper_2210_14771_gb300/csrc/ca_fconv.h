@@ -72,4 +72,37 @@ CA_FCONV_HD float u128_to_f32(uint64_t hi, uint64_t lo) {
     return f * f32_from_bits_((uint32_t)(127 + sh) << 23);
 }
 
+// Nearest binary32 (ties to even) of num / den, den != 0, |num| and |den|
+// below 2^37; +0 for num = 0.  The quotient is taken to 25 or 26 significant
+// bits (the operands shifted by a power of two), estimated by a binary32
+// division and corrected to the exact integer quotient with 64-bit products;
+// the bits below the 24 kept and the remainder then decide the rounding.
+CA_FCONV_HD float ratio_to_f32(int64_t num, int64_t den) {
+    if (num == 0) return 0.0f;
+    const bool neg = (num < 0) != (den < 0);
+    const uint64_t a = num < 0 ? 0ull - (uint64_t)num : (uint64_t)num;
+    const uint64_t b = den < 0 ? 0ull - (uint64_t)den : (uint64_t)den;
+    const int sh = 25 - (clz64_(b) - clz64_(a));   // a 2^sh / b in [2^24, 2^26)
+    const uint64_t n = sh >= 0 ? a << sh : a;        // below 2^63
+    const uint64_t d = sh >= 0 ? b : b << -sh;
+#if defined(__CUDA_ARCH__)
+    uint64_t q = __float2uint_rz(__fdiv_rn(u64_to_f32(n), u64_to_f32(d)));
+#else
+    uint64_t q = (uint64_t)(u64_to_f32(n) / u64_to_f32(d));
+#endif
+    for (int i = 0; i < 64 && q * d > n; ++i) --q;        // the estimate is within a few units
+    for (int i = 0; i < 64 && (q + 1) * d <= n; ++i) ++q;
+    bool sticky = n - q * d != 0;
+    int e2 = -sh;                                        // num / den = (q + rem / d) 2^e2
+    if (q >> 25) {
+        sticky = sticky || (q & 1u);
+        q >>= 1;
+        ++e2;
+    }
+    uint32_t mant = (uint32_t)(q >> 1);                  // 24 bits; q's bit 0 rounds
+    if ((q & 1u) && (sticky || (mant & 1u))) ++mant;     // 2^24 at most: still exact
+    const float v = (float)mant * f32_from_bits_((uint32_t)(127 + e2 + 1) << 23);
+    return neg ? -v : v;
+}
+
 }  // namespace ca

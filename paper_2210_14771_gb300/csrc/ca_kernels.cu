@@ -756,15 +756,10 @@ __device__ __forceinline__ bool circumcircle(int ax, int ay, int bx, int by, int
     const long long c2 = (long long)cx * cx + (long long)cy * cy;
     const long long Ux = a2 * (by - cy) + b2 * (cy - ay) + c2 * (ay - by);
     const long long Uy = a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax);
-    const long long aD = D < 0 ? -D : D;
-    if (aD < 65536) {   // nearly collinear: binary64 quotient
-        o.cx = __double2float_rn(__ddiv_rn(__ll2double_rn(Ux), __ll2double_rn(D)));
-        o.cy = __double2float_rn(__ddiv_rn(__ll2double_rn(Uy), __ll2double_rn(D)));
-    } else {
-        const float fD = i64_to_f32(D);
-        o.cx = __fdiv_rn(i64_to_f32(Ux), fD);
-        o.cy = __fdiv_rn(i64_to_f32(Uy), fD);
-    }
+    // each coordinate the binary32 value nearest to the exact ratio
+    // (integer steps: ca_fconv.h)
+    o.cx = ratio_to_f32(Ux, D);
+    o.cy = ratio_to_f32(Uy, D);
     const float dx = __fsub_rn(__int2float_rn(ax), o.cx);
     const float dy = __fsub_rn(__int2float_rn(ay), o.cy);
     o.r = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));

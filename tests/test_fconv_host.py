@@ -86,3 +86,60 @@ def test_integer_to_f32_conversions_round_like_the_compiler(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatches 0" in r.stdout
+
+
+RATIO_LIB = r"""
+#include <cstdint>
+#include "ca_fconv.h"
+extern "C" float ratio(int64_t num, int64_t den) { return ca::ratio_to_f32(num, den); }
+"""
+
+
+def test_ratio_rounds_to_the_nearest_binary32(tmp_path):
+    """The circumcentre quotient of the fit (csrc/ca_fconv.h, host build):
+    the binary32 value nearest to an integer ratio, against exact rational
+    rounding on random ratios over the operand range of 4096-pixel frames,
+    both signs, and exact halfway cases."""
+    import ctypes
+    from fractions import Fraction
+
+    import numpy as np
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no g++")
+    src = tmp_path / "ratio.cpp"
+    so = tmp_path / "libratio.so"
+    src.write_text(RATIO_LIB)
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", HDR, str(src), "-o", str(so)],
+                   check=True)
+    lib = ctypes.CDLL(str(so))
+    lib.ratio.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    lib.ratio.restype = ctypes.c_float
+
+    def bits(v):
+        return int(np.array(v, np.float32).view(np.uint32))
+
+    def nearest(fr):
+        f = np.float32(float(fr))
+        best = None
+        for c in (np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))):
+            d = abs(Fraction(float(c)) - fr)
+            if best is None or d < best[0] or (d == best[0] and bits(c) & 1 == 0):
+                best = (d, c)
+        return best[1]
+
+    rng = np.random.default_rng(5)
+    cases = [(1, 3), (-1, 3), (2, 3), (10, -7), ((1 << 37) - 1, 3), (3, (1 << 37) - 1)]
+    for _ in range(20000):
+        den = int(rng.integers(1, 1 << int(rng.integers(1, 37))))
+        num = int(rng.integers(-(1 << int(rng.integers(1, 37))), 1 << 36))
+        if num == 0:
+            continue
+        cases.append((num, den if rng.random() < 0.5 else -den))
+    for k in range(3):
+        m = (1 << 23) + 999 + k
+        cases += [(2 * m + 1, 2), (2 * m + 3, 2), (-(2 * m + 1), -2)]
+    for num, den in cases:
+        got = lib.ratio(num, den)
+        assert bits(got) == bits(nearest(Fraction(num, den))), (num, den, got)
+    assert lib.ratio(0, 5) == 0.0

@@ -266,8 +266,45 @@ def test_circumcircle_closed_forms(orc):
     assert orc.circumcircle((0, 0), (1, 1), (5, 5)) is None
 
 
+def _nearest_f32(fr):
+    """The binary32 value nearest to the rational fr, ties to even (from the
+    exact distances of the candidates around a first estimate)."""
+    f = np.float32(float(fr))
+    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+    best = None
+    for c in cands:
+        d = abs(Fraction(float(c)) - fr)
+        even = int(np.array(c, np.float32).view(np.uint32)) & 1 == 0
+        if best is None or d < best[0] or (d == best[0] and even):
+            best = (d, c)
+    return np.float32(best[1])
+
+
+def test_rn_ratio_is_the_nearest_binary32(orc):
+    """The circumcentre quotient: the binary32 value nearest to an integer
+    ratio, against exact rational rounding -- random ratios over the operand
+    range of 4096-pixel frames, both signs, and exact halfway cases (both
+    tie directions)."""
+    rng = np.random.default_rng(11)
+    cases = [(1, 3), (-1, 3), (2, 3), (10, -7), (1 << 37, 3), (3, 1 << 37), (0, 5)]
+    for _ in range(3000):
+        den = int(rng.integers(1, 1 << int(rng.integers(1, 36))))
+        num = int(rng.integers(-(1 << int(rng.integers(1, 37))), 1 << 36))
+        cases.append((num, den if rng.random() < 0.5 else -den))
+    for k in range(3):
+        # (2 m + 1) / 2 with m of 24 bits: halfway between two binary32 values
+        m = (1 << 23) + 12345 + k
+        cases += [(2 * m + 1, 2), (2 * m + 3, 2), (-(2 * m + 1), 2)]
+    for num, den in cases:
+        got = orc.rn_ratio(num, den)
+        want = _nearest_f32(Fraction(num, den))
+        bits = lambda v: int(np.array(v, np.float32).view(np.uint32))
+        assert bits(got) == bits(want) or (num == 0 and got == 0), (num, den, got, want)
+
+
 def test_circumcircle_vs_exact_bisectors(orc):
-    """Against the exact rational intersection of two perpendicular bisectors."""
+    """Against the exact rational intersection of two perpendicular bisectors:
+    the centre is its nearest binary32 point, bit for bit."""
     rng = np.random.default_rng(2)
     for _ in range(300):
         a, b, c = rng.integers(-1900, 1900, size=(3, 2)).tolist()
@@ -284,8 +321,8 @@ def test_circumcircle_vs_exact_bisectors(orc):
         px = Fraction(r1 * m22 - r2 * m12, det)
         py = Fraction(m11 * r2 - m21 * r1, det)
         r = math.sqrt(float((px - a[0]) ** 2 + (py - a[1]) ** 2))
+        assert out[0] == _nearest_f32(px) and out[1] == _nearest_f32(py), (a, b, c, out, px, py)
         tol = 4e-7 * max(1.0, abs(float(px)), abs(float(py)))
-        assert abs(out[0] - float(px)) <= tol and abs(out[1] - float(py)) <= tol
         assert abs(out[2] - r) <= 4e-7 * max(1.0, r) + 2 * tol
 
 
