@@ -280,6 +280,17 @@ __device__ __forceinline__ void stage_rows(unsigned char *stage, const SegInfo &
 
 __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Zeroes the guard rows (8 above and 8 below the segment) of `n_planes`
+// consecutive planes from `planes`.
+template <class G>
+__device__ __forceinline__ void zero_guards(unsigned char *planes, int n_planes) {
+    for (int i = threadIdx.x; i < n_planes * kGuard * 2; i += blockDim.x) {
+        const int plane = i / (2 * kGuard), g = i % (2 * kGuard);
+        const int row = g < kGuard ? g : G::kRows + g;   // rows [0, 8) and [520, 528)
+        *reinterpret_cast<uint4 *>(planes + plane * G::kPlane + row * 16) = make_uint4(0, 0, 0, 0);
+    }
+}
+
 // Common prologue of the scorer kernels: zero guard rows of `n_planes`
 // planes from `sm`, init the barriers, allocate TMEM, start the weight copy.
 template <class G>
@@ -288,11 +299,7 @@ __device__ __forceinline__ uint32_t sc_prologue(unsigned char *sm, int n_planes,
                                                 unsigned char *wdst, const unsigned char *wsrc,
                                                 uint32_t wbytes, void *vdst, const void *vsrc) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    for (int i = tid; i < n_planes * kGuard * 2; i += blockDim.x) {
-        const int plane = i / (2 * kGuard), g = i % (2 * kGuard);
-        const int row = g < kGuard ? g : G::kRows + g;   // rows [0, 8) and [520, 528)
-        *reinterpret_cast<uint4 *>(sm + plane * G::kPlane + row * 16) = make_uint4(0, 0, 0, 0);
-    }
+    zero_guards<G>(sm, n_planes);
     if (tid == 0) {
         bar_init(bar_w, 1);
         bar_init(bar_m, 1);
@@ -474,55 +481,82 @@ cudaError_t sc_launch_infer(const ScSource &src, const unsigned char *block, uin
 // (g = blockIdx.x + k gridDim.x) so that every run sums the same gradient
 // terms in the same order.  Per segment: forward (features -> a1 -> a2 ->
 // head), loss and its gradient at the logits, then for layers 3, 2, 1 the
-// weight gradient (tcgen05, MN-major operands: M = 64 output channels of
-// which 32 are real, N = input channels, K = 16 columns per MMA, one
-// accumulator per tap) and, for layers 3 and 2, the input gradient (a
-// forward convolution of the gradient planes with the reversed, transposed
+// weight gradient and, for layers 3 and 2, the input gradient (a forward
+// convolution of the gradient planes with the reversed, transposed
 // weights).  The sums of the CTA go to its own slice of `partial`.
+//
+// Weight gradients: dW_t[co][ci] = sum_x dz[x][co] in[x + t - 3][ci] on
+// tcgen05 (MN-major operands, N = input channels, K = 16 columns per MMA).
+// tcgen05 has no M = 32, so one M = 64 MMA takes two taps: its rows 0-31 read
+// the gradient planes dz and its rows 32-63 the next four planes, dz1, which
+// hold dz one column later (dz1[x] = dz[x - 1]).  With `in` shifted by t, rows
+// 32-63 sum dz[y] in[y + t - 2] over y = 0 .. 510: tap t + 1.  The term it
+// leaves out, y = 511, is zero, as dz is zero on the 9 context columns at
+// each end of the segment.  Taps (0, 1), (2, 3), (4, 5), (6, -): 4 x 32 MMAs
+// per layer.  The weight gradients of consecutive layers go to two TMEM
+// accumulator sets, so a layer's sums are added into `partial` while the next
+// layer's MMAs run.
 constexpr int kTrainThreads = 256;   // 8 warps: two per TMEM lane quarter
-constexpr int kTrainPlanes = 14;   // D (4) | A1 (4) | A2 (4) | X0 (2)
+constexpr int kTrainPlanes = 18;   // D (4) | D1 (4) | A1 (4) | A2 (4) | X0 (2)
+constexpr int kTapPairs = (kTaps + 1) / 2;
 constexpr size_t kTrainStageBytes = (size_t)kTaps * 32 * 32 * sizeof(float);   // one layer's dW
+static_assert(kTrainStageBytes <= 4 * (size_t)SegT::kPlane, "a layer's dW is staged in 4 planes");
 constexpr size_t kTrainSmem = (size_t)kTrainPlanes * SegT::kPlane + (kScBlockBytes - kScVecBytes) +
-                              kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float) + kTrainStageBytes;
-constexpr int kDwCol = 128;        // TMEM columns of the weight-gradient accumulators (7 x 32)
+                              kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float);
+constexpr int kDwCol = 128;   // TMEM columns of the weight-gradient sets: [128, 256), [256, 384)
+constexpr int kDwSet = 32 * kTapPairs;
 
 namespace {
 
-// Weight-gradient MMAs of one layer: for every tap t, dW_t[co][ci] +=
-// sum_x dz[x][co] in[x + t - 3][ci] over the 512 rows of the segment.
+// Weight-gradient MMAs of one layer into the accumulator set at `tmem`:
+// columns 32 p hold taps 2p (rows 0-31) and 2p + 1 (rows 32-63), summed over
+// the 512 rows of the segment.  dz: the planes dz (4), then dz1 (4).
 template <class G>
 __device__ __forceinline__ void issue_dw(uint32_t tmem, const unsigned char *dz,
                                          const unsigned char *in, int n_in) {
     const uint32_t idesc = idesc_bf16(64, 8 * n_in, true, true);
     const uint64_t da = sdesc(smem_u32(dz) + kGuard * 16, 128, G::kPlane);
     const uint64_t db = sdesc(smem_u32(in) + (kGuard - 3) * 16, 128, G::kPlane);
-    for (int t = 0; t < kTaps; ++t)
+    for (int p = 0; p < kTapPairs; ++p)
 #pragma unroll 4
         for (int k = 0; k < G::kRows / 16; ++k)
-            mma_bf16(tmem + kDwCol + 32 * t, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k + t),
-                     idesc, k != 0);
+            mma_bf16(tmem + 32 * p, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k + 2 * p), idesc,
+                     k != 0);
+}
+
+// Row r of the gradient planes dz and row r + 1 of dz1 (row 0 of dz1, the
+// column before the segment, is zero).
+template <class G>
+__device__ __forceinline__ void store_dz(unsigned char *dz, int r, const float (&v)[32]) {
+    store_row32<G>(dz, r, v);
+    store_row32<G>(dz + 4 * G::kPlane, r + 1, v);
+    if (r == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dz + (4 + c) * G::kPlane + kGuard * 16) = make_uint4(0, 0, 0, 0);
+    }
 }
 
 // Adds the weight gradient of a layer into the CTA's partial sums (layout
 // [t][co][ci] per layer; written instead of added on the CTA's first
 // segment).  An M = 64 accumulator keeps rows 16q .. 16q+15 in lanes 0-15 of
-// TMEM lane quarter q: output channels 0-15 are read by warp 0 and 16-31 by
-// warp 1 into shared memory, then every thread adds its share with 16-byte
-// loads and stores.
+// TMEM lane quarter q, so quarter q of pair p holds output channels
+// 16 (q & 1) .. +15 of tap 2p + (q >> 1).  Warps 0-3 read pairs 0 and 1,
+// warps 4-7 pairs 2 and 3, into `stage`; then every thread adds its share
+// with 16-byte loads and stores.
 __device__ __forceinline__ void flush_dw(uint32_t tmem, float *stage, float *part, int off,
                                          int n_in_real, bool first) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 2) {
-        const int co = 16 * warp + lane;
-        for (int t = 0; t < kTaps; ++t) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + kDwCol + 32 * t, v);
-            if (lane < 16) {
-                float *row = stage + (t * 32 + co) * n_in_real;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
+    for (int p = 2 * (warp >> 2); p < 2 * (warp >> 2) + 2; ++p) {
+        const int t = 2 * p + (q >> 1);
+        if (t >= kTaps) continue;   // rows 32-63 of the last pair: no tap 7
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32 * p, v);
+        if (lane < 16) {
+            float *row = stage + (t * 32 + 16 * (q & 1) + lane) * n_in_real;
 #pragma unroll
-                for (int ci = 0; ci < 32; ++ci)
-                    if (ci < n_in_real) row[ci] = v[ci];
-            }
+            for (int ci = 0; ci < 32; ++ci)
+                if (ci < n_in_real) row[ci] = v[ci];
         }
     }
     __syncthreads();
@@ -574,17 +608,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                const unsigned char *__restrict__ wblock, float *__restrict__ partial,
                int total_segs, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *D = sm;                          // gradient planes; planes 4-7 read as M padding
-    unsigned char *A1 = sm + 4 * SegT::kPlane;
-    unsigned char *A2 = sm + 8 * SegT::kPlane;
-    unsigned char *X0 = sm + 12 * SegT::kPlane;
+    unsigned char *D = sm;                      // gradient planes dz, then dz1 (planes 4-7)
+    unsigned char *A1 = sm + 8 * SegT::kPlane;
+    unsigned char *A2 = sm + 12 * SegT::kPlane;   // also the dW stage once a2 is no longer read
+    unsigned char *X0 = sm + 16 * SegT::kPlane;
     unsigned char *Wall = sm + kTrainPlanes * SegT::kPlane;
     ScVec *vec = reinterpret_cast<ScVec *>(Wall + (kScBlockBytes - kScVecBytes));
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kScVecBytes);
     uint64_t *bar_m = bar_w + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_m + 1);
     float *red = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(bar_w) + 64);
-    float *stage = red + 3 * 4 * 32;   // 16-byte aligned
+    float *stage = reinterpret_cast<float *>(A2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t tmem = sc_prologue<SegT>(sm, kTrainPlanes, bar_w, bar_m, tslot, 512, Wall, wblock,
                                       kScBlockBytes - kScVecBytes, vec, wblock + kScOffVec);
@@ -687,7 +721,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                     gb3[c] = __fadd_rn(gb3[c], dz);
                     v[c] = dz;
                 }
-                store_row32<SegT>(D, r, v);
+                store_dz<SegT>(D, r, v);
             }
             flush_vec32(gwh, red, part, kScPWh, first);
             flush_vec32(gb3, red + 128, part, kScPB3, first);
@@ -706,16 +740,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             }
         }
         mma_sync_point();
-        // ---- layers 3 and 2: weight gradient and input gradient
+        // ---- layers 3 and 2: weight gradient (sets 0, 1) and input gradient
         for (int l = 2; l >= 1; --l) {
             const unsigned char *in = l == 2 ? A2 : A1;
             if (tid == 0) {
                 issue_conv<SegT, 4>(tmem, D, l == 2 ? Wb3 : Wb2);   // input gradient, columns [0, 128)
-                issue_dw<SegT>(tmem, D, in, 4);
+                issue_dw<SegT>(tmem + kDwCol + (l == 2 ? 0 : kDwSet), D, in, 4);
                 mma_commit(bar_m);
             }
+            if (l == 1)   // layer 3's weight gradient, while these MMAs run
+                flush_dw(tmem + kDwCol, stage, part, kScPW3, kCh, first);
             if (!wait_mma()) break;
-            flush_dw(tmem, stage, part, l == 2 ? kScPW3 : kScPW2, kCh, first);
             float gb[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) gb[c] = 0.0f;
@@ -729,20 +764,22 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                     v[c] = a[c] > 0.0f ? __bfloat162float(__float2bfloat16_rn(v[c])) : 0.0f;
                     gb[c] = __fadd_rn(gb[c], v[c]);
                 }
-                store_row32<SegT>(D, r, v);   // every MMA reading D has completed
+                store_dz<SegT>(D, r, v);   // every MMA reading D has completed
             }
             __syncthreads();
             flush_vec32(gb, red, part, l == 2 ? kScPB2 : kScPB1, first);
             mma_sync_point();
         }
-        // ---- layer 1: weight gradient only
+        // ---- layer 1: weight gradient only (set 0; layer 2's is added meanwhile)
         if (abort) break;
         if (tid == 0) {
-            issue_dw<SegT>(tmem, D, X0, 2);
+            issue_dw<SegT>(tmem + kDwCol, D, X0, 2);
             mma_commit(bar_m);
         }
+        flush_dw(tmem + kDwCol + kDwSet, stage, part, kScPW2, kCh, first);
         if (!wait_mma()) break;
-        flush_dw(tmem, stage, part, kScPW1, kScCin, first);
+        flush_dw(tmem + kDwCol, stage, part, kScPW1, kScCin, first);
+        zero_guards<SegT>(A2, 4);   // the stage overwrote them; the next forward reads them
         tc_before_sync();
     }
     __syncthreads();

@@ -87,11 +87,15 @@ def test_forward_matches_oracle(ca, orc, W):
     print("max |logit - oracle| =", worst)
 
 
-def test_gradient_matches_oracle(ca, orc):
-    W, H = 700, 480
+@pytest.mark.parametrize("W,n", [(700, 6), (600, 160)])
+def test_gradient_matches_oracle(ca, orc, W, n):
+    """6 strips: 12 segments, one per CTA.  160 strips: 320 segments on one
+    CTA per SM, so CTAs take two or three segments in turn (their sums added
+    to the first segment's, the planes and accumulators reused)."""
+    H = 480
     p = _params(3, 0.1)
     ca.scorer_set_params(p)
-    s, ys, lab = _strips(4, 6, W, H)
+    s, ys, lab = _strips(4, n, W, H)
     ds, dy, dl = _to_dev(s, ys, lab)
     pw = 8.0
     loss, g = ca.scorer_step(ds, dy, dl, H, pos_weight=pw, apply=False)
