@@ -509,12 +509,16 @@ cudaError_t sc2_launch_infer(const Sc2Source &src, const unsigned char *block, u
 // (g = blockIdx.x + k gridDim.x) so that every run sums the same gradient
 // terms in the same order.  Per segment: forward (features -> a1 -> a2 ->
 // a3 -> head), soft cross-entropy and its gradient at the logits, then for
-// layers 3, 2, 1 the weight gradient (tcgen05 with MN-major operands: M = 64
-// rows of output channels of which 8 / 16 / 32 are real, N = input channels,
-// K = 16 columns per MMA, one accumulator per tap) and, for layers 3 and 2,
+// layers 3, 2, 1 the weight gradient (tcgen05 with MN-major operands, M = 64
+// rows, N = input channels, K = 16 columns per MMA) and, for layers 3 and 2,
 // the input gradient (a forward convolution of the gradient planes with the
-// transposed weights).  Gradient sums stay in shared memory across the CTA's
-// segments; the CTA writes them to its own slice of `partial` at the end.
+// transposed weights).  Layer 3's weight gradient has one accumulator per tap
+// (32 of the 64 rows real).  Layers 2 and 1 have 3 and 5 gradient rows of 16
+// and 8 channels: their 6 and 5 planes fill the M dimension together, and one
+// accumulator per input row and column tap holds the terms of every gradient
+// row with that input row (each the term of one row tap).  Gradient sums stay
+// in shared memory across the CTA's segments; the CTA writes them to its own
+// slice of `partial` at the end.
 constexpr int kTrain2Threads = 256;
 constexpr int kTrain2Planes = 24;   // D (6: dz3, then dz2, then dz1) | X (7) | A1 (5) | A2 (6)
 constexpr int kTrain2Sum = 6272;    // floats of the CTA's gradient sums (+ loss)
@@ -549,6 +553,61 @@ __device__ __forceinline__ void issue_dw2(uint32_t tmem, const unsigned char *dz
                              (r | k) != 0);
             }
         }
+}
+
+// Weight-gradient MMAs of layer 2 or 1 with the gradient rows stacked in M:
+// A = the 8 planes from `dz` (rows of 16 or 8 channels, the planes after the
+// last row unused), B = input row rho (one 8-channel plane) shifted by the
+// column tap dx.  Accumulator (rho, dx), at kDw + 8 (3 rho + dx), holds in row
+// (r, co) the sum over x of dz[r][x][co] in[rho][x + dx - 1][ci]: the term
+// of gradient row r for row tap dr = rho - r.
+__device__ __forceinline__ void issue_dw2_stacked(uint32_t tmem, const unsigned char *dz,
+                                                  const unsigned char *in, int n_rho) {
+    const uint32_t idesc = idesc_bf16(64, 8, true, true);
+    const uint64_t da = sdesc(smem_u32(dz) + kG * 16, 128, kPlane);
+    for (int rho = 0; rho < n_rho; ++rho)
+        for (int dx = 0; dx < 3; ++dx) {
+            const uint32_t d = tmem + kDw + 8 * (3 * rho + dx);
+            const uint64_t db = sdesc(smem_u32(in + rho * kPlane) + (kG + dx - 1) * 16, 128, kPlane);
+#pragma unroll 4
+            for (int k = 0; k < kCols / 16; ++k)
+                mma_bf16(d, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc, k != 0);
+        }
+}
+
+// Adds the stacked accumulators of layer 2 or 1 (R gradient rows of n_out
+// channels, n_in input channels, n_rho = R + 2 input rows) into the sums,
+// layout [co][ci][dr][dx] at `off`.  Row 8 g + c of an M = 64 accumulator
+// (plane g of dz, channel c) is in lane 8 (g % 2) + c of TMEM lane quarter
+// g / 2.  Each lane copies the terms of its gradient row to
+// stage[r][co][ci][dr][dx] (each written once: rho = r + dr), then the R
+// terms of every weight are summed in row order.
+__device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, float *sum, int off,
+                                                  int R, int n_out, int n_in) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+    const int ppr = n_out / 8;                       // planes per gradient row
+    const int g = 2 * q + ((lane >> 3) & 1);         // plane of this lane's row
+    const int r = g / ppr, co = 8 * (g % ppr) + (lane & 7);
+    const bool mine = lane < 16 && r < R;
+    const int per_r = n_out * n_in * 9;
+    if (2 * q < R * ppr) {   // the quarter holds gradient rows (uniform over the warp)
+        for (int p = h; p < 3 * (R + 2); p += 2) {   // the quarter's two warps share the accumulators
+            const int rho = p / 3, dx = p - 3 * rho, dr = rho - r;
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + kDw + 8 * p, v);
+            if (mine && dr >= 0 && dr <= 2) {
+                float *dst = stage + r * per_r + co * n_in * 9 + 3 * dr + dx;
+                for (int ci = 0; ci < n_in; ++ci) dst[9 * ci] = v[ci];
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < per_r; t += blockDim.x) {
+        float a = stage[t];
+        for (int rr = 1; rr < R; ++rr) a = __fadd_rn(a, stage[rr * per_r + t]);
+        sum[off + t] = __fadd_rn(sum[off + t], a);
+    }
+    __syncthreads();
 }
 
 // Adds the weight-gradient accumulators of a layer (n_out real output
@@ -610,10 +669,11 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
                 const unsigned char *__restrict__ wblock, float *__restrict__ partial,
                 int total_segs, uint32_t *err) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char *D = sm;                     // gradient planes (the 6 after them pad M = 64)
+    unsigned char *D = sm;                     // gradient planes (the planes after them pad M = 64)
     unsigned char *X = sm + 6 * kPlane;
     unsigned char *A1 = X + 7 * kPlane;
-    unsigned char *A2 = A1 + 5 * kPlane;
+    unsigned char *A2 = A1 + 5 * kPlane;       // also the weight-gradient stage of layers 2 and 1
+    float *stage = reinterpret_cast<float *>(A2);
     unsigned char *Wall = sm + kTrain2Planes * kPlane;
     Sc2Vec *vec = reinterpret_cast<Sc2Vec *>(Wall + (kSc2BlockBytes - kSc2VecBytes));
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(vec) + kSc2VecBytes);
@@ -808,10 +868,10 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             flush_vec<16>(gb, red, sum, kSc2PB2);
         }
         sync_point();
-        // ---- layer 2: weight gradient (N = 8) and the input gradient da1
-        // (5 rows x 16 columns of which 8 real per tile)
+        // ---- layer 2: weight gradient (N = 8, the 3 gradient rows stacked in M)
+        // and the input gradient da1 (5 rows x 16 columns of which 8 real per tile)
         if (tid == 0) {
-            issue_dw2(tmem, D, 2 * kPlane, A1, kPlane, 1, 3);
+            issue_dw2_stacked(tmem, D, A1, 5);
             constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
             for (int j = 0; j < kSc2Tiles; ++j)
                 for (int r1 = 0; r1 < 5; ++r1) {
@@ -832,7 +892,7 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
-        flush_dw2(tmem, sum, kSc2PW2, 16, 8, 1);
+        flush_dw2_stacked(tmem, stage, sum, kSc2PW2, 3, 16, 8);   // a2 is no longer read
         {
             float gb[8];
 #pragma unroll
@@ -858,13 +918,15 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             flush_vec<8>(gb, red, sum, kSc2PB1);
         }
         sync_point();
-        // ---- layer 1: weight gradient only (N = 8, of which 5 real)
+        // ---- layer 1: weight gradient only (N = 8, of which 5 real; the 5 gradient
+        // rows stacked in M)
         if (tid == 0) {
-            issue_dw2(tmem, D, kPlane, X, kPlane, 1, 5);
+            issue_dw2_stacked(tmem, D, X, 7);
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
-        flush_dw2(tmem, sum, kSc2PW1, 8, 5, 1);
+        flush_dw2_stacked(tmem, stage, sum, kSc2PW1, 5, 8, 5);
+        zero_guards(A2, 6);   // the stage overwrote them; the next forward reads them
         tc_before_sync();
     }
     __syncthreads();

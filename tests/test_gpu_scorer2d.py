@@ -111,12 +111,15 @@ def _strips7(seed, n, W, H):
             s, rows, tg)
 
 
-@pytest.mark.parametrize("pw", [1.0, 6.0])
-def test_gradient_matches_oracle(ca, orc, pw):
-    W, H = 700, 480
+@pytest.mark.parametrize("pw,W,n", [(1.0, 700, 6), (6.0, 700, 6), (6.0, 600, 160)])
+def test_gradient_matches_oracle(ca, orc, pw, W, n):
+    """6 strips: 12 segments, one per CTA.  160 strips: 320 segments on one
+    CTA per SM, so CTAs take two or three segments in turn (the planes, the
+    accumulators and the shared-memory sums reused)."""
+    H = 480
     p = _params(3, 0.2)
     ca.scorer2d_set_params(p)
-    ds, dr, dt, s, rows, tg = _strips7(4, 6, W, H)
+    ds, dr, dt, s, rows, tg = _strips7(4, n, W, H)
     loss, g = ca.scorer2d_step(ds, dr, dt, H, pos_weight=pw, apply=False)
     ref = np.zeros(orc.SC2_NPARAM)
     ref_loss = 0.0
