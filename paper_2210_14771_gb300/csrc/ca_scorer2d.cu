@@ -555,20 +555,24 @@ __device__ __forceinline__ void issue_dw2(uint32_t tmem, const unsigned char *dz
         }
 }
 
-// Weight-gradient MMAs of layer 2 or 1 with the gradient rows stacked in M:
-// A = the 8 planes from `dz` (rows of 16 or 8 channels, the planes after the
-// last row unused), B = input row rho (one 8-channel plane) shifted by the
-// column tap dx.  Accumulator (rho, dx), at kDw + 8 (3 rho + dx), holds in row
-// (r, co) the sum over x of dz[r][x][co] in[rho][x + dx - 1][ci]: the term
-// of gradient row r for row tap dr = rho - r.
+// Weight-gradient MMAs of layer 2 or 1 with the gradient rows stacked in M
+// and two input rows in N: A = the 8 planes from `dz` (rows of 16 or 8
+// channels, the planes after the last row unused), B = input rows 2p and
+// 2p + 1 (one 8-channel plane each, consecutive) shifted by the column tap
+// dx.  Accumulator (p, dx), 16 columns at kDw + 16 (3 p + dx), holds in row
+// (r, co), column 8 u + ci, the sum over x of dz[r][x][co] in[2p + u][x + dx
+// - 1][ci]: the term of gradient row r for row tap dr = 2p + u - r.  With an
+// odd number of input rows the last pair's second row is the plane after
+// them, and its columns are not read.
 __device__ __forceinline__ void issue_dw2_stacked(uint32_t tmem, const unsigned char *dz,
                                                   const unsigned char *in, int n_rho) {
-    const uint32_t idesc = idesc_bf16(64, 8, true, true);
+    const uint32_t idesc = idesc_bf16(64, 16, true, true);
     const uint64_t da = sdesc(smem_u32(dz) + kG * 16, 128, kPlane);
-    for (int rho = 0; rho < n_rho; ++rho)
+    for (int p = 0; 2 * p < n_rho; ++p)
         for (int dx = 0; dx < 3; ++dx) {
-            const uint32_t d = tmem + kDw + 8 * (3 * rho + dx);
-            const uint64_t db = sdesc(smem_u32(in + rho * kPlane) + (kG + dx - 1) * 16, 128, kPlane);
+            const uint32_t d = tmem + kDw + 16 * (3 * p + dx);
+            const uint64_t db =
+                sdesc(smem_u32(in + 2 * p * kPlane) + (kG + dx - 1) * 16, 128, kPlane);
 #pragma unroll 4
             for (int k = 0; k < kCols / 16; ++k)
                 mma_bf16(d, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc, k != 0);
@@ -576,11 +580,11 @@ __device__ __forceinline__ void issue_dw2_stacked(uint32_t tmem, const unsigned 
 }
 
 // Adds the stacked accumulators of layer 2 or 1 (R gradient rows of n_out
-// channels, n_in input channels, n_rho = R + 2 input rows) into the sums,
+// channels, n_in input channels, R + 2 input rows) into the sums,
 // layout [co][ci][dr][dx] at `off`.  Row 8 g + c of an M = 64 accumulator
 // (plane g of dz, channel c) is in lane 8 (g % 2) + c of TMEM lane quarter
 // g / 2.  Each lane copies the terms of its gradient row to
-// stage[r][co][ci][dr][dx] (each written once: rho = r + dr), then the R
+// stage[r][co][ci][dr][dx] (each written once: input row r + dr), then the R
 // terms of every weight are summed in row order.
 __device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, float *sum, int off,
                                                   int R, int n_out, int n_in) {
@@ -591,13 +595,18 @@ __device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, f
     const bool mine = lane < 16 && r < R;
     const int per_r = n_out * n_in * 9;
     if (2 * q < R * ppr) {   // the quarter holds gradient rows (uniform over the warp)
-        for (int p = h; p < 3 * (R + 2); p += 2) {   // the quarter's two warps share the accumulators
-            const int rho = p / 3, dx = p - 3 * rho, dr = rho - r;
-            float v[8];
-            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + kDw + 8 * p, v);
-            if (mine && dr >= 0 && dr <= 2) {
-                float *dst = stage + r * per_r + co * n_in * 9 + 3 * dr + dx;
-                for (int ci = 0; ci < n_in; ++ci) dst[9 * ci] = v[ci];
+        // accumulators (p, dx), i = 3 p + dx; the quarter's two warps share them
+        for (int i = h; i < 3 * ((R + 3) / 2); i += 2) {
+            const int p = i / 3, dx = i - 3 * p;
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + kDw + 16 * i, v);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int dr = 2 * p + u - r;
+                if (mine && dr >= 0 && dr <= 2) {
+                    float *dst = stage + r * per_r + co * n_in * 9 + 3 * dr + dx;
+                    for (int ci = 0; ci < n_in; ++ci) dst[9 * ci] = v[8 * u + ci];
+                }
             }
         }
     }
