@@ -512,11 +512,10 @@ cudaError_t sc2_launch_infer(const Sc2Source &src, const unsigned char *block, u
 // layers 3, 2, 1 the weight gradient (tcgen05 with MN-major operands, M = 64
 // rows, N = input channels, K = 16 columns per MMA) and, for layers 3 and 2,
 // the input gradient (a forward convolution of the gradient planes with the
-// transposed weights).  Layer 3's weight gradient has one accumulator per tap
-// (32 of the 64 rows real).  Layers 2 and 1 have 3 and 5 gradient rows of 16
-// and 8 channels: their 6 and 5 planes fill the M dimension together, and one
-// accumulator per input row and column tap holds the terms of every gradient
-// row with that input row (each the term of one row tap).  Gradient sums stay
+// transposed weights).  A weight-gradient MMA takes every gradient row of the
+// layer in M (1 row of 32 channels, 3 of 16, 5 of 8: 32, 48 and 40 of the 64
+// rows) and every input row in N (3 rows of 16 channels, 5 and 7 of 8), one
+// accumulator per column tap: 3 x 24 MMAs per layer.  Gradient sums stay
 // in shared memory across the CTA's segments; the CTA writes them to its own
 // slice of `partial` at the end.
 constexpr int kTrain2Threads = 256;
@@ -530,60 +529,56 @@ static_assert(kTrain2Sum == kSc2PartialStride, "partial stride");
 
 namespace {
 
-// Weight-gradient MMAs of one layer, for every tap (dr, dx) one accumulator
-// of N = 8 n_in_planes columns at kDw + N (3 dr + dx):
-//   dW[co][ci][dr][dx] += sum_r sum_x dz[r][x][co] in[r + dr][x + dx - 1][ci].
-// dz rows: planes dz + r dz_rs (M = 64: 8 planes from there, the padding rows
-// are ignored); in rows: planes in + (r + dr) in_rs, n_in_planes planes each.
-__device__ __forceinline__ void issue_dw2(uint32_t tmem, const unsigned char *dz, int dz_rs,
-                                          const unsigned char *in, int in_rs, int n_in_planes,
-                                          int rows) {
-    const int N = 8 * n_in_planes;
+// Weight-gradient MMAs of one layer, dW[co][ci][dr][dx] = sum over gradient
+// rows r and columns x of dz[r][x][co] in[r + dr][x + dx - 1][ci], with every
+// gradient row in M and every input row in N.  A = the 8 planes from `dz`
+// (the layer's gradient rows: 1 of 32 channels, 3 of 16 or 5 of 8, row by
+// row; planes after the last row unused), B = the n_in planes of all the
+// layer's input rows (consecutive, row by row) shifted by the column tap dx.
+// Accumulator dx, N = 8 n_in columns at kDw + N dx, holds in row (r, co),
+// column 8 p + c (input plane p, channel c), the sum over x of dz[r][x][co]
+// plane_p[x + dx - 1][c]: the term of gradient row r for the input row of
+// plane p, i.e. of row tap dr = (that input row) - r.
+__device__ __forceinline__ void issue_dw2(uint32_t tmem, const unsigned char *dz,
+                                          const unsigned char *in, int n_in) {
+    const int N = 8 * n_in;
     const uint32_t idesc = idesc_bf16(64, N, true, true);
-    for (int dr = 0; dr < 3; ++dr)
-        for (int dx = 0; dx < 3; ++dx) {
-            const uint32_t d = tmem + kDw + N * (3 * dr + dx);
-            for (int r = 0; r < rows; ++r) {
-                const uint64_t da = sdesc(smem_u32(dz + r * dz_rs) + kG * 16, 128, kPlane);
-                const uint64_t db =
-                    sdesc(smem_u32(in + (r + dr) * in_rs) + (kG + dx - 1) * 16, 128, kPlane);
+    const uint64_t da = sdesc(smem_u32(dz) + kG * 16, 128, kPlane);
+    for (int dx = 0; dx < 3; ++dx) {
+        const uint64_t db = sdesc(smem_u32(in) + (kG + dx - 1) * 16, 128, kPlane);
 #pragma unroll 4
-                for (int k = 0; k < kCols / 16; ++k)
-                    mma_bf16(d, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc,
-                             (r | k) != 0);
+        for (int k = 0; k < kCols / 16; ++k)
+            mma_bf16(tmem + kDw + N * dx, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc,
+                     k != 0);
+    }
+}
+
+// Adds layer 3's weight gradient (one gradient row of 32 channels, input
+// rows of two planes) into the sums, layout [co][ci][dr][dx] at `off`.  Row
+// co of an M = 64 accumulator is in lane co % 16 of TMEM lane quarter co / 16;
+// the quarter's two warps share the 9 taps.
+__device__ __forceinline__ void flush_dw2_l3(uint32_t tmem, float *sum, int off) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+    if (q >= 2) return;
+    const int co = 16 * q + lane;
+    for (int t = h; t < 9; t += 2) {
+        const int dr = t / 3, dx = t - 3 * dr;
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + kDw + 48 * dx + 16 * dr, v);
+        if (lane < 16) {
+            for (int ci = 0; ci < 16; ++ci) {
+                float &dst = sum[off + (co * 16 + ci) * 9 + t];
+                dst = __fadd_rn(dst, v[ci]);
             }
         }
+    }
 }
 
-// Weight-gradient MMAs of layer 2 or 1 with the gradient rows stacked in M
-// and two input rows in N: A = the 8 planes from `dz` (rows of 16 or 8
-// channels, the planes after the last row unused), B = input rows 2p and
-// 2p + 1 (one 8-channel plane each, consecutive) shifted by the column tap
-// dx.  Accumulator (p, dx), 16 columns at kDw + 16 (3 p + dx), holds in row
-// (r, co), column 8 u + ci, the sum over x of dz[r][x][co] in[2p + u][x + dx
-// - 1][ci]: the term of gradient row r for row tap dr = 2p + u - r.  With an
-// odd number of input rows the last pair's second row is the plane after
-// them, and its columns are not read.
-__device__ __forceinline__ void issue_dw2_stacked(uint32_t tmem, const unsigned char *dz,
-                                                  const unsigned char *in, int n_rho) {
-    const uint32_t idesc = idesc_bf16(64, 16, true, true);
-    const uint64_t da = sdesc(smem_u32(dz) + kG * 16, 128, kPlane);
-    for (int p = 0; 2 * p < n_rho; ++p)
-        for (int dx = 0; dx < 3; ++dx) {
-            const uint32_t d = tmem + kDw + 16 * (3 * p + dx);
-            const uint64_t db =
-                sdesc(smem_u32(in + 2 * p * kPlane) + (kG + dx - 1) * 16, 128, kPlane);
-#pragma unroll 4
-            for (int k = 0; k < kCols / 16; ++k)
-                mma_bf16(d, da + (uint32_t)(16 * k), db + (uint32_t)(16 * k), idesc, k != 0);
-        }
-}
-
-// Adds the stacked accumulators of layer 2 or 1 (R gradient rows of n_out
-// channels, n_in input channels, R + 2 input rows) into the sums,
-// layout [co][ci][dr][dx] at `off`.  Row 8 g + c of an M = 64 accumulator
-// (plane g of dz, channel c) is in lane 8 (g % 2) + c of TMEM lane quarter
-// g / 2.  Each lane copies the terms of its gradient row to
+// Adds the weight gradient of layer 2 or 1 (R gradient rows of n_out
+// channels, R + 2 input rows of one plane of n_in real channels) into the
+// sums, layout [co][ci][dr][dx] at `off`.  Row 8 g + c of an M = 64
+// accumulator (plane g of dz, channel c) is in lane 8 (g % 2) + c of TMEM
+// lane quarter g / 2.  Each lane copies the terms of its gradient row to
 // stage[r][co][ci][dr][dx] (each written once: input row r + dr), then the R
 // terms of every weight are summed in row order.
 __device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, float *sum, int off,
@@ -594,19 +589,16 @@ __device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, f
     const int r = g / ppr, co = 8 * (g % ppr) + (lane & 7);
     const bool mine = lane < 16 && r < R;
     const int per_r = n_out * n_in * 9;
+    const int N = 8 * (R + 2);
     if (2 * q < R * ppr) {   // the quarter holds gradient rows (uniform over the warp)
-        // accumulators (p, dx), i = 3 p + dx; the quarter's two warps share them
-        for (int i = h; i < 3 * ((R + 3) / 2); i += 2) {
-            const int p = i / 3, dx = i - 3 * p;
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + kDw + 16 * i, v);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int dr = 2 * p + u - r;
-                if (mine && dr >= 0 && dr <= 2) {
-                    float *dst = stage + r * per_r + co * n_in * 9 + 3 * dr + dx;
-                    for (int ci = 0; ci < n_in; ++ci) dst[9 * ci] = v[8 * u + ci];
-                }
+        // (input row rho, column tap dx), i = 3 rho + dx; the quarter's two warps share them
+        for (int i = h; i < 3 * (R + 2); i += 2) {
+            const int rho = i / 3, dx = i - 3 * rho, dr = rho - r;
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + kDw + N * dx + 8 * rho, v);
+            if (mine && dr >= 0 && dr <= 2) {
+                float *dst = stage + r * per_r + co * n_in * 9 + 3 * dr + dx;
+                for (int ci = 0; ci < n_in; ++ci) dst[9 * ci] = v[ci];
             }
         }
     }
@@ -617,37 +609,6 @@ __device__ __forceinline__ void flush_dw2_stacked(uint32_t tmem, float *stage, f
         sum[off + t] = __fadd_rn(sum[off + t], a);
     }
     __syncthreads();
-}
-
-// Adds the weight-gradient accumulators of a layer (n_out real output
-// channels, n_in real input channels of N = 8 n_in_planes) into the sums,
-// layout [co][ci][dr][dx] at `off`.  Row co of an M = 64 accumulator is in
-// lane co % 16 of TMEM lane quarter co / 16: warp w (< n_out / 16, or warp 0
-// for 8 outputs) reads its quarter.
-__device__ __forceinline__ void flush_dw2(uint32_t tmem, float *sum, int off, int n_out, int n_in,
-                                          int n_in_planes) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int N = 8 * n_in_planes;
-    if (warp < (n_out + 15) / 16) {
-        const int co = 16 * warp + lane;
-        for (int t = 0; t < 9; ++t) {
-            float v[16];
-            if (N == 16) {
-                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kDw + N * t, v);
-            } else {
-                float v8[8];
-                tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + kDw + N * t, v8);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = v8[c];
-            }
-            if (lane < 16 && co < n_out) {
-                for (int ci = 0; ci < n_in; ++ci) {
-                    float &dst = sum[off + (co * n_in + ci) * 9 + t];
-                    dst = __fadd_rn(dst, v[ci]);
-                }
-            }
-        }
-    }
 }
 
 // Sums a per-thread vector of n values over the CTA (fixed order) into
@@ -828,10 +789,10 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             flush_vec<2>(tail, red, sum, kSc2PBh);   // bh, then the loss slot after it
         }
         sync_point();
-        // ---- layer 3: weight gradient (N = 16 over the two a2 planes of a row)
-        // and the input gradient da2 (3 rows x 16 channels per tile)
+        // ---- layer 3: weight gradient (M: the 32 channels of dz3, N: the 3 a2
+        // rows of 16) and the input gradient da2 (3 rows x 16 channels per tile)
         if (tid == 0) {
-            issue_dw2(tmem, D, 0, A2, 2 * kPlane, 2, 1);
+            issue_dw2(tmem, D, A2, 6);
             constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
             for (int j = 0; j < kSc2Tiles; ++j)
                 for (int dr = 0; dr < 3; ++dr)
@@ -847,7 +808,7 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
-        flush_dw2(tmem, sum, kSc2PW3, 32, 16, 2);
+        flush_dw2_l3(tmem, sum, kSc2PW3);
         {
             float gb[16];
 #pragma unroll
@@ -877,10 +838,11 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             flush_vec<16>(gb, red, sum, kSc2PB2);
         }
         sync_point();
-        // ---- layer 2: weight gradient (N = 8, the 3 gradient rows stacked in M)
-        // and the input gradient da1 (5 rows x 16 columns of which 8 real per tile)
+        // ---- layer 2: weight gradient (M: the 3 dz2 rows of 16 channels, N: the
+        // 5 a1 rows of 8) and the input gradient da1 (5 rows x 16 columns of which
+        // 8 real per tile)
         if (tid == 0) {
-            issue_dw2_stacked(tmem, D, A1, 5);
+            issue_dw2(tmem, D, A1, 5);
             constexpr uint32_t idesc = idesc_bf16(128, 16, false, false);
             for (int j = 0; j < kSc2Tiles; ++j)
                 for (int r1 = 0; r1 < 5; ++r1) {
@@ -927,10 +889,10 @@ __global__ void __launch_bounds__(kTrain2Threads, 1)
             flush_vec<8>(gb, red, sum, kSc2PB1);
         }
         sync_point();
-        // ---- layer 1: weight gradient only (N = 8, of which 5 real; the 5 gradient
-        // rows stacked in M)
+        // ---- layer 1: weight gradient only (M: the 5 dz1 rows of 8 channels,
+        // N: the 7 feature rows of 8, of which 5 real)
         if (tid == 0) {
-            issue_dw2_stacked(tmem, D, X, 7);
+            issue_dw2(tmem, D, X, 7);
             mma_commit(bar_m);
         }
         if (!wait_mma()) break;
