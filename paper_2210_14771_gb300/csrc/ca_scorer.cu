@@ -505,6 +505,9 @@ constexpr size_t kTrainSmem = (size_t)kTrainPlanes * SegT::kPlane + (kScBlockByt
                               kScVecBytes + 64 + 3 * 4 * 32 * sizeof(float);
 constexpr int kDwCol = 128;   // TMEM columns of the weight-gradient sets: [128, 256), [256, 384)
 constexpr int kDwSet = 32 * kTapPairs;
+static_assert(kDwCol >= 32 * kScTrainTiles && kDwCol + 2 * kDwSet <= 512,
+              "convolution and weight-gradient accumulators fit the 512 TMEM columns");
+static_assert(kTrainSmem <= 227 * 1024, "training shared memory fits one CTA per SM");
 
 namespace {
 

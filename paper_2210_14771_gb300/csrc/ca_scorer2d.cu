@@ -526,6 +526,10 @@ constexpr size_t kTrain2Smem = (size_t)kTrain2Planes * kPlane + (kSc2BlockBytes 
 constexpr int kDw = 256;            // TMEM column of the weight-gradient accumulators
 static_assert(kTrain2Sum >= kScorer2dNParam + 1 && kTrain2Sum % 4 == 0, "sum slots");
 static_assert(kTrain2Sum == kSc2PartialStride, "partial stride");
+static_assert(kTrain2Smem <= 227 * 1024, "training shared memory fits one CTA per SM");
+// weight-gradient accumulators: 3 column taps x (input planes x 8) columns
+// (layer 1: 7 planes, layer 3: 6, layer 2: 5) above the convolutions' 240
+static_assert(kDw >= 3 * 80 && kDw + 3 * 8 * 7 <= 512, "TMEM columns of the training kernel");
 
 namespace {
 
