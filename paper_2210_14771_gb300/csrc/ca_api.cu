@@ -1184,14 +1184,9 @@ ca_status sc_step_async(ca_handle *h, const uint8_t *strips, const int32_t *ys,
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_train launch");
     const float scale = 1.0f / (float)((double)n * W);
     e = sc_launch_sgd(S.params, S.mom, S.partial, grid, scale, tp.lr, tp.momentum, tp.apply,
-                      tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, s);
+                      tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, S.block, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_sgd launch");
     h->launches += (tp.apply && tp.clip_norm > 0.0f) ? 3 : 2;
-    if (tp.apply) {
-        e = sc_launch_pack(S.params, S.block, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc_pack launch");
-        h->launches += 1;
-    }
     return CA_OK;
 }
 
@@ -1738,14 +1733,9 @@ ca_status sc2_step_async(ca_handle *h, const uint8_t *strips7, const int32_t *ro
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_train launch");
     const float scale = 1.0f / (float)((double)n * W);
     e = sc2_launch_sgd(S.params, S.mom, S.partial, grid, scale, tp.lr, tp.momentum, tp.apply,
-                       tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, s);
+                       tp.clip_norm, S.grads, S.norm, grads_dev, loss_dev, S.block, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_sgd launch");
     h->launches += (tp.apply && tp.clip_norm > 0.0f) ? 3 : 2;
-    if (tp.apply) {
-        e = sc2_launch_pack(S.params, S.block, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "k_sc2_pack launch");
-        h->launches += 1;
-    }
     return CA_OK;
 }
 

@@ -212,10 +212,12 @@ cudaError_t sc_launch_train(const ScSource &src, const uint8_t *labels, float po
                             const unsigned char *block, float *partial, int total_segs,
                             uint32_t *err, int grid, cudaStream_t s);
 // One SGD step from the partials (two launches when clip > 0 and apply;
-// gbuf: kScNParam floats, norm_part: kScSgdBlocks floats of scratch).
+// gbuf: kScNParam floats, norm_part: kScSgdBlocks floats of scratch).  With
+// apply, the updated weights are also written into `block`.
 cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
                           float lr, float momentum, int apply, float clip, float *gbuf,
-                          float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
+                          float *norm_part, float *grads_out, float *loss_out,
+                          unsigned char *block, cudaStream_t s);
 
 // ---- The paper's 2-D scorer (ca_scorer2d.cu, Sec. 2.2.4): 3x3 convolutions
 // to 8, 16, 32 features over 7-row RGBXY strips, on tcgen05.
@@ -260,9 +262,12 @@ size_t sc2_train_smem();
 cudaError_t sc2_launch_train(const Sc2Source &src, const float *targets, float pos_weight,
                              const unsigned char *block, float *partial, int total_segs,
                              uint32_t *err, int grid, cudaStream_t s);
+// As sc_launch_sgd, for the 2-D scorer (gbuf: kScorer2dNParam floats,
+// norm_part: kSc2SgdBlocks floats).
 cudaError_t sc2_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
                            float lr, float momentum, int apply, float clip, float *gbuf,
-                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s);
+                           float *norm_part, float *grads_out, float *loss_out,
+                           unsigned char *block, cudaStream_t s);
 
 // Kernel launchers (ca_kernels.cu).  Each returns the CUDA error of the launch.
 

@@ -867,10 +867,8 @@ cudaError_t sc_launch_pick(const DevFrame *frames, int B, const int32_t *rows, c
 // Packs the f32 parameters into the device weight block: the bf16 B operands
 // of the forward convolutions and of the input-gradient convolutions, the
 // biases, the bf16-rounded head weights and the head bias.
-__global__ void k_sc_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= kScNParam) return;
-    const float w = prm[p];
+// Writes parameter p (value w) into its places in the device weight block.
+__device__ __forceinline__ void sc_pack_one(int p, float w, unsigned char *blk) {
     const __nv_bfloat16 wb = __float2bfloat16_rn(w);
     ScVec *vec = reinterpret_cast<ScVec *>(blk + kScOffVec);
     auto put = [&](int off) { *reinterpret_cast<__nv_bfloat16 *>(blk + off) = wb; };
@@ -898,20 +896,27 @@ __global__ void k_sc_pack(const float *__restrict__ prm, unsigned char *__restri
     }
 }
 
+__global__ void k_sc_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < kScNParam) sc_pack_one(p, prm[p], blk);
+}
+
 cudaError_t sc_launch_pack(const float *params, unsigned char *block, cudaStream_t s) {
     k_sc_pack<<<(kScNParam + 255) / 256, 256, 0, s>>>(params, block);
     return cudaGetLastError();
 }
 
 // Sums the per-CTA gradient partials in a fixed order, then optionally takes
-// an SGD step with momentum:  v = momentum v + scale g,  w = w - lr v.
-// Weight blocks of the partials are laid out [t][co][ci]; the parameters are
-// [co][ci][t].  A block reduces 64 parameters with 4 threads each (partials
-// c = q, q + 4, ...), combined in order.  With norm_part set (gradient
-// clipping) it takes no step: it stores the summed gradient in gbuf and the
-// block's sum of squares of the mean gradient in norm_part[block], and
-// k_sc_clip_step takes the step once the whole norm is known.
-constexpr int kSgdParams = 64;
+// an SGD step with momentum:  v = momentum v + scale g,  w = w - lr v, and
+// writes w into the device weight block.  Weight blocks of the partials are
+// laid out [t][co][ci]; the parameters are [co][ci][t].  A block reduces 64
+// parameters with 16 threads each (partials c = q, q + 16, ...), combined in
+// order.  With norm_part set (gradient clipping) it takes no step: it stores
+// the summed gradient in gbuf and the block's sum of squares of the mean
+// gradient in norm_part[block], and k_sc_clip_step takes the step once the
+// whole norm is known.
+constexpr int kSgdParams = 64;   // parameters per block
+constexpr int kSgdQ = 16;        // threads per parameter, each summing every 16th partial
 static_assert(kScSgdBlocks == (kScNParam + 1 + kSgdParams - 1) / kSgdParams, "sgd grid");
 
 __device__ __forceinline__ int partial_index(int p) {
@@ -925,30 +930,32 @@ __device__ __forceinline__ int partial_index(int p) {
     return p;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSgdQ * kSgdParams)
     k_sc_sgd(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ part,
              int n_part, float scale, float lr, float momentum, int apply,
              float *__restrict__ grads_out, float *__restrict__ loss_out,
-             float *__restrict__ gbuf, float *__restrict__ norm_part) {
-    __shared__ float red[4][kSgdParams];
+             float *__restrict__ gbuf, float *__restrict__ norm_part, unsigned char *__restrict__ blk) {
+    __shared__ float red[kSgdQ][kSgdParams];
     const int pl = threadIdx.x % kSgdParams, q = threadIdx.x / kSgdParams;
     const int p = blockIdx.x * kSgdParams + pl;
     float g = 0.0f;
     if (p <= kScNParam) {
         const float *src = part + partial_index(p);
         int c = q;
-        for (; c + 28 < n_part; c += 32) {   // eight loads in flight, added in order
+        for (; c + 7 * kSgdQ < n_part; c += 8 * kSgdQ) {   // eight loads in flight, added in order
             float t[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = __ldcg(src + (size_t)(c + 4 * u) * kScPartialStride);
+            for (int u = 0; u < 8; ++u) t[u] = __ldcg(src + (size_t)(c + kSgdQ * u) * kScPartialStride);
 #pragma unroll
             for (int u = 0; u < 8; ++u) g = __fadd_rn(g, t[u]);
         }
-        for (; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(src + (size_t)c * kScPartialStride));
+        for (; c < n_part; c += kSgdQ) g = __fadd_rn(g, __ldcg(src + (size_t)c * kScPartialStride));
     }
     red[q][pl] = g;
     __syncthreads();
-    g = __fadd_rn(__fadd_rn(__fadd_rn(red[0][pl], red[1][pl]), red[2][pl]), red[3][pl]);
+    g = red[0][pl];
+#pragma unroll
+    for (int k = 1; k < kSgdQ; ++k) g = __fadd_rn(g, red[k][pl]);
     if (norm_part) {   // clipping: squares of the mean gradient, summed in order by thread 0
         __syncthreads();
         if (q == 0) {
@@ -972,19 +979,21 @@ __global__ void __launch_bounds__(256)
         gbuf[p] = g;
     } else if (apply) {
         const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), __fmul_rn(scale, g));
+        const float w = __fsub_rn(prm[p], __fmul_rn(lr, v));
         mom[p] = v;
-        prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+        prm[p] = w;
+        sc_pack_one(p, w, blk);
     }
 }
 
 // The clipped step: every block sums the kScSgdBlocks partial squares in the
 // same order (strided per thread, then a fixed tree, so all blocks agree on
 // the norm), f = min(1, clip / |scale g|), then
-// v = momentum v + f (scale g),  w = w - lr v.
+// v = momentum v + f (scale g),  w = w - lr v, and w into the weight block.
 __global__ void __launch_bounds__(kSgdParams)
     k_sc_clip_step(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ gbuf,
                    const float *__restrict__ norm_part, float scale, float lr, float momentum,
-                   float clip) {
+                   float clip, unsigned char *__restrict__ blk) {
     __shared__ float red[kSgdParams];
     __shared__ float f_s;
     float t = 0.0f;
@@ -1005,20 +1014,23 @@ __global__ void __launch_bounds__(kSgdParams)
     if (p >= kScNParam) return;
     const float m = __fmul_rn(f_s, __fmul_rn(scale, gbuf[p]));
     const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), m);
+    const float w = __fsub_rn(prm[p], __fmul_rn(lr, v));
     mom[p] = v;
-    prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+    prm[p] = w;
+    sc_pack_one(p, w, blk);
 }
 
 cudaError_t sc_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
                           float lr, float momentum, int apply, float clip, float *gbuf,
-                          float *norm_part, float *grads_out, float *loss_out, cudaStream_t s) {
+                          float *norm_part, float *grads_out, float *loss_out,
+                          unsigned char *block, cudaStream_t s) {
     const bool clipped = apply && clip > 0.0f;
-    k_sc_sgd<<<kScSgdBlocks, 256, 0, s>>>(params, mom, partial, n_partials, scale, lr, momentum,
-                                          apply, grads_out, loss_out, clipped ? gbuf : nullptr,
-                                          clipped ? norm_part : nullptr);
+    k_sc_sgd<<<kScSgdBlocks, kSgdQ * kSgdParams, 0, s>>>(
+        params, mom, partial, n_partials, scale, lr, momentum, apply, grads_out, loss_out,
+        clipped ? gbuf : nullptr, clipped ? norm_part : nullptr, block);
     if (clipped)
         k_sc_clip_step<<<kScSgdBlocks, kSgdParams, 0, s>>>(params, mom, gbuf, norm_part, scale, lr,
-                                                           momentum, clip);
+                                                           momentum, clip, block);
     return cudaGetLastError();
 }
 

@@ -277,10 +277,8 @@ __device__ __forceinline__ uint4 relu_row8(const float *v, const float *b, bool 
 
 // =============================================================== pack ==
 // f32 parameters -> the device weight block (bf16 B operands, floats).
-__global__ void k_sc2_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= kScorer2dNParam) return;
-    const float w = prm[p];
+// Writes parameter p (value w) into its places in the block.
+__device__ __forceinline__ void sc2_pack_one(int p, float w, unsigned char *blk) {
     const __nv_bfloat16 wb = __float2bfloat16_rn(w);
     Sc2Vec *vec = reinterpret_cast<Sc2Vec *>(blk + kSc2OffVec);
     auto put = [&](int off) { *reinterpret_cast<__nv_bfloat16 *>(blk + off) = wb; };
@@ -312,6 +310,11 @@ __global__ void k_sc2_pack(const float *__restrict__ prm, unsigned char *__restr
     } else {
         vec->bh = w;
     }
+}
+
+__global__ void k_sc2_pack(const float *__restrict__ prm, unsigned char *__restrict__ blk) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < kScorer2dNParam) sc2_pack_one(p, prm[p], blk);
 }
 
 cudaError_t sc2_launch_pack(const float *params, unsigned char *block, cudaStream_t s) {
@@ -933,23 +936,38 @@ cudaError_t sc2_launch_train(const Sc2Source &src, const float *targets, float p
 // ================================================================ SGD ==
 // Sums the per-CTA partials in a fixed order, then optionally a momentum SGD
 // step (clipped by the global gradient norm when clip > 0), as the 1-D
-// scorer's step: v = momentum v + f scale g, w = w - lr v.
+// scorer's step: v = momentum v + f scale g, w = w - lr v, with w written
+// into the device weight block.  64 parameters per block, 16 threads each
+// (partials c = q, q + 16, ...), combined in order.
 constexpr int kSgd2Params = 64;
+constexpr int kSgd2Q = 16;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSgd2Q * kSgd2Params)
     k_sc2_sgd(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ part,
               int n_part, float scale, float lr, float momentum, int apply,
               float *__restrict__ grads_out, float *__restrict__ loss_out,
-              float *__restrict__ gbuf, float *__restrict__ norm_part) {
-    __shared__ float red2[4][kSgd2Params];
+              float *__restrict__ gbuf, float *__restrict__ norm_part, unsigned char *__restrict__ blk) {
+    __shared__ float red2[kSgd2Q][kSgd2Params];
     const int pl = threadIdx.x % kSgd2Params, qq = threadIdx.x / kSgd2Params;
     const int p = blockIdx.x * kSgd2Params + pl;
     float g = 0.0f;
-    if (p <= kScorer2dNParam)
-        for (int c = qq; c < n_part; c += 4) g = __fadd_rn(g, __ldcg(part + (size_t)c * kSc2PartialStride + p));
+    if (p <= kScorer2dNParam) {
+        const float *src = part + p;
+        int c = qq;
+        for (; c + 7 * kSgd2Q < n_part; c += 8 * kSgd2Q) {   // eight loads in flight, added in order
+            float t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = __ldcg(src + (size_t)(c + kSgd2Q * u) * kSc2PartialStride);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) g = __fadd_rn(g, t[u]);
+        }
+        for (; c < n_part; c += kSgd2Q) g = __fadd_rn(g, __ldcg(src + (size_t)c * kSc2PartialStride));
+    }
     red2[qq][pl] = g;
     __syncthreads();
-    g = __fadd_rn(__fadd_rn(__fadd_rn(red2[0][pl], red2[1][pl]), red2[2][pl]), red2[3][pl]);
+    g = red2[0][pl];
+#pragma unroll
+    for (int k = 1; k < kSgd2Q; ++k) g = __fadd_rn(g, red2[k][pl]);
     if (norm_part) {
         __syncthreads();
         if (qq == 0) {
@@ -973,15 +991,17 @@ __global__ void __launch_bounds__(256)
         gbuf[p] = g;
     } else if (apply) {
         const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), __fmul_rn(scale, g));
+        const float w = __fsub_rn(prm[p], __fmul_rn(lr, v));
         mom[p] = v;
-        prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+        prm[p] = w;
+        sc2_pack_one(p, w, blk);
     }
 }
 
 __global__ void __launch_bounds__(kSgd2Params)
     k_sc2_clip_step(float *__restrict__ prm, float *__restrict__ mom, const float *__restrict__ gbuf,
                     const float *__restrict__ norm_part, float scale, float lr, float momentum,
-                    float clip) {
+                    float clip, unsigned char *__restrict__ blk) {
     __shared__ float red2[kSgd2Params];
     __shared__ float f_s;
     float t = 0.0f;
@@ -1001,20 +1021,23 @@ __global__ void __launch_bounds__(kSgd2Params)
     if (p >= kScorer2dNParam) return;
     const float m = __fmul_rn(f_s, __fmul_rn(scale, gbuf[p]));
     const float v = __fadd_rn(__fmul_rn(momentum, mom[p]), m);
+    const float w = __fsub_rn(prm[p], __fmul_rn(lr, v));
     mom[p] = v;
-    prm[p] = __fsub_rn(prm[p], __fmul_rn(lr, v));
+    prm[p] = w;
+    sc2_pack_one(p, w, blk);
 }
 
 cudaError_t sc2_launch_sgd(float *params, float *mom, float *partial, int n_partials, float scale,
                            float lr, float momentum, int apply, float clip, float *gbuf,
-                           float *norm_part, float *grads_out, float *loss_out, cudaStream_t s) {
+                           float *norm_part, float *grads_out, float *loss_out,
+                           unsigned char *block, cudaStream_t s) {
     const bool clipped = apply && clip > 0.0f;
-    k_sc2_sgd<<<kSc2SgdBlocks, 256, 0, s>>>(params, mom, partial, n_partials, scale, lr, momentum,
-                                            apply, grads_out, loss_out, clipped ? gbuf : nullptr,
-                                            clipped ? norm_part : nullptr);
+    k_sc2_sgd<<<kSc2SgdBlocks, kSgd2Q * kSgd2Params, 0, s>>>(
+        params, mom, partial, n_partials, scale, lr, momentum, apply, grads_out, loss_out,
+        clipped ? gbuf : nullptr, clipped ? norm_part : nullptr, block);
     if (clipped)
         k_sc2_clip_step<<<kSc2SgdBlocks, kSgd2Params, 0, s>>>(params, mom, gbuf, norm_part, scale,
-                                                              lr, momentum, clip);
+                                                              lr, momentum, clip, block);
     return cudaGetLastError();
 }
 
