@@ -557,9 +557,6 @@ uint64_t shape_key(const ca_frame *frames, int B, const ca_params &p) {
 
 int default_wave(const ca_handle *h, int B, const ca_params &p, int T) {
     // about two resident CTAs' worth of strip items per wave
-    DevParams P{};
-    P.N = p.n_strips;
-    P.K = p.cands_per_strip;
     const int spf = strip_items_of(p.n_strips, p.cands_per_strip);
     const int resident = h->sm_count * 4;
     (void)T;
